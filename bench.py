@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Throughput of the mechanical-interaction step (grid + force +
+displacement) on GB300: agent-updates/s, with the force kernel's HBM
+roofline fraction, an end-to-end figure through the C ABI with host
+buffers, and the CPU oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+                    [--workload clustered_8M|plain_fp64_4096|uniform_200M|batched_sweep_256]
+                    [--precision 1|0] [--static 0|1]
+
+One step = one iteration of every simulation of the workload.  Under
+torchrun (N > 1) every rank steps its own replica of the workload (the
+single-domain workloads do not shard) and the value is the whole-job
+aggregate over ranks; timing is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "agent-updates/s (grid+force+displace)"
+UNIT = "agent-updates/s"
+# Algorithmic bytes of the force kernel (FP32-force path): per agent the
+# FP64 position (24 B), an FP32 diameter (4 B), the static flag (1 B), the
+# FP32 force (12 B) and the nnz count (1 B); per occupied box 8 B.  FP64
+# path: FP64 diameter (8 B) and FP64 force (24 B).
+ALG_BYTES_AGENT = {1: 42.0, 0: 58.0}
+ALG_BYTES_BOX = 8.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--workload", default="clustered_8M")
+    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--static", type=int, default=0)
+    ap.add_argument("--settle", type=int, default=50, help="untimed iterations before warm-up")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name: str, precision: int, static: int):
+    from paper_2503_10796_gb300 import workloads as W
+    if name == "clustered_8M":
+        pops = [W.clustered(precision=precision, detect_static=static, sort_interval=10)]
+        desc = dict(workload="clustered_8M", agents=8388608, clusters=64, sigma=200.0, side=1.0e4,
+                    diameters="U[8,12]", sort_interval=10)
+    elif name == "plain_fp64_4096":
+        pops = [W.plain_fp64(precision=precision)]
+        desc = dict(workload="plain_4096", agents=4096, side=160.0, diameters="U[8,12]")
+    elif name == "uniform_200M":
+        pops = [W.uniform_fraction(200_000_000, precision=precision)]
+        desc = dict(workload="uniform_200M", agents=200_000_000, volume_fraction=0.3)
+    elif name == "batched_sweep_256":
+        pops = W.batched_sweep(precision=precision)
+        desc = dict(workload="batched_sweep_256", sims=256, agents=int(sum(p.n for p in pops)))
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    for p in pops:
+        p.params.detect_static = static
+    desc.update(precision="fp32-force/fp64-position" if precision == 1 else "fp64", static_skip=bool(static),
+                l2="inputs larger than L2 (no flush needed)" if sum(p.n for p in pops) > 1_000_000 else
+                "working set inside L2")
+    return pops, desc
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(name: str):
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    from paper_2503_10796_gb300 import workloads as W
+    oracle.build()
+    if name == "clustered_8M":
+        pop = W.clustered(n_clusters=8)
+        iters, sample = 3, "3 iterations of 8 of the 64 clusters (1,048,576 agents), same per-cluster shape"
+    elif name == "plain_fp64_4096":
+        pop = W.plain_fp64()
+        iters, sample = 10, "the full workload, 10 iterations"
+    elif name == "uniform_200M":
+        pop = W.uniform_fraction(1_000_000)
+        iters, sample = 2, "2 iterations of 1,000,000 agents at the same volume fraction"
+    else:
+        pops = W.batched_sweep()
+        pop = pops[int(np.argsort([p.n for p in pops])[len(pops) // 2])]
+        iters, sample = 5, f"5 iterations of the median simulation ({pop.n} agents)"
+    s = oracle.Sim(pop.xyz, pop.diameter, pop.params)
+    t0 = time.perf_counter()
+    s.step(iters)
+    dt = time.perf_counter() - t0
+    return {"value": pop.n * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds": dt}
+
+
+def reference_arm(args):
+    """--impl reference: the oracle on the host cores, one bounded sample per step."""
+    import oracle
+    from paper_2503_10796_gb300 import workloads as W
+    oracle.build()
+    if args.workload == "clustered_8M":
+        pop = W.clustered(n_clusters=2)
+        sample = "each step: 1 iteration of 2 of the 64 clusters (262,144 agents)"
+    elif args.workload == "plain_fp64_4096":
+        pop = W.plain_fp64()
+        sample = "each step: 1 iteration of the full workload"
+    elif args.workload == "uniform_200M":
+        pop = W.uniform_fraction(250_000)
+        sample = "each step: 1 iteration of 250,000 agents at the same volume fraction"
+    else:
+        pops = W.batched_sweep()
+        pop = pops[int(np.argsort([p.n for p in pops])[len(pops) // 2])]
+        sample = f"each step: 1 iteration of the median simulation ({pop.n} agents)"
+    s = oracle.Sim(pop.xyz, pop.diameter, pop.params)
+    for _ in range(args.warmup):
+        s.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(1)
+    dt = time.perf_counter() - t0
+    v = pop.n * args.steps / dt
+    _, desc = make_workload(args.workload, args.precision, args.static) if args.workload != "uniform_200M" else (
+        None, dict(workload="uniform_200M"))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": desc,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2503_10796_gb300 import binding
+    torch.cuda.set_device(local)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    pops, desc = make_workload(args.workload, args.precision, args.static)
+    total_agents = sum(max(p.n, p.params.capacity) for p in pops)
+    # a dedicated stream: the library captures CUDA graphs on it, which the
+    # legacy default stream does not allow
+    stream = torch.cuda.Stream(device=local)
+    ctx = binding.Context([binding.make_params(p.params) for p in pops], total_agents + 1024, device=local,
+                          stream=stream.cuda_stream)
+    for s, p in enumerate(pops):
+        ctx.set_agents(s, p.xyz, p.diameter)
+    n_agents = sum(p.n for p in pops)
+    if args.settle > 0:
+        ctx.step(args.settle)
+    ctx.step(args.warmup)
+    ctx.sync()
+    ctx.profile(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ctx.sync()
+    prof = ctx.get_profile()
+    ctx.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_agents * args.steps / (ms * 1e-3)
+
+    # roofline of the force kernel
+    f = prof["force"]
+    force_ms = f["ms"] / max(f["launches"], 1)
+    occupied = 0
+    st_static = 0
+    for s in range(len(pops)):
+        box, _, _ = ctx.grid(s)
+        occupied += int(np.unique(box).size)
+        st_static += ctx.stats(s)["static_agents"]
+    prec = args.precision
+    alg = ALG_BYTES_AGENT[prec] * (n_agents - st_static) + ALG_BYTES_BOX * occupied
+    peak, peak_kind = peaks()
+    achieved = alg / (force_ms * 1e-3) / 1e9
+    launches_per_iter = 9 + (1 if any(p.params.sort_interval > 0 for p in pops) else 0) + (
+        1 if any(p.params.growth_rate > 0 for p in pops) else 0)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        xs = [np.ascontiguousarray(p.xyz) for p in pops]
+        ds = [np.ascontiguousarray(p.diameter) for p in pops]
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for s in range(len(pops)):
+                ctx.set_agents(s, xs[s], ds[s])
+            ctx.step(1)
+            for s in range(len(pops)):
+                xs[s], ds[s] = ctx.get_agents(s)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * n_agents * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(n_agents * 32), "d2h_bytes_per_step": int(n_agents * 32),
+               "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-force/f64-position" if prec == 1 else "f64", "data": "synthetic",
+            "config": dict(desc, parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                           settle_iterations=args.settle),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_force",
+                         "peak_source": f"{peak_kind} hbm_gbs", "force_ms_per_launch": force_ms,
+                         "alg_bytes_per_launch": alg},
+            "stages_ms_per_iter": {k: v["ms"] / max(v["launches"], 1) for k, v in prof.items() if v["launches"]},
+            "static_agents_last_iter": st_static,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": launches_per_iter * args.steps + math.ceil(args.steps / 256),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

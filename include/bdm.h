@@ -1,0 +1,184 @@
+/*
+ * bdm.h -- C ABI of the GB300 (sm_103a) mechanical-interaction step for
+ * spherical agents, after the BioDynaMo thesis (arXiv 2503.10796).
+ *
+ * One iteration, as the thesis's simulation loop runs it (§5.2,
+ * Algorithm 8), under the copy execution context (§5.2, "Different
+ * Execution Contexts"): all agents see the state at the start of the
+ * iteration and the changes are committed at its end.
+ *
+ *   S0  bounding box and box length: origin o = per-axis minimum of the
+ *       centers; box length L = user value, else the largest diameter
+ *       (§4.4.3 "Environment"); boxes per axis n_a = floor((max_a-o_a)/L)+1.
+ *   S1  box index per agent: c_a = floor((x_a - o_a) / L) in IEEE FP64,
+ *       index c_x + n_x (c_y + n_y c_z) (§5.3.1, Fig 5.4B).
+ *   S2  grid build with per-box timestamps, so that empty boxes are never
+ *       cleared (§5.3.1): count, prefix sum over box leaders, placement.
+ *   S3  Morton re-sort of the agent storage every `sort_interval`
+ *       iterations (§5.4.2, Fig 5.4); results never depend on it.
+ *   S4  pairwise force over the 27-box stencil, Eq 4.1 / Eq 4.2 (§4.5.1):
+ *       delta = r_i + r_j - dist, r = r_i r_j / (r_i + r_j),
+ *       F_N = k delta - gamma sqrt(r delta), along (x_i - x_j) / dist.
+ *   S5  displacement: none while |F| <= adherence, else dt F with its norm
+ *       clamped to max_displacement (§4.5.1; Table D.1 MechanicalForcesOp).
+ *   S6  static agents skip S4/S5 (§5.5, conditions (i)-(iv)).
+ *   S7  growth and division (Table D.1 GrowthDivision).
+ *
+ * Conventions.
+ *   - Every call returns BDM_OK (0) or a negative BDM_E_* code; the text of
+ *     the last error of a context is returned by bdm_last_error().
+ *   - Host pointers are owned by the caller; the library copies in and out
+ *     and never keeps them.  With BDM_DEVICE_PTRS the pointers are device
+ *     pointers, read or written on the context's stream.
+ *   - A context is not thread-safe: use it from one host thread.
+ *   - Agent IDs are the row indices given to bdm_set_agents (per
+ *     simulation); agents created by division get the next IDs, in
+ *     ascending parent-ID order.  IDs survive every re-sort.
+ *   - bdm_step is asynchronous.  Errors found on the device (capacity,
+ *     non-finite values, a bounded wait that ran out) are latched and
+ *     reported by the next bdm_sync or bdm_get_* call.
+ */
+#ifndef BDM_H_
+#define BDM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  BDM_OK = 0,
+  BDM_E_INVAL = -1,     /* bad argument or input value */
+  BDM_E_NOMEM = -2,     /* device or host allocation failed */
+  BDM_E_CUDA = -3,      /* CUDA runtime error */
+  BDM_E_CAPACITY = -4,  /* output buffer, agent capacity or box table too small */
+  BDM_E_TIMEOUT = -5,   /* a bounded device wait ran out */
+  BDM_E_NONFINITE = -6, /* a position or force became NaN or infinite */
+  BDM_E_STATE = -7      /* call not valid in the current state */
+};
+
+enum { BDM_PREC_FP64 = 0, BDM_PREC_FP32_FORCE = 1 };
+
+/* flags of bdm_set_agents / bdm_get_agents */
+enum { BDM_DEVICE_PTRS = 1 };
+
+/* Per-simulation parameters (thesis Param and Cell attributes). */
+typedef struct {
+  double k;                /* Eq 4.1 repulsion coefficient (thesis default 2) */
+  double gamma;            /* Eq 4.1 adhesion coefficient (thesis default 1) */
+  double adherence;        /* an agent moves only if |F| > adherence */
+  double max_displacement; /* norm clamp of one iteration's displacement */
+  double dt;               /* simulation time step */
+  double box_length;       /* grid box length; 0 = largest diameter of each iteration */
+  double growth_rate;      /* volume growth per unit time; 0 = no growth */
+  double divide_volume;    /* volume at which an agent divides (growth only) */
+  int32_t precision;       /* BDM_PREC_FP64 or BDM_PREC_FP32_FORCE */
+  int32_t detect_static;   /* 1: skip the force of static agents (§5.5) */
+  int32_t sort_interval;   /* Morton re-sort every n iterations; 0 = never */
+  int32_t reserved;        /* must be 0 */
+  uint64_t seed;           /* key of the counter-based generator (division axes) */
+  int64_t capacity;        /* agent capacity of this simulation; 0 = count at bdm_set_agents */
+} bdm_params;
+
+/* Counters of one simulation (bdm_get_stats). */
+typedef struct {
+  int64_t agents;          /* current agent count */
+  int64_t iterations;      /* iterations stepped since bdm_set_agents */
+  int64_t static_agents;   /* agents skipped as static in the last iteration */
+  int64_t moved_agents;    /* agents with a non-zero displacement in the last iteration */
+  double origin_len[4];    /* grid of the last iteration: origin x, y, z and box length */
+  int64_t dims[3];         /* boxes per axis of that grid */
+  int64_t reserved[4];
+} bdm_stats;
+
+typedef struct bdm_ctx bdm_ctx;
+
+/* Create a context on CUDA device `device` for `n_sims` independent
+ * simulations whose agent capacities sum to at most `max_agents_total`.
+ * `per_sim` holds n_sims parameter sets.  `cuda_stream` is a cudaStream_t
+ * to run on (for example a PyTorch stream), or NULL for a stream the
+ * context creates.  The context owns all device memory it allocates.
+ * Errors: BDM_E_INVAL (n_sims < 1, bad parameters), BDM_E_NOMEM,
+ * BDM_E_CUDA. */
+int bdm_create(const bdm_params* per_sim, int32_t n_sims, int64_t max_agents_total,
+               int32_t device, void* cuda_stream, bdm_ctx** out);
+
+/* Replace the agents of simulation `sim`: n rows of (x, y, z) in `xyz`
+ * (n x 3, row-major) and n diameters.  Row i becomes agent ID i.  The
+ * iteration counter and all history (static flags) restart.  Errors:
+ * BDM_E_INVAL (sim out of range, n < 0, non-finite value, diameter <= 0),
+ * BDM_E_CAPACITY (n above the simulation's capacity, or the capacities of
+ * all simulations above max_agents_total). */
+int bdm_set_agents(bdm_ctx* ctx, int32_t sim, int64_t n, const double* xyz,
+                   const double* diameter, int32_t flags);
+
+/* Run n_iterations iterations of every simulation (S0-S7), asynchronously
+ * on the context's stream.  Errors: BDM_E_STATE (a simulation has no
+ * agents set), BDM_E_NOMEM (box table growth failed), BDM_E_CUDA. */
+int bdm_step(bdm_ctx* ctx, int32_t n_iterations);
+
+/* Wait for the context's stream and report latched device errors. */
+int bdm_sync(bdm_ctx* ctx);
+
+/* Copy the agents of `sim` out in caller-ID order: xyz (cap x 3) and
+ * diameter (cap), either may be NULL.  *n_out receives the agent count.
+ * Returns BDM_E_CAPACITY, writing nothing, if the count exceeds cap. */
+int bdm_get_agents(bdm_ctx* ctx, int32_t sim, int64_t cap, double* xyz, double* diameter,
+                   int64_t* n_out, int32_t flags);
+
+/* Unordered neighbor pairs {i, j}, i < j in caller IDs, sorted by (i, j),
+ * of the current agents of `sim` (§4.4.3 ForEachNeighbor).  radius >= 0:
+ * pairs with squared center distance < radius * radius; radius < 0:
+ * overlapping pairs (delta > 0, the pairs that interact in Eq 4.1).  The
+ * decision is taken in FP64 exactly as in the definitions above.  A radius
+ * above the box length uses a grid of box length = radius.  pairs holds
+ * 2 x cap int64 values (may be NULL when cap = 0); *n_out receives the pair
+ * count; BDM_E_CAPACITY (nothing written) if it exceeds cap. */
+int bdm_neighbors(bdm_ctx* ctx, int32_t sim, double radius, int64_t cap, int64_t* pairs,
+                  int64_t* n_out);
+
+/* Grid that the next iteration would build from the current agents of
+ * `sim` (S0, S1): box index per caller ID in box_id (cap entries, may be
+ * NULL), origin x, y, z and box length in origin_len, boxes per axis in
+ * dims.  BDM_E_CAPACITY (nothing written) if the agent count exceeds cap. */
+int bdm_get_grid(bdm_ctx* ctx, int32_t sim, int64_t cap, int64_t* box_id, double origin_len[4],
+                 int64_t dims[3]);
+
+/* Per-agent results of the last iteration of `sim`, by caller ID: the
+ * net force (cap x 3; zero for static agents), the number of non-zero pair
+ * forces and the static flag.  Any output may be NULL.  Agents created in
+ * the last iteration report zeros. */
+int bdm_get_forces(bdm_ctx* ctx, int32_t sim, int64_t cap, double* force, int32_t* nnz,
+                   uint8_t* is_static, int64_t* n_out);
+
+/* Caller IDs of `sim` in device storage order (the order that the Morton
+ * re-sort arranges). */
+int bdm_get_storage_order(bdm_ctx* ctx, int32_t sim, int64_t cap, int64_t* ids, int64_t* n_out);
+
+/* Counters of `sim` after the last iteration. */
+int bdm_get_stats(bdm_ctx* ctx, int32_t sim, bdm_stats* out);
+
+/* Per-stage timing.  While enabled, every stage of bdm_step is bracketed by
+ * CUDA events on the context's stream; bdm_get_profile returns, for each
+ * stage, the number of launches and the summed device time in ms since
+ * profiling was enabled, and the stage names in `names` (NULL allowed).
+ * Stages: 0 bbox, 1 grid count, 2 grid scan, 3 grid place, 4 force,
+ * 5 displace, 6 growth/division, 7 morton sort. */
+enum { BDM_NUM_STAGES = 8 };
+int bdm_profile(bdm_ctx* ctx, int32_t enable);
+int bdm_get_profile(bdm_ctx* ctx, int64_t launches[BDM_NUM_STAGES], double ms[BDM_NUM_STAGES],
+                    const char* names[BDM_NUM_STAGES]);
+
+/* Release everything the context owns. */
+void bdm_destroy(bdm_ctx* ctx);
+
+/* Text of the last error of ctx (or of the last failed bdm_create when ctx
+ * is NULL).  Valid until the next call on the same context. */
+const char* bdm_last_error(const bdm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BDM_H_ */

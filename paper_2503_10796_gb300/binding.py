@@ -1,0 +1,226 @@
+"""Thin ctypes binding of the C ABI (``include/bdm.h``).
+
+Argument marshalling only: every step of the mechanics runs in the CUDA
+library.  There is no fallback: if ``_build/libbdm.so`` cannot be loaded the
+import of the library fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BDM_OK = 0
+ERRORS = {-1: "BDM_E_INVAL", -2: "BDM_E_NOMEM", -3: "BDM_E_CUDA", -4: "BDM_E_CAPACITY",
+          -5: "BDM_E_TIMEOUT", -6: "BDM_E_NONFINITE", -7: "BDM_E_STATE"}
+PREC_FP64, PREC_FP32_FORCE = 0, 1
+DEVICE_PTRS = 1
+NUM_STAGES = 8
+
+# Every symbol the header declares, with (restype, argtypes).
+_P = C.POINTER
+_vp, _i32, _i64, _dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+
+
+class BdmParams(C.Structure):
+    _fields_ = [
+        ("k", C.c_double), ("gamma", C.c_double), ("adherence", C.c_double),
+        ("max_displacement", C.c_double), ("dt", C.c_double), ("box_length", C.c_double),
+        ("growth_rate", C.c_double), ("divide_volume", C.c_double),
+        ("precision", C.c_int32), ("detect_static", C.c_int32), ("sort_interval", C.c_int32),
+        ("reserved", C.c_int32), ("seed", C.c_uint64), ("capacity", C.c_int64),
+    ]
+
+
+class BdmStats(C.Structure):
+    _fields_ = [("agents", C.c_int64), ("iterations", C.c_int64), ("static_agents", C.c_int64),
+                ("moved_agents", C.c_int64), ("origin_len", C.c_double * 4), ("dims", C.c_int64 * 3),
+                ("reserved", C.c_int64 * 4)]
+
+
+SIGNATURES = {
+    "bdm_create": (C.c_int, [_P(BdmParams), _i32, _i64, _i32, _vp, _P(_vp)]),
+    "bdm_set_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _i32]),
+    "bdm_step": (C.c_int, [_vp, _i32]),
+    "bdm_sync": (C.c_int, [_vp]),
+    "bdm_get_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _P(_i64), _i32]),
+    "bdm_neighbors": (C.c_int, [_vp, _i32, _dbl, _i64, _vp, _P(_i64)]),
+    "bdm_get_grid": (C.c_int, [_vp, _i32, _i64, _vp, _P(_dbl), _P(_i64)]),
+    "bdm_get_forces": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _vp, _P(_i64)]),
+    "bdm_get_storage_order": (C.c_int, [_vp, _i32, _i64, _vp, _P(_i64)]),
+    "bdm_get_stats": (C.c_int, [_vp, _i32, _P(BdmStats)]),
+    "bdm_profile": (C.c_int, [_vp, _i32]),
+    "bdm_get_profile": (C.c_int, [_vp, _P(_i64), _P(_dbl), _P(C.c_char_p)]),
+    "bdm_destroy": (None, [_vp]),
+    "bdm_last_error": (C.c_char_p, [_vp]),
+}
+
+_lib = None
+
+
+def load_library(path: str | None = None, build: bool = True):
+    """Load (building first if needed) the sm_103a library."""
+    global _lib
+    if _lib is None:
+        if path is None:
+            path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library not built: {path}")
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class BdmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def make_params(p=None, **kw) -> BdmParams:
+    d = dict(k=2.0, gamma=1.0, adherence=0.4, max_displacement=3.0, dt=0.01, box_length=0.0,
+             growth_rate=0.0, divide_volume=0.0, precision=PREC_FP32_FORCE, detect_static=0,
+             sort_interval=0, seed=0, capacity=0)
+    if p is not None:
+        src = p.as_dict() if hasattr(p, "as_dict") else dict(p)
+        for k in d:
+            if k in src:
+                d[k] = src[k]
+    d.update(kw)
+    return BdmParams(d["k"], d["gamma"], d["adherence"], d["max_displacement"], d["dt"], d["box_length"],
+                     d["growth_rate"], d["divide_volume"], int(d["precision"]), int(d["detect_static"]),
+                     int(d["sort_interval"]), 0, int(d["seed"]) & (2**64 - 1), int(d["capacity"]))
+
+
+def _dptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data)
+
+
+class Context:
+    """A set of independent simulations on one GPU (``bdm_create``)."""
+
+    def __init__(self, params, max_agents_total: int, device: int = 0, stream=None):
+        self._lib = load_library()
+        plist = params if isinstance(params, (list, tuple)) else [params]
+        arr = (BdmParams * len(plist))(*[p if isinstance(p, BdmParams) else make_params(p) for p in plist])
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        rc = self._lib.bdm_create(arr, len(plist), int(max_agents_total), int(device), st, C.byref(h))
+        if rc != BDM_OK:
+            raise BdmError(rc, self._lib.bdm_last_error(None).decode())
+        self._h = h
+        self.n_sims = len(plist)
+
+    def _check(self, rc):
+        if rc != BDM_OK:
+            raise BdmError(rc, self._lib.bdm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bdm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- agents ------------------------------------------------------------
+    def set_agents(self, sim: int, xyz, diameter):
+        """Host numpy arrays, or CUDA torch tensors (passed as device pointers)."""
+        if hasattr(xyz, "data_ptr") and getattr(xyz, "is_cuda", False):
+            n = int(xyz.shape[0])
+            self._check(self._lib.bdm_set_agents(self._h, sim, n, C.c_void_p(xyz.data_ptr()),
+                                                 C.c_void_p(diameter.data_ptr()), DEVICE_PTRS))
+            return
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        d = np.ascontiguousarray(diameter, dtype=np.float64).reshape(-1)
+        if d.shape[0] != xyz.shape[0]:
+            raise ValueError("xyz and diameter differ in length")
+        self._check(self._lib.bdm_set_agents(self._h, sim, xyz.shape[0], _dptr(xyz), _dptr(d), 0))
+
+    def step(self, iterations: int = 1):
+        self._check(self._lib.bdm_step(self._h, int(iterations)))
+
+    def sync(self):
+        self._check(self._lib.bdm_sync(self._h))
+
+    def count(self, sim: int) -> int:
+        return self.stats(sim)["agents"]
+
+    def get_agents(self, sim: int):
+        n = C.c_int64()
+        rc = self._lib.bdm_get_agents(self._h, sim, 0, None, None, C.byref(n), 0)
+        if rc not in (BDM_OK, -4):
+            self._check(rc)
+        xyz = np.empty((n.value, 3)); d = np.empty(n.value)
+        self._check(self._lib.bdm_get_agents(self._h, sim, n.value, _dptr(xyz), _dptr(d), C.byref(n), 0))
+        return xyz, d
+
+    def get_agents_device(self, sim: int, xyz_t, d_t):
+        """Write into CUDA tensors (n x 3 and n float64) on the context stream."""
+        n = C.c_int64()
+        self._check(self._lib.bdm_get_agents(self._h, sim, int(xyz_t.shape[0]), C.c_void_p(xyz_t.data_ptr()),
+                                             C.c_void_p(d_t.data_ptr()), C.byref(n), DEVICE_PTRS))
+        return n.value
+
+    # -- queries -----------------------------------------------------------
+    def neighbors(self, sim: int, radius: float) -> np.ndarray:
+        n = C.c_int64()
+        rc = self._lib.bdm_neighbors(self._h, sim, float(radius), 0, None, C.byref(n))
+        if rc not in (BDM_OK, -4):
+            self._check(rc)
+        out = np.empty((max(n.value, 1), 2), np.int64)
+        self._check(self._lib.bdm_neighbors(self._h, sim, float(radius), n.value, _dptr(out), C.byref(n)))
+        return out[: n.value]
+
+    def grid(self, sim: int):
+        st = self.stats(sim)
+        n = max(st["agents"], 1)
+        box = np.empty(n, np.int64); ol = (C.c_double * 4)(); dims = (C.c_int64 * 3)()
+        self._check(self._lib.bdm_get_grid(self._h, sim, n, _dptr(box), ol, dims))
+        return box[: st["agents"]], np.array(list(ol)), np.array(list(dims), np.int64)
+
+    def forces(self, sim: int):
+        n = C.c_int64()
+        rc = self._lib.bdm_get_forces(self._h, sim, 0, None, None, None, C.byref(n))
+        if rc not in (BDM_OK, -4):
+            self._check(rc)
+        m = max(n.value, 1)
+        F = np.empty((m, 3)); nnz = np.empty(m, np.int32); st = np.empty(m, np.uint8)
+        self._check(self._lib.bdm_get_forces(self._h, sim, m, _dptr(F), _dptr(nnz), _dptr(st), C.byref(n)))
+        k = n.value
+        return F[:k], nnz[:k], st[:k].astype(bool)
+
+    def storage_order(self, sim: int) -> np.ndarray:
+        n = C.c_int64()
+        rc = self._lib.bdm_get_storage_order(self._h, sim, 0, None, C.byref(n))
+        if rc not in (BDM_OK, -4):
+            self._check(rc)
+        out = np.empty(max(n.value, 1), np.int64)
+        self._check(self._lib.bdm_get_storage_order(self._h, sim, n.value, _dptr(out), C.byref(n)))
+        return out[: n.value]
+
+    def stats(self, sim: int) -> dict:
+        s = BdmStats()
+        self._check(self._lib.bdm_get_stats(self._h, sim, C.byref(s)))
+        return dict(agents=s.agents, iterations=s.iterations, static_agents=s.static_agents,
+                    moved_agents=s.moved_agents, origin_len=list(s.origin_len), dims=list(s.dims))
+
+    # -- profiling ---------------------------------------------------------
+    def profile(self, enable: bool = True):
+        self._check(self._lib.bdm_profile(self._h, 1 if enable else 0))
+
+    def get_profile(self) -> dict:
+        launches = (C.c_int64 * NUM_STAGES)(); ms = (C.c_double * NUM_STAGES)()
+        names = (C.c_char_p * NUM_STAGES)()
+        self._check(self._lib.bdm_get_profile(self._h, launches, ms, names))
+        return {names[k].decode(): dict(launches=launches[k], ms=ms[k]) for k in range(NUM_STAGES)}

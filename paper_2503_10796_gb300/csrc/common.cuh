@@ -1,0 +1,241 @@
+// Shared device structures and helpers of the sm_103a mechanics library.
+//
+// Data layout (all simulations of a context share each array):
+//   storage arrays, indexed by slot: simulation s owns slots
+//     [base_s, base_s + cap_s); its agents occupy [base_s, base_s + n_s).
+//   cell arrays, indexed by cell position: agents grouped by grid box, the
+//     boxes of simulation s contiguous in [cell_base_s, cell_base_s + n_s).
+//   box table: one 64-bit word per box (stamp | dirty | count) and one
+//     32-bit first-cell index; simulation s owns entries
+//     [table_base_s, table_base_s + table_cap_s).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bdm.h"
+
+namespace bdm {
+
+// Latched device error bits.
+enum : uint32_t {
+  ERR_CAPACITY = 1u,   // agent capacity reached while dividing (informational)
+  ERR_NONFINITE = 2u,  // NaN or infinity in a position or force
+  ERR_TIMEOUT = 4u,    // a bounded retry loop ran out
+  ERR_TABLE = 8u,      // box table region too small for the grid
+  ERR_COORD = 16u,     // box coordinate beyond 2^21 per axis
+};
+
+// Flags per slot.
+enum : uint8_t { FLAG_CHANGED = 1u, FLAG_STATIC = 2u };
+
+// Flags per cell (written by the placement kernel for the force kernel).
+enum : uint8_t { CELL_STATIC_ELIGIBLE = 1u };
+
+constexpr int kStages = BDM_NUM_STAGES;
+constexpr int kCoordBits = 21;
+constexpr uint64_t kCoordMask = (1ull << kCoordBits) - 1ull;
+
+// Per-simulation constants (host-written).
+struct SimConst {
+  double k, gamma, adherence, max_disp, dt, box_length, growth_rate, divide_volume;
+  float kf, gammaf, adherence2f, max_disp2f, max_dispf, dtf;
+  int32_t precision, detect_static, sort_interval, grows;
+  uint64_t seed;
+  int64_t base, cap;
+  int64_t table_base, table_cap;
+};
+
+// Per-simulation state (device-written).
+struct SimState {
+  int64_t n;                  // agent count
+  unsigned long long bmin[3]; // order-preserving keys of the per-axis minimum
+  unsigned long long bmax[3]; // ... maximum
+  unsigned long long dmax;    // ... largest diameter
+  double o[3], L;             // grid of the current iteration
+  int64_t dims[3];
+  int64_t nboxes;
+  float Lh, Ll;               // L as float-float
+  float ilh, ill;             // 1/L as float-float
+  float marg;                 // conservative margin of the FP32 pair filter
+  int32_t same_grid;          // grid equals the previous iteration's
+  int32_t valid;              // grid fits the table region
+  int32_t has_prev;
+  double prev_o[3], prev_L;
+  int64_t prev_dims[3];
+  int64_t cell_base;
+  int64_t ncell;              // agents placed in the cells of the last build
+  int64_t t;                  // iterations completed
+  int64_t it;                 // index of the iteration being computed
+  unsigned long long n_static, n_moved;
+};
+
+// Global counters of a context.
+struct Globals {
+  uint32_t stamp;             // grid timestamp (all simulations, every build)
+  uint32_t err;               // latched error bits
+  int64_t n_cells;            // agents over all simulations
+  int64_t n_new;              // agents created in the current division round
+};
+
+struct Agents {               // storage arrays (per slot)
+  double *x, *y, *z, *d, *v;
+  int32_t *id;                // caller ID
+  int32_t *sim;               // owning simulation (every slot of a region)
+  uint64_t *pkey;             // packed box coordinates c_x | c_y << 21 | c_z << 42
+  uint64_t *pkey_hist;        // box coordinates in the last iteration's grid
+  uint32_t *rank;             // position inside the box
+  uint8_t *flags;
+  uint8_t *nnz;               // non-zero pair forces of the last evaluation (saturating)
+};
+
+struct Cells {                // cell arrays (per cell position)
+  int32_t *slot;
+  int32_t *sim;
+  uint64_t *pkey;
+  float4 *r0;                 // FP32 path: (w_hi.xyz, r_hi): offset inside the own box
+  float4 *r1;                 //            (w_lo.xyz, r_lo)
+  double4_32a *r64;               // FP64 path: (x, y, z, r)
+  uint8_t *flag;
+  float4 *f32;                // net force (FP32 path)
+  double4_32a *f64;               // net force (FP64 path)
+  uint8_t *nnz;
+  uint8_t *stat;
+};
+
+struct Table {
+  unsigned long long *cnt;    // stamp << 32 | dirty << 31 | count
+  uint32_t *start;            // first cell position of the box
+};
+
+struct DevCtx {
+  SimConst *sc;
+  SimState *ss;
+  Globals *g;
+  Agents a;
+  Cells c;                    // cells of the last iteration
+  Cells q;                    // cells of the last neighbor query
+  Table tab;
+  int32_t *order;             // simulations in slot-region order (-1 padded)
+  int32_t n_sims;
+  int64_t total_slots;
+};
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ord_key(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double ord_val(unsigned long long k) {
+  unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ uint64_t pack_coords(int64_t cx, int64_t cy, int64_t cz) {
+  return (uint64_t)cx | ((uint64_t)cy << kCoordBits) | ((uint64_t)cz << (2 * kCoordBits));
+}
+
+__device__ __forceinline__ void unpack_coords(uint64_t p, int64_t &cx, int64_t &cy, int64_t &cz) {
+  cx = (int64_t)(p & kCoordMask);
+  cy = (int64_t)((p >> kCoordBits) & kCoordMask);
+  cz = (int64_t)((p >> (2 * kCoordBits)) & kCoordMask);
+}
+
+__device__ __forceinline__ int64_t linear_box(const SimState &s, int64_t cx, int64_t cy, int64_t cz) {
+  return cx + s.dims[0] * (cy + s.dims[1] * cz);
+}
+
+// Error-free transformations in FP32 (Knuth two-sum, fma two-product).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// 2^k as a float for -126 <= k <= 127.
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+// Split a finite double into hi + lo floats (hi: leading 24 significant bits,
+// truncated; lo: the remaining 29 bits rounded to 24).  Integer operations
+// only, except for zero, tiny or huge magnitudes.
+__device__ __forceinline__ void split_ff(double a, float &hi, float &lo) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  int e = (int)((b >> 52) & 0x7FF);
+  unsigned int sign = (unsigned int)(b >> 63) << 31;
+  if (e >= 1023 - 126 + 52 && e <= 1023 + 127) {
+    unsigned int hb = sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)((b >> 29) & 0x7FFFFF);
+    hi = __uint_as_float(hb);
+    float l = __fmul_rn(__uint2float_rn((unsigned int)(b & 0x1FFFFFFF)), pow2f(e - 1075));
+    lo = sign ? -l : l;
+  } else if (a == 0.0) {
+    hi = 0.0f;
+    lo = 0.0f;
+  } else {
+    hi = __double2float_rn(a);
+    lo = __double2float_rn(__dsub_rn(a, (double)hi));
+  }
+}
+
+// Exact float -> double conversion with integer operations for normal
+// values.
+__device__ __forceinline__ double f2d(float f) {
+  unsigned int u = __float_as_uint(f);
+  unsigned int e = (u >> 23) & 0xFF;
+  if (e == 0 || e == 0xFF) return (double)f;
+  unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                         ((unsigned long long)(e + (1023 - 127)) << 52) |
+                         ((unsigned long long)(u & 0x7FFFFF) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+// floor(fl64(a / L)) for a >= 0, exactly as IEEE FP64 division and floor
+// give it.  (ah, al) split a; (ilh, ill) is 1/L as float-float.  The
+// float-float quotient decides unless it lies within a relative 2^-36 of
+// an integer; only then is the FP64 division evaluated.
+__device__ __forceinline__ int64_t box_coord(double a, float ah, float al, float ilh, float ill,
+                                             double L) {
+  float p, e;
+  two_prod(ah, ilh, p, e);
+  e = __fadd_rn(e, __fadd_rn(__fmul_rn(ah, ill), __fmul_rn(al, ilh)));
+  float c = floorf(p);
+  float g = __fsub_rn(p, c);  // exact: fractional bits of p
+  float m = __fmaf_rn(p, 0x1p-36f, 0x1p-40f);
+  if (g >= 0x1p-10f && g <= 1.0f - 0x1p-10f) return (int64_t)c;
+  float t = (g < 0.5f) ? __fadd_rn(g, e) : __fadd_rn(__fsub_rn(g, 1.0f), e);
+  if (g < 0.5f) {
+    if (t >= m) return (int64_t)c;
+    if (t <= -m) return (int64_t)c - 1;
+  } else {
+    if (t <= -m) return (int64_t)c;
+    if (t >= m) return (int64_t)c + 1;
+  }
+  return (int64_t)floor(__ddiv_rn(a, L));
+}
+
+// Warp-aggregated atomic add of a per-lane count into *dst.
+__device__ __forceinline__ void warp_add(unsigned long long *dst, unsigned int v) {
+  unsigned int mask = __activemask();
+  unsigned int s = __reduce_add_sync(mask, v);
+  int leader = __ffs(mask) - 1;
+  if ((int)(threadIdx.x & 31) == leader && s) atomicAdd(dst, (unsigned long long)s);
+}
+
+__device__ __forceinline__ void set_err(Globals *g, uint32_t bits) { atomicOr(&g->err, bits); }
+
+// Grid-stride helpers sized for 152 SMs.
+constexpr int kThreads = 256;
+
+}  // namespace bdm

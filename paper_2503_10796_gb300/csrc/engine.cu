@@ -1,0 +1,837 @@
+// Host engine behind the C ABI of include/bdm.h: context and memory
+// ownership, simulation regions, box-table sizing, the per-iteration stage
+// sequence (captured once into a CUDA graph and replayed), per-stage CUDA
+// event profiling and error reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace bdm;
+
+namespace {
+
+const char *kStageNames[kStages] = {"bbox", "grid_count", "grid_scan", "grid_place",
+                                    "force", "displace", "growth_division", "morton_sort"};
+
+std::string g_create_error;
+int g_alloc_counter = 0;
+
+// Host-side fault injection for tests: BDM_FAULT_ALLOC=n makes the n-th
+// device allocation of the process report failure.
+bool fault_alloc() {
+  const char *e = getenv("BDM_FAULT_ALLOC");
+  if (!e) return false;
+  int n = atoi(e);
+  return n > 0 && ++g_alloc_counter == n;
+}
+
+}  // namespace
+
+struct bdm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int32_t n_sims = 0;
+  std::vector<bdm_params> params;
+  std::vector<SimConst> h_sc;
+  std::vector<int64_t> n_set;  // agents given at the last bdm_set_agents (-1: never)
+  int64_t max_total = 0, used_slots = 0;
+  bool any_fp32 = false, any_fp64 = false, any_grow = false, any_sort = false;
+  DevCtx D{};
+  uint32_t *d_partial = nullptr;
+  int64_t table_entries = 0;
+  void *d_sort = nullptr;
+  size_t sort_bytes = 0;
+  void *d_grow = nullptr;
+  size_t grow_bytes = 0;
+  std::vector<void *> allocs;
+  // profiling
+  bool profiling = false;
+  struct Ev { int stage; cudaEvent_t a, b; };
+  std::vector<Ev> evs;
+  std::vector<cudaEvent_t> pool;
+  int64_t prof_launches[kStages] = {};
+  double prof_ms[kStages] = {};
+  // graph of one iteration
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_dirty = true;
+  std::string err;
+  uint32_t pending_err = 0;
+};
+
+namespace {
+
+int fail(bdm_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(bdm_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, BDM_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+int dalloc(bdm_ctx *c, T **p, size_t count, const char *what) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  if (fault_alloc()) return fail(c, BDM_E_NOMEM, std::string("injected allocation failure: ") + what);
+  cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, BDM_E_NOMEM, std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+  }
+  c->allocs.push_back((void *)*p);
+  return BDM_OK;
+}
+
+void dfree(bdm_ctx *c, void *p) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+  cudaFree(p);
+}
+
+int check_params(const bdm_params &p, std::string &why) {
+  auto fin = [](double v) { return std::isfinite(v); };
+  if (!fin(p.k) || !fin(p.gamma) || !fin(p.adherence) || !fin(p.max_displacement) || !fin(p.dt) ||
+      !fin(p.box_length) || !fin(p.growth_rate) || !fin(p.divide_volume)) {
+    why = "non-finite parameter";
+    return BDM_E_INVAL;
+  }
+  if (p.k < 0 || p.gamma < 0 || p.adherence < 0 || p.max_displacement < 0 || p.dt < 0 || p.box_length < 0 ||
+      p.growth_rate < 0 || p.divide_volume < 0) {
+    why = "negative parameter";
+    return BDM_E_INVAL;
+  }
+  if (p.precision != BDM_PREC_FP64 && p.precision != BDM_PREC_FP32_FORCE) {
+    why = "precision must be BDM_PREC_FP64 or BDM_PREC_FP32_FORCE";
+    return BDM_E_INVAL;
+  }
+  if (p.sort_interval < 0 || p.capacity < 0 || p.reserved != 0) {
+    why = "sort_interval, capacity must be >= 0 and reserved 0";
+    return BDM_E_INVAL;
+  }
+  if (p.growth_rate > 0 && !(p.divide_volume > 0)) {
+    why = "growth needs divide_volume > 0";
+    return BDM_E_INVAL;
+  }
+  return BDM_OK;
+}
+
+SimConst make_const(const bdm_params &p) {
+  SimConst s{};
+  s.k = p.k;
+  s.gamma = p.gamma;
+  s.adherence = p.adherence;
+  s.max_disp = p.max_displacement;
+  s.dt = p.dt;
+  s.box_length = p.box_length;
+  s.growth_rate = p.growth_rate;
+  s.divide_volume = p.divide_volume;
+  s.kf = (float)p.k;
+  s.gammaf = (float)p.gamma;
+  s.adherence2f = (float)(p.adherence * p.adherence);
+  s.max_disp2f = (float)(p.max_displacement * p.max_displacement);
+  s.max_dispf = (float)p.max_displacement;
+  s.dtf = (float)p.dt;
+  s.precision = p.precision;
+  s.detect_static = p.detect_static ? 1 : 0;
+  s.sort_interval = p.sort_interval;
+  s.grows = p.growth_rate > 0 ? 1 : 0;
+  s.seed = p.seed;
+  s.base = -1;
+  s.cap = 0;
+  s.table_base = 0;
+  s.table_cap = 0;
+  return s;
+}
+
+int upload_consts(bdm_ctx *c) {
+  cudaError_t e = cudaMemcpyAsync(c->D.sc, c->h_sc.data(), sizeof(SimConst) * c->h_sc.size(),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "uploading simulation constants");
+  return BDM_OK;
+}
+
+void stage_begin(bdm_ctx *c, int stage) {
+  if (!c->profiling) return;
+  cudaEvent_t a, b;
+  if (c->pool.size() >= 2) {
+    a = c->pool.back(); c->pool.pop_back();
+    b = c->pool.back(); c->pool.pop_back();
+  } else {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  cudaEventRecord(a, c->stream);
+  c->evs.push_back({stage, a, b});
+}
+
+void stage_end(bdm_ctx *c) {
+  if (!c->profiling) return;
+  cudaEventRecord(c->evs.back().b, c->stream);
+}
+
+void harvest_events(bdm_ctx *c) {
+  for (auto &e : c->evs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      c->prof_ms[e.stage] += ms;
+      c->prof_launches[e.stage] += 1;
+    }
+    c->pool.push_back(e.a);
+    c->pool.push_back(e.b);
+  }
+  c->evs.clear();
+  cudaGetLastError();
+}
+
+// One iteration of every simulation.
+void launch_iteration(bdm_ctx *c) {
+  const DevCtx &D = c->D;
+  cudaStream_t st = c->stream;
+  if (c->any_sort) {
+    stage_begin(c, 7);
+    launch_morton(D, st, c->d_sort, c->sort_bytes, 63);
+    stage_end(c);
+  }
+  stage_begin(c, 0);
+  launch_bbox(D, st);
+  launch_params(D, st, 1);
+  stage_end(c);
+  stage_begin(c, 1);
+  launch_count(D, st, 1);
+  stage_end(c);
+  stage_begin(c, 2);
+  launch_scan(D, st, c->d_partial);
+  stage_end(c);
+  stage_begin(c, 3);
+  launch_place(D, st, 1);
+  stage_end(c);
+  stage_begin(c, 4);
+  launch_force(D, st);
+  stage_end(c);
+  stage_begin(c, 5);
+  launch_displace(D, st);
+  stage_end(c);
+  if (c->any_grow) {
+    stage_begin(c, 6);
+    launch_growth(D, st, c->d_grow, c->grow_bytes);
+    stage_end(c);
+  }
+}
+
+// Read the current bounding boxes and size the box table so that the next
+// `iters` iterations fit: extents may grow by the clamp (and the division
+// offset) per iteration on each side, and the box length may shrink to the
+// smallest daughter diameter when cells divide.
+int ensure_table(bdm_ctx *c, int iters, bool *resized) {
+  *resized = false;
+  launch_bbox(c->D, c->stream);
+  std::vector<SimState> ss(c->n_sims);
+  cudaError_t e = cudaMemcpyAsync(ss.data(), c->D.ss, sizeof(SimState) * c->n_sims, cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reading bounding boxes");
+  auto val = [](unsigned long long k) {
+    unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    double d;
+    memcpy(&d, &b, 8);
+    return d;
+  };
+  int64_t total = 0;
+  std::vector<int64_t> need(c->n_sims, 0);
+  for (int s = 0; s < c->n_sims; ++s) {
+    const SimConst &sc = c->h_sc[s];
+    if (sc.base < 0 || ss[s].n <= 0) continue;
+    double dmax = val(ss[s].dmax);
+    double L = sc.box_length > 0 ? sc.box_length : dmax;
+    double step = sc.max_disp;
+    double Lmin = L;
+    if (sc.grows) {
+      double ddiv = std::cbrt(6.0 * sc.divide_volume / M_PI);
+      step += 0.25 * std::max(dmax, ddiv);
+      if (!(sc.box_length > 0)) Lmin = std::min(dmax, ddiv * 0.7937005259840998) * 0.999;
+    }
+    if (!(Lmin > 0) || !std::isfinite(Lmin)) return fail(c, BDM_E_INVAL, "box length is not positive");
+    double nb = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      double ext = val(ss[s].bmax[a]) - val(ss[s].bmin[a]);
+      if (!std::isfinite(ext)) return fail(c, BDM_E_NONFINITE, "non-finite agent position");
+      double dims = std::floor((ext + 2.0 * iters * step) / Lmin) + 3.0;
+      if (dims >= (double)(1ll << kCoordBits))
+        return fail(c, BDM_E_CAPACITY, "grid needs more than 2^21 boxes per axis");
+      nb *= dims;
+    }
+    if (nb > 4.0e10) return fail(c, BDM_E_CAPACITY, "grid needs more than 4e10 boxes");
+    need[s] = (int64_t)nb;
+    total += need[s];
+  }
+  if (total < 1) total = 1;
+  int64_t base = 0;
+  bool changed = false;
+  for (int s = 0; s < c->n_sims; ++s) {
+    SimConst &sc = c->h_sc[s];
+    if (sc.table_base != base || sc.table_cap < need[s]) changed = true;
+    sc.table_base = base;
+    sc.table_cap = need[s];
+    base += need[s];
+  }
+  if (total > c->table_entries) {
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    int64_t want = std::max<int64_t>(total, c->table_entries * 5 / 4);
+    size_t bytes = (size_t)want * 12;
+    size_t have = (size_t)c->table_entries * 12;
+    if (bytes > (size_t)((freeb + have) * 0.85)) {
+      want = total;
+      bytes = (size_t)want * 12;
+      if (bytes > (size_t)((freeb + have) * 0.85))
+        return fail(c, BDM_E_CAPACITY, "box table does not fit in device memory");
+    }
+    dfree(c, c->D.tab.cnt);
+    dfree(c, c->D.tab.start);
+    c->D.tab.cnt = nullptr;
+    c->D.tab.start = nullptr;
+    c->table_entries = 0;
+    int rc = dalloc(c, &c->D.tab.cnt, (size_t)want, "box table");
+    if (rc) return rc;
+    rc = dalloc(c, &c->D.tab.start, (size_t)want, "box table starts");
+    if (rc) return rc;
+    cudaMemsetAsync(c->D.tab.cnt, 0, sizeof(unsigned long long) * (size_t)want, c->stream);
+    c->table_entries = want;
+    changed = true;
+  }
+  if (changed) {
+    int rc = upload_consts(c);
+    if (rc) return rc;
+    *resized = true;
+  }
+  return BDM_OK;
+}
+
+int latched_error(bdm_ctx *c) {
+  uint32_t bits = 0;
+  cudaError_t e = cudaMemcpyAsync(&bits, &c->D.g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronizing");
+  if (!bits) return BDM_OK;
+  cudaMemsetAsync(&c->D.g->err, 0, sizeof(uint32_t), c->stream);
+  cudaStreamSynchronize(c->stream);
+  if (bits & ERR_TIMEOUT) return fail(c, BDM_E_TIMEOUT, "a bounded device retry loop ran out");
+  if (bits & ERR_NONFINITE) return fail(c, BDM_E_NONFINITE, "a position, force or grid value became non-finite");
+  if (bits & ERR_TABLE) return fail(c, BDM_E_CAPACITY, "grid outgrew its box table region");
+  if (bits & ERR_COORD) return fail(c, BDM_E_CAPACITY, "box coordinate beyond 2^21 per axis");
+  return BDM_OK;  // ERR_CAPACITY (division stopped at the cap) is informational
+}
+
+int check_sim(bdm_ctx *c, int32_t sim) {
+  if (!c) return BDM_E_INVAL;
+  if (sim < 0 || sim >= c->n_sims) return fail(c, BDM_E_INVAL, "simulation index out of range");
+  return BDM_OK;
+}
+
+int read_state(bdm_ctx *c, int32_t sim, SimState *out) {
+  cudaError_t e = cudaMemcpyAsync(out, &c->D.ss[sim], sizeof(SimState), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reading simulation state");
+  return BDM_OK;
+}
+
+// Build the grid of the current agents for queries (no step bookkeeping).
+int query_grid(bdm_ctx *c, bool with_cells, const std::vector<double> *boxes) {
+  bool resized;
+  int rc = ensure_table(c, 1, &resized);
+  if (rc) return rc;
+  if (boxes) {
+    // temporary box lengths for radius queries
+    std::vector<SimConst> tmp = c->h_sc;
+    for (int s = 0; s < c->n_sims; ++s) tmp[s].box_length = (*boxes)[s];
+    cudaMemcpyAsync(c->D.sc, tmp.data(), sizeof(SimConst) * tmp.size(), cudaMemcpyHostToDevice, c->stream);
+  }
+  launch_bbox(c->D, c->stream);
+  launch_params(c->D, c->stream, 0);
+  if (with_cells) {
+    launch_count(c->D, c->stream, 0);
+    launch_scan(c->D, c->stream, c->d_partial);
+    launch_place(c->D, c->stream, 0);
+  }
+  if (boxes) upload_consts(c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "query grid");
+  return BDM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_total, int32_t device,
+               void *cuda_stream, bdm_ctx **out) {
+  if (!out) return fail(nullptr, BDM_E_INVAL, "out is NULL");
+  *out = nullptr;
+  if (!per_sim || n_sims < 1 || max_agents_total < 1 || max_agents_total > (1ll << 31) - 1)
+    return fail(nullptr, BDM_E_INVAL, "need per_sim, n_sims >= 1 and 1 <= max_agents_total < 2^31");
+  std::string why;
+  for (int s = 0; s < n_sims; ++s)
+    if (check_params(per_sim[s], why)) return fail(nullptr, BDM_E_INVAL, "simulation " + std::to_string(s) + ": " + why);
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return fail(nullptr, BDM_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  bdm_ctx *c = new bdm_ctx();
+  c->device = device;
+  c->n_sims = n_sims;
+  c->max_total = max_agents_total;
+  c->params.assign(per_sim, per_sim + n_sims);
+  c->n_set.assign(n_sims, -1);
+  for (int s = 0; s < n_sims; ++s) {
+    c->h_sc.push_back(make_const(per_sim[s]));
+    if (per_sim[s].precision == BDM_PREC_FP64) c->any_fp64 = true;
+    else c->any_fp32 = true;
+    if (per_sim[s].growth_rate > 0) c->any_grow = true;
+    if (per_sim[s].sort_interval > 0) c->any_sort = true;
+  }
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      return fail(nullptr, BDM_E_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    c->own_stream = true;
+  }
+  size_t M = (size_t)max_agents_total;
+  DevCtx &D = c->D;
+  D.n_sims = n_sims;
+  int rc = BDM_OK;
+#define ALLOC(ptr, n, what) \
+  if (!rc) rc = dalloc(c, &(ptr), (n), what)
+  ALLOC(D.sc, (size_t)n_sims, "simulation constants");
+  ALLOC(D.ss, (size_t)n_sims, "simulation state");
+  ALLOC(D.g, 1, "globals");
+  ALLOC(D.order, (size_t)n_sims, "simulation order");
+  ALLOC(c->d_partial, 2048, "scan partials");
+  ALLOC(D.a.x, M, "x"); ALLOC(D.a.y, M, "y"); ALLOC(D.a.z, M, "z"); ALLOC(D.a.d, M, "diameter");
+  ALLOC(D.a.v, M, "volume"); ALLOC(D.a.id, M, "ids"); ALLOC(D.a.sim, M, "slot simulation");
+  ALLOC(D.a.pkey, M, "box keys"); ALLOC(D.a.pkey_hist, M, "box history"); ALLOC(D.a.rank, M, "ranks");
+  ALLOC(D.a.flags, M, "flags"); ALLOC(D.a.nnz, M, "nnz");
+  ALLOC(D.c.slot, M, "cell slots"); ALLOC(D.c.sim, M, "cell sims"); ALLOC(D.c.pkey, M, "cell keys");
+  ALLOC(D.c.flag, M, "cell flags"); ALLOC(D.c.nnz, M, "cell nnz"); ALLOC(D.c.stat, M, "cell static");
+  if (c->any_fp32) {
+    ALLOC(D.c.r0, M, "FP32 records hi"); ALLOC(D.c.r1, M, "FP32 records lo"); ALLOC(D.c.f32, M, "FP32 forces");
+  }
+  if (c->any_fp64) {
+    ALLOC(D.c.r64, M, "FP64 records"); ALLOC(D.c.f64, M, "FP64 forces");
+  }
+#undef ALLOC
+  if (!rc && c->any_sort) {
+    c->sort_bytes = morton_scratch_bytes((int64_t)M);
+    rc = dalloc(c, (char **)&c->d_sort, c->sort_bytes, "morton sort scratch");
+  }
+  if (!rc && c->any_grow) {
+    c->grow_bytes = growth_scratch_bytes((int64_t)M, n_sims);
+    rc = dalloc(c, (char **)&c->d_grow, c->grow_bytes, "growth scratch");
+  }
+  if (rc) {
+    g_create_error = c->err;
+    bdm_destroy(c);
+    return rc;
+  }
+  // slot -> simulation map: unassigned slots belong to no simulation
+  cudaMemsetAsync(D.a.sim, 0xff, sizeof(int32_t) * M, c->stream);
+  cudaMemsetAsync(D.ss, 0, sizeof(SimState) * (size_t)n_sims, c->stream);
+  cudaMemsetAsync(D.g, 0, sizeof(Globals), c->stream);
+  cudaMemsetAsync(D.order, 0xff, sizeof(int32_t) * (size_t)n_sims, c->stream);
+  std::vector<SimState> ss0(n_sims);
+  memset(ss0.data(), 0, sizeof(SimState) * n_sims);
+  for (auto &s : ss0) {
+    for (int a = 0; a < 3; ++a) { s.bmin[a] = ~0ull; s.bmax[a] = 0ull; }
+  }
+  cudaMemcpyAsync(D.ss, ss0.data(), sizeof(SimState) * n_sims, cudaMemcpyHostToDevice, c->stream);
+  rc = upload_consts(c);
+  e = cudaStreamSynchronize(c->stream);
+  if (!rc && e != cudaSuccess) rc = cuda_fail(c, e, "initialising the context");
+  if (rc) {
+    g_create_error = c->err;
+    bdm_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return BDM_OK;
+}
+
+int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const double *diameter, int32_t flags) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!xyz || !diameter))) return fail(c, BDM_E_INVAL, "n < 0 or NULL input");
+  bool dev = (flags & BDM_DEVICE_PTRS) != 0;
+  if (!dev) {
+    for (int64_t i = 0; i < n; ++i) {
+      if (!std::isfinite(xyz[3 * i]) || !std::isfinite(xyz[3 * i + 1]) || !std::isfinite(xyz[3 * i + 2]))
+        return fail(c, BDM_E_INVAL, "non-finite position at row " + std::to_string(i));
+      if (!(diameter[i] > 0) || !std::isfinite(diameter[i]))
+        return fail(c, BDM_E_INVAL, "diameter must be finite and > 0 (row " + std::to_string(i) + ")");
+    }
+  }
+  SimConst &sc = c->h_sc[sim];
+  int64_t want = std::max<int64_t>(n, c->params[sim].capacity);
+  if (want < 1) want = 1;
+  if (sc.base < 0) {
+    if (c->used_slots + want > c->max_total)
+      return fail(c, BDM_E_CAPACITY, "agent capacity of the context exhausted");
+    sc.base = c->used_slots;
+    sc.cap = want;
+    c->used_slots += want;
+  } else if (n > sc.cap) {
+    if (sc.base + sc.cap == c->used_slots && sc.base + want <= c->max_total) {
+      c->used_slots = sc.base + want;
+      sc.cap = want;
+    } else {
+      return fail(c, BDM_E_CAPACITY, "n exceeds the capacity of this simulation's region");
+    }
+  }
+  c->D.total_slots = c->used_slots;
+  c->graph_dirty = true;
+  // upload
+  const double *dx = xyz, *dd = diameter;
+  double *tmp = nullptr;
+  if (!dev && n > 0) {
+    rc = dalloc(c, &tmp, (size_t)(4 * n), "upload buffer");
+    if (rc) return rc;
+    cudaMemcpyAsync(tmp, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(tmp + 3 * n, diameter, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+    dx = tmp;
+    dd = tmp + 3 * n;
+  } else if (dev && n > 0) {
+    uint32_t *bad = nullptr;
+    rc = dalloc(c, &bad, 1, "input check");
+    if (rc) return rc;
+    cudaMemsetAsync(bad, 0, sizeof(uint32_t), c->stream);
+    launch_check_input(c->stream, n, xyz, diameter, bad);
+    uint32_t hb = 0;
+    cudaMemcpyAsync(&hb, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    dfree(c, bad);
+    if (hb) return fail(c, BDM_E_INVAL, "non-finite position or diameter <= 0 in device input");
+  }
+  upload_consts(c);
+  launch_set_agents(c->D, c->stream, sim, sc.base, n, sc.cap, dx, dd);
+  SimState s0;
+  memset(&s0, 0, sizeof(s0));
+  s0.n = n;
+  for (int a = 0; a < 3; ++a) { s0.bmin[a] = ~0ull; s0.bmax[a] = 0ull; }
+  cudaMemcpyAsync(&c->D.ss[sim], &s0, sizeof(SimState), cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (tmp) dfree(c, tmp);
+  if (e != cudaSuccess) return cuda_fail(c, e, "uploading agents");
+  c->n_set[sim] = n;
+  // region order for the device loops
+  std::vector<int32_t> order;
+  for (int s = 0; s < c->n_sims; ++s)
+    if (c->h_sc[s].base >= 0) order.push_back(s);
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return c->h_sc[a].base < c->h_sc[b].base; });
+  while ((int)order.size() < c->n_sims) order.push_back(-1);
+  cudaMemcpyAsync(c->D.order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, c->stream);
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "uploading agents");
+  return BDM_OK;
+}
+
+int bdm_step(bdm_ctx *c, int32_t n_iterations) {
+  if (!c) return BDM_E_INVAL;
+  if (n_iterations < 0) return fail(c, BDM_E_INVAL, "n_iterations < 0");
+  for (int s = 0; s < c->n_sims; ++s)
+    if (c->n_set[s] < 0) return fail(c, BDM_E_STATE, "simulation " + std::to_string(s) + " has no agents set");
+  int done = 0;
+  while (done < n_iterations) {
+    int chunk = std::min(n_iterations - done, 256);
+    bool resized = false;
+    int rc = ensure_table(c, chunk, &resized);
+    if (rc) return rc;
+    if (resized) c->graph_dirty = true;
+    if (c->profiling) {
+      for (int i = 0; i < chunk; ++i) launch_iteration(c);
+    } else {
+      if (c->graph_dirty || !c->gexec) {
+        if (c->gexec) {
+          cudaGraphExecDestroy(c->gexec);
+          c->gexec = nullptr;
+        }
+        cudaGraph_t g;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(c, e, "beginning graph capture");
+        launch_iteration(c);
+        e = cudaStreamEndCapture(c->stream, &g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "capturing the iteration graph");
+        e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "instantiating the iteration graph");
+        c->graph_dirty = false;
+      }
+      for (int i = 0; i < chunk; ++i) {
+        cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "launching the iteration graph");
+      }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "launching an iteration");
+    done += chunk;
+  }
+  return BDM_OK;
+}
+
+int bdm_sync(bdm_ctx *c) {
+  if (!c) return BDM_E_INVAL;
+  return latched_error(c);
+}
+
+int bdm_get_agents(bdm_ctx *c, int32_t sim, int64_t cap, double *xyz, double *diameter, int64_t *n_out,
+                   int32_t flags) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  rc = latched_error(c);
+  if (rc) return rc;
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  if (n_out) *n_out = s.n;
+  if (s.n > cap) return fail(c, BDM_E_CAPACITY, "cap below the agent count");
+  if (s.n == 0) return BDM_OK;
+  bool dev = (flags & BDM_DEVICE_PTRS) != 0;
+  double *bx = xyz, *bd = diameter, *tmp = nullptr;
+  if (!dev) {
+    rc = dalloc(c, &tmp, (size_t)(4 * s.n), "download buffer");
+    if (rc) return rc;
+    bx = xyz ? tmp : nullptr;
+    bd = diameter ? tmp + 3 * s.n : nullptr;
+  }
+  launch_gather_agents(c->D, c->stream, sim, c->h_sc[sim].base, s.n, bx, bd);
+  if (!dev) {
+    if (xyz) cudaMemcpyAsync(xyz, tmp, sizeof(double) * 3 * s.n, cudaMemcpyDeviceToHost, c->stream);
+    if (diameter) cudaMemcpyAsync(diameter, tmp + 3 * s.n, sizeof(double) * s.n, cudaMemcpyDeviceToHost, c->stream);
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (tmp) dfree(c, tmp);
+  if (e != cudaSuccess) return cuda_fail(c, e, "downloading agents");
+  return BDM_OK;
+}
+
+int bdm_get_grid(bdm_ctx *c, int32_t sim, int64_t cap, int64_t *box_id, double origin_len[4], int64_t dims[3]) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  rc = latched_error(c);
+  if (rc) return rc;
+  if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
+  rc = query_grid(c, false, nullptr);
+  if (rc) return rc;
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  if (origin_len) { origin_len[0] = s.o[0]; origin_len[1] = s.o[1]; origin_len[2] = s.o[2]; origin_len[3] = s.L; }
+  if (dims) { dims[0] = s.dims[0]; dims[1] = s.dims[1]; dims[2] = s.dims[2]; }
+  if (s.n > cap && box_id) return fail(c, BDM_E_CAPACITY, "cap below the agent count");
+  if (box_id && s.n > 0) {
+    int64_t *tmp = nullptr;
+    rc = dalloc(c, &tmp, (size_t)s.n, "box id buffer");
+    if (rc) return rc;
+    launch_boxids(c->D, c->stream, sim, tmp);
+    cudaMemcpyAsync(box_id, tmp, sizeof(int64_t) * s.n, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    dfree(c, tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "box ids");
+  }
+  return latched_error(c);
+}
+
+int bdm_neighbors(bdm_ctx *c, int32_t sim, double radius, int64_t cap, int64_t *pairs, int64_t *n_out) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  rc = latched_error(c);
+  if (rc) return rc;
+  if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
+  if (!std::isfinite(radius)) return fail(c, BDM_E_INVAL, "radius must be finite");
+  size_t M = (size_t)c->max_total;
+  if (!c->D.q.r64) {
+    int r2 = BDM_OK;
+    if (!r2) r2 = dalloc(c, &c->D.q.slot, M, "query slots");
+    if (!r2) r2 = dalloc(c, &c->D.q.sim, M, "query sims");
+    if (!r2) r2 = dalloc(c, &c->D.q.pkey, M, "query keys");
+    if (!r2) r2 = dalloc(c, &c->D.q.r64, M, "query records");
+    if (r2) return r2;
+    c->graph_dirty = true;
+  }
+  // Box length for the query: the step's, or the radius when larger.
+  SimState s;
+  rc = query_grid(c, false, nullptr);
+  if (rc) return rc;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  std::vector<double> boxes(c->n_sims);
+  for (int k = 0; k < c->n_sims; ++k) boxes[k] = c->h_sc[k].box_length;
+  if (radius >= 0 && radius > s.L) boxes[sim] = radius;
+  rc = query_grid(c, true, &boxes);
+  if (rc) return rc;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  int64_t n = s.n;
+  int64_t *counts = nullptr, *offsets = nullptr;
+  rc = dalloc(c, &counts, (size_t)(n + 1), "pair counts");
+  if (rc) return rc;
+  rc = dalloc(c, &offsets, (size_t)(n + 1024 + 2), "pair offsets");
+  if (rc) { dfree(c, counts); return rc; }
+  cudaError_t e = cudaSuccess;
+  int64_t total = launch_pairs(c->D, c->stream, sim, s.cell_base, n, radius, counts, offsets, nullptr, 0,
+                               c->d_partial, &e);
+  if (e != cudaSuccess) {
+    dfree(c, counts); dfree(c, offsets);
+    return cuda_fail(c, e, "counting pairs");
+  }
+  if (n_out) *n_out = total;
+  if (total > cap) {
+    dfree(c, counts); dfree(c, offsets);
+    return fail(c, BDM_E_CAPACITY, "cap below the pair count");
+  }
+  if (total > 0) {
+    int64_t *dp = nullptr;
+    rc = dalloc(c, &dp, (size_t)(2 * total), "pairs");
+    if (rc) { dfree(c, counts); dfree(c, offsets); return rc; }
+    launch_pairs(c->D, c->stream, sim, s.cell_base, n, radius, counts, offsets, dp, total, c->d_partial, &e);
+    cudaMemcpyAsync(pairs, dp, sizeof(int64_t) * 2 * total, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    dfree(c, dp);
+    if (e == cudaSuccess) e = e2;
+  }
+  dfree(c, counts);
+  dfree(c, offsets);
+  if (e != cudaSuccess) return cuda_fail(c, e, "writing pairs");
+  return latched_error(c);
+}
+
+int bdm_get_forces(bdm_ctx *c, int32_t sim, int64_t cap, double *force, int32_t *nnz, uint8_t *is_static,
+                   int64_t *n_out) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  rc = latched_error(c);
+  if (rc) return rc;
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  if (n_out) *n_out = s.n;
+  if (s.n > cap) return fail(c, BDM_E_CAPACITY, "cap below the agent count");
+  if (s.n == 0) return BDM_OK;
+  // cells of the last iteration: [cell_base, cell_base + ncell)
+  int64_t n = s.n;
+  double *df = nullptr;
+  int32_t *dn = nullptr;
+  uint8_t *ds = nullptr;
+  rc = dalloc(c, &df, (size_t)(3 * n), "force buffer");
+  if (!rc) rc = dalloc(c, &dn, (size_t)n, "nnz buffer");
+  if (!rc) rc = dalloc(c, &ds, (size_t)n, "static buffer");
+  if (rc) { dfree(c, df); dfree(c, dn); dfree(c, ds); return rc; }
+  cudaMemsetAsync(df, 0, sizeof(double) * 3 * n, c->stream);
+  cudaMemsetAsync(dn, 0, sizeof(int32_t) * n, c->stream);
+  cudaMemsetAsync(ds, 0, n, c->stream);
+  if (s.t > 0) launch_gather_forces(c->D, c->stream, sim, s.cell_base, std::min(s.ncell, n), df, dn, ds);
+  if (force) cudaMemcpyAsync(force, df, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream);
+  if (nnz) cudaMemcpyAsync(nnz, dn, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream);
+  if (is_static) cudaMemcpyAsync(is_static, ds, n, cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  dfree(c, df); dfree(c, dn); dfree(c, ds);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reading forces");
+  return BDM_OK;
+}
+
+int bdm_get_storage_order(bdm_ctx *c, int32_t sim, int64_t cap, int64_t *ids, int64_t *n_out) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  if (n_out) *n_out = s.n;
+  if (s.n > cap) return fail(c, BDM_E_CAPACITY, "cap below the agent count");
+  if (s.n == 0 || !ids) return BDM_OK;
+  std::vector<int32_t> tmp(s.n);
+  cudaMemcpyAsync(tmp.data(), c->D.a.id + c->h_sc[sim].base, sizeof(int32_t) * s.n, cudaMemcpyDeviceToHost,
+                  c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reading storage order");
+  for (int64_t i = 0; i < s.n; ++i) ids[i] = tmp[i];
+  return BDM_OK;
+}
+
+int bdm_get_stats(bdm_ctx *c, int32_t sim, bdm_stats *out) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  if (!out) return fail(c, BDM_E_INVAL, "out is NULL");
+  rc = latched_error(c);
+  if (rc) return rc;
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  memset(out, 0, sizeof(*out));
+  out->agents = s.n;
+  out->iterations = s.t;
+  for (int a = 0; a < 3; ++a) { out->origin_len[a] = s.o[a]; out->dims[a] = s.dims[a]; }
+  out->origin_len[3] = s.L;
+  if (s.t > 0 && s.n > 0) {
+    unsigned long long *cnt = nullptr;
+    rc = dalloc(c, &cnt, 2, "stat counters");
+    if (rc) return rc;
+    cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), c->stream);
+    launch_count_flags(c->D, c->stream, sim, s.cell_base, s.ncell, cnt);
+    unsigned long long h[2] = {0, 0};
+    cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    dfree(c, cnt);
+    if (e != cudaSuccess) return cuda_fail(c, e, "counting flags");
+    out->static_agents = (int64_t)h[0];
+    out->moved_agents = (int64_t)h[1];
+  }
+  return BDM_OK;
+}
+
+int bdm_profile(bdm_ctx *c, int32_t enable) {
+  if (!c) return BDM_E_INVAL;
+  cudaStreamSynchronize(c->stream);
+  harvest_events(c);
+  c->profiling = enable != 0;
+  for (int k = 0; k < kStages; ++k) { c->prof_launches[k] = 0; c->prof_ms[k] = 0.0; }
+  return BDM_OK;
+}
+
+int bdm_get_profile(bdm_ctx *c, int64_t launches[BDM_NUM_STAGES], double ms[BDM_NUM_STAGES],
+                    const char *names[BDM_NUM_STAGES]) {
+  if (!c) return BDM_E_INVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronizing");
+  harvest_events(c);
+  for (int k = 0; k < kStages; ++k) {
+    if (launches) launches[k] = c->prof_launches[k];
+    if (ms) ms[k] = c->prof_ms[k];
+    if (names) names[k] = kStageNames[k];
+  }
+  return BDM_OK;
+}
+
+void bdm_destroy(bdm_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto &e : c->evs) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (void *p : c->allocs) cudaFree(p);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char *bdm_last_error(const bdm_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

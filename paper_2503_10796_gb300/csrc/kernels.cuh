@@ -1,0 +1,42 @@
+// Host-side launchers of the device stages (one translation unit each).
+#pragma once
+
+#include "common.cuh"
+
+namespace bdm {
+
+// grid.cu
+void launch_bbox(const DevCtx &C, cudaStream_t st);
+void launch_params(const DevCtx &C, cudaStream_t st, int step);
+void launch_count(const DevCtx &C, cudaStream_t st, int step);
+void launch_scan(const DevCtx &C, cudaStream_t st, uint32_t *partial);
+void launch_place(const DevCtx &C, cudaStream_t st, int step);
+
+// force.cu
+void launch_force(const DevCtx &C, cudaStream_t st);
+void launch_displace(const DevCtx &C, cudaStream_t st);
+
+// query.cu
+void launch_boxids(const DevCtx &C, cudaStream_t st, int sim, int64_t *out_by_id);
+int64_t launch_pairs(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, double radius,
+                     int64_t *counts, int64_t *offsets, int64_t *pairs_dev, int64_t cap, uint32_t *partial,
+                     cudaError_t *err);
+void launch_gather_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, double *xyz,
+                          double *diam);
+void launch_gather_forces(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, double *force,
+                          int32_t *nnz, uint8_t *stat);
+void launch_count_flags(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n,
+                        unsigned long long *counts2);
+void launch_set_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, int64_t cap,
+                       const double *xyz, const double *diam);
+void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, uint32_t *bad);
+
+// sort.cu
+void launch_morton(const DevCtx &C, cudaStream_t st, void *scratch, size_t scratch_bytes, int key_bits);
+size_t morton_scratch_bytes(int64_t total_slots);
+
+// growth.cu
+void launch_growth(const DevCtx &C, cudaStream_t st, void *scratch, size_t scratch_bytes);
+size_t growth_scratch_bytes(int64_t total_slots, int n_sims);
+
+}  // namespace bdm

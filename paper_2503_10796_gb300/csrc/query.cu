@@ -1,0 +1,321 @@
+// Queries and transfers: box index per agent (parity hook of S1), neighbor
+// pairs (§4.4.3 ForEachNeighbor: radius query or overlap query, decided in
+// FP64 exactly as defined), gathers by caller ID, and agent upload.
+#include "kernels.cuh"
+
+namespace bdm {
+
+static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
+
+// Box index per caller ID, computed as S1 computes it (no table needed).
+__global__ void k_boxids(DevCtx C, int sim, int64_t *out) {
+  const SimConst &sc = C.sc[sim];
+  const SimState &s = C.ss[sim];
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  int64_t slot = sc.base + i;
+  int64_t id = C.a.id[slot];
+  if (!s.valid) {
+    out[id] = -1;
+    return;
+  }
+  double p[3] = {C.a.x[slot], C.a.y[slot], C.a.z[slot]};
+  int64_t c[3];
+  for (int a = 0; a < 3; ++a) {
+    double av = __dsub_rn(p[a], s.o[a]);
+    float ah, al;
+    split_ff(av, ah, al);
+    int64_t ca = box_coord(av, ah, al, s.ilh, s.ill, s.L);
+    c[a] = ca < 0 ? 0 : (ca >= s.dims[a] ? s.dims[a] - 1 : ca);
+  }
+  out[id] = linear_box(s, c[0], c[1], c[2]);
+}
+
+void launch_boxids(const DevCtx &C, cudaStream_t st, int sim, int64_t *out_by_id) {
+  int64_t n = C.total_slots;
+  k_boxids<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, sim, out_by_id);
+}
+
+// ---------------------------------------------------------------------------
+// Neighbor pairs over the query cells (FP64 records).  Every agent i counts
+// (then writes) the j with ID above its own that satisfy the predicate;
+// offsets come from an exclusive scan over IDs, and each agent sorts its own
+// short list, so the output is ordered by (i, j).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool pair_hit(double4_32a a, double4_32a b, double R2, bool radius_mode) {
+  double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y), dz = __dsub_rn(a.z, b.z);
+  double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  if (radius_mode) return s < R2;
+  return __dsub_rn(__dadd_rn(a.w, b.w), __dsqrt_rn(s)) > 0.0;
+}
+
+template <bool kWrite>
+__global__ void k_pairs(DevCtx C, int sim, int64_t cell_base, int64_t n, double R2, int radius_mode,
+                        int64_t *counts, const int64_t *offsets, int64_t *pairs, int64_t cap) {
+  int64_t p = cell_base + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= cell_base + n) return;
+  const SimConst &sc = C.sc[sim];
+  const SimState &s = C.ss[sim];
+  const Cells &Q = C.q;
+  int64_t id = C.a.id[Q.slot[p]];
+  double4_32a o = Q.r64[p];
+  int64_t cx, cy, cz;
+  unpack_coords(Q.pkey[p], cx, cy, cz);
+  uint32_t stamp = C.g->stamp;
+  int64_t cnt = 0;
+  int64_t off = kWrite ? offsets[id] : 0;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int64_t z = cz + dz;
+    if (z < 0 || z >= s.dims[2]) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int64_t y = cy + dy;
+      if (y < 0 || y >= s.dims[1]) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        int64_t x = cx + dx;
+        if (x < 0 || x >= s.dims[0]) continue;
+        int64_t idx = sc.table_base + linear_box(s, x, y, z);
+        unsigned long long e = C.tab.cnt[idx];
+        if ((uint32_t)(e >> 32) != stamp) continue;
+        uint32_t c = (uint32_t)(e & 0x7FFFFFFFull);
+        int64_t start = C.tab.start[idx];
+        for (int64_t j = start; j < start + c; ++j) {
+          int64_t jd = C.a.id[Q.slot[j]];
+          if (jd <= id) continue;
+          if (!pair_hit(o, Q.r64[j], R2, radius_mode != 0)) continue;
+          if (kWrite) {
+            int64_t k = off + cnt;
+            if (k < cap) {
+              // insertion into this agent's sorted run
+              int64_t m = k;
+              while (m > off && pairs[2 * (m - 1) + 1] > jd) {
+                pairs[2 * m] = pairs[2 * (m - 1)];
+                pairs[2 * m + 1] = pairs[2 * (m - 1) + 1];
+                --m;
+              }
+              pairs[2 * m] = id;
+              pairs[2 * m + 1] = jd;
+            }
+          }
+          ++cnt;
+        }
+      }
+    }
+  }
+  if (!kWrite) counts[id] = cnt;
+}
+
+// Exclusive scan of n int64 values in place; returns the total through
+// *total_dev (device).
+__global__ void __launch_bounds__(1024) k_scan64_up(const int64_t *v, int64_t n, int64_t chunk, int64_t *part) {
+  __shared__ long long sh[32];
+  int64_t b = (int64_t)blockIdx.x * chunk, e = b + chunk < n ? b + chunk : n;
+  long long s = 0;
+  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) s += v[i];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_scan64_top(int64_t *part, int G, int64_t *total) {
+  if (threadIdx.x != 0) return;
+  int64_t run = 0;
+  for (int g = 0; g < G; ++g) {
+    int64_t v = part[g];
+    part[g] = run;
+    run += v;
+  }
+  *total = run;
+}
+
+__global__ void __launch_bounds__(1024) k_scan64_down(int64_t *v, int64_t n, int64_t chunk, const int64_t *part) {
+  __shared__ long long sh[33];
+  int64_t b = (int64_t)blockIdx.x * chunk, e = b + chunk < n ? b + chunk : n;
+  long long base = part[blockIdx.x];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t t0 = b; t0 < e; t0 += blockDim.x) {
+    int64_t i = t0 + threadIdx.x;
+    long long x = i < e ? v[i] : 0, inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long run = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        long long t = sh[w];
+        sh[w] = run;
+        run += t;
+      }
+      sh[32] = run;
+    }
+    __syncthreads();
+    if (i < e) v[i] = base + sh[warp] + inc - x;
+    base += sh[32];
+    __syncthreads();
+  }
+}
+
+int64_t launch_pairs(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, double radius,
+                     int64_t *counts, int64_t *offsets, int64_t *pairs_dev, int64_t cap, uint32_t *partial,
+                     cudaError_t *err) {
+  (void)partial;
+  bool rmode = radius >= 0.0;
+  double R2 = radius * radius;
+  unsigned int nb = blocks_for(n > 0 ? n : 1, kThreads);
+  if (pairs_dev == nullptr) {
+    k_pairs<false><<<nb, kThreads, 0, st>>>(C, sim, cell_base, n, R2, rmode, counts, nullptr, nullptr, 0);
+    // exclusive scan counts -> offsets (offsets also holds the part sums
+    // after n entries: offsets has n + 1024 + 1 slots)
+    cudaMemcpyAsync(offsets, counts, sizeof(int64_t) * (size_t)(n > 0 ? n : 1), cudaMemcpyDeviceToDevice, st);
+    int64_t G = (n + 4095) / 4096;
+    if (G > 1024) G = 1024;
+    if (G < 1) G = 1;
+    int64_t chunk = (n + G - 1) / G;
+    chunk = (chunk + 1023) / 1024 * 1024;
+    if (chunk < 1024) chunk = 1024;
+    G = (n + chunk - 1) / chunk;
+    if (G < 1) G = 1;
+    int64_t *part = offsets + n;
+    int64_t *total = part + 1024;
+    k_scan64_up<<<(unsigned int)G, 1024, 0, st>>>(offsets, n, chunk, part);
+    k_scan64_top<<<1, 32, 0, st>>>(part, (int)G, total);
+    k_scan64_down<<<(unsigned int)G, 1024, 0, st>>>(offsets, n, chunk, part);
+    int64_t h_total = 0;
+    cudaMemcpyAsync(&h_total, total, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    *err = cudaStreamSynchronize(st);
+    return h_total;
+  }
+  k_pairs<true><<<nb, kThreads, 0, st>>>(C, sim, cell_base, n, R2, rmode, counts, offsets, pairs_dev, cap);
+  *err = cudaGetLastError();
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Gathers by caller ID and uploads.
+// ---------------------------------------------------------------------------
+__global__ void k_gather_agents(DevCtx C, int64_t base, int64_t n, double *xyz, double *diam) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t slot = base + i;
+  int64_t id = C.a.id[slot];
+  if (xyz) {
+    xyz[3 * id] = C.a.x[slot];
+    xyz[3 * id + 1] = C.a.y[slot];
+    xyz[3 * id + 2] = C.a.z[slot];
+  }
+  if (diam) diam[id] = C.a.d[slot];
+}
+
+void launch_gather_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, double *xyz,
+                          double *diam) {
+  (void)sim;
+  if (n <= 0) return;
+  k_gather_agents<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, xyz, diam);
+}
+
+__global__ void k_gather_forces(DevCtx C, int sim, int64_t cell_base, int64_t n, double *force, int32_t *nnz,
+                                uint8_t *stat) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t p = cell_base + i;
+  if (C.c.sim[p] != sim) return;
+  int64_t id = C.a.id[C.c.slot[p]];
+  bool st = C.c.stat[p] != 0;
+  double f[3] = {0.0, 0.0, 0.0};
+  if (!st) {
+    if (C.sc[sim].precision == BDM_PREC_FP64) {
+      double4_32a F = C.c.f64[p];
+      f[0] = F.x; f[1] = F.y; f[2] = F.z;
+    } else {
+      float4 F = C.c.f32[p];
+      f[0] = F.x; f[1] = F.y; f[2] = F.z;
+    }
+  }
+  if (force) {
+    force[3 * id] = f[0];
+    force[3 * id + 1] = f[1];
+    force[3 * id + 2] = f[2];
+  }
+  if (nnz) nnz[id] = st ? (int32_t)C.a.nnz[C.c.slot[p]] : (int32_t)C.c.nnz[p];
+  if (stat) stat[id] = st ? 1 : 0;
+}
+
+void launch_gather_forces(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, double *force,
+                          int32_t *nnz, uint8_t *stat) {
+  if (n <= 0) return;
+  k_gather_forces<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, sim, cell_base, n, force, nnz, stat);
+}
+
+__global__ void k_count_flags(DevCtx C, int sim, int64_t cell_base, int64_t n, unsigned long long *counts2) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned int st = 0, mv = 0;
+  if (i < n) {
+    int64_t p = cell_base + i;
+    if (C.c.sim[p] == sim) {
+      st = C.c.stat[p] ? 1u : 0u;
+      mv = (!st && (C.a.flags[C.c.slot[p]] & FLAG_CHANGED)) ? 1u : 0u;
+    }
+  }
+  unsigned int a = __reduce_add_sync(0xffffffffu, st), b = __reduce_add_sync(0xffffffffu, mv);
+  if ((threadIdx.x & 31) == 0) {
+    if (a) atomicAdd(&counts2[0], (unsigned long long)a);
+    if (b) atomicAdd(&counts2[1], (unsigned long long)b);
+  }
+}
+
+void launch_count_flags(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n,
+                        unsigned long long *counts2) {
+  if (n <= 0) return;
+  k_count_flags<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, sim, cell_base, n, counts2);
+}
+
+// Upload: xyz is n x 3 row-major (device memory), diam n values.
+__global__ void k_set_agents(DevCtx C, int sim, int64_t base, int64_t n, int64_t cap, const double *xyz,
+                             const double *diam) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap) return;
+  int64_t slot = base + i;
+  C.a.sim[slot] = sim;
+  if (i >= n) return;
+  C.a.x[slot] = xyz[3 * i];
+  C.a.y[slot] = xyz[3 * i + 1];
+  C.a.z[slot] = xyz[3 * i + 2];
+  double d = diam[i];
+  C.a.d[slot] = d;
+  // volume of a sphere of diameter d: (pi * ((d * d) * d)) / 6
+  C.a.v[slot] = __ddiv_rn(__dmul_rn(3.141592653589793, __dmul_rn(__dmul_rn(d, d), d)), 6.0);
+  C.a.id[slot] = (int32_t)i;
+  C.a.flags[slot] = FLAG_CHANGED;
+  C.a.nnz[slot] = 0;
+  C.a.pkey[slot] = 0;
+  C.a.pkey_hist[slot] = 0;
+  C.a.rank[slot] = 0;
+}
+
+void launch_set_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, int64_t cap,
+                       const double *xyz, const double *diam) {
+  if (cap <= 0) return;
+  k_set_agents<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, sim, base, n, cap, xyz, diam);
+}
+
+__global__ void k_check_input(int64_t n, const double *xyz, const double *diam, uint32_t *bad) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool ok = isfinite(xyz[3 * i]) && isfinite(xyz[3 * i + 1]) && isfinite(xyz[3 * i + 2]) && diam[i] > 0.0 &&
+            isfinite(diam[i]);
+  if (!ok) atomicOr(bad, 1u);
+}
+
+void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, uint32_t *bad) {
+  if (n <= 0) return;
+  k_check_input<<<blocks_for(n, kThreads), kThreads, 0, st>>>(n, xyz, diam, bad);
+}
+
+}  // namespace bdm

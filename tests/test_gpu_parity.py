@@ -1,0 +1,234 @@
+"""Parity of the sm_103a library (through the C ABI) with the CPU oracle.
+
+Bit-exact: box indices, grid origin/length/dims, neighbor pair sets, nnz in
+the FP64 path.  Forces: |F_gpu - F_oracle| / s_i <= 1e-12 (FP64 path) or
+1e-5 (FP32-force path) with s_i = sum_j (k delta + gamma sqrt(r delta)), the
+magnitude sum of agent i's pair forces.
+"""
+import numpy as np
+import pytest
+
+from paper_2503_10796_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+def ctx_for(pop_or_list, max_total=None, **kw):
+    from paper_2503_10796_gb300 import binding
+    pops = pop_or_list if isinstance(pop_or_list, list) else [pop_or_list]
+    params = [binding.make_params(p.params, **kw) for p in pops]
+    total = max_total or sum(max(p.n, p.params.capacity) for p in pops) + 16
+    ctx = binding.Context(params, total)
+    for s, p in enumerate(pops):
+        ctx.set_agents(s, p.xyz, p.diameter)
+    return ctx
+
+
+def orc_for(pop, **kw):
+    import oracle
+    return oracle.Sim(pop.xyz, pop.diameter, pop.params, **kw)
+
+
+def small_pops():
+    return [
+        workloads.plain_fp64(),                                                  # 4096, full size
+        workloads.Population(*workloads.uniform_cube(1025, 90.0, seed=3)),       # ragged tail
+        workloads.clustered(n_clusters=5, per_cluster=700, side=600.0, sigma=25.0, seed=2),
+        workloads.Population(*workloads.uniform_cube(3, 12.0, seed=1)),
+    ]
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_grid_bit_exact(orc, k):
+    pop = small_pops()[k]
+    ctx = ctx_for(pop)
+    box, ol, dims = ctx.grid(0)
+    obox, ool, odims = orc_for(pop).grid()
+    assert np.array_equal(ol, ool)
+    assert np.array_equal(dims, odims)
+    assert np.array_equal(box, obox)
+
+
+def test_grid_boundary_cases(orc):
+    """Centers exactly on box boundaries, and one ulp on either side."""
+    L = 10.0
+    base = np.array([[0.0, 0, 0], [40.0, 40, 40]])
+    pts = [base]
+    for c in (10.0, 20.0, 30.0):
+        for v in (c, np.nextafter(c, 0), np.nextafter(c, 100)):
+            pts.append(np.array([[v, 5.0, 5.0], [5.0, v, 5.0], [5.0, 5.0, v]]))
+    xyz = np.concatenate(pts)
+    pop = workloads.Population(xyz, np.full(len(xyz), 1.0), workloads.SimParams(box_length=L))
+    ctx = ctx_for(pop)
+    box, ol, dims = ctx.grid(0)
+    obox, ool, odims = orc_for(pop).grid()
+    assert np.array_equal(box, obox) and np.array_equal(dims, odims)
+
+
+@pytest.mark.parametrize("k", range(3))
+@pytest.mark.parametrize("radius", [-1.0, 6.0, 25.0])
+def test_neighbor_pairs_bit_exact(orc, k, radius):
+    pop = small_pops()[k]
+    ctx = ctx_for(pop)
+    got = ctx.neighbors(0, radius)
+    want = orc_for(pop).neighbors(radius)
+    assert got.shape == want.shape
+    assert np.array_equal(got, want)
+
+
+def check_forces(pop, precision, orc_sim=None):
+    ctx = ctx_for(pop, precision=precision)
+    o = orc_sim or orc_for(pop)
+    F0, nnz0, smag = o.forces()
+    ctx.step(1)
+    ctx.sync()
+    F, nnz, st = ctx.forces(0)
+    assert not st.any()
+    scale = np.maximum(smag, 1e-300)
+    err = np.linalg.norm(F - F0, axis=1) / scale
+    err[smag == 0] = np.linalg.norm(F[smag == 0], axis=1)
+    assert err.max() <= TOL[precision], (err.max(), np.argmax(err))
+    if precision == 0:
+        assert np.array_equal(nnz, nnz0)
+    else:
+        assert np.mean(nnz == nnz0) > 0.999
+    return ctx, o, err
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("k", range(4))
+def test_one_step_forces_and_positions(orc, precision, k):
+    pop = small_pops()[k]
+    ctx, o, err = check_forces(pop, precision)
+    o.step(1)
+    x_o, _, _ = o.get()
+    x_g, d_g = ctx.get_agents(0)
+    assert np.array_equal(d_g, pop.diameter)
+    F0, D0, _, _, _ = o.last()
+    # agents whose |F| sits within the tolerance of the adherence threshold
+    # may take the other side of the decision
+    _, _, smag = orc_for(pop).forces()
+    fn = np.linalg.norm(F0, axis=1)
+    flip = np.abs(fn - pop.params.adherence) <= 4 * TOL[precision] * np.maximum(smag, 1e-300)
+    dx = np.abs(x_g - x_o).max(axis=1)
+    bound = pop.params.dt * (4 * TOL[precision] * smag) + 4 * np.spacing(np.abs(x_o).max(axis=1))
+    bad = (dx > bound) & ~flip
+    assert not bad.any(), (dx[bad][:5], bound[bad][:5])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multi_step_trajectory(orc, precision):
+    """10 iterations of the plain workload: position error against the oracle."""
+    pop = workloads.plain_fp64()
+    ctx = ctx_for(pop, precision=precision)
+    o = orc_for(pop)
+    ctx.step(10)
+    o.step(10)
+    x_g, _ = ctx.get_agents(0)
+    x_o, _, _ = o.get()
+    err = np.abs(x_g - x_o).max()
+    L = pop.diameter.max()
+    if precision == 0:
+        assert err <= 1e-9 * L, err
+    else:
+        assert err <= 1e-4 * L, err
+
+
+def test_two_sphere_closed_form_on_gpu(orc):
+    for precision in (0, 1):
+        pop = workloads.Population(np.array([[0.0, 0, 0], [8.0, 0, 0]]), np.array([10.0, 10.0]))
+        ctx = ctx_for(pop, precision=precision)
+        ctx.step(1)
+        F, nnz, _ = ctx.forces(0)
+        want = 4.0 - np.sqrt(5.0)
+        assert F[0, 0] == pytest.approx(-want, rel=TOL[precision])
+        assert nnz.tolist() == [1, 1]
+
+
+def test_tiny_overlaps_keep_relative_accuracy(orc):
+    """Pairs whose overlap is 1e-3 .. 1e-9 of the radius: the FP32 path must
+    still meet its relative tolerance (the sqrt(r delta) term dominates)."""
+    rng = np.random.default_rng(0)
+    rows, diam = [], []
+    for k, depth in enumerate(10.0 ** -rng.uniform(1, 9, 200)):
+        c = np.array([k * 40.0, 0.0, 0.0])
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        d1, d2 = rng.uniform(8, 12, 2)
+        rows += [c, c + u * ((d1 + d2) / 2 - depth)]
+        diam += [d1, d2]
+    pop = workloads.Population(np.array(rows), np.array(diam))
+    check_forces(pop, 1)
+    check_forces(pop, 0)
+
+
+def test_empty_and_single(orc):
+    from paper_2503_10796_gb300 import binding
+    ctx = binding.Context([binding.make_params(), binding.make_params()], 8)
+    ctx.set_agents(0, np.zeros((0, 3)), np.zeros(0))
+    ctx.set_agents(1, np.array([[1.0, 2.0, 3.0]]), np.array([10.0]))
+    ctx.step(3)
+    ctx.sync()
+    x, d = ctx.get_agents(0)
+    assert x.shape == (0, 3)
+    x, d = ctx.get_agents(1)
+    assert x.tolist() == [[1.0, 2.0, 3.0]]
+    assert ctx.neighbors(1, -1.0).shape == (0, 2)
+
+
+def test_invalid_input_is_rejected(orc):
+    from paper_2503_10796_gb300 import binding
+    ctx = binding.Context(binding.make_params(), 8)
+    with pytest.raises(binding.BdmError) as e:
+        ctx.set_agents(0, np.array([[np.nan, 0, 0]]), np.array([1.0]))
+    assert e.value.code == -1
+    with pytest.raises(binding.BdmError) as e:
+        ctx.set_agents(0, np.array([[0.0, 0, 0]]), np.array([-1.0]))
+    assert e.value.code == -1
+    with pytest.raises(binding.BdmError) as e:
+        ctx.set_agents(0, np.zeros((9, 3)), np.ones(9))
+    assert e.value.code == -4
+    with pytest.raises(binding.BdmError) as e:
+        ctx.step(1)  # nothing set yet
+    assert e.value.code == -7
+
+
+def test_batched_simulations_match_single_ones(orc):
+    pops = workloads.batched_sweep(n_sims=6, lo=50, hi=3000, seed=4)
+    ctx = ctx_for(pops)
+    ctx.step(5)
+    for s, p in enumerate(pops):
+        single = ctx_for(p)
+        single.step(5)
+        a, _ = ctx.get_agents(s)
+        b, _ = single.get_agents(0)
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-4)
+        o = orc_for(p)
+        o.step(5)
+        x_o, _, _ = o.get()
+        np.testing.assert_allclose(a, x_o, rtol=0, atol=1e-3)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_static_skip_matches_no_skip(orc, precision):
+    from tests.test_oracle_pins import perturbed_scene
+    xyz, d = perturbed_scene()
+    pop = workloads.Population(xyz, d, workloads.SimParams(dt=0.05, precision=precision))
+    on = ctx_for(pop, detect_static=1)
+    off = ctx_for(pop, detect_static=0)
+    o = orc_for(pop, detect_static=1)
+    n_static = 0
+    for _ in range(15):
+        on.step(1); off.step(1); o.step(1)
+        _, _, st = on.forces(0)
+        n_static += int(st.sum())
+    a, _ = on.get_agents(0)
+    b, _ = off.get_agents(0)
+    c, _, _ = o.get()
+    tol = 1e-12 if precision == 0 else 1e-5
+    np.testing.assert_allclose(a, b, rtol=0, atol=tol * 100)
+    np.testing.assert_allclose(a, c, rtol=0, atol=tol * 100)
+    assert n_static > 0
+    assert on.stats(0)["static_agents"] >= 0
