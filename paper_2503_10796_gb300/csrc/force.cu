@@ -9,9 +9,10 @@
 // the float-float refinement only ever see magnitudes below 2L.  Pairs
 // deeper than kFastDelta use the plain FP32 overlap; shallower pairs
 // recompute the overlap as (R^2 - s) / (R + dist) in float-float, which
-// keeps its relative accuracy when delta -> 0.  Only when that numerator is
-// within 2^-26 of zero is the FP64 expression of the definition evaluated
-// to decide the sign exactly.
+// keeps its relative accuracy as delta shrinks.  The float-float numerator
+// carries an absolute error near 1e-12, so when it is within 2^-19 of zero
+// (delta below about 1e-7, a rare pair) the FP64 expression of the
+// definition gives the sign and size of delta instead.
 //
 // FP64 path.  The definition, operation by operation, with IEEE FP64
 // intrinsics (no contraction): the pair set and the per-pair forces equal
@@ -21,7 +22,7 @@
 namespace bdm {
 
 constexpr float kFastDelta = 2.0f;
-constexpr float kTinyNum = 0x1p-26f;
+constexpr float kTinyNum = 0x1p-19f;
 
 __device__ __forceinline__ void ff_diff(float hi_i, float lo_i, float hi_j, float lo_j, float off_h,
                                         float off_l, float &dh, float &dl) {
