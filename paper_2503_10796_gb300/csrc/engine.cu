@@ -48,6 +48,7 @@ struct bdm_ctx {
   int64_t table_entries = 0;
   void *d_sort = nullptr;
   size_t sort_bytes = 0;
+  int sort_key_bits = 0;     // simulation-rank bits + 3 x bits per box coordinate
   void *d_grow = nullptr;
   size_t grow_bytes = 0;
   std::vector<void *> allocs;
@@ -198,11 +199,6 @@ void harvest_events(bdm_ctx *c) {
 void launch_iteration(bdm_ctx *c) {
   const DevCtx &D = c->D;
   cudaStream_t st = c->stream;
-  if (c->any_sort) {
-    stage_begin(c, 7);
-    launch_morton(D, st, c->d_sort, c->sort_bytes, 63);
-    stage_end(c);
-  }
   stage_begin(c, 0);
   launch_bbox(D, st);
   launch_params(D, st, 1);
@@ -210,6 +206,12 @@ void launch_iteration(bdm_ctx *c) {
   stage_begin(c, 1);
   launch_count(D, st, 1);
   stage_end(c);
+  if (c->any_sort) {
+    // re-sort by the Morton code of the boxes just counted (when due)
+    stage_begin(c, 7);
+    launch_morton(D, st, c->d_sort, c->sort_bytes, c->sort_key_bits);
+    stage_end(c);
+  }
   stage_begin(c, 2);
   launch_scan(D, st, c->d_partial);
   stage_end(c);
@@ -248,6 +250,7 @@ int ensure_table(bdm_ctx *c, int iters, bool *resized) {
     return d;
   };
   int64_t total = 0;
+  double max_dims = 1.0;
   std::vector<int64_t> need(c->n_sims, 0);
   for (int s = 0; s < c->n_sims; ++s) {
     const SimConst &sc = c->h_sc[s];
@@ -270,6 +273,7 @@ int ensure_table(bdm_ctx *c, int iters, bool *resized) {
       if (dims >= (double)(1ll << kCoordBits))
         return fail(c, BDM_E_CAPACITY, "grid needs more than 2^21 boxes per axis");
       nb *= dims;
+      max_dims = std::max(max_dims, dims);
     }
     if (nb > 4.0e10) return fail(c, BDM_E_CAPACITY, "grid needs more than 4e10 boxes");
     need[s] = (int64_t)nb;
@@ -278,6 +282,16 @@ int ensure_table(bdm_ctx *c, int iters, bool *resized) {
   if (total < 1) total = 1;
   int64_t base = 0;
   bool changed = false;
+  {
+    int bpa = 1, sim_bits = 0;
+    while ((double)(1ll << bpa) < max_dims) ++bpa;
+    while ((1 << sim_bits) < c->n_sims) ++sim_bits;
+    int kb = sim_bits + 3 * bpa;
+    if (kb != c->sort_key_bits) {
+      c->sort_key_bits = kb;
+      *resized = true;
+    }
+  }
   for (int s = 0; s < c->n_sims; ++s) {
     SimConst &sc = c->h_sc[s];
     if (sc.table_base != base || sc.table_cap < need[s]) changed = true;
@@ -318,6 +332,7 @@ int ensure_table(bdm_ctx *c, int iters, bool *resized) {
   return BDM_OK;
 }
 
+
 int latched_error(bdm_ctx *c) {
   uint32_t bits = 0;
   cudaError_t e = cudaMemcpyAsync(&bits, &c->D.g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
@@ -351,6 +366,7 @@ int query_grid(bdm_ctx *c, bool with_cells, const std::vector<double> *boxes) {
   bool resized;
   int rc = ensure_table(c, 1, &resized);
   if (rc) return rc;
+  if (resized) c->graph_dirty = true;
   if (boxes) {
     // temporary box lengths for radius queries
     std::vector<SimConst> tmp = c->h_sc;

@@ -232,3 +232,46 @@ def test_static_skip_matches_no_skip(orc, precision):
     np.testing.assert_allclose(a, c, rtol=0, atol=tol * 100)
     assert n_static > 0
     assert on.stats(0)["static_agents"] >= 0
+
+
+def morton_codes(box, dims):
+    import oracle
+    nx, ny = int(dims[0]), int(dims[1])
+    return np.array([oracle.interleave(3, [b % nx, (b // nx) % ny, b // (nx * ny)]) for b in box], np.uint64)
+
+
+@pytest.mark.parametrize("n_sims", [1, 3])
+def test_morton_sort_orders_storage(orc, n_sims):
+    """With no movement (huge adherence) the grid after the step equals the
+    grid the re-sort used: storage must then be in Morton order of boxes,
+    ties in any order, and hold every agent once."""
+    pops = [workloads.clustered(n_clusters=3, per_cluster=900 + 37 * s, side=500.0, sigma=30.0, seed=s)
+            for s in range(n_sims)]
+    ctx = ctx_for(pops, adherence=1e9, sort_interval=1)
+    ctx.step(1)
+    for s, p in enumerate(pops):
+        order = ctx.storage_order(s)
+        assert np.array_equal(np.sort(order), np.arange(p.n))
+        box, ol, dims = ctx.grid(s)
+        codes = morton_codes(box, dims)
+        seq = codes[order]
+        assert np.all(seq[1:] >= seq[:-1])
+        o = orc_for(p)
+        want = codes[o.morton_agent_order()]
+        assert np.array_equal(seq, want)
+        x, _ = ctx.get_agents(s)
+        assert np.array_equal(x, p.xyz)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sorting_does_not_change_results(orc, precision):
+    pop = workloads.plain_fp64()
+    a = ctx_for(pop, precision=precision, sort_interval=3)
+    b = ctx_for(pop, precision=precision, sort_interval=0)
+    a.step(7)
+    b.step(7)
+    xa, _ = a.get_agents(0)
+    xb, _ = b.get_agents(0)
+    tol = 1e-9 if precision == 0 else 1e-4
+    np.testing.assert_allclose(xa, xb, rtol=0, atol=tol * pop.diameter.max())
+    assert not np.array_equal(a.storage_order(0), np.arange(pop.n))
