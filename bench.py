@@ -60,6 +60,12 @@ def make_workload(name: str, precision: int, static: int):
         pops = [W.clustered(precision=precision, detect_static=static, sort_interval=10)]
         desc = dict(workload="clustered_8M", agents=8388608, clusters=64, sigma=200.0, side=1.0e4,
                     diameters="U[8,12]", sort_interval=10)
+    elif name == "clustered_1M":
+        # profiling case: 8 clusters of the same shape in a 5,000 cube
+        pops = [W.clustered(n_clusters=8, side=5000.0, precision=precision, detect_static=static,
+                            sort_interval=10)]
+        desc = dict(workload="clustered_1M", agents=1048576, clusters=8, sigma=200.0, side=5.0e3,
+                    diameters="U[8,12]", sort_interval=10)
     elif name == "plain_fp64_4096":
         pops = [W.plain_fp64(precision=precision)]
         desc = dict(workload="plain_4096", agents=4096, side=160.0, diameters="U[8,12]")
