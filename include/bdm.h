@@ -170,6 +170,38 @@ int bdm_profile(bdm_ctx* ctx, int32_t enable);
 int bdm_get_profile(bdm_ctx* ctx, int64_t launches[BDM_NUM_STAGES], double ms[BDM_NUM_STAGES],
                     const char* names[BDM_NUM_STAGES]);
 
+/* Net force on each of n spheres, without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (code recorded inside a CUDA stream capture,
+ * allocator-free runtimes, programs that hand out every byte of device
+ * memory from their own pool).  It builds the grid of the given positions
+ * and evaluates the force of one iteration exactly as bdm_step does for its
+ * first iteration (S0-S4), but it calls no cudaMalloc, cudaFree or
+ * allocating library routine: its working memory is one fixed array of
+ * about 5 MB in the library's device memory, held by every GPU that loads
+ * the library until the process exits.
+ *
+ * params: one parameter set (growth, static and sort fields are ignored).
+ * xyz: device pointer, n x 3 doubles, row-major; diameter: device pointer,
+ * n doubles; force: device pointer, n x 3 doubles written in row order;
+ * nnz: device pointer, n int32 (non-zero pair forces per agent), or NULL.
+ * cuda_stream: the stream to run on (NULL: the legacy default stream).
+ * The caller owns all four buffers.
+ *
+ * Limits: n <= 16384 and at most 131072 grid boxes; beyond them the call
+ * returns BDM_E_CAPACITY (n too large: before any work; too many boxes:
+ * after the run, with force contents undefined).
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress while that device is current; make that first call
+ * before any stream capture.  The call waits for its stream to finish.
+ * All calls on a device share the one array: calls that overlap on the GPU
+ * race and give undefined results.
+ * Errors: BDM_E_INVAL (NULL pointer, n < 0, bad params), BDM_E_CAPACITY,
+ * BDM_E_NONFINITE, BDM_E_CUDA. */
+int bdm_forces_noalloc(const bdm_params* params, int64_t n, const double* xyz, const double* diameter,
+                       double* force, int32_t* nnz, void* cuda_stream);
+
 /* Release everything the context owns. */
 void bdm_destroy(bdm_ctx* ctx);
 

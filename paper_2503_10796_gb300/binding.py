@@ -54,6 +54,7 @@ SIGNATURES = {
     "bdm_get_stats": (C.c_int, [_vp, _i32, _P(BdmStats)]),
     "bdm_profile": (C.c_int, [_vp, _i32]),
     "bdm_get_profile": (C.c_int, [_vp, _P(_i64), _P(_dbl), _P(C.c_char_p)]),
+    "bdm_forces_noalloc": (C.c_int, [_P(BdmParams), _i64, _vp, _vp, _vp, _vp, _vp]),
     "bdm_destroy": (None, [_vp]),
     "bdm_last_error": (C.c_char_p, [_vp]),
 }
