@@ -66,6 +66,11 @@ def make_workload(name: str, precision: int, static: int):
                             sort_interval=10)]
         desc = dict(workload="clustered_1M", agents=1048576, clusters=8, sigma=200.0, side=5.0e3,
                     diameters="U[8,12]", sort_interval=10)
+    elif name == "growth_division_65536":
+        pops = [W.growth_division(precision=precision)]
+        desc = dict(workload="growth_division_65536", agents_start=65536, agents_cap=2097152,
+                    lattice=[32, 32, 64], spacing=10.0, diameter=9.0, divide_diameter=12.0,
+                    growth_rate=4000.0, dt=0.01)
     elif name == "plain_fp64_4096":
         pops = [W.plain_fp64(precision=precision)]
         desc = dict(workload="plain_4096", agents=4096, side=160.0, diameters="U[8,12]")
@@ -252,6 +257,7 @@ def main():
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
+    upd0 = sum(ctx.stats(s)["agent_updates"] for s in range(len(pops)))
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -268,7 +274,9 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * n_agents * args.steps / (ms * 1e-3)
+    upd1 = sum(ctx.stats(s)["agent_updates"] for s in range(len(pops)))
+    n_agents = sum(ctx.count(s) for s in range(len(pops)))
+    value = world * (upd1 - upd0) / (ms * 1e-3)
 
     # roofline of the force kernel
     f = prof["force"]

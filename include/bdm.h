@@ -89,7 +89,8 @@ typedef struct {
   int64_t moved_agents;    /* agents with a non-zero displacement in the last iteration */
   double origin_len[4];    /* grid of the last iteration: origin x, y, z and box length */
   int64_t dims[3];         /* boxes per axis of that grid */
-  int64_t reserved[4];
+  int64_t agent_updates;   /* sum over stepped iterations of the agent count at their start */
+  int64_t reserved[3];
 } bdm_stats;
 
 typedef struct bdm_ctx bdm_ctx;

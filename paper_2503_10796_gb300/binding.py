@@ -38,7 +38,7 @@ class BdmParams(C.Structure):
 class BdmStats(C.Structure):
     _fields_ = [("agents", C.c_int64), ("iterations", C.c_int64), ("static_agents", C.c_int64),
                 ("moved_agents", C.c_int64), ("origin_len", C.c_double * 4), ("dims", C.c_int64 * 3),
-                ("reserved", C.c_int64 * 4)]
+                ("agent_updates", C.c_int64), ("reserved", C.c_int64 * 3)]
 
 
 SIGNATURES = {
@@ -214,7 +214,8 @@ class Context:
         s = BdmStats()
         self._check(self._lib.bdm_get_stats(self._h, sim, C.byref(s)))
         return dict(agents=s.agents, iterations=s.iterations, static_agents=s.static_agents,
-                    moved_agents=s.moved_agents, origin_len=list(s.origin_len), dims=list(s.dims))
+                    moved_agents=s.moved_agents, origin_len=list(s.origin_len), dims=list(s.dims),
+                    agent_updates=s.agent_updates)
 
     # -- profiling ---------------------------------------------------------
     def profile(self, enable: bool = True):

@@ -68,6 +68,7 @@ struct SimState {
   int64_t t;                  // iterations completed
   int64_t it;                 // index of the iteration being computed
   unsigned long long n_static, n_moved;
+  unsigned long long updates;  // agent-updates stepped since the agents were set
 };
 
 // Global counters of a context.

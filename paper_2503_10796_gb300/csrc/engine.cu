@@ -797,6 +797,7 @@ int bdm_get_stats(bdm_ctx *c, int32_t sim, bdm_stats *out) {
   out->iterations = s.t;
   for (int a = 0; a < 3; ++a) { out->origin_len[a] = s.o[a]; out->dims[a] = s.dims[a]; }
   out->origin_len[3] = s.L;
+  out->agent_updates = (int64_t)s.updates;
   if (s.t > 0 && s.n > 0) {
     unsigned long long *cnt = nullptr;
     rc = dalloc(c, &cnt, 2, "stat counters");

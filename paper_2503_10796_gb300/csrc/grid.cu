@@ -143,6 +143,7 @@ __global__ void k_params(DevCtx C, int32_t step) {
     if (step) {
       st.it = st.t;
       st.t += 1;
+      st.updates += (unsigned long long)(st.n > 0 ? st.n : 0);
     }
     if (st.n <= 0) {
       for (int a = 0; a < 3; ++a) { st.bmin[a] = ~0ull; st.bmax[a] = 0ull; }

@@ -275,3 +275,38 @@ def test_sorting_does_not_change_results(orc, precision):
     tol = 1e-9 if precision == 0 else 1e-4
     np.testing.assert_allclose(xa, xb, rtol=0, atol=tol * pop.diameter.max())
     assert not np.array_equal(a.storage_order(0), np.arange(pop.n))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_growth_division_matches_oracle(orc, precision):
+    """Synchronised growth and division on a small lattice: the agent count
+    of every iteration, the diameters and volumes are exact; positions stay
+    within the trajectory tolerance."""
+    pop = workloads.growth_division(shape=(4, 4, 4), cap_factor=8, precision=precision)
+    ctx = ctx_for(pop)
+    o = orc_for(pop)
+    for t in range(45):
+        ctx.step(1)
+        o.step(1)
+        assert ctx.count(0) == o.n, t
+    x_g, d_g = ctx.get_agents(0)
+    x_o, d_o, _ = o.get()
+    assert np.array_equal(d_g, d_o)
+    tol = 1e-9 if precision == 0 else 1e-3
+    np.testing.assert_allclose(x_g, x_o, rtol=0, atol=tol * d_o.max())
+    st = ctx.stats(0)
+    assert st["iterations"] == 45 and st["agents"] == o.n
+
+
+def test_division_stops_at_capacity(orc):
+    pop = workloads.growth_division(shape=(3, 3, 3), cap_factor=1)
+    pop.params.capacity = 40  # 27 agents; only 13 may divide
+    ctx = ctx_for(pop)
+    o = orc_for(pop)
+    ctx.step(16)
+    o.step(16)
+    assert ctx.count(0) == o.n == 40
+    x_g, d_g = ctx.get_agents(0)
+    x_o, d_o, _ = o.get()
+    assert np.array_equal(d_g, d_o)
+    np.testing.assert_allclose(x_g, x_o, rtol=0, atol=1e-3)
