@@ -236,6 +236,29 @@ __device__ __forceinline__ void warp_add(unsigned long long *dst, unsigned int v
 
 __device__ __forceinline__ void set_err(Globals *g, uint32_t bits) { atomicOr(&g->err, bits); }
 
+// Static check (§5.5): the agent itself is eligible (unchanged in the last
+// iteration, at most one non-zero pair force, grid unchanged) and no box of
+// its stencil carries a dirty mark of the current build.
+__device__ __forceinline__ bool is_static_cell(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
+                                          int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
+  if (!sc.detect_static || !s.same_grid || !(C.c.flag[p] & CELL_STATIC_ELIGIBLE)) return false;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int64_t z = cz + dz;
+    if (z < 0 || z >= s.dims[2]) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int64_t y = cy + dy;
+      if (y < 0 || y >= s.dims[1]) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        int64_t x = cx + dx;
+        if (x < 0 || x >= s.dims[0]) continue;
+        unsigned long long e = C.tab.cnt[sc.table_base + linear_box(s, x, y, z)];
+        if ((uint32_t)(e >> 32) == stamp && (e & 0x80000000ull)) return false;
+      }
+    }
+  }
+  return true;
+}
+
 // Grid-stride helpers sized for 152 SMs.
 constexpr int kThreads = 256;
 

@@ -48,7 +48,8 @@ struct bdm_ctx {
   int64_t table_entries = 0;
   void *d_sort = nullptr;
   size_t sort_bytes = 0;
-  int sort_key_bits = 0;     // simulation-rank bits + 3 x bits per box coordinate
+  int sort_key_bits = 0;
+  int force_variant = 0;     // 0: queue kernel for the FP32 path; 1: reference kernel     // simulation-rank bits + 3 x bits per box coordinate
   void *d_grow = nullptr;
   size_t grow_bytes = 0;
   std::vector<void *> allocs;
@@ -219,7 +220,7 @@ void launch_iteration(bdm_ctx *c) {
   launch_place(D, st, 1);
   stage_end(c);
   stage_begin(c, 4);
-  launch_force(D, st);
+  launch_force(D, st, c->force_variant, c->any_fp32, c->any_fp64);
   stage_end(c);
   stage_begin(c, 5);
   launch_displace(D, st);

@@ -44,29 +44,6 @@ __device__ __noinline__ double exact_delta(const DevCtx &C, int32_t si, int32_t 
   return __dsub_rn(R, __dsqrt_rn(s));
 }
 
-// Static check (§5.5): the agent itself is eligible (unchanged in the last
-// iteration, at most one non-zero pair force, grid unchanged) and no box of
-// its stencil carries a dirty mark of the current build.
-__device__ __forceinline__ bool is_static(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
-                                          int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
-  if (!sc.detect_static || !s.same_grid || !(C.c.flag[p] & CELL_STATIC_ELIGIBLE)) return false;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int64_t z = cz + dz;
-    if (z < 0 || z >= s.dims[2]) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int64_t y = cy + dy;
-      if (y < 0 || y >= s.dims[1]) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        int64_t x = cx + dx;
-        if (x < 0 || x >= s.dims[0]) continue;
-        unsigned long long e = C.tab.cnt[sc.table_base + linear_box(s, x, y, z)];
-        if ((uint32_t)(e >> 32) == stamp && (e & 0x80000000ull)) return false;
-      }
-    }
-  }
-  return true;
-}
-
 __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
                                         int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
   const float4 o0 = C.c.r0[p];
@@ -208,17 +185,19 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
 }
 
-__global__ void __launch_bounds__(kThreads) k_force(DevCtx C) {
+// fp64_only: leave FP32-path simulations to the queue kernel (force32.cu).
+__global__ void __launch_bounds__(kThreads) k_force(DevCtx C, int fp64_only) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
   int sim = C.c.sim[p];
   const SimConst &sc = C.sc[sim];
   const SimState &s = C.ss[sim];
   if (!s.valid) return;
+  if (fp64_only && sc.precision != BDM_PREC_FP64) return;
   int64_t cx, cy, cz;
   unpack_coords(C.c.pkey[p], cx, cy, cz);
   uint32_t stamp = C.g->stamp;
-  bool st = is_static(C, sc, s, p, cx, cy, cz, stamp);
+  bool st = is_static_cell(C, sc, s, p, cx, cy, cz, stamp);
   C.c.stat[p] = st ? 1 : 0;
   if (st) return;
   if (sc.precision == BDM_PREC_FP64)
@@ -284,8 +263,13 @@ __global__ void __launch_bounds__(kThreads) k_displace(DevCtx C) {
 
 static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
-void launch_force(const DevCtx &C, cudaStream_t st) {
-  k_force<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C);
+void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64) {
+  if (variant == 0) {
+    if (has_fp32) launch_force32q(C, st);
+    if (has_fp64) k_force<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 1);
+  } else {
+    k_force<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 0);
+  }
 }
 
 void launch_displace(const DevCtx &C, cudaStream_t st) {

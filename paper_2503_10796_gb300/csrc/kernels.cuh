@@ -12,8 +12,11 @@ void launch_count(const DevCtx &C, cudaStream_t st, int step);
 void launch_scan(const DevCtx &C, cudaStream_t st, uint32_t *partial);
 void launch_place(const DevCtx &C, cudaStream_t st, int step);
 
-// force.cu
-void launch_force(const DevCtx &C, cudaStream_t st);
+// force.cu, force32.cu
+// variant 0: FP32-path simulations by the queue kernel, FP64 ones by the
+// reference kernel; variant 1: the reference kernel for all.
+void launch_force(const DevCtx &C, cudaStream_t st, int variant = 0, bool has_fp32 = true, bool has_fp64 = true);
+void launch_force32q(const DevCtx &C, cudaStream_t st);
 void launch_displace(const DevCtx &C, cudaStream_t st);
 
 // query.cu
