@@ -264,8 +264,11 @@ __global__ void __launch_bounds__(kThreads) k_displace(DevCtx C) {
 static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
 void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64) {
-  if (variant == 0) {
-    if (has_fp32) launch_force32q(C, st);
+  if (variant == 0 || variant == 2) {
+    if (has_fp32) {
+      if (variant == 0) launch_force32s(C, st);
+      else launch_force32q(C, st);
+    }
     if (has_fp64) k_force<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 1);
   } else {
     k_force<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 0);
