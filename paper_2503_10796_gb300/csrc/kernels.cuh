@@ -13,13 +13,13 @@ void launch_scan(const DevCtx &C, cudaStream_t st, uint32_t *partial);
 void launch_place(const DevCtx &C, cudaStream_t st, int step);
 
 // force.cu, force32.cu
-// variant 0: FP32-path simulations by the staged kernel (force32s.cu),
-// FP64 ones by the reference kernel (force.cu); variant 1: the reference
-// kernel for all; variant 2: the global-memory queue kernel (force32.cu)
-// for the FP32 path.
+// variant 0: FP32-path simulations by the block-staged kernel, FP64 ones
+// by the reference kernel (both force.cu); variant 1: the reference kernel
+// for all; variant 2: the global-memory queue kernel (force32.cu) for the
+// FP32 path.
 void launch_force(const DevCtx &C, cudaStream_t st, int variant = 0, bool has_fp32 = true, bool has_fp64 = true);
 void launch_force32q(const DevCtx &C, cudaStream_t st);
-void launch_force32s(const DevCtx &C, cudaStream_t st);
+void launch_force32b(const DevCtx &C, cudaStream_t st);
 void launch_displace(const DevCtx &C, cudaStream_t st);
 
 // query.cu
