@@ -409,8 +409,10 @@ __global__ void __launch_bounds__(kBT, 4) k_force32b(DevCtx C) {
   if (staged) {
     // round 1: table words of the region
     bool over = false;
+    const int irx = (int)rx, irxy = (int)(rx * ry);
     for (int b = tid; b < (int)V; b += kBT) {
-      const int64_t bx = lox + b % rx, by = loy + (b / rx) % ry, bz = loz + b / (rx * ry);
+      const int bz_ = b / irxy, rem = b - bz_ * irxy, by_ = rem / irx, bx_ = rem - by_ * irx;
+      const int64_t bx = lox + bx_, by = loy + by_, bz = loz + bz_;
       const int64_t idx = scu.table_base + bx + su.dims[0] * (by + su.dims[1] * bz);
       const unsigned long long e = C.tab.cnt[idx];
       uint32_t c = ((uint32_t)(e >> 32) == stamp) ? (uint32_t)(e & 0x7FFFFFFFull) : 0u;
