@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--settle", type=int, default=50, help="untimed iterations before warm-up")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--force-variant", type=int, default=-1, help="-1: autotune; else the variant")
+    ap.add_argument("--sort-interval", type=int, default=-2, help="-2: autotune/workload default")
     return ap.parse_args()
 
 
@@ -249,6 +251,13 @@ def main():
     n_agents = sum(p.n for p in pops)
     if args.settle > 0:
         ctx.step(args.settle)
+    tuning = None
+    if args.force_variant < 0:
+        tuning = ctx.autotune(3)
+    else:
+        ctx.set_tuning(force_variant=args.force_variant,
+                       sort_interval=args.sort_interval if args.sort_interval >= -1 else -1)
+        tuning = ctx.get_tuning()
     ctx.step(args.warmup)
     ctx.sync()
     ctx.profile(True)
@@ -335,6 +344,7 @@ def main():
                          "alg_bytes_per_launch": alg},
             "stages_ms_per_iter": {k: v["ms"] / max(v["launches"], 1) for k, v in prof.items() if v["launches"]},
             "static_agents_last_iter": st_static,
+            "tuning": tuning,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": launches_per_iter * args.steps + math.ceil(args.steps / 256),

@@ -203,6 +203,27 @@ int bdm_get_profile(bdm_ctx* ctx, int64_t launches[BDM_NUM_STAGES], double ms[BD
 int bdm_forces_noalloc(const bdm_params* params, int64_t n, const double* xyz, const double* diameter,
                        double* force, int32_t* nnz, void* cuda_stream);
 
+/* Tuning knobs of a context.  None of them changes results beyond the
+ * order of floating-point sums over neighbors. */
+typedef struct {
+  int32_t force_variant;   /* force kernel of the FP32 path: 0 direct loop (default),
+                              2 global queue, 3 block-staged; FP64 always direct */
+  int32_t sort_interval;   /* -1: every simulation's own sort_interval;
+                              >= 0: this Morton re-sort interval for all simulations */
+  int32_t reserved[6];     /* must be 0 */
+} bdm_tuning;
+
+int bdm_set_tuning(bdm_ctx* ctx, const bdm_tuning* tuning);
+int bdm_get_tuning(bdm_ctx* ctx, bdm_tuning* tuning);
+
+/* Autotuner (the thesis proposes automatic tuning of performance
+ * parameters such as the sorting frequency, §7.1.7): from the current
+ * agents, time `iterations` iterations for every force-kernel variant and
+ * then for several re-sort intervals, restoring the saved state after each
+ * trial, and keep the fastest setting; *chosen (may be NULL) receives it.
+ * The agents' state after the call equals the state before it. */
+int bdm_autotune(bdm_ctx* ctx, int32_t iterations, bdm_tuning* chosen);
+
 /* Release everything the context owns. */
 void bdm_destroy(bdm_ctx* ctx);
 

@@ -41,6 +41,10 @@ class BdmStats(C.Structure):
                 ("agent_updates", C.c_int64), ("reserved", C.c_int64 * 3)]
 
 
+class BdmTuning(C.Structure):
+    _fields_ = [("force_variant", C.c_int32), ("sort_interval", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
 SIGNATURES = {
     "bdm_create": (C.c_int, [_P(BdmParams), _i32, _i64, _i32, _vp, _P(_vp)]),
     "bdm_set_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _i32]),
@@ -54,6 +58,9 @@ SIGNATURES = {
     "bdm_get_stats": (C.c_int, [_vp, _i32, _P(BdmStats)]),
     "bdm_profile": (C.c_int, [_vp, _i32]),
     "bdm_get_profile": (C.c_int, [_vp, _P(_i64), _P(_dbl), _P(C.c_char_p)]),
+    "bdm_set_tuning": (C.c_int, [_vp, _P(BdmTuning)]),
+    "bdm_get_tuning": (C.c_int, [_vp, _P(BdmTuning)]),
+    "bdm_autotune": (C.c_int, [_vp, _i32, _P(BdmTuning)]),
     "bdm_forces_noalloc": (C.c_int, [_P(BdmParams), _i64, _vp, _vp, _vp, _vp, _vp]),
     "bdm_destroy": (None, [_vp]),
     "bdm_last_error": (C.c_char_p, [_vp]),
@@ -216,6 +223,21 @@ class Context:
         return dict(agents=s.agents, iterations=s.iterations, static_agents=s.static_agents,
                     moved_agents=s.moved_agents, origin_len=list(s.origin_len), dims=list(s.dims),
                     agent_updates=s.agent_updates)
+
+    # -- tuning ------------------------------------------------------------
+    def set_tuning(self, force_variant: int = 0, sort_interval: int = -1):
+        t = BdmTuning(int(force_variant), int(sort_interval))
+        self._check(self._lib.bdm_set_tuning(self._h, C.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = BdmTuning()
+        self._check(self._lib.bdm_get_tuning(self._h, C.byref(t)))
+        return dict(force_variant=t.force_variant, sort_interval=t.sort_interval)
+
+    def autotune(self, iterations: int = 5) -> dict:
+        t = BdmTuning()
+        self._check(self._lib.bdm_autotune(self._h, int(iterations), C.byref(t)))
+        return dict(force_variant=t.force_variant, sort_interval=t.sort_interval)
 
     # -- profiling ---------------------------------------------------------
     def profile(self, enable: bool = True):

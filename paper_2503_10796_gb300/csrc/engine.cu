@@ -49,7 +49,8 @@ struct bdm_ctx {
   void *d_sort = nullptr;
   size_t sort_bytes = 0;
   int sort_key_bits = 0;
-  int force_variant = 0;     // 0: queue kernel for the FP32 path; 1: reference kernel     // simulation-rank bits + 3 x bits per box coordinate
+  int force_variant = 0;     // force kernel variant of the FP32 path (see launch_force)
+  int sort_override = -1;    // -1: per-simulation sort intervals     // simulation-rank bits + 3 x bits per box coordinate
   void *d_grow = nullptr;
   size_t grow_bytes = 0;
   std::vector<void *> allocs;
@@ -276,7 +277,7 @@ int ensure_table(bdm_ctx *c, int iters, bool *resized) {
       nb *= dims;
       max_dims = std::max(max_dims, dims);
     }
-    if (nb > 4.0e10) return fail(c, BDM_E_CAPACITY, "grid needs more than 4e10 boxes");
+    if (nb >= 4294967296.0) return fail(c, BDM_E_CAPACITY, "grid needs 2^32 or more boxes");
     need[s] = (int64_t)nb;
     total += need[s];
   }
@@ -837,6 +838,174 @@ int bdm_get_profile(bdm_ctx *c, int64_t launches[BDM_NUM_STAGES], double ms[BDM_
     if (names) names[k] = kStageNames[k];
   }
   return BDM_OK;
+}
+
+int bdm_set_tuning(bdm_ctx *c, const bdm_tuning *t) {
+  if (!c || !t) return BDM_E_INVAL;
+  if (t->force_variant != 0 && t->force_variant != 1 && t->force_variant != 2 && t->force_variant != 3)
+    return fail(c, BDM_E_INVAL, "force_variant must be 0, 1, 2 or 3");
+  if (t->sort_interval < -1) return fail(c, BDM_E_INVAL, "sort_interval must be >= -1");
+  for (int k = 0; k < 6; ++k)
+    if (t->reserved[k]) return fail(c, BDM_E_INVAL, "reserved fields must be 0");
+  cudaStreamSynchronize(c->stream);
+  c->force_variant = t->force_variant;
+  c->sort_override = t->sort_interval;
+  bool any = false;
+  for (int s = 0; s < c->n_sims; ++s) {
+    int iv = t->sort_interval >= 0 ? t->sort_interval : c->params[s].sort_interval;
+    c->h_sc[s].sort_interval = iv;
+    if (iv > 0) any = true;
+  }
+  if (any && !c->d_sort) {
+    c->sort_bytes = morton_scratch_bytes(c->max_total);
+    int rc = dalloc(c, (char **)&c->d_sort, c->sort_bytes, "morton sort scratch");
+    if (rc) return rc;
+  }
+  c->any_sort = any;
+  c->graph_dirty = true;
+  return upload_consts(c);
+}
+
+int bdm_get_tuning(bdm_ctx *c, bdm_tuning *t) {
+  if (!c || !t) return BDM_E_INVAL;
+  memset(t, 0, sizeof(*t));
+  t->force_variant = c->force_variant;
+  t->sort_interval = c->sort_override;
+  return BDM_OK;
+}
+
+namespace {
+
+// Saved per-slot state and simulation states (autotuner trials).
+struct Snapshot {
+  double *x = nullptr, *y = nullptr, *z = nullptr, *d = nullptr, *v = nullptr;
+  int32_t *id = nullptr;
+  uint64_t *pk = nullptr, *ph = nullptr;
+  uint8_t *fl = nullptr, *nz = nullptr;
+  std::vector<SimState> ss;
+};
+
+int snap_alloc(bdm_ctx *c, Snapshot &S, size_t M) {
+  int rc = BDM_OK;
+  if (!rc) rc = dalloc(c, &S.x, M, "snapshot x");
+  if (!rc) rc = dalloc(c, &S.y, M, "snapshot y");
+  if (!rc) rc = dalloc(c, &S.z, M, "snapshot z");
+  if (!rc) rc = dalloc(c, &S.d, M, "snapshot d");
+  if (!rc) rc = dalloc(c, &S.v, M, "snapshot v");
+  if (!rc) rc = dalloc(c, &S.id, M, "snapshot id");
+  if (!rc) rc = dalloc(c, &S.pk, M, "snapshot keys");
+  if (!rc) rc = dalloc(c, &S.ph, M, "snapshot key history");
+  if (!rc) rc = dalloc(c, &S.fl, M, "snapshot flags");
+  if (!rc) rc = dalloc(c, &S.nz, M, "snapshot nnz");
+  return rc;
+}
+
+void snap_free(bdm_ctx *c, Snapshot &S) {
+  dfree(c, S.x); dfree(c, S.y); dfree(c, S.z); dfree(c, S.d); dfree(c, S.v);
+  dfree(c, S.id); dfree(c, S.pk); dfree(c, S.ph); dfree(c, S.fl); dfree(c, S.nz);
+}
+
+int snap_copy(bdm_ctx *c, Snapshot &S, size_t M, bool save) {
+  const Agents &A = c->D.a;
+  auto cp = [&](void *snap, void *live, size_t bytes) {
+    return save ? cudaMemcpyAsync(snap, live, bytes, cudaMemcpyDeviceToDevice, c->stream)
+                : cudaMemcpyAsync(live, snap, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  };
+  cudaError_t e = cudaSuccess;
+  if (!e) e = cp(S.x, A.x, 8 * M);
+  if (!e) e = cp(S.y, A.y, 8 * M);
+  if (!e) e = cp(S.z, A.z, 8 * M);
+  if (!e) e = cp(S.d, A.d, 8 * M);
+  if (!e) e = cp(S.v, A.v, 8 * M);
+  if (!e) e = cp(S.id, A.id, 4 * M);
+  if (!e) e = cp(S.pk, A.pkey, 8 * M);
+  if (!e) e = cp(S.ph, A.pkey_hist, 8 * M);
+  if (!e) e = cp(S.fl, A.flags, M);
+  if (!e) e = cp(S.nz, A.nnz, M);
+  if (save) {
+    S.ss.resize(c->n_sims);
+    if (!e) e = cudaMemcpyAsync(S.ss.data(), c->D.ss, sizeof(SimState) * c->n_sims, cudaMemcpyDeviceToHost, c->stream);
+  } else {
+    if (!e) e = cudaMemcpyAsync(c->D.ss, S.ss.data(), sizeof(SimState) * c->n_sims, cudaMemcpyHostToDevice, c->stream);
+  }
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune snapshot");
+  return BDM_OK;
+}
+
+int timed_trial(bdm_ctx *c, int iters, float *ms) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  // one untimed iteration builds the graph and warms the caches
+  int rc = bdm_step(c, 1);
+  if (!rc) {
+    cudaEventRecord(a, c->stream);
+    rc = bdm_step(c, iters);
+    cudaEventRecord(b, c->stream);
+  }
+  cudaError_t e = cudaEventSynchronize(b);
+  if (!rc && e == cudaSuccess) cudaEventElapsedTime(ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (!rc) rc = latched_error(c);
+  return rc;
+}
+
+}  // namespace
+
+int bdm_autotune(bdm_ctx *c, int32_t iterations, bdm_tuning *chosen) {
+  if (!c) return BDM_E_INVAL;
+  if (iterations < 1) return fail(c, BDM_E_INVAL, "iterations must be >= 1");
+  for (int s = 0; s < c->n_sims; ++s)
+    if (c->n_set[s] < 0) return fail(c, BDM_E_STATE, "simulation " + std::to_string(s) + " has no agents set");
+  int rc = latched_error(c);
+  if (rc) return rc;
+  const bool prof = c->profiling;
+  c->profiling = false;
+  const size_t M = (size_t)c->used_slots;
+  Snapshot S;
+  rc = snap_alloc(c, S, M > 0 ? M : 1);
+  if (!rc) rc = snap_copy(c, S, M, true);
+  bdm_tuning best;
+  bdm_get_tuning(c, &best);
+  float best_ms = 1e30f;
+  std::vector<int> variants = {0};
+  if (c->any_fp32) variants = {0, 2, 3};
+  for (int v : variants) {
+    if (rc) break;
+    bdm_tuning t = best;
+    t.force_variant = v;
+    rc = bdm_set_tuning(c, &t);
+    float ms = 0.f;
+    if (!rc) rc = timed_trial(c, iterations, &ms);
+    if (!rc && ms < best_ms) { best_ms = ms; best.force_variant = v; }
+    if (!rc) rc = snap_copy(c, S, M, false);
+  }
+  // re-sort interval: compare the time per iteration, each trial covering
+  // two re-sorts
+  float best_per = best_ms / (float)iterations;
+  for (int iv : {0, 5, 10, 25}) {
+    if (rc) break;
+    if (iv == best.sort_interval) continue;
+    bdm_tuning t = best;
+    t.sort_interval = iv;
+    rc = bdm_set_tuning(c, &t);
+    const int n = std::max(iterations, 2 * std::max(iv, 1));
+    float ms = 0.f;
+    if (!rc) rc = timed_trial(c, n, &ms);
+    if (!rc && ms / (float)n < best_per) {
+      best_per = ms / (float)n;
+      best.sort_interval = iv;
+    }
+    if (!rc) rc = snap_copy(c, S, M, false);
+  }
+  int rc2 = bdm_set_tuning(c, &best);
+  if (!rc) rc = rc2;
+  snap_free(c, S);
+  c->profiling = prof;
+  if (chosen) *chosen = best;
+  return rc;
 }
 
 void bdm_destroy(bdm_ctx *c) {

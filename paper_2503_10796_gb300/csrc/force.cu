@@ -21,7 +21,7 @@
 
 namespace bdm {
 
-constexpr float kFastDelta = 2.0f;
+constexpr float kFastDelta = 0.5f;
 constexpr float kTinyNum = 0x1p-19f;
 
 __device__ __forceinline__ void ff_diff(float hi_i, float lo_i, float hi_j, float lo_j, float off_h,
@@ -44,40 +44,65 @@ __device__ __noinline__ double exact_delta(const DevCtx &C, int32_t si, int32_t 
   return __dsub_rn(R, __dsqrt_rn(s));
 }
 
+// Stencil bounds of a box: neighbor offsets that stay inside the grid.
+struct Stencil {
+  int xlo, xhi, ylo, yhi, zlo, zhi;
+  int cx, cy, cz, d0, d1;
+  const unsigned long long *cnt;  // this simulation's table words
+  const uint32_t *start;          // and first cells
+};
+
+__device__ __forceinline__ Stencil make_stencil(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t cx,
+                                                int64_t cy, int64_t cz) {
+  Stencil t;
+  t.cx = (int)cx; t.cy = (int)cy; t.cz = (int)cz;
+  t.d0 = (int)s.dims[0]; t.d1 = (int)s.dims[1];
+  const int d2 = (int)s.dims[2];
+  t.xlo = t.cx > 0 ? -1 : 0; t.xhi = t.cx < t.d0 - 1 ? 1 : 0;
+  t.ylo = t.cy > 0 ? -1 : 0; t.yhi = t.cy < t.d1 - 1 ? 1 : 0;
+  t.zlo = t.cz > 0 ? -1 : 0; t.zhi = t.cz < d2 - 1 ? 1 : 0;
+  t.cnt = C.tab.cnt + sc.table_base;
+  t.start = C.tab.start + sc.table_base;
+  return t;
+}
+
+// Direct FP32 loop: per stencil box the own offset is shifted into the
+// neighbour box's frame once; per candidate the FP32 filter, and for pairs
+// that pass either the plain FP32 overlap (deep pairs) or the float-float
+// overlap (shallow pairs).  Box indices are 32-bit offsets inside the
+// simulation's table region (the grid holds fewer than 2^32 boxes).
 __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
                                         int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
   const float4 o0 = C.c.r0[p];
   const float4 o1 = C.c.r1[p];
   const float Lh = s.Lh, Ll = s.Ll, marg = s.marg;
   const float kf = sc.kf, gf = sc.gammaf;
+  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
   float fx = 0.f, fy = 0.f, fz = 0.f;
   uint32_t nnz = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int64_t z = cz + dz;
-    if (z < 0 || z >= s.dims[2]) continue;
-    const float ozh = dz ? (dz > 0 ? Lh : -Lh) : 0.f, ozl = dz ? (dz > 0 ? Ll : -Ll) : 0.f;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int64_t y = cy + dy;
-      if (y < 0 || y >= s.dims[1]) continue;
-      const float oyh = dy ? (dy > 0 ? Lh : -Lh) : 0.f, oyl = dy ? (dy > 0 ? Ll : -Ll) : 0.f;
-      for (int dx = -1; dx <= 1; ++dx) {
-        int64_t x = cx + dx;
-        if (x < 0 || x >= s.dims[0]) continue;
-        const float oxh = dx ? (dx > 0 ? Lh : -Lh) : 0.f, oxl = dx ? (dx > 0 ? Ll : -Ll) : 0.f;
-        int64_t idx = sc.table_base + linear_box(s, x, y, z);
-        unsigned long long e = C.tab.cnt[idx];
+  for (int dz = t.zlo; dz <= t.zhi; ++dz) {
+    const float fdz = (float)dz;
+    const float sz = __fsub_rn(o0.z, __fmul_rn(fdz, Lh));
+    for (int dy = t.ylo; dy <= t.yhi; ++dy) {
+      const float fdy = (float)dy;
+      const float sy = __fsub_rn(o0.y, __fmul_rn(fdy, Lh));
+      const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
+                           (uint32_t)t.cx;
+      for (int dx = t.xlo; dx <= t.xhi; ++dx) {
+        const unsigned long long e = t.cnt[row + dx];
         if ((uint32_t)(e >> 32) != stamp) continue;
-        uint32_t cnt = (uint32_t)(e & 0x7FFFFFFFull);
-        int64_t start = C.tab.start[idx];
-        for (int64_t j = start; j < start + cnt; ++j) {
+        const uint32_t cnt = (uint32_t)e & 0x7FFFFFFFu;
+        const int64_t j0 = t.start[row + dx];
+        const float fdx = (float)dx;
+        const float sx = __fsub_rn(o0.x, __fmul_rn(fdx, Lh));
+        for (uint32_t m = 0; m < cnt; ++m) {
+          const int64_t j = j0 + m;
           if (j == p) continue;
           const float4 q = C.c.r0[j];
-          float ddx = __fsub_rn(__fsub_rn(o0.x, q.x), oxh);
-          float ddy = __fsub_rn(__fsub_rn(o0.y, q.y), oyh);
-          float ddz = __fsub_rn(__fsub_rn(o0.z, q.z), ozh);
-          float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
-          float R = __fadd_rn(o0.w, q.w);
-          float Rm = __fadd_rn(R, marg);
+          const float ddx = __fsub_rn(sx, q.x), ddy = __fsub_rn(sy, q.y), ddz = __fsub_rn(sz, q.z);
+          const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+          const float R = __fadd_rn(o0.w, q.w);
+          const float Rm = __fadd_rn(R, marg);
           if (!(s2 < __fmul_rn(Rm, Rm))) continue;
           float dist = sqrtf(s2);
           float del = __fsub_rn(R, dist);
@@ -86,9 +111,9 @@ __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, con
             // float-float overlap
             const float4 q1 = C.c.r1[j];
             float xh, xl, yh, yl, zh, zl;
-            ff_diff(o0.x, o1.x, q.x, q1.x, oxh, oxl, xh, xl);
-            ff_diff(o0.y, o1.y, q.y, q1.y, oyh, oyl, yh, yl);
-            ff_diff(o0.z, o1.z, q.z, q1.z, ozh, ozl, zh, zl);
+            ff_diff(o0.x, o1.x, q.x, q1.x, __fmul_rn(fdx, Lh), __fmul_rn(fdx, Ll), xh, xl);
+            ff_diff(o0.y, o1.y, q.y, q1.y, __fmul_rn(fdy, Lh), __fmul_rn(fdy, Ll), yh, yl);
+            ff_diff(o0.z, o1.z, q.z, q1.z, __fmul_rn(fdz, Lh), __fmul_rn(fdz, Ll), zh, zl);
             float p0, e0, p1, e1, p2, e2;
             two_prod(xh, xh, p0, e0);
             e0 = __fmaf_rn(__fmul_rn(2.f, xh), xl, e0);
@@ -96,38 +121,38 @@ __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, con
             e1 = __fmaf_rn(__fmul_rn(2.f, yh), yl, e1);
             two_prod(zh, zh, p2, e2);
             e2 = __fmaf_rn(__fmul_rn(2.f, zh), zl, e2);
-            float S, Se, S2, Se2;
-            two_sum(p0, p1, S, Se);
-            two_sum(S, p2, S2, Se2);
-            float sl = __fadd_rn(__fadd_rn(Se, Se2), __fadd_rn(__fadd_rn(e0, e1), e2));
+            float Sa, Sea, Sb, Seb;
+            two_sum(p0, p1, Sa, Sea);
+            two_sum(Sa, p2, Sb, Seb);
+            const float sl = __fadd_rn(__fadd_rn(Sea, Seb), __fadd_rn(__fadd_rn(e0, e1), e2));
             float sh, sll;
-            fast_two_sum(S2, sl, sh, sll);
+            fast_two_sum(Sb, sl, sh, sll);
             float Rh, Rl;
             two_sum(o0.w, q.w, Rh, Rl);
             Rl = __fadd_rn(Rl, __fadd_rn(o1.w, q1.w));
             float Qh, Ql;
             two_prod(Rh, Rh, Qh, Ql);
             Ql = __fmaf_rn(__fmul_rn(2.f, Rh), Rl, Ql);
-            float num = __fadd_rn(__fsub_rn(Qh, sh), __fsub_rn(Ql, sll));
+            const float num = __fadd_rn(__fsub_rn(Qh, sh), __fsub_rn(Ql, sll));
             dist = sqrtf(sh);
             if (fabsf(num) < kTinyNum) {
-              double d64 = exact_delta(C, C.c.slot[p], C.c.slot[j]);
-              del = d64 > 0.0 ? (float)d64 : 0.f;
+              const double d64 = exact_delta(C, C.c.slot[p], C.c.slot[j]);
               if (!(d64 > 0.0)) continue;
+              del = (float)d64;
             } else {
               if (!(num > 0.f)) continue;
               del = __fdividef(num, __fadd_rn(Rh, dist));
             }
             ux = xh; uy = yh; uz = zh;
           }
-          float rr = __fdividef(__fmul_rn(o0.w, q.w), R);
-          float fn = __fsub_rn(__fmul_rn(kf, del), __fmul_rn(gf, sqrtf(__fmul_rn(rr, del))));
+          const float rr = __fdividef(__fmul_rn(o0.w, q.w), R);
+          const float fn = __fsub_rn(__fmul_rn(kf, del), __fmul_rn(gf, sqrtf(__fmul_rn(rr, del))));
           nnz += (fn != 0.f);
           if (dist > 0.f) {
-            float sc_ = __fdividef(fn, dist);
-            fx = __fmaf_rn(sc_, ux, fx);
-            fy = __fmaf_rn(sc_, uy, fy);
-            fz = __fmaf_rn(sc_, uz, fz);
+            const float f = __fdividef(fn, dist);
+            fx = __fmaf_rn(f, ux, fx);
+            fy = __fmaf_rn(f, uy, fy);
+            fz = __fmaf_rn(f, uz, fz);
           }
         }
       }
@@ -141,36 +166,33 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
                                         int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
   const double4_32a o = C.c.r64[p];
   const double k = sc.k, gam = sc.gamma;
+  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
   double fx = 0.0, fy = 0.0, fz = 0.0;
   uint32_t nnz = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int64_t z = cz + dz;
-    if (z < 0 || z >= s.dims[2]) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int64_t y = cy + dy;
-      if (y < 0 || y >= s.dims[1]) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        int64_t x = cx + dx;
-        if (x < 0 || x >= s.dims[0]) continue;
-        int64_t idx = sc.table_base + linear_box(s, x, y, z);
-        unsigned long long e = C.tab.cnt[idx];
+  for (int dz = t.zlo; dz <= t.zhi; ++dz) {
+    for (int dy = t.ylo; dy <= t.yhi; ++dy) {
+      const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
+                           (uint32_t)t.cx;
+      for (int dx = t.xlo; dx <= t.xhi; ++dx) {
+        const unsigned long long e = t.cnt[row + dx];
         if ((uint32_t)(e >> 32) != stamp) continue;
-        uint32_t cnt = (uint32_t)(e & 0x7FFFFFFFull);
-        int64_t start = C.tab.start[idx];
-        for (int64_t j = start; j < start + cnt; ++j) {
+        const uint32_t cnt = (uint32_t)e & 0x7FFFFFFFu;
+        const int64_t j0 = t.start[row + dx];
+        for (uint32_t m = 0; m < cnt; ++m) {
+          const int64_t j = j0 + m;
           if (j == p) continue;
           const double4_32a q = C.c.r64[j];
-          double ddx = __dsub_rn(o.x, q.x), ddy = __dsub_rn(o.y, q.y), ddz = __dsub_rn(o.z, q.z);
-          double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-          double R = __dadd_rn(o.w, q.w);
+          const double ddx = __dsub_rn(o.x, q.x), ddy = __dsub_rn(o.y, q.y), ddz = __dsub_rn(o.z, q.z);
+          const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+          const double R = __dadd_rn(o.w, q.w);
           if (!(s2 < __dmul_rn(R, R) * 1.0000001)) continue;  // cheap reject far beyond contact
-          double dist = __dsqrt_rn(s2);
-          double del = __dsub_rn(R, dist);
+          const double dist = __dsqrt_rn(s2);
+          const double del = __dsub_rn(R, dist);
           if (!(del > 0.0)) continue;
-          double rr = __ddiv_rn(__dmul_rn(o.w, q.w), R);
-          double rep = __dmul_rn(k, del);
-          double adh = __dmul_rn(gam, __dsqrt_rn(__dmul_rn(rr, del)));
-          double fn = __dsub_rn(rep, adh);
+          const double rr = __ddiv_rn(__dmul_rn(o.w, q.w), R);
+          const double rep = __dmul_rn(k, del);
+          const double adh = __dmul_rn(gam, __dsqrt_rn(__dmul_rn(rr, del)));
+          const double fn = __dsub_rn(rep, adh);
           nnz += (fn != 0.0);
           if (dist > 0.0) {
             fx = __dadd_rn(fx, __dmul_rn(fn, __ddiv_rn(ddx, dist)));
@@ -554,9 +576,9 @@ void launch_force32b(const DevCtx &C, cudaStream_t st) {
 static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
 void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64) {
-  if (variant == 0 || variant == 2) {
+  if (variant == 2 || variant == 3) {
     if (has_fp32) {
-      if (variant == 0) launch_force32b(C, st);
+      if (variant == 3) launch_force32b(C, st);
       else launch_force32q(C, st);
     }
     if (has_fp64) k_force<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 1);

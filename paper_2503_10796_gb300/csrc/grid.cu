@@ -170,7 +170,7 @@ __global__ void k_params(DevCtx C, int32_t step) {
     }
     if (!ok) set_err(g, ERR_COORD | ERR_NONFINITE);
     st.nboxes = nb;
-    if (ok && nb > sc.table_cap) {
+    if (ok && (nb > sc.table_cap || nb >= (1ll << 32))) {
       set_err(g, ERR_TABLE);
       ok = false;
     }

@@ -310,3 +310,39 @@ def test_division_stops_at_capacity(orc):
     x_o, d_o, _ = o.get()
     assert np.array_equal(d_g, d_o)
     np.testing.assert_allclose(x_g, x_o, rtol=0, atol=1e-3)
+
+
+@pytest.mark.parametrize("variant", [0, 2, 3])
+def test_force_variants_match_oracle(orc, variant):
+    """Every force-kernel variant of the FP32 path meets the tolerance."""
+    for pop in (workloads.plain_fp64(seed=5),
+                workloads.clustered(n_clusters=4, per_cluster=2000, side=500.0, sigma=30.0, seed=1)):
+        ctx = ctx_for(pop, precision=1, sort_interval=1)
+        ctx.set_tuning(force_variant=variant)
+        o = orc_for(pop)
+        F0, nnz0, smag = o.forces()
+        ctx.step(1)
+        ctx.sync()
+        F, nnz, _ = ctx.forces(0)
+        err = np.linalg.norm(F - F0, axis=1) / np.maximum(smag, 1e-300)
+        err[smag == 0] = np.linalg.norm(F[smag == 0], axis=1)
+        assert err.max() <= TOL[1], (variant, err.max())
+
+
+def test_autotune_restores_state(orc):
+    pop = workloads.clustered(n_clusters=4, per_cluster=3000, side=600.0, sigma=30.0, seed=3)
+    a = ctx_for(pop, sort_interval=10)
+    b = ctx_for(pop, sort_interval=10)
+    a.step(3)
+    b.step(3)
+    x_before, _ = a.get_agents(0)
+    chosen = a.autotune(3)
+    assert chosen["force_variant"] in (0, 2, 3)
+    x_after, _ = a.get_agents(0)
+    assert np.array_equal(x_before, x_after)
+    assert a.stats(0)["iterations"] == 3
+    a.step(4)
+    b.step(4)
+    xa, _ = a.get_agents(0)
+    xb, _ = b.get_agents(0)
+    np.testing.assert_allclose(xa, xb, rtol=0, atol=1e-3)
