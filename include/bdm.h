@@ -209,8 +209,10 @@ typedef struct {
   int32_t force_variant;   /* force kernel of the FP32 path: 0 direct loop (default),
                               2 global queue, 3 block-staged; FP64 always direct */
   int32_t sort_interval;   /* -1: every simulation's own sort_interval;
-                              >= 0: this Morton re-sort interval for all simulations */
-  int32_t reserved[6];     /* must be 0 */
+                              >= 0: this re-sort interval for all simulations */
+  int32_t sort_curve;      /* order the re-sort gives the storage: 0 Morton order of the
+                              boxes (default, §5.4.2); 1 row-major box order */
+  int32_t reserved[5];     /* must be 0 */
 } bdm_tuning;
 
 int bdm_set_tuning(bdm_ctx* ctx, const bdm_tuning* tuning);
@@ -218,8 +220,8 @@ int bdm_get_tuning(bdm_ctx* ctx, bdm_tuning* tuning);
 
 /* Autotuner (the thesis proposes automatic tuning of performance
  * parameters such as the sorting frequency, §7.1.7): from the current
- * agents, time `iterations` iterations for every force-kernel variant and
- * then for several re-sort intervals, restoring the saved state after each
+ * agents, time `iterations` iterations for every force-kernel variant,
+ * both storage curves and several re-sort intervals, restoring the saved state after each
  * trial, and keep the fastest setting; *chosen (may be NULL) receives it.
  * The agents' state after the call equals the state before it. */
 int bdm_autotune(bdm_ctx* ctx, int32_t iterations, bdm_tuning* chosen);

@@ -42,7 +42,8 @@ class BdmStats(C.Structure):
 
 
 class BdmTuning(C.Structure):
-    _fields_ = [("force_variant", C.c_int32), ("sort_interval", C.c_int32), ("reserved", C.c_int32 * 6)]
+    _fields_ = [("force_variant", C.c_int32), ("sort_interval", C.c_int32), ("sort_curve", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 SIGNATURES = {
@@ -225,19 +226,19 @@ class Context:
                     agent_updates=s.agent_updates)
 
     # -- tuning ------------------------------------------------------------
-    def set_tuning(self, force_variant: int = 0, sort_interval: int = -1):
-        t = BdmTuning(int(force_variant), int(sort_interval))
+    def set_tuning(self, force_variant: int = 0, sort_interval: int = -1, sort_curve: int = 0):
+        t = BdmTuning(int(force_variant), int(sort_interval), int(sort_curve))
         self._check(self._lib.bdm_set_tuning(self._h, C.byref(t)))
 
     def get_tuning(self) -> dict:
         t = BdmTuning()
         self._check(self._lib.bdm_get_tuning(self._h, C.byref(t)))
-        return dict(force_variant=t.force_variant, sort_interval=t.sort_interval)
+        return dict(force_variant=t.force_variant, sort_interval=t.sort_interval, sort_curve=t.sort_curve)
 
     def autotune(self, iterations: int = 5) -> dict:
         t = BdmTuning()
         self._check(self._lib.bdm_autotune(self._h, int(iterations), C.byref(t)))
-        return dict(force_variant=t.force_variant, sort_interval=t.sort_interval)
+        return dict(force_variant=t.force_variant, sort_interval=t.sort_interval, sort_curve=t.sort_curve)
 
     # -- profiling ---------------------------------------------------------
     def profile(self, enable: bool = True):

@@ -50,7 +50,8 @@ struct bdm_ctx {
   size_t sort_bytes = 0;
   int sort_key_bits = 0;
   int force_variant = 0;     // force kernel variant of the FP32 path (see launch_force)
-  int sort_override = -1;    // -1: per-simulation sort intervals     // simulation-rank bits + 3 x bits per box coordinate
+  int sort_override = -1;    // -1: per-simulation sort intervals
+  int sort_curve = 0;        // 0: Morton order of boxes; 1: row-major box order     // simulation-rank bits + 3 x bits per box coordinate
   void *d_grow = nullptr;
   size_t grow_bytes = 0;
   std::vector<void *> allocs;
@@ -211,7 +212,7 @@ void launch_iteration(bdm_ctx *c) {
   if (c->any_sort) {
     // re-sort by the Morton code of the boxes just counted (when due)
     stage_begin(c, 7);
-    launch_morton(D, st, c->d_sort, c->sort_bytes, c->sort_key_bits);
+    launch_morton(D, st, c->d_sort, c->sort_bytes, c->sort_key_bits, c->sort_curve);
     stage_end(c);
   }
   stage_begin(c, 2);
@@ -845,11 +846,13 @@ int bdm_set_tuning(bdm_ctx *c, const bdm_tuning *t) {
   if (t->force_variant != 0 && t->force_variant != 1 && t->force_variant != 2 && t->force_variant != 3)
     return fail(c, BDM_E_INVAL, "force_variant must be 0, 1, 2 or 3");
   if (t->sort_interval < -1) return fail(c, BDM_E_INVAL, "sort_interval must be >= -1");
-  for (int k = 0; k < 6; ++k)
+  if (t->sort_curve != 0 && t->sort_curve != 1) return fail(c, BDM_E_INVAL, "sort_curve must be 0 or 1");
+  for (int k = 0; k < 5; ++k)
     if (t->reserved[k]) return fail(c, BDM_E_INVAL, "reserved fields must be 0");
   cudaStreamSynchronize(c->stream);
   c->force_variant = t->force_variant;
   c->sort_override = t->sort_interval;
+  c->sort_curve = t->sort_curve;
   bool any = false;
   for (int s = 0; s < c->n_sims; ++s) {
     int iv = t->sort_interval >= 0 ? t->sort_interval : c->params[s].sort_interval;
@@ -871,6 +874,7 @@ int bdm_get_tuning(bdm_ctx *c, bdm_tuning *t) {
   memset(t, 0, sizeof(*t));
   t->force_variant = c->force_variant;
   t->sort_interval = c->sort_override;
+  t->sort_curve = c->sort_curve;
   return BDM_OK;
 }
 
@@ -981,6 +985,20 @@ int bdm_autotune(bdm_ctx *c, int32_t iterations, bdm_tuning *chosen) {
     if (!rc) rc = timed_trial(c, iterations, &ms);
     if (!rc && ms < best_ms) { best_ms = ms; best.force_variant = v; }
     if (!rc) rc = snap_copy(c, S, M, false);
+  }
+  // storage curve of the re-sort
+  if (c->any_sort || best.sort_interval > 0) {
+    for (int cv : {0, 1}) {
+      if (rc) break;
+      if (cv == best.sort_curve) continue;
+      bdm_tuning t = best;
+      t.sort_curve = cv;
+      rc = bdm_set_tuning(c, &t);
+      float ms = 0.f;
+      if (!rc) rc = timed_trial(c, iterations, &ms);
+      if (!rc && ms < best_ms) { best_ms = ms; best.sort_curve = cv; }
+      if (!rc) rc = snap_copy(c, S, M, false);
+    }
   }
   // re-sort interval: compare the time per iteration, each trial covering
   // two re-sorts

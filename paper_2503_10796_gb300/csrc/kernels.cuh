@@ -38,7 +38,8 @@ void launch_set_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, 
 void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, uint32_t *bad);
 
 // sort.cu
-void launch_morton(const DevCtx &C, cudaStream_t st, void *scratch, size_t scratch_bytes, int key_bits);
+void launch_morton(const DevCtx &C, cudaStream_t st, void *scratch, size_t scratch_bytes, int key_bits,
+                   int curve = 0);
 size_t morton_scratch_bytes(int64_t total_slots);
 
 // growth.cu

@@ -87,7 +87,10 @@ size_t morton_scratch_bytes(int64_t total_slots) {
 
 // Decide whether the re-sort is due (some simulation with an interval whose
 // current iteration is a multiple of it) and build the keys.
-__global__ void k_sort_keys(DevCtx C, SortBufs B, int mbits) {
+// curve 0: Morton code of the box (§5.4.2); curve 1: row-major box index
+// (x fastest), the order in which a warp's lanes read neighbouring table
+// words and records contiguously.
+__global__ void k_sort_keys(DevCtx C, SortBufs B, int mbits, int curve) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   __shared__ int due;
   if (threadIdx.x == 0) {
@@ -114,7 +117,16 @@ __global__ void k_sort_keys(DevCtx C, SortBufs B, int mbits) {
   }
   int s = C.order[lo];
   int64_t slot = C.sc[s].base + (k - C.ss[s].cell_base);
-  uint64_t key = ((uint64_t)lo << mbits) | morton3(C.a.pkey[slot]);
+  const uint64_t pk = C.a.pkey[slot];
+  uint64_t code;
+  if (curve == 1) {
+    int64_t bx, by, bz;
+    unpack_coords(pk, bx, by, bz);
+    code = (uint64_t)linear_box(C.ss[s], bx, by, bz);
+  } else {
+    code = morton3(pk);
+  }
+  uint64_t key = ((uint64_t)lo << mbits) | code;
   B.ka[k] = key;
   B.va[k] = (int32_t)slot;
 }
@@ -244,7 +256,8 @@ __global__ void k_sort_writeback(DevCtx C, SortBufs B, const int32_t *perm) {
   C.a.nnz[dst] = B.nnz[k];
 }
 
-void launch_morton(const DevCtx &C, cudaStream_t st, void *scratch, size_t scratch_bytes, int key_bits) {
+void launch_morton(const DevCtx &C, cudaStream_t st, void *scratch, size_t scratch_bytes, int key_bits,
+                   int curve) {
   (void)scratch_bytes;
   int64_t M = C.total_slots;
   if (M <= 0) return;
@@ -257,7 +270,7 @@ void launch_morton(const DevCtx &C, cudaStream_t st, void *scratch, size_t scrat
   int total_bits = mbits + sim_bits;
   int passes = (total_bits + 7) / 8;
   unsigned int nb = (unsigned int)((M + kSortThreads - 1) / kSortThreads);
-  k_sort_keys<<<nb, kSortThreads, 0, st>>>(C, B, mbits);
+  k_sort_keys<<<nb, kSortThreads, 0, st>>>(C, B, mbits, curve);
   int64_t G = (M + 8191) / 8192;
   if (G > 2048) G = 2048;
   if (G < 1) G = 1;

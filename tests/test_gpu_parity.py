@@ -346,3 +346,15 @@ def test_autotune_restores_state(orc):
     xa, _ = a.get_agents(0)
     xb, _ = b.get_agents(0)
     np.testing.assert_allclose(xa, xb, rtol=0, atol=1e-3)
+
+
+def test_row_major_curve_orders_storage(orc):
+    pop = workloads.clustered(n_clusters=3, per_cluster=1500, side=500.0, sigma=30.0, seed=8)
+    ctx = ctx_for(pop, adherence=1e9, sort_interval=1)
+    ctx.set_tuning(force_variant=0, sort_interval=1, sort_curve=1)
+    ctx.step(1)
+    order = ctx.storage_order(0)
+    box, _, _ = ctx.grid(0)
+    seq = box[order]
+    assert np.all(seq[1:] >= seq[:-1])
+    assert np.array_equal(np.sort(order), np.arange(pop.n))
