@@ -77,6 +77,28 @@ __global__ void __launch_bounds__(kThreads) k_bbox(DevCtx C, int64_t chunk) {
   int cur = -1;  // simulation accumulated by the block
   int64_t begin = (int64_t)blockIdx.x * chunk;
   int64_t end = begin + chunk < C.total_slots ? begin + chunk : C.total_slots;
+  if (begin >= end) return;
+  {
+    // Regions are contiguous: a chunk whose ends lie in one simulation lies
+    // in it entirely, and needs no per-tile checks.
+    const int s0 = C.a.sim[begin], s1 = C.a.sim[end - 1];
+    if (s0 == s1 && s0 >= 0) {
+      const int64_t last = C.sc[s0].base + C.ss[s0].n;
+      for (int64_t slot = begin + threadIdx.x; slot < end && slot < last; slot += blockDim.x) {
+        const unsigned long long kx = ord_key(C.a.x[slot]), ky = ord_key(C.a.y[slot]), kz = ord_key(C.a.z[slot]);
+        const unsigned long long kd = ord_key(C.a.d[slot]);
+        acc.mn[0] = kx < acc.mn[0] ? kx : acc.mn[0];
+        acc.mn[1] = ky < acc.mn[1] ? ky : acc.mn[1];
+        acc.mn[2] = kz < acc.mn[2] ? kz : acc.mn[2];
+        acc.mx[0] = kx > acc.mx[0] ? kx : acc.mx[0];
+        acc.mx[1] = ky > acc.mx[1] ? ky : acc.mx[1];
+        acc.mx[2] = kz > acc.mx[2] ? kz : acc.mx[2];
+        acc.dm = kd > acc.dm ? kd : acc.dm;
+      }
+      flush_box(C, s0, acc, sh);
+      return;
+    }
+  }
   for (int64_t t0 = begin; t0 < end; t0 += blockDim.x) {
     int64_t slot = t0 + threadIdx.x;
     int sim = slot < end ? C.a.sim[slot] : -1;
@@ -204,7 +226,7 @@ __global__ void k_params(DevCtx C, int32_t step) {
 // Add one agent (count) and/or a dirty mark to a box entry; returns the
 // agent's rank inside the box.  Entries whose stamp is not the current one
 // are empty, whatever their count says.
-__device__ __forceinline__ uint32_t tab_add(unsigned long long *e, uint32_t stamp, bool dirty, bool count,
+__device__ __forceinline__ uint32_t tab_add(unsigned long long *e, uint32_t stamp, bool dirty, uint32_t count,
                                             Globals *g) {
   unsigned long long old = *(volatile unsigned long long *)e;
   for (int tries = 0; tries < (1 << 22); ++tries) {
@@ -212,7 +234,7 @@ __device__ __forceinline__ uint32_t tab_add(unsigned long long *e, uint32_t stam
     uint32_t st = (uint32_t)(assumed >> 32), lo = (uint32_t)assumed;
     uint32_t cnt = (st == stamp) ? (lo & 0x7FFFFFFFu) : 0u;
     uint32_t dir = (st == stamp) ? (lo & 0x80000000u) : 0u;
-    uint32_t nlo = (cnt + (count ? 1u : 0u)) | dir | (dirty ? 0x80000000u : 0u);
+    uint32_t nlo = (cnt + count) | dir | (dirty ? 0x80000000u : 0u);
     unsigned long long nv = ((unsigned long long)stamp << 32) | nlo;
     if (nv == assumed) return cnt;
     old = atomicCAS(e, assumed, nv);
@@ -251,12 +273,22 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
   bool changed = hist && (C.a.flags[slot] & FLAG_CHANGED) != 0;
   uint32_t stamp = C.g->stamp;
   int64_t idx = sc.table_base + linear_box(s, c[0], c[1], c[2]);
-  C.a.rank[slot] = tab_add(&C.tab.cnt[idx], stamp, changed, true, C.g);
+  // Lanes of a warp that share a box add their count with one atomic
+  // (neighbouring slots mostly share boxes once the storage is sorted).
+  const unsigned mask = __activemask();
+  const unsigned peers = __match_any_sync(mask, (unsigned long long)idx);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  const unsigned dirty_any = __reduce_or_sync(peers, changed ? 1u : 0u);
+  uint32_t base = 0;
+  if (lane == leader) base = tab_add(&C.tab.cnt[idx], stamp, dirty_any != 0, (uint32_t)__popc(peers), C.g);
+  base = __shfl_sync(peers, base, leader);
+  C.a.rank[slot] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
   if (changed && s.same_grid && pk_prev != pk) {
     int64_t px, py, pz;
     unpack_coords(pk_prev, px, py, pz);
     if (px < s.dims[0] && py < s.dims[1] && pz < s.dims[2])
-      tab_add(&C.tab.cnt[sc.table_base + linear_box(s, px, py, pz)], stamp, true, false, C.g);
+      tab_add(&C.tab.cnt[sc.table_base + linear_box(s, px, py, pz)], stamp, true, 0u, C.g);
   }
 }
 

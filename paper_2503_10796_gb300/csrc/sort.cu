@@ -37,6 +37,7 @@ struct SortBufs {
   uint64_t *ka, *kb;
   int32_t *va, *vb;
   uint32_t *hist;   // kDigits x G counts, digit-major
+  uint32_t *dbase;  // kDigits: first output position of each digit
   uint32_t *flag;   // [0] = sort due this iteration
   // permutation scratch
   double *x, *y, *z, *d, *v;
@@ -61,6 +62,7 @@ static SortBufs carve(void *scratch, int64_t M) {
   b.va = (int32_t *)take(4 * M);
   b.vb = (int32_t *)take(4 * M);
   b.hist = (uint32_t *)take(4 * (size_t)kDigits * 2048);
+  b.dbase = (uint32_t *)take(4 * (size_t)kDigits);
   b.flag = (uint32_t *)take(16);
   b.x = (double *)take(8 * M);
   b.y = (double *)take(8 * M);
@@ -79,7 +81,8 @@ static SortBufs carve(void *scratch, int64_t M) {
 size_t morton_scratch_bytes(int64_t total_slots) {
   size_t M = (size_t)(total_slots > 0 ? total_slots : 1);
   size_t b = 0;
-  for (size_t s : {8 * M, 8 * M, 4 * M, 4 * M, (size_t)4 * kDigits * 2048, (size_t)16, 8 * M, 8 * M, 8 * M,
+  for (size_t s : {8 * M, 8 * M, 4 * M, 4 * M, (size_t)4 * kDigits * 2048, (size_t)4 * kDigits, (size_t)16, 8 * M,
+                   8 * M, 8 * M,
                    8 * M, 8 * M, 4 * M, 8 * M, 8 * M, 4 * M, M, M})
     b += align256(s);
   return b;
@@ -144,32 +147,52 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(DevCtx C, SortBufs B
   for (int i = threadIdx.x; i < kDigits; i += blockDim.x) B.hist[(size_t)i * gridDim.x + blockIdx.x] = h[i];
 }
 
-// Exclusive scan of the digit-major histogram (kDigits x G <= 2^19 values)
-// in one block.
-__global__ void __launch_bounds__(1024) k_sort_scan(SortBufs B, int G) {
+// Exclusive scan of the digit-major histogram: one block per digit scans
+// that digit's G block counts in place (and writes the digit total to
+// dbase); a second small kernel turns the totals into digit bases.
+__global__ void __launch_bounds__(1024) k_sort_scan_digit(SortBufs B, int G) {
   if (!B.flag[0]) return;
-  __shared__ uint32_t part[1024];
-  int total = kDigits * G;
-  int per = (total + blockDim.x - 1) / blockDim.x;
-  int b = threadIdx.x * per, e = b + per < total ? b + per : total;
-  uint32_t s = 0;
-  for (int i = b; i < e; ++i) s += B.hist[i];
-  part[threadIdx.x] = s;
+  __shared__ uint32_t wsum[33];
+  const int d = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *h = B.hist + (size_t)d * G;
+  const int per = (G + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int b = threadIdx.x * per, e = b + per < G ? b + per : G;
+  uint32_t tsum = 0;
+  for (int i = b; i < e; ++i) tsum += h[i];
+  uint32_t inc = tsum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[warp] = inc;
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t run = 0;
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      uint32_t v = part[t];
-      part[t] = run;
-      run += v;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      const uint32_t t = wsum[w];
+      wsum[w] = run;
+      run += t;
     }
+    wsum[32] = run;
   }
   __syncthreads();
-  uint32_t run = part[threadIdx.x];
+  uint32_t run = wsum[warp] + inc - tsum;
   for (int i = b; i < e; ++i) {
-    uint32_t v = B.hist[i];
-    B.hist[i] = run;
+    const uint32_t v = h[i];
+    h[i] = run;
     run += v;
+  }
+  if (threadIdx.x == 0) B.dbase[d] = wsum[32];
+}
+
+__global__ void k_sort_scan_base(SortBufs B) {
+  if (!B.flag[0]) return;
+  if (threadIdx.x != 0) return;
+  uint32_t run = 0;
+  for (int d = 0; d < kDigits; ++d) {
+    const uint32_t t = B.dbase[d];
+    B.dbase[d] = run;
+    run += t;
   }
 }
 
@@ -183,7 +206,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(DevCtx C, SortBuf
   constexpr int W = kSortThreads / 32;
   __shared__ uint32_t base[kDigits];
   __shared__ uint32_t wcnt[W][kDigits];
-  for (int i = threadIdx.x; i < kDigits; i += blockDim.x) base[i] = B.hist[(size_t)i * gridDim.x + blockIdx.x];
+  for (int i = threadIdx.x; i < kDigits; i += blockDim.x)
+    base[i] = B.hist[(size_t)i * gridDim.x + blockIdx.x] + B.dbase[i];
   int64_t n = C.g->n_cells;
   int64_t b = (int64_t)blockIdx.x * chunk, e = b + chunk < n ? b + chunk : n;
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -283,7 +307,8 @@ void launch_morton(const DevCtx &C, cudaStream_t st, void *scratch, size_t scrat
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
     k_sort_hist<<<(unsigned int)G, kSortThreads, 0, st>>>(C, B, kin, shift, chunk);
-    k_sort_scan<<<1, 1024, 0, st>>>(B, (int)G);
+    k_sort_scan_digit<<<kDigits, 1024, 0, st>>>(B, (int)G);
+    k_sort_scan_base<<<1, 32, 0, st>>>(B);
     k_sort_scatter<<<(unsigned int)G, kSortThreads, 0, st>>>(C, B, kin, vin, kout, vout, shift, chunk);
     uint64_t *tk = kin; kin = kout; kout = tk;
     int32_t *tv = vin; vin = vout; vout = tv;
