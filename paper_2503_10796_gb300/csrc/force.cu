@@ -88,11 +88,23 @@ __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, con
       const float sy = __fsub_rn(o0.y, __fmul_rn(fdy, Lh));
       const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
                            (uint32_t)t.cx;
-      for (int dx = t.xlo; dx <= t.xhi; ++dx) {
-        const unsigned long long e = t.cnt[row + dx];
+      // the row's (up to) three table words and starts, loaded together
+      unsigned long long ew[3];
+      uint32_t sw[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int dx = q - 1;
+        const bool in = dx >= t.xlo && dx <= t.xhi;
+        ew[q] = in ? __ldg(t.cnt + row + dx) : 0ull;
+        sw[q] = in ? __ldg(t.start + row + dx) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int dx = q - 1;
+        const unsigned long long e = ew[q];
         if ((uint32_t)(e >> 32) != stamp) continue;
         const uint32_t cnt = (uint32_t)e & 0x7FFFFFFFu;
-        const int64_t j0 = t.start[row + dx];
+        const int64_t j0 = sw[q];
         const float fdx = (float)dx;
         const float sx = __fsub_rn(o0.x, __fmul_rn(fdx, Lh));
         for (uint32_t m = 0; m < cnt; ++m) {
@@ -208,7 +220,7 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
 }
 
 // fp64_only: leave FP32-path simulations to the queue kernel (force32.cu).
-__global__ void __launch_bounds__(kThreads) k_force(DevCtx C, int fp64_only) {
+__global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C, int fp64_only) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
   int sim = C.c.sim[p];
