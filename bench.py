@@ -77,7 +77,7 @@ def make_workload(name: str, precision: int, static: int):
         pops = [W.plain_fp64(precision=precision)]
         desc = dict(workload="plain_4096", agents=4096, side=160.0, diameters="U[8,12]")
     elif name == "uniform_200M":
-        pops = [W.uniform_fraction(200_000_000, precision=precision)]
+        pops = [W.uniform_fraction(200_000_000, precision=precision, sort_interval=10)]
         desc = dict(workload="uniform_200M", agents=200_000_000, volume_fraction=0.3)
     elif name == "batched_sweep_256":
         pops = W.batched_sweep(precision=precision)
@@ -240,6 +240,15 @@ def main():
             dist.barrier()
 
     pops, desc = make_workload(args.workload, args.precision, args.static)
+    if world > 1 and args.workload == "batched_sweep_256":
+        # independent simulations: shard them, no exchange on the data path
+        from paper_2503_10796_gb300 import sharding
+        _, pops = sharding.shard(pops, [p.n for p in pops], rank, world)
+        parallelism = f"{world} ranks, simulations sharded (longest-processing-time)"
+    elif world > 1:
+        parallelism = f"{world} independent replicas"
+    else:
+        parallelism = "1 GPU"
     total_agents = sum(max(p.n, p.params.capacity) for p in pops)
     # a dedicated stream: the library captures CUDA graphs on it, which the
     # legacy default stream does not allow
@@ -279,13 +288,17 @@ def main():
     ctx.sync()
     prof = ctx.get_profile()
     ctx.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     upd1 = sum(ctx.stats(s)["agent_updates"] for s in range(len(pops)))
     n_agents = sum(ctx.count(s) for s in range(len(pops)))
-    value = world * (upd1 - upd0) / (ms * 1e-3)
+    updates = float(upd1 - upd0)
+    if world > 1:
+        t = torch.tensor([ms, updates], device="cuda", dtype=torch.float64)
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tu = t[1:].clone()
+        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+        ms, updates = float(tm.item()), float(tu.item())
+    value = updates / (ms * 1e-3)
 
     # roofline of the force kernel
     f = prof["force"]
@@ -336,8 +349,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32-force/f64-position" if prec == 1 else "f64", "data": "synthetic",
-            "config": dict(desc, parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
-                           settle_iterations=args.settle),
+            "config": dict(desc, parallelism=parallelism, settle_iterations=args.settle),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_force",
                          "peak_source": f"{peak_kind} hbm_gbs", "force_ms_per_launch": force_ms,
