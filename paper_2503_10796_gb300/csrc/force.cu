@@ -579,6 +579,175 @@ __global__ void __launch_bounds__(kBT, 4) k_force32b(DevCtx C) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 path, row-queue variant: the direct loop's row-batched table loads,
+// one flattened loop over the candidates of the three boxes of a row (no
+// reloads), and the pairs that pass the FP32 filter queued per warp and
+// evaluated 32 at a time by the full warp (float-float overlap), results
+// added to the owner's accumulator in shared memory.
+// ---------------------------------------------------------------------------
+struct RowQueueSmem {
+  uint2 q[kBT / 32][kBQ];
+  float acc[4][kBT];
+};
+
+__device__ __forceinline__ void eval_rq(const DevCtx &C, RowQueueSmem &S, uint2 qe, int64_t block_p0, int warp) {
+  const int owner = warp * 32 + (int)(qe.y & 31u);
+  const int code = (int)(qe.y >> 8);
+  const uint32_t j = qe.x;
+  const int64_t po = block_p0 + owner;
+  const int sim = C.c.sim[po];
+  const SimConst &sc = C.sc[sim];
+  const SimState &s = C.ss[sim];
+  const float4 o0 = C.c.r0[po], o1 = C.c.r1[po];
+  const float4 q0 = C.c.r0[j], q1 = C.c.r1[j];
+  const float fdx = (float)(code % 3 - 1), fdy = (float)((code / 3) % 3 - 1), fdz = (float)(code / 9 - 1);
+  float xh, xl, yh, yl, zh, zl;
+  ff_diff(o0.x, o1.x, q0.x, q1.x, __fmul_rn(fdx, s.Lh), __fmul_rn(fdx, s.Ll), xh, xl);
+  ff_diff(o0.y, o1.y, q0.y, q1.y, __fmul_rn(fdy, s.Lh), __fmul_rn(fdy, s.Ll), yh, yl);
+  ff_diff(o0.z, o1.z, q0.z, q1.z, __fmul_rn(fdz, s.Lh), __fmul_rn(fdz, s.Ll), zh, zl);
+  float p0, e0, p1, e1, p2, e2;
+  two_prod(xh, xh, p0, e0);
+  e0 = __fmaf_rn(__fmul_rn(2.f, xh), xl, e0);
+  two_prod(yh, yh, p1, e1);
+  e1 = __fmaf_rn(__fmul_rn(2.f, yh), yl, e1);
+  two_prod(zh, zh, p2, e2);
+  e2 = __fmaf_rn(__fmul_rn(2.f, zh), zl, e2);
+  float Sa, Sea, Sb, Seb;
+  two_sum(p0, p1, Sa, Sea);
+  two_sum(Sa, p2, Sb, Seb);
+  const float sl = __fadd_rn(__fadd_rn(Sea, Seb), __fadd_rn(__fadd_rn(e0, e1), e2));
+  float sh, sll;
+  fast_two_sum(Sb, sl, sh, sll);
+  float Rh, Rl;
+  two_sum(o0.w, q0.w, Rh, Rl);
+  Rl = __fadd_rn(Rl, __fadd_rn(o1.w, q1.w));
+  float Qh, Ql;
+  two_prod(Rh, Rh, Qh, Ql);
+  Ql = __fmaf_rn(__fmul_rn(2.f, Rh), Rl, Ql);
+  const float num = __fadd_rn(__fsub_rn(Qh, sh), __fsub_rn(Ql, sll));
+  const float dist = sqrtf(sh);
+  float del;
+  if (fabsf(num) < kTinyNum) {
+    const double d64 = exact_delta(C, C.c.slot[po], C.c.slot[j]);
+    if (!(d64 > 0.0)) return;
+    del = (float)d64;
+  } else {
+    if (!(num > 0.f)) return;
+    del = __fdividef(num, __fadd_rn(Rh, dist));
+  }
+  const float rr = __fdividef(__fmul_rn(o0.w, q0.w), Rh);
+  const float fn = __fsub_rn(__fmul_rn(sc.kf, del), __fmul_rn(sc.gammaf, sqrtf(__fmul_rn(rr, del))));
+  if (fn != 0.f) atomicAdd(&S.acc[3][owner], 1.0f);
+  if (dist > 0.f) {
+    const float f = __fdividef(fn, dist);
+    atomicAdd(&S.acc[0][owner], __fmul_rn(f, xh));
+    atomicAdd(&S.acc[1][owner], __fmul_rn(f, yh));
+    atomicAdd(&S.acc[2][owner], __fmul_rn(f, zh));
+  }
+}
+
+__global__ void __launch_bounds__(kBT, 4) k_force32rq(DevCtx C) {
+  __shared__ RowQueueSmem S;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const int64_t p0 = (int64_t)blockIdx.x * kBT;
+  const int64_t p = p0 + tid;
+  const int64_t ncell = C.g->n_cells;
+  if (p0 >= ncell) return;
+  const uint32_t stamp = C.g->stamp;
+  bool active = p < ncell;
+  const int sim = active ? C.c.sim[p] : 0;
+  const SimConst &sc = C.sc[sim];
+  const SimState &s = C.ss[sim];
+  if (active && (!s.valid || sc.precision != BDM_PREC_FP32_FORCE)) active = false;
+  int64_t cx = 0, cy = 0, cz = 0;
+  if (active) {
+    unpack_coords(C.c.pkey[p], cx, cy, cz);
+    const bool st = is_static_cell(C, sc, s, p, cx, cy, cz, stamp);
+    C.c.stat[p] = st ? 1 : 0;
+    if (st) active = false;
+  }
+  S.acc[0][tid] = 0.f; S.acc[1][tid] = 0.f; S.acc[2][tid] = 0.f; S.acc[3][tid] = 0.f;
+  __syncwarp();
+  if (!__any_sync(FULL, active)) return;
+  const float4 o0 = active ? C.c.r0[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float Lh = active ? s.Lh : 0.f, marg = active ? s.marg : 0.f;
+  Stencil t;
+  if (active) t = make_stencil(C, sc, s, cx, cy, cz);
+  const float sx0 = __fadd_rn(o0.x, Lh), sx1 = o0.x, sx2 = __fsub_rn(o0.x, Lh);
+  int qn = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int r = 0; r < 9; ++r) {
+    const int dy = r % 3 - 1, dz = r / 3 - 1;
+    uint32_t c[3] = {0u, 0u, 0u}, sw[3] = {0u, 0u, 0u};
+    float sy = 0.f, sz = 0.f;
+    if (active && dy >= t.ylo && dy <= t.yhi && dz >= t.zlo && dz <= t.zhi) {
+      const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
+                           (uint32_t)t.cx;
+      unsigned long long ew[3];
+#pragma unroll
+      for (int qq = 0; qq < 3; ++qq) {
+        const int dx = qq - 1;
+        const bool in = dx >= t.xlo && dx <= t.xhi;
+        ew[qq] = in ? __ldg(t.cnt + row + dx) : 0ull;
+        sw[qq] = in ? __ldg(t.start + row + dx) : 0u;
+      }
+#pragma unroll
+      for (int qq = 0; qq < 3; ++qq) c[qq] = ((uint32_t)(ew[qq] >> 32) == stamp) ? ((uint32_t)ew[qq] & 0x7FFFFFFFu) : 0u;
+      sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh));
+      sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
+    }
+    const uint32_t total = c[0] + c[1] + c[2];
+    const uint32_t kmax = __reduce_max_sync(FULL, total);
+    for (uint32_t k = 0; k < kmax; ++k) {
+      bool hit = false;
+      uint32_t j = 0;
+      int code = 0;
+      if (k < total) {
+        const int qq = k < c[0] ? 0 : (k < c[0] + c[1] ? 1 : 2);
+        const uint32_t m = qq == 0 ? k : (qq == 1 ? k - c[0] : k - c[0] - c[1]);
+        j = sw[qq] + m;
+        code = (dz + 1) * 9 + (dy + 1) * 3 + qq;
+        if ((int64_t)j != p) {
+          const float4 qv = C.c.r0[j];
+          const float sx = qq == 0 ? sx0 : (qq == 1 ? sx1 : sx2);
+          const float ddx = __fsub_rn(sx, qv.x), ddy = __fsub_rn(sy, qv.y), ddz = __fsub_rn(sz, qv.z);
+          const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+          const float Rm = __fadd_rn(__fadd_rn(o0.w, qv.w), marg);
+          hit = s2 < __fmul_rn(Rm, Rm);
+        }
+      }
+      const unsigned bal = __ballot_sync(FULL, hit);
+      if (bal) {
+        if (hit) S.q[warp][qn + __popc(bal & lt)] = make_uint2(j, (uint32_t)lane | ((uint32_t)code << 8));
+        qn += __popc(bal);
+        if (qn >= 32) {
+          __syncwarp();
+          eval_rq(C, S, S.q[warp][lane], p0, warp);
+          __syncwarp();
+          if (lane < qn - 32) S.q[warp][lane] = S.q[warp][32 + lane];
+          __syncwarp();
+          qn -= 32;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (lane < qn) eval_rq(C, S, S.q[warp][lane], p0, warp);
+  __syncwarp();
+  if (active) {
+    C.c.f32[p] = make_float4(S.acc[0][tid], S.acc[1][tid], S.acc[2][tid], 0.f);
+    const float nz = S.acc[3][tid];
+    C.c.nnz[p] = (uint8_t)(nz > 255.f ? 255u : (unsigned)nz);
+  }
+}
+
+void launch_force32rq(const DevCtx &C, cudaStream_t st) {
+  const unsigned int nb = (unsigned int)((C.total_slots + kBT - 1) / kBT);
+  k_force32rq<<<nb, kBT, 0, st>>>(C);
+}
+
 void launch_force32b(const DevCtx &C, cudaStream_t st) {
   cudaFuncSetAttribute(k_force32b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BlockStage));
   const unsigned int nb = (unsigned int)((C.total_slots + kBT - 1) / kBT);
@@ -588,9 +757,10 @@ void launch_force32b(const DevCtx &C, cudaStream_t st) {
 static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
 void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64) {
-  if (variant == 2 || variant == 3) {
+  if (variant == 2 || variant == 3 || variant == 4) {
     if (has_fp32) {
       if (variant == 3) launch_force32b(C, st);
+      else if (variant == 4) launch_force32rq(C, st);
       else launch_force32q(C, st);
     }
     if (has_fp64) k_force<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 1);

@@ -141,25 +141,21 @@ __global__ void __launch_bounds__(kThreads) k_bbox(DevCtx C, int64_t chunk) {
 }
 
 // ---------------------------------------------------------------------------
-// Grid parameters of every simulation (one thread): origin, box length,
-// boxes per axis (floor((max - o) / L) + 1 in IEEE FP64), table fit, the
-// float-float constants of the FP32 path and the cell ranges.
+// Grid parameters of every simulation: origin, box length, boxes per axis
+// (floor((max - o) / L) + 1 in IEEE FP64), table fit, the float-float
+// constants of the FP32 path and the cell ranges.
 // ---------------------------------------------------------------------------
 __device__ void split_pos(double v, float &h, float &l) { split_ff(v, h, l); }
 
+// One thread per simulation; thread 0 then lays out the cell ranges.
 __global__ void k_params(DevCtx C, int32_t step) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Globals *g = C.g;
-  g->stamp += 1u;
-  int64_t cells = 0;
-  for (int k = 0; k < C.n_sims; ++k) {
+  for (int k = threadIdx.x; k < C.n_sims; k += blockDim.x) {
     int s = C.order[k];
-    if (s < 0) break;
+    if (s < 0) continue;
     const SimConst &sc = C.sc[s];
     SimState &st = C.ss[s];
-    st.cell_base = cells;
     st.ncell = st.n;
-    cells += st.n;
     st.valid = 0;
     st.same_grid = 0;
     if (step) {
@@ -216,7 +212,18 @@ __global__ void k_params(DevCtx C, int32_t step) {
     for (int a = 0; a < 3; ++a) { st.bmin[a] = ~0ull; st.bmax[a] = 0ull; }
     st.dmax = 0ull;
   }
-  g->n_cells = cells;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    g->stamp += 1u;
+    int64_t cells = 0;
+    for (int k = 0; k < C.n_sims; ++k) {
+      const int s = C.order[k];
+      if (s < 0) break;
+      C.ss[s].cell_base = cells;
+      cells += C.ss[s].n;
+    }
+    g->n_cells = cells;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -447,7 +454,7 @@ void launch_bbox(const DevCtx &C, cudaStream_t st) {
   k_bbox<<<(unsigned int)G, kThreads, 0, st>>>(C, chunk);
 }
 
-void launch_params(const DevCtx &C, cudaStream_t st, int step) { k_params<<<1, 32, 0, st>>>(C, step); }
+void launch_params(const DevCtx &C, cudaStream_t st, int step) { k_params<<<1, 256, 0, st>>>(C, step); }
 
 void launch_count(const DevCtx &C, cudaStream_t st, int step) {
   k_count<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, step ? C.a.pkey_hist : nullptr);
