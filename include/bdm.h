@@ -119,7 +119,10 @@ int bdm_set_agents(bdm_ctx* ctx, int32_t sim, int64_t n, const double* xyz,
  * agents set), BDM_E_NOMEM (box table growth failed), BDM_E_CUDA. */
 int bdm_step(bdm_ctx* ctx, int32_t n_iterations);
 
-/* Wait for the context's stream and report latched device errors. */
+/* Wait for the context's stream and report latched device errors:
+ * BDM_E_CAPACITY when a grid outgrew its box table or a box held more than
+ * 1023 agents (that iteration's results are then undefined),
+ * BDM_E_NONFINITE, BDM_E_TIMEOUT. */
 int bdm_sync(bdm_ctx* ctx);
 
 /* Copy the agents of `sim` out in caller-ID order: xyz (cap x 3) and

@@ -104,10 +104,26 @@ struct Cells {                // cell arrays (per cell position)
   uint8_t *stat;
 };
 
+// Box table: one 64-bit word per box of the bounding grid,
+//   stamp (21 bits) << 43 | dirty << 42 | count (10 bits) << 32 | first cell.
+// A box is empty unless its stamp equals the current build's; the host
+// clears the table before the stamp counter would wrap.
 struct Table {
-  unsigned long long *cnt;    // stamp << 32 | dirty << 31 | count
-  uint32_t *start;            // first cell position of the box
+  unsigned long long *e;
 };
+
+constexpr int kStampBits = 21;
+constexpr uint32_t kStampMask = (1u << kStampBits) - 1u;
+constexpr uint32_t kMaxBoxCount = 1023u;
+
+__host__ __device__ __forceinline__ uint32_t ent_stamp(unsigned long long e) { return (uint32_t)(e >> 43); }
+__host__ __device__ __forceinline__ bool ent_dirty(unsigned long long e) { return ((e >> 42) & 1ull) != 0; }
+__host__ __device__ __forceinline__ uint32_t ent_count(unsigned long long e) { return (uint32_t)(e >> 32) & 0x3FFu; }
+__host__ __device__ __forceinline__ uint32_t ent_start(unsigned long long e) { return (uint32_t)e; }
+// agents of a box in the current build (0 for a box of an older build)
+__host__ __device__ __forceinline__ uint32_t ent_live(unsigned long long e, uint32_t stamp) {
+  return ent_stamp(e) == stamp ? ent_count(e) : 0u;
+}
 
 struct DevCtx {
   SimConst *sc;
@@ -251,8 +267,8 @@ __device__ __forceinline__ bool is_static_cell(const DevCtx &C, const SimConst &
       for (int dx = -1; dx <= 1; ++dx) {
         int64_t x = cx + dx;
         if (x < 0 || x >= s.dims[0]) continue;
-        unsigned long long e = C.tab.cnt[sc.table_base + linear_box(s, x, y, z)];
-        if ((uint32_t)(e >> 32) == stamp && (e & 0x80000000ull)) return false;
+        const unsigned long long e = C.tab.e[sc.table_base + linear_box(s, x, y, z)];
+        if (ent_stamp(e) == stamp && ent_dirty(e)) return false;
       }
     }
   }

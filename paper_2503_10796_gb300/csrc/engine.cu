@@ -46,6 +46,7 @@ struct bdm_ctx {
   DevCtx D{};
   uint32_t *d_partial = nullptr;
   int64_t table_entries = 0;
+  int64_t builds = 0;        // grid builds since the box table was last cleared
   void *d_sort = nullptr;
   size_t sort_bytes = 0;
   int sort_key_bits = 0;
@@ -306,24 +307,20 @@ int ensure_table(bdm_ctx *c, int iters, bool *resized) {
     size_t freeb = 0, totb = 0;
     cudaMemGetInfo(&freeb, &totb);
     int64_t want = std::max<int64_t>(total, c->table_entries * 5 / 4);
-    size_t bytes = (size_t)want * 12;
-    size_t have = (size_t)c->table_entries * 12;
+    size_t bytes = (size_t)want * 8;
+    size_t have = (size_t)c->table_entries * 8;
     if (bytes > (size_t)((freeb + have) * 0.85)) {
       want = total;
-      bytes = (size_t)want * 12;
+      bytes = (size_t)want * 8;
       if (bytes > (size_t)((freeb + have) * 0.85))
         return fail(c, BDM_E_CAPACITY, "box table does not fit in device memory");
     }
-    dfree(c, c->D.tab.cnt);
-    dfree(c, c->D.tab.start);
-    c->D.tab.cnt = nullptr;
-    c->D.tab.start = nullptr;
+    dfree(c, c->D.tab.e);
+    c->D.tab.e = nullptr;
     c->table_entries = 0;
-    int rc = dalloc(c, &c->D.tab.cnt, (size_t)want, "box table");
+    int rc = dalloc(c, &c->D.tab.e, (size_t)want, "box table");
     if (rc) return rc;
-    rc = dalloc(c, &c->D.tab.start, (size_t)want, "box table starts");
-    if (rc) return rc;
-    cudaMemsetAsync(c->D.tab.cnt, 0, sizeof(unsigned long long) * (size_t)want, c->stream);
+    cudaMemsetAsync(c->D.tab.e, 0, sizeof(unsigned long long) * (size_t)want, c->stream);
     c->table_entries = want;
     changed = true;
   }
@@ -336,6 +333,20 @@ int ensure_table(bdm_ctx *c, int iters, bool *resized) {
 }
 
 
+// Table words carry a 21-bit stamp; before the build counter would reach it,
+// clear the table and restart the counter (both on the stream, so CUDA
+// graphs replayed later see the cleared state).
+int reserve_builds(bdm_ctx *c, int64_t n) {
+  if (c->builds + n + 2 >= (int64_t)kStampMask) {
+    cudaError_t e = cudaMemsetAsync(c->D.tab.e, 0, sizeof(unsigned long long) * (size_t)c->table_entries, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->D.g->stamp, 0, sizeof(uint32_t), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "clearing the box table");
+    c->builds = 0;
+  }
+  c->builds += n;
+  return BDM_OK;
+}
+
 int latched_error(bdm_ctx *c) {
   uint32_t bits = 0;
   cudaError_t e = cudaMemcpyAsync(&bits, &c->D.g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
@@ -344,10 +355,11 @@ int latched_error(bdm_ctx *c) {
   if (!bits) return BDM_OK;
   cudaMemsetAsync(&c->D.g->err, 0, sizeof(uint32_t), c->stream);
   cudaStreamSynchronize(c->stream);
+  if (bits & ERR_TABLE)
+    return fail(c, BDM_E_CAPACITY, "grid outgrew its box table region, or a box held more than 1023 agents");
+  if (bits & ERR_COORD) return fail(c, BDM_E_CAPACITY, "box coordinate beyond 2^21 per axis");
   if (bits & ERR_TIMEOUT) return fail(c, BDM_E_TIMEOUT, "a bounded device retry loop ran out");
   if (bits & ERR_NONFINITE) return fail(c, BDM_E_NONFINITE, "a position, force or grid value became non-finite");
-  if (bits & ERR_TABLE) return fail(c, BDM_E_CAPACITY, "grid outgrew its box table region");
-  if (bits & ERR_COORD) return fail(c, BDM_E_CAPACITY, "box coordinate beyond 2^21 per axis");
   return BDM_OK;  // ERR_CAPACITY (division stopped at the cap) is informational
 }
 
@@ -370,6 +382,8 @@ int query_grid(bdm_ctx *c, bool with_cells, const std::vector<double> *boxes) {
   int rc = ensure_table(c, 1, &resized);
   if (rc) return rc;
   if (resized) c->graph_dirty = true;
+  rc = reserve_builds(c, 1);
+  if (rc) return rc;
   if (boxes) {
     // temporary box lengths for radius queries
     std::vector<SimConst> tmp = c->h_sc;
@@ -469,6 +483,10 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   cudaMemsetAsync(D.ss, 0, sizeof(SimState) * (size_t)n_sims, c->stream);
   cudaMemsetAsync(D.g, 0, sizeof(Globals), c->stream);
   cudaMemsetAsync(D.order, 0xff, sizeof(int32_t) * (size_t)n_sims, c->stream);
+  // cells that a failed build leaves unplaced still hold valid indices
+  cudaMemsetAsync(D.c.slot, 0, sizeof(int32_t) * M, c->stream);
+  cudaMemsetAsync(D.c.sim, 0, sizeof(int32_t) * M, c->stream);
+  cudaMemsetAsync(D.c.pkey, 0, sizeof(uint64_t) * M, c->stream);
   std::vector<SimState> ss0(n_sims);
   memset(ss0.data(), 0, sizeof(SimState) * n_sims);
   for (auto &s : ss0) {
@@ -576,6 +594,8 @@ int bdm_step(bdm_ctx *c, int32_t n_iterations) {
     int rc = ensure_table(c, chunk, &resized);
     if (rc) return rc;
     if (resized) c->graph_dirty = true;
+    rc = reserve_builds(c, chunk);
+    if (rc) return rc;
     if (c->profiling) {
       for (int i = 0; i < chunk; ++i) launch_iteration(c);
     } else {
@@ -685,6 +705,9 @@ int bdm_neighbors(bdm_ctx *c, int32_t sim, double radius, int64_t cap, int64_t *
     if (!r2) r2 = dalloc(c, &c->D.q.pkey, M, "query keys");
     if (!r2) r2 = dalloc(c, &c->D.q.r64, M, "query records");
     if (r2) return r2;
+    cudaMemsetAsync(c->D.q.slot, 0, sizeof(int32_t) * M, c->stream);
+    cudaMemsetAsync(c->D.q.sim, 0, sizeof(int32_t) * M, c->stream);
+    cudaMemsetAsync(c->D.q.pkey, 0, sizeof(uint64_t) * M, c->stream);
     c->graph_dirty = true;
   }
   // Box length for the query: the step's, or the radius when larger.

@@ -48,8 +48,7 @@ __device__ __noinline__ double exact_delta(const DevCtx &C, int32_t si, int32_t 
 struct Stencil {
   int xlo, xhi, ylo, yhi, zlo, zhi;
   int cx, cy, cz, d0, d1;
-  const unsigned long long *cnt;  // this simulation's table words
-  const uint32_t *start;          // and first cells
+  const unsigned long long *e;    // this simulation's table words
 };
 
 __device__ __forceinline__ Stencil make_stencil(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t cx,
@@ -61,8 +60,7 @@ __device__ __forceinline__ Stencil make_stencil(const DevCtx &C, const SimConst 
   t.xlo = t.cx > 0 ? -1 : 0; t.xhi = t.cx < t.d0 - 1 ? 1 : 0;
   t.ylo = t.cy > 0 ? -1 : 0; t.yhi = t.cy < t.d1 - 1 ? 1 : 0;
   t.zlo = t.cz > 0 ? -1 : 0; t.zhi = t.cz < d2 - 1 ? 1 : 0;
-  t.cnt = C.tab.cnt + sc.table_base;
-  t.start = C.tab.start + sc.table_base;
+  t.e = C.tab.e + sc.table_base;
   return t;
 }
 
@@ -90,21 +88,19 @@ __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, con
                            (uint32_t)t.cx;
       // the row's (up to) three table words and starts, loaded together
       unsigned long long ew[3];
-      uint32_t sw[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const int dx = q - 1;
         const bool in = dx >= t.xlo && dx <= t.xhi;
-        ew[q] = in ? __ldg(t.cnt + row + dx) : 0ull;
-        sw[q] = in ? __ldg(t.start + row + dx) : 0u;
+        ew[q] = in ? __ldg(t.e + row + dx) : 0ull;
       }
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         const int dx = q - 1;
         const unsigned long long e = ew[q];
-        if ((uint32_t)(e >> 32) != stamp) continue;
-        const uint32_t cnt = (uint32_t)e & 0x7FFFFFFFu;
-        const int64_t j0 = sw[q];
+        const uint32_t cnt = ent_live(e, stamp);
+        if (!cnt) continue;
+        const int64_t j0 = ent_start(e);
         const float fdx = (float)dx;
         const float sx = __fsub_rn(o0.x, __fmul_rn(fdx, Lh));
         for (uint32_t m = 0; m < cnt; ++m) {
@@ -186,10 +182,10 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
       const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
                            (uint32_t)t.cx;
       for (int dx = t.xlo; dx <= t.xhi; ++dx) {
-        const unsigned long long e = t.cnt[row + dx];
-        if ((uint32_t)(e >> 32) != stamp) continue;
-        const uint32_t cnt = (uint32_t)e & 0x7FFFFFFFu;
-        const int64_t j0 = t.start[row + dx];
+        const unsigned long long e = t.e[row + dx];
+        const uint32_t cnt = ent_live(e, stamp);
+        if (!cnt) continue;
+        const int64_t j0 = ent_start(e);
         for (uint32_t m = 0; m < cnt; ++m) {
           const int64_t j = j0 + m;
           if (j == p) continue;
@@ -230,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C, int fp64_only) 
   if (fp64_only && sc.precision != BDM_PREC_FP64) return;
   int64_t cx, cy, cz;
   unpack_coords(C.c.pkey[p], cx, cy, cz);
-  uint32_t stamp = C.g->stamp;
+  uint32_t stamp = C.g->stamp & kStampMask;
   bool st = is_static_cell(C, sc, s, p, cx, cy, cz, stamp);
   C.c.stat[p] = st ? 1 : 0;
   if (st) return;
@@ -393,7 +389,7 @@ __global__ void __launch_bounds__(kBT, 4) k_force32b(DevCtx C) {
   const int64_t p = p0 + tid;
   const int64_t ncell = C.g->n_cells;
   if (p0 >= ncell) return;
-  const uint32_t stamp = C.g->stamp;
+  const uint32_t stamp = C.g->stamp & kStampMask;
   bool active = p < ncell;
   const int sim = active ? C.c.sim[p] : 0;
   const SimConst &sc = C.sc[sim];
@@ -448,11 +444,11 @@ __global__ void __launch_bounds__(kBT, 4) k_force32b(DevCtx C) {
       const int bz_ = b / irxy, rem = b - bz_ * irxy, by_ = rem / irx, bx_ = rem - by_ * irx;
       const int64_t bx = lox + bx_, by = loy + by_, bz = loz + bz_;
       const int64_t idx = scu.table_base + bx + su.dims[0] * (by + su.dims[1] * bz);
-      const unsigned long long e = C.tab.cnt[idx];
-      uint32_t c = ((uint32_t)(e >> 32) == stamp) ? (uint32_t)(e & 0x7FFFFFFFull) : 0u;
+      const unsigned long long e = C.tab.e[idx];
+      uint32_t c = ent_live(e, stamp);
       if (c > (uint32_t)kBRK) { over = true; c = 0; }
       S.rcnt[b] = (uint16_t)c;
-      S.rstart[b] = c ? C.tab.start[idx] : 0u;
+      S.rstart[b] = c ? ent_start(e) : 0u;
     }
     over = __syncthreads_or(over);
     // exclusive prefix over the region's counts: 4 boxes per thread
@@ -655,7 +651,7 @@ __global__ void __launch_bounds__(kBT, 4) k_force32rq(DevCtx C) {
   const int64_t p = p0 + tid;
   const int64_t ncell = C.g->n_cells;
   if (p0 >= ncell) return;
-  const uint32_t stamp = C.g->stamp;
+  const uint32_t stamp = C.g->stamp & kStampMask;
   bool active = p < ncell;
   const int sim = active ? C.c.sim[p] : 0;
   const SimConst &sc = C.sc[sim];
@@ -690,11 +686,13 @@ __global__ void __launch_bounds__(kBT, 4) k_force32rq(DevCtx C) {
       for (int qq = 0; qq < 3; ++qq) {
         const int dx = qq - 1;
         const bool in = dx >= t.xlo && dx <= t.xhi;
-        ew[qq] = in ? __ldg(t.cnt + row + dx) : 0ull;
-        sw[qq] = in ? __ldg(t.start + row + dx) : 0u;
+        ew[qq] = in ? __ldg(t.e + row + dx) : 0ull;
       }
 #pragma unroll
-      for (int qq = 0; qq < 3; ++qq) c[qq] = ((uint32_t)(ew[qq] >> 32) == stamp) ? ((uint32_t)ew[qq] & 0x7FFFFFFFu) : 0u;
+      for (int qq = 0; qq < 3; ++qq) {
+        c[qq] = ent_live(ew[qq], stamp);
+        sw[qq] = ent_start(ew[qq]);
+      }
       sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh));
       sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
     }

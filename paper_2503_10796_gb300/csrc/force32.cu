@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kFT, 3) k_force32q(DevCtx C) {
   const int64_t p0 = (int64_t)blockIdx.x * kFT;
   const int64_t p = p0 + tid;
   const int64_t ncell = C.g->n_cells;
-  const uint32_t stamp = C.g->stamp;
+  const uint32_t stamp = C.g->stamp & kStampMask;
   bool active = p < ncell;
   int sim = active ? C.c.sim[p] : 0;
   const SimConst &sc = C.sc[sim];
@@ -146,10 +146,10 @@ __global__ void __launch_bounds__(kFT, 3) k_force32q(DevCtx C) {
         for (int dx = -1; dx <= 1; ++dx) {
           const int64_t x = cx + dx;
           if (rowok && x >= 0 && x < d0) {
-            unsigned long long e = C.tab.cnt[row + dx];
-            uint32_t cnt = ((uint32_t)(e >> 32) == stamp) ? (uint32_t)(e & 0x7FFFFFFFull) : 0u;
+            const unsigned long long e = C.tab.e[row + dx];
+            uint32_t cnt = ent_live(e, stamp);
             if (cnt) {
-              uint32_t st0 = C.tab.start[row + dx];
+              uint32_t st0 = ent_start(e);
               const int code = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
               S.ent[m * kFT + tid] = make_uint2(st0, (cnt & 0xFFFFFFu) | ((uint32_t)code << 24));
               ++m;

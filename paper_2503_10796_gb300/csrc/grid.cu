@@ -237,12 +237,19 @@ __device__ __forceinline__ uint32_t tab_add(unsigned long long *e, uint32_t stam
                                             Globals *g) {
   unsigned long long old = *(volatile unsigned long long *)e;
   for (int tries = 0; tries < (1 << 22); ++tries) {
-    unsigned long long assumed = old;
-    uint32_t st = (uint32_t)(assumed >> 32), lo = (uint32_t)assumed;
-    uint32_t cnt = (st == stamp) ? (lo & 0x7FFFFFFFu) : 0u;
-    uint32_t dir = (st == stamp) ? (lo & 0x80000000u) : 0u;
-    uint32_t nlo = (cnt + count) | dir | (dirty ? 0x80000000u : 0u);
-    unsigned long long nv = ((unsigned long long)stamp << 32) | nlo;
+    const unsigned long long assumed = old;
+    const bool live = ent_stamp(assumed) == stamp;
+    const uint32_t cnt = live ? ent_count(assumed) : 0u;
+    const bool dir = (live && ent_dirty(assumed)) || dirty;
+    uint32_t ncnt = cnt + count;
+    if (ncnt > kMaxBoxCount) {
+      // more agents in one box than the table word holds: the step is
+      // invalid (latched error); placement skips the agents beyond it
+      set_err(g, ERR_TABLE);
+      ncnt = kMaxBoxCount;
+    }
+    const unsigned long long nv = ((unsigned long long)stamp << 43) | ((unsigned long long)(dir ? 1u : 0u) << 42) |
+                                  ((unsigned long long)ncnt << 32) | (live ? (assumed & 0xFFFFFFFFull) : 0ull);
     if (nv == assumed) return cnt;
     old = atomicCAS(e, assumed, nv);
     if (old == assumed) return cnt;
@@ -278,7 +285,7 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
     hist[slot] = pk;
   }
   bool changed = hist && (C.a.flags[slot] & FLAG_CHANGED) != 0;
-  uint32_t stamp = C.g->stamp;
+  const uint32_t stamp = C.g->stamp & kStampMask;
   int64_t idx = sc.table_base + linear_box(s, c[0], c[1], c[2]);
   // Lanes of a warp that share a box add their count with one atomic
   // (neighbouring slots mostly share boxes once the storage is sorted).
@@ -288,14 +295,14 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
   const int leader = __ffs(peers) - 1;
   const unsigned dirty_any = __reduce_or_sync(peers, changed ? 1u : 0u);
   uint32_t base = 0;
-  if (lane == leader) base = tab_add(&C.tab.cnt[idx], stamp, dirty_any != 0, (uint32_t)__popc(peers), C.g);
+  if (lane == leader) base = tab_add(&C.tab.e[idx], stamp, dirty_any != 0, (uint32_t)__popc(peers), C.g);
   base = __shfl_sync(peers, base, leader);
   C.a.rank[slot] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
   if (changed && s.same_grid && pk_prev != pk) {
     int64_t px, py, pz;
     unpack_coords(pk_prev, px, py, pz);
     if (px < s.dims[0] && py < s.dims[1] && pz < s.dims[2])
-      tab_add(&C.tab.cnt[sc.table_base + linear_box(s, px, py, pz)], stamp, true, 0u, C.g);
+      tab_add(&C.tab.e[sc.table_base + linear_box(s, px, py, pz)], stamp, true, 0u, C.g);
   }
 }
 
@@ -316,7 +323,7 @@ __device__ __forceinline__ uint32_t leader_value(const DevCtx &C, int64_t slot, 
   int64_t cx, cy, cz;
   unpack_coords(C.a.pkey[slot], cx, cy, cz);
   idx = sc.table_base + linear_box(s, cx, cy, cz);
-  return (uint32_t)(C.tab.cnt[idx] & 0x7FFFFFFFull);
+  return ent_count(C.tab.e[idx]);
 }
 
 __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sh) {
@@ -393,7 +400,7 @@ __global__ void __launch_bounds__(1024) k_scan_down(DevCtx C, int64_t chunk, con
     uint32_t v = slot < end ? leader_value(C, slot, idx) : 0u;
     uint32_t total;
     uint32_t ex = block_exscan_u32(v, sh, &total);
-    if (idx >= 0) C.tab.start[idx] = base + ex;
+    if (idx >= 0) C.tab.e[idx] = (C.tab.e[idx] & 0xFFFFFFFF00000000ull) | (unsigned long long)(base + ex);
     base += total;
   }
 }
@@ -412,7 +419,10 @@ __global__ void __launch_bounds__(kThreads) k_place(DevCtx C, Cells cells, int f
   int64_t c[3];
   unpack_coords(pk, c[0], c[1], c[2]);
   int64_t idx = sc.table_base + linear_box(s, c[0], c[1], c[2]);
-  int64_t p = (int64_t)C.tab.start[idx] + C.a.rank[slot];
+  const unsigned long long e = C.tab.e[idx];
+  const uint32_t rank = C.a.rank[slot];
+  if (rank >= ent_count(e)) return;  // box overflow (error latched by the count)
+  int64_t p = (int64_t)ent_start(e) + rank;
   cells.slot[p] = (int32_t)slot;
   cells.sim[p] = sim;
   cells.pkey[p] = pk;

@@ -51,9 +51,8 @@ constexpr size_t oCNnz = oCFlag + up(kM);
 constexpr size_t oCStat = oCNnz + up(kM);
 constexpr size_t oCF32 = oCStat + up(kM);
 constexpr size_t oCF64 = oCF32 + up(16 * kM);
-constexpr size_t oTabCnt = oCF64 + up(32 * kM);
-constexpr size_t oTabStart = oTabCnt + up(8 * (size_t)kMaxBoxes);
-constexpr size_t kBytes = oTabStart + up(4 * (size_t)kMaxBoxes);
+constexpr size_t oTab = oCF64 + up(32 * kM);
+constexpr size_t kBytes = oTab + up(8 * (size_t)kMaxBoxes);
 
 // The working memory: about 5 MB per GPU.
 static __device__ __align__(256) unsigned char g_scratch[kBytes];
@@ -114,8 +113,7 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   D.c.r0 = at<float4>(base, oCR0); D.c.r1 = at<float4>(base, oCR1); D.c.r64 = at<double4_32a>(base, oCR64);
   D.c.flag = at<uint8_t>(base, oCFlag); D.c.nnz = at<uint8_t>(base, oCNnz); D.c.stat = at<uint8_t>(base, oCStat);
   D.c.f32 = at<float4>(base, oCF32); D.c.f64 = at<double4_32a>(base, oCF64);
-  D.tab.cnt = at<unsigned long long>(base, oTabCnt);
-  D.tab.start = at<uint32_t>(base, oTabStart);
+  D.tab.e = at<unsigned long long>(base, oTab);
   uint32_t *partial = at<uint32_t>(base, oPart);
 
   // Constants and cleared state: every call starts from zero, because the
@@ -137,7 +135,7 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   if (e == cudaSuccess) e = cudaMemcpyAsync(D.ss, &ss, sizeof(ss), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(D.order, &order0, sizeof(order0), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(D.g, 0, sizeof(Globals), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(D.tab.cnt, 0, sizeof(unsigned long long) * (size_t)kMaxBoxes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(D.tab.e, 0, sizeof(unsigned long long) * (size_t)kMaxBoxes, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return BDM_E_CUDA;

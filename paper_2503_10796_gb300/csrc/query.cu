@@ -61,7 +61,7 @@ __global__ void k_pairs(DevCtx C, int sim, int64_t cell_base, int64_t n, double 
   double4_32a o = Q.r64[p];
   int64_t cx, cy, cz;
   unpack_coords(Q.pkey[p], cx, cy, cz);
-  uint32_t stamp = C.g->stamp;
+  uint32_t stamp = C.g->stamp & kStampMask;
   int64_t cnt = 0;
   int64_t off = kWrite ? offsets[id] : 0;
   for (int dz = -1; dz <= 1; ++dz) {
@@ -74,10 +74,10 @@ __global__ void k_pairs(DevCtx C, int sim, int64_t cell_base, int64_t n, double 
         int64_t x = cx + dx;
         if (x < 0 || x >= s.dims[0]) continue;
         int64_t idx = sc.table_base + linear_box(s, x, y, z);
-        unsigned long long e = C.tab.cnt[idx];
-        if ((uint32_t)(e >> 32) != stamp) continue;
-        uint32_t c = (uint32_t)(e & 0x7FFFFFFFull);
-        int64_t start = C.tab.start[idx];
+        const unsigned long long e = C.tab.e[idx];
+        const uint32_t c = ent_live(e, stamp);
+        if (!c) continue;
+        const int64_t start = ent_start(e);
         for (int64_t j = start; j < start + c; ++j) {
           int64_t jd = C.a.id[Q.slot[j]];
           if (jd <= id) continue;

@@ -358,3 +358,17 @@ def test_row_major_curve_orders_storage(orc):
     seq = box[order]
     assert np.all(seq[1:] >= seq[:-1])
     assert np.array_equal(np.sort(order), np.arange(pop.n))
+
+
+def test_box_overflow_is_reported(orc):
+    """More agents in one box than a table word counts: the step reports
+    BDM_E_CAPACITY instead of silently dropping agents."""
+    from paper_2503_10796_gb300 import binding
+    rng = np.random.default_rng(0)
+    xyz = rng.uniform(0.0, 50.0, (1100, 3))
+    pop = workloads.Population(xyz, np.full(1100, 1.0), workloads.SimParams(box_length=60.0))
+    ctx = ctx_for(pop)
+    ctx.step(1)
+    with pytest.raises(binding.BdmError) as e:
+        ctx.sync()
+    assert e.value.code == -4
