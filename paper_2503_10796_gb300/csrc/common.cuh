@@ -5,9 +5,9 @@
 //     [base_s, base_s + cap_s); its agents occupy [base_s, base_s + n_s).
 //   cell arrays, indexed by cell position: agents grouped by grid box, the
 //     boxes of simulation s contiguous in [cell_base_s, cell_base_s + n_s).
-//   box table: one 64-bit word per box (stamp | dirty | count) and one
-//     32-bit first-cell index; simulation s owns entries
-//     [table_base_s, table_base_s + table_cap_s).
+//   box table: one 64-bit word per box (stamp | dirty | count | first
+//     cell); simulation s owns entries [table_base_s, table_base_s +
+//     table_cap_s).
 #pragma once
 
 #include <cstdint>
@@ -134,6 +134,8 @@ struct DevCtx {
   Cells q;                    // cells of the last neighbor query
   Table tab;
   int32_t *order;             // simulations in slot-region order (-1 padded)
+  uint32_t *lv;               // per slot: box count + 1 for box leaders, else 0 (scan)
+  uint32_t *partial;          // per scan tile: leader sum, then its exclusive prefix
   int32_t n_sims;
   int64_t total_slots;
 };

@@ -217,7 +217,7 @@ void launch_iteration(bdm_ctx *c) {
     stage_end(c);
   }
   stage_begin(c, 2);
-  launch_scan(D, st, c->d_partial);
+  launch_scan(D, st);
   stage_end(c);
   stage_begin(c, 3);
   launch_place(D, st, 1);
@@ -394,7 +394,7 @@ int query_grid(bdm_ctx *c, bool with_cells, const std::vector<double> *boxes) {
   launch_params(c->D, c->stream, 0);
   if (with_cells) {
     launch_count(c->D, c->stream, 0);
-    launch_scan(c->D, c->stream, c->d_partial);
+    launch_scan(c->D, c->stream);
     launch_place(c->D, c->stream, 0);
   }
   if (boxes) upload_consts(c);
@@ -451,7 +451,9 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   ALLOC(D.ss, (size_t)n_sims, "simulation state");
   ALLOC(D.g, 1, "globals");
   ALLOC(D.order, (size_t)n_sims, "simulation order");
-  ALLOC(c->d_partial, 2048, "scan partials");
+  ALLOC(c->d_partial, (size_t)(scan_tiles((int64_t)M) + 2048), "scan partials");
+  ALLOC(D.lv, M, "scan leader values");
+  D.partial = c->d_partial;
   ALLOC(D.a.x, M, "x"); ALLOC(D.a.y, M, "y"); ALLOC(D.a.z, M, "z"); ALLOC(D.a.d, M, "diameter");
   ALLOC(D.a.v, M, "volume"); ALLOC(D.a.id, M, "ids"); ALLOC(D.a.sim, M, "slot simulation");
   ALLOC(D.a.pkey, M, "box keys"); ALLOC(D.a.pkey_hist, M, "box history"); ALLOC(D.a.rank, M, "ranks");
@@ -866,8 +868,8 @@ int bdm_get_profile(bdm_ctx *c, int64_t launches[BDM_NUM_STAGES], double ms[BDM_
 
 int bdm_set_tuning(bdm_ctx *c, const bdm_tuning *t) {
   if (!c || !t) return BDM_E_INVAL;
-  if (t->force_variant < 0 || t->force_variant > 4)
-    return fail(c, BDM_E_INVAL, "force_variant must be 0 to 4");
+  if (t->force_variant < 0 || t->force_variant > 5)
+    return fail(c, BDM_E_INVAL, "force_variant must be 0 to 5");
   if (t->sort_interval < -1) return fail(c, BDM_E_INVAL, "sort_interval must be >= -1");
   if (t->sort_curve != 0 && t->sort_curve != 1) return fail(c, BDM_E_INVAL, "sort_curve must be 0 or 1");
   for (int k = 0; k < 5; ++k)
@@ -998,7 +1000,7 @@ int bdm_autotune(bdm_ctx *c, int32_t iterations, bdm_tuning *chosen) {
   bdm_get_tuning(c, &best);
   float best_ms = 1e30f;
   std::vector<int> variants = {0};
-  if (c->any_fp32) variants = {0, 2, 3, 4};
+  if (c->any_fp32) variants = {0, 2, 3, 4, 5};
   for (int v : variants) {
     if (rc) break;
     bdm_tuning t = best;

@@ -170,6 +170,152 @@ __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, con
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
 }
 
+// Contribution of candidate j (record q, neighbour-box offset (fdx, fdy,
+// fdz)) to the force on p: FP32 overlap for deep pairs, float-float for
+// shallow ones, the FP64 definition when the float-float numerator is
+// within rounding of zero.  Returns false when the pair does not interact.
+__device__ __forceinline__ bool pair32(const DevCtx &C, int64_t p, const float4 &o0, const float4 &o1, int64_t j,
+                                       const float4 &q, float fdx, float fdy, float fdz, float Lh, float Ll,
+                                       float kf, float gf, float &fx, float &fy, float &fz, uint32_t &nnz) {
+  const float sx = __fsub_rn(o0.x, __fmul_rn(fdx, Lh)), sy = __fsub_rn(o0.y, __fmul_rn(fdy, Lh)),
+              sz = __fsub_rn(o0.z, __fmul_rn(fdz, Lh));
+  const float ddx = __fsub_rn(sx, q.x), ddy = __fsub_rn(sy, q.y), ddz = __fsub_rn(sz, q.z);
+  const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+  const float R = __fadd_rn(o0.w, q.w);
+  float dist = sqrtf(s2);
+  float del = __fsub_rn(R, dist);
+  float ux = ddx, uy = ddy, uz = ddz;
+  if (!(del > kFastDelta)) {
+    const float4 q1 = C.c.r1[j];
+    float xh, xl, yh, yl, zh, zl;
+    ff_diff(o0.x, o1.x, q.x, q1.x, __fmul_rn(fdx, Lh), __fmul_rn(fdx, Ll), xh, xl);
+    ff_diff(o0.y, o1.y, q.y, q1.y, __fmul_rn(fdy, Lh), __fmul_rn(fdy, Ll), yh, yl);
+    ff_diff(o0.z, o1.z, q.z, q1.z, __fmul_rn(fdz, Lh), __fmul_rn(fdz, Ll), zh, zl);
+    float p0, e0, p1, e1, p2, e2;
+    two_prod(xh, xh, p0, e0);
+    e0 = __fmaf_rn(__fmul_rn(2.f, xh), xl, e0);
+    two_prod(yh, yh, p1, e1);
+    e1 = __fmaf_rn(__fmul_rn(2.f, yh), yl, e1);
+    two_prod(zh, zh, p2, e2);
+    e2 = __fmaf_rn(__fmul_rn(2.f, zh), zl, e2);
+    float Sa, Sea, Sb, Seb;
+    two_sum(p0, p1, Sa, Sea);
+    two_sum(Sa, p2, Sb, Seb);
+    const float sl = __fadd_rn(__fadd_rn(Sea, Seb), __fadd_rn(__fadd_rn(e0, e1), e2));
+    float sh, sll;
+    fast_two_sum(Sb, sl, sh, sll);
+    float Rh, Rl;
+    two_sum(o0.w, q.w, Rh, Rl);
+    Rl = __fadd_rn(Rl, __fadd_rn(o1.w, q1.w));
+    float Qh, Ql;
+    two_prod(Rh, Rh, Qh, Ql);
+    Ql = __fmaf_rn(__fmul_rn(2.f, Rh), Rl, Ql);
+    const float num = __fadd_rn(__fsub_rn(Qh, sh), __fsub_rn(Ql, sll));
+    dist = sqrtf(sh);
+    if (fabsf(num) < kTinyNum) {
+      const double d64 = exact_delta(C, C.c.slot[p], C.c.slot[j]);
+      if (!(d64 > 0.0)) return false;
+      del = (float)d64;
+    } else {
+      if (!(num > 0.f)) return false;
+      del = __fdividef(num, __fadd_rn(Rh, dist));
+    }
+    ux = xh; uy = yh; uz = zh;
+  }
+  const float rr = __fdividef(__fmul_rn(o0.w, q.w), R);
+  const float fn = __fsub_rn(__fmul_rn(kf, del), __fmul_rn(gf, sqrtf(__fmul_rn(rr, del))));
+  nnz += (fn != 0.f);
+  if (dist > 0.f) {
+    const float f = __fdividef(fn, dist);
+    fx = __fmaf_rn(f, ux, fx);
+    fy = __fmaf_rn(f, uy, fy);
+    fz = __fmaf_rn(f, uz, fz);
+  }
+  return true;
+}
+
+// Batched direct loop: per stencil row the three boxes' candidates form one
+// sequence, read four records at a time with independent loads (more loads
+// in flight per thread), the next row's table words prefetched while the
+// current row is filtered; pairs that pass the FP32 filter are evaluated
+// afterwards, their records re-read from L1.
+__device__ __forceinline__ void force32_batched(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
+                                                int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
+  const float4 o0 = C.c.r0[p];
+  const float4 o1 = C.c.r1[p];
+  const float Lh = s.Lh, Ll = s.Ll, marg = s.marg;
+  const float kf = sc.kf, gf = sc.gammaf;
+  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  uint32_t nnz = 0;
+  const int ny = t.yhi - t.ylo + 1, nz = t.zhi - t.zlo + 1, nrows = ny * nz;
+  auto row_of = [&](int r, int &dy, int &dz) {
+    dy = t.ylo + r % ny;
+    dz = t.zlo + r / ny;
+    return ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 + (uint32_t)t.cx;
+  };
+  unsigned long long ew[3];
+  {
+    int dy, dz;
+    const uint32_t row = row_of(0, dy, dz);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int dx = q - 1;
+      ew[q] = (dx >= t.xlo && dx <= t.xhi) ? __ldg(t.e + row + dx) : 0ull;
+    }
+  }
+  for (int r = 0; r < nrows; ++r) {
+    int dy, dz;
+    row_of(r, dy, dz);
+    const uint32_t c0 = ent_live(ew[0], stamp), c1 = ent_live(ew[1], stamp), c2 = ent_live(ew[2], stamp);
+    const uint32_t s0 = ent_start(ew[0]), s1 = ent_start(ew[1]), s2 = ent_start(ew[2]);
+    // prefetch the next row's table words
+    if (r + 1 < nrows) {
+      int dy2, dz2;
+      const uint32_t row2 = row_of(r + 1, dy2, dz2);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int dx = q - 1;
+        ew[q] = (dx >= t.xlo && dx <= t.xhi) ? __ldg(t.e + row2 + dx) : 0ull;
+      }
+    }
+    const float fdy = (float)dy, fdz = (float)dz;
+    const float sy = __fsub_rn(o0.y, __fmul_rn(fdy, Lh)), sz = __fsub_rn(o0.z, __fmul_rn(fdz, Lh));
+    const uint32_t total = c0 + c1 + c2;
+    for (uint32_t k0 = 0; k0 < total; k0 += 4) {
+      float4 qv[4];
+      uint32_t hits = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t k = k0 + u;
+        const uint32_t j = k < c0 ? s0 + k : (k < c0 + c1 ? s1 + (k - c0) : s2 + (k - c0 - c1));
+        qv[u] = k < total ? C.c.r0[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t k = k0 + u;
+        const int dx = k < c0 ? -1 : (k < c0 + c1 ? 0 : 1);
+        const uint32_t j = k < c0 ? s0 + k : (k < c0 + c1 ? s1 + (k - c0) : s2 + (k - c0 - c1));
+        const float sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
+        const float ddx = __fsub_rn(sx, qv[u].x), ddy = __fsub_rn(sy, qv[u].y), ddz = __fsub_rn(sz, qv[u].z);
+        const float d2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+        const float Rm = __fadd_rn(__fadd_rn(o0.w, qv[u].w), marg);
+        if (k < total && (int64_t)j != p && d2 < __fmul_rn(Rm, Rm)) hits |= 1u << u;
+      }
+      while (hits) {
+        const int u = __ffs(hits) - 1;
+        hits &= hits - 1;
+        const uint32_t k = k0 + u;
+        const int dx = k < c0 ? -1 : (k < c0 + c1 ? 0 : 1);
+        const uint32_t j = k < c0 ? s0 + k : (k < c0 + c1 ? s1 + (k - c0) : s2 + (k - c0 - c1));
+        pair32(C, p, o0, o1, j, C.c.r0[j], (float)dx, fdy, fdz, Lh, Ll, kf, gf, fx, fy, fz, nnz);
+      }
+    }
+  }
+  C.c.f32[p] = make_float4(fx, fy, fz, 0.f);
+  C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
+}
+
 __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
                                         int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
   const double4_32a o = C.c.r64[p];
@@ -215,7 +361,9 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
 }
 
-// fp64_only: leave FP32-path simulations to the queue kernel (force32.cu).
+// fp64_only: leave FP32-path simulations to another kernel; kBatched: the
+// FP32 path runs the batched loop.
+template <int kBatched>
 __global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C, int fp64_only) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
@@ -232,6 +380,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C, int fp64_only) 
   if (st) return;
   if (sc.precision == BDM_PREC_FP64)
     force64(C, sc, s, p, cx, cy, cz, stamp);
+  else if (kBatched)
+    force32_batched(C, sc, s, p, cx, cy, cz, stamp);
   else
     force32(C, sc, s, p, cx, cy, cz, stamp);
 }
@@ -761,9 +911,12 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, 
       else if (variant == 4) launch_force32rq(C, st);
       else launch_force32q(C, st);
     }
-    if (has_fp64) k_force<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 1);
+    if (has_fp64) k_force<0><<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 1);
   } else {
-    k_force<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 0);
+    if (variant == 5)
+      k_force<1><<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 0);
+    else
+      k_force<0><<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 0);
   }
 }
 

@@ -230,45 +230,52 @@ __global__ void k_params(DevCtx C, int32_t step) {
 // S1: box index, per-box count with timestamps, dirty marks for static
 // detection (§5.5).
 // ---------------------------------------------------------------------------
-// Add one agent (count) and/or a dirty mark to a box entry; returns the
-// agent's rank inside the box.  Entries whose stamp is not the current one
-// are empty, whatever their count says.
+// Table update without a retry loop.  A max with (stamp << 43) turns an
+// entry of an older build into an empty current one (count 0, clean) and
+// leaves a current entry alone, since every current word is at least that
+// value; the add that follows (same thread, same address, so ordered after
+// the max) returns the count before it, i.e. the rank of the first agent
+// added.  Dirty marks are an OR.  A count that would pass the 10-bit field
+// (or a returned word of another stamp, which only such a carry makes) is a
+// table error: the scan then empties every box of the build, so no later
+// kernel indexes cells through a corrupted word.
+__device__ __forceinline__ void tab_revive(unsigned long long *e, uint32_t stamp) {
+  atomicMax(e, (unsigned long long)stamp << 43);
+}
+
 __device__ __forceinline__ uint32_t tab_add(unsigned long long *e, uint32_t stamp, bool dirty, uint32_t count,
                                             Globals *g) {
-  unsigned long long old = *(volatile unsigned long long *)e;
-  for (int tries = 0; tries < (1 << 22); ++tries) {
-    const unsigned long long assumed = old;
-    const bool live = ent_stamp(assumed) == stamp;
-    const uint32_t cnt = live ? ent_count(assumed) : 0u;
-    const bool dir = (live && ent_dirty(assumed)) || dirty;
-    uint32_t ncnt = cnt + count;
-    if (ncnt > kMaxBoxCount) {
-      // more agents in one box than the table word holds: the step is
-      // invalid (latched error); placement skips the agents beyond it
-      set_err(g, ERR_TABLE);
-      ncnt = kMaxBoxCount;
-    }
-    const unsigned long long nv = ((unsigned long long)stamp << 43) | ((unsigned long long)(dir ? 1u : 0u) << 42) |
-                                  ((unsigned long long)ncnt << 32) | (live ? (assumed & 0xFFFFFFFFull) : 0ull);
-    if (nv == assumed) return cnt;
-    old = atomicCAS(e, assumed, nv);
-    if (old == assumed) return cnt;
-  }
-  set_err(g, ERR_TIMEOUT);
-  return 0u;
+  tab_revive(e, stamp);
+  const unsigned long long old = atomicAdd(e, (unsigned long long)count << 32);
+  if (dirty) atomicOr(e, 1ull << 42);
+  const uint32_t cnt = ent_count(old);
+  if (ent_stamp(old) != stamp || cnt + count > kMaxBoxCount) set_err(g, ERR_TABLE);
+  return cnt;
+}
+
+__device__ __forceinline__ void tab_mark_dirty(unsigned long long *e, uint32_t stamp) {
+  tab_revive(e, stamp);
+  atomicOr(e, 1ull << 42);
 }
 
 // hist: the per-slot box history (the step passes it; queries pass null so
-// that the history of the last iteration survives them).
+// that the history of the last iteration survives them).  Every load that
+// does not depend on another is issued before the first test, so that one
+// thread waits for few round trips in a row.
 __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
-  int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= C.total_slots) return;
-  int sim = C.a.sim[slot];
-  if (sim < 0) return;
-  const SimConst &sc = C.sc[sim];
-  const SimState &s = C.ss[sim];
-  if (slot - sc.base >= s.n || !s.valid) return;
-  double p[3] = {C.a.x[slot], C.a.y[slot], C.a.z[slot]};
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = slot < C.total_slots;
+  const int64_t sl = in ? slot : C.total_slots - 1;
+  const int sim = C.a.sim[sl];
+  const double p[3] = {C.a.x[sl], C.a.y[sl], C.a.z[sl]};
+  const uint64_t pk_prev_in = hist ? hist[sl] : 0ull;
+  const uint8_t fl = hist ? C.a.flags[sl] : (uint8_t)0;
+  const uint32_t stamp = C.g->stamp & kStampMask;
+  const SimConst &sc = C.sc[sim < 0 ? 0 : sim];
+  const SimState &s = C.ss[sim < 0 ? 0 : sim];
+  const bool valid = in && sim >= 0 && sl - sc.base < s.n && s.valid;
+  const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+  if (!valid) return;
   int64_t c[3];
   for (int a = 0; a < 3; ++a) {
     double av = __dsub_rn(p[a], s.o[a]);
@@ -277,33 +284,27 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
     int64_t ca = box_coord(av, ah, al, s.ilh, s.ill, s.L);
     c[a] = ca < 0 ? 0 : (ca >= s.dims[a] ? s.dims[a] - 1 : ca);
   }
-  uint64_t pk = pack_coords(c[0], c[1], c[2]);
-  C.a.pkey[slot] = pk;
-  uint64_t pk_prev = pk;
-  if (hist) {
-    pk_prev = hist[slot];
-    hist[slot] = pk;
-  }
-  bool changed = hist && (C.a.flags[slot] & FLAG_CHANGED) != 0;
-  const uint32_t stamp = C.g->stamp & kStampMask;
-  int64_t idx = sc.table_base + linear_box(s, c[0], c[1], c[2]);
+  const uint64_t pk = pack_coords(c[0], c[1], c[2]);
+  const int64_t idx = sc.table_base + linear_box(s, c[0], c[1], c[2]);
   // Lanes of a warp that share a box add their count with one atomic
   // (neighbouring slots mostly share boxes once the storage is sorted).
-  const unsigned mask = __activemask();
-  const unsigned peers = __match_any_sync(mask, (unsigned long long)idx);
+  const unsigned peers = __match_any_sync(vmask, (unsigned long long)idx);
+  const bool changed = hist && (fl & FLAG_CHANGED) != 0;
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
   const unsigned dirty_any = __reduce_or_sync(peers, changed ? 1u : 0u);
   uint32_t base = 0;
   if (lane == leader) base = tab_add(&C.tab.e[idx], stamp, dirty_any != 0, (uint32_t)__popc(peers), C.g);
+  C.a.pkey[slot] = pk;
+  if (hist) hist[slot] = pk;
+  if (changed && s.same_grid && pk_prev_in != pk) {
+    int64_t px, py, pz;
+    unpack_coords(pk_prev_in, px, py, pz);
+    if (px < s.dims[0] && py < s.dims[1] && pz < s.dims[2])
+      tab_mark_dirty(&C.tab.e[sc.table_base + linear_box(s, px, py, pz)], stamp);
+  }
   base = __shfl_sync(peers, base, leader);
   C.a.rank[slot] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-  if (changed && s.same_grid && pk_prev != pk) {
-    int64_t px, py, pz;
-    unpack_coords(pk_prev, px, py, pz);
-    if (px < s.dims[0] && py < s.dims[1] && pz < s.dims[2])
-      tab_add(&C.tab.e[sc.table_base + linear_box(s, px, py, pz)], stamp, true, 0u, C.g);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -311,20 +312,9 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
 // contributes the box's count), in slot order, giving every box its first
 // cell position; then placement of every agent at start + rank.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t leader_value(const DevCtx &C, int64_t slot, int64_t &idx) {
-  idx = -1;
-  if (slot >= C.total_slots) return 0u;
-  int sim = C.a.sim[slot];
-  if (sim < 0) return 0u;
-  const SimConst &sc = C.sc[sim];
-  const SimState &s = C.ss[sim];
-  if (slot - sc.base >= s.n || !s.valid) return 0u;
-  if (C.a.rank[slot] != 0u) return 0u;
-  int64_t cx, cy, cz;
-  unpack_coords(C.a.pkey[slot], cx, cy, cz);
-  idx = sc.table_base + linear_box(s, cx, cy, cz);
-  return ent_count(C.tab.e[idx]);
-}
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int64_t kScanTile = (int64_t)kScanThreads * kScanItems;
 
 __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sh) {
   v = __reduce_add_sync(0xffffffffu, v);
@@ -368,40 +358,110 @@ __device__ __forceinline__ uint32_t block_exscan_u32(uint32_t v, uint32_t *sh, u
   return r;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_up(DevCtx C, int64_t chunk, uint32_t *partial) {
+// Pass 1: each thread takes kScanItems slots of its tile (strided, so that
+// loads coalesce), issues all their loads before any is used, records the
+// leader value count + 1 (0 for non-leaders) and sums the counts per tile.
+__global__ void __launch_bounds__(kScanThreads) k_scan_up(DevCtx C) {
   __shared__ uint32_t sh[33];
-  int64_t begin = (int64_t)blockIdx.x * chunk;
-  int64_t end = begin + chunk < C.total_slots ? begin + chunk : C.total_slots;
-  uint32_t sum = 0;
-  for (int64_t slot = begin + threadIdx.x; slot < end; slot += blockDim.x) {
-    int64_t idx;
-    sum += leader_value(C, slot, idx);
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+  uint32_t rank[kScanItems];
+  uint64_t pk[kScanItems];
+  int sim[kScanItems];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t slot = base + (int64_t)i * kScanThreads;
+    const int64_t sl = slot < C.total_slots ? slot : C.total_slots - 1;
+    rank[i] = C.a.rank[sl];
+    pk[i] = C.a.pkey[sl];
+    sim[i] = slot < C.total_slots ? C.a.sim[sl] : -1;
   }
-  uint32_t t = block_sum_u32(sum, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  unsigned long long e[kScanItems];
+  bool lead[kScanItems];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t slot = base + (int64_t)i * kScanThreads;
+    lead[i] = false;
+    e[i] = 0ull;
+    if (sim[i] >= 0) {
+      const SimConst &sc = C.sc[sim[i]];
+      const SimState &s = C.ss[sim[i]];
+      if (slot - sc.base < s.n && s.valid && rank[i] == 0u) {
+        int64_t cx, cy, cz;
+        unpack_coords(pk[i], cx, cy, cz);
+        e[i] = C.tab.e[sc.table_base + linear_box(s, cx, cy, cz)];
+        lead[i] = true;
+      }
+    }
+  }
+  uint32_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t slot = base + (int64_t)i * kScanThreads;
+    const uint32_t cnt = lead[i] ? ent_count(e[i]) : 0u;
+    if (slot < C.total_slots) C.lv[slot] = lead[i] ? cnt + 1u : 0u;
+    sum += cnt;
+  }
+  const uint32_t t = block_sum_u32(sum, sh);
+  if (threadIdx.x == 0) C.partial[blockIdx.x] = t;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *partial, int n) {
+// Exclusive scan of the n tile sums in one block; each thread takes a
+// contiguous run of them.
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t *partial, int64_t n) {
   __shared__ uint32_t sh[33];
-  uint32_t v = (int)threadIdx.x < n ? partial[threadIdx.x] : 0u;
+  const int64_t per = (n + kScanThreads - 1) / kScanThreads;
+  const int64_t b = (int64_t)threadIdx.x * per;
+  const int64_t e = b + per < n ? b + per : n;
+  uint32_t sum = 0;
+  for (int64_t i = b; i < e; ++i) sum += partial[i];
   uint32_t total;
-  uint32_t ex = block_exscan_u32(v, sh, &total);
-  if ((int)threadIdx.x < n) partial[threadIdx.x] = ex;
+  uint32_t run = block_exscan_u32(sum, sh, &total);
+  for (int64_t i = b; i < e; ++i) {
+    const uint32_t v = partial[i];
+    partial[i] = run;
+    run += v;
+  }
 }
 
-__global__ void __launch_bounds__(1024) k_scan_down(DevCtx C, int64_t chunk, const uint32_t *partial) {
+// Pass 2: exclusive prefix of the leader counts in slot order; each leader
+// writes its box's first cell into the low half of the table word (a 32-bit
+// store: the high half, stamp | dirty | count, stays as the count left it).
+// After a table error every leader writes an empty current word instead, so
+// that placement, forces and queries see no agents in any box of the build.
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(DevCtx C) {
   __shared__ uint32_t sh[33];
-  int64_t begin = (int64_t)blockIdx.x * chunk;
-  int64_t end = begin + chunk < C.total_slots ? begin + chunk : C.total_slots;
-  uint32_t base = partial[blockIdx.x];
-  for (int64_t t0 = begin; t0 < end; t0 += blockDim.x) {
-    int64_t slot = t0 + threadIdx.x;
-    int64_t idx = -1;
-    uint32_t v = slot < end ? leader_value(C, slot, idx) : 0u;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+  uint32_t v[kScanItems];
+  uint64_t pk[kScanItems];
+  int sim[kScanItems];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t slot = base + (int64_t)i * kScanThreads;
+    const int64_t sl = slot < C.total_slots ? slot : C.total_slots - 1;
+    v[i] = slot < C.total_slots ? C.lv[sl] : 0u;
+    pk[i] = C.a.pkey[sl];
+    sim[i] = C.a.sim[sl];
+  }
+  const bool bad = (C.g->err & ERR_TABLE) != 0u;
+  const uint32_t stamp = C.g->stamp & kStampMask;
+  uint32_t off = C.partial[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
     uint32_t total;
-    uint32_t ex = block_exscan_u32(v, sh, &total);
-    if (idx >= 0) C.tab.e[idx] = (C.tab.e[idx] & 0xFFFFFFFF00000000ull) | (unsigned long long)(base + ex);
-    base += total;
+    const uint32_t cnt = v[i] ? v[i] - 1u : 0u;
+    const uint32_t ex = block_exscan_u32(cnt, sh, &total);
+    if (v[i]) {
+      const SimConst &sc = C.sc[sim[i]];
+      const SimState &s = C.ss[sim[i]];
+      int64_t cx, cy, cz;
+      unpack_coords(pk[i], cx, cy, cz);
+      unsigned long long *w = &C.tab.e[sc.table_base + linear_box(s, cx, cy, cz)];
+      if (bad)
+        *w = (unsigned long long)stamp << 43;
+      else
+        *reinterpret_cast<uint32_t *>(w) = off + ex;
+    }
+    off += total;
   }
 }
 
@@ -470,17 +530,13 @@ void launch_count(const DevCtx &C, cudaStream_t st, int step) {
   k_count<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, step ? C.a.pkey_hist : nullptr);
 }
 
-void launch_scan(const DevCtx &C, cudaStream_t st, uint32_t *partial) {
-  int64_t G = blocks_for(C.total_slots, 4096);
-  if (G > 1024) G = 1024;
-  if (G < 1) G = 1;
-  int64_t chunk = (C.total_slots + G - 1) / G;
-  chunk = (chunk + 1023) / 1024 * 1024;
-  G = (C.total_slots + chunk - 1) / chunk;
-  if (G < 1) G = 1;
-  k_scan_up<<<(unsigned int)G, 1024, 0, st>>>(C, chunk, partial);
-  k_scan_top<<<1, 1024, 0, st>>>(partial, (int)G);
-  k_scan_down<<<(unsigned int)G, 1024, 0, st>>>(C, chunk, partial);
+int64_t scan_tiles(int64_t total_slots) { return (total_slots + kScanTile - 1) / kScanTile; }
+
+void launch_scan(const DevCtx &C, cudaStream_t st) {
+  const int64_t G = scan_tiles(C.total_slots);
+  k_scan_up<<<(unsigned int)G, kScanThreads, 0, st>>>(C);
+  k_scan_top<<<1, kScanThreads, 0, st>>>(C.partial, G);
+  k_scan_down<<<(unsigned int)G, kScanThreads, 0, st>>>(C);
 }
 
 void launch_place(const DevCtx &C, cudaStream_t st, int step) {

@@ -28,7 +28,8 @@ constexpr size_t oSS = oSC + up(sizeof(SimConst));
 constexpr size_t oG = oSS + up(sizeof(SimState));
 constexpr size_t oOrder = oG + up(sizeof(Globals));
 constexpr size_t oPart = oOrder + up(sizeof(int32_t));
-constexpr size_t oAX = oPart + up(2048 * sizeof(uint32_t));
+constexpr size_t oLv = oPart + up(2048 * sizeof(uint32_t));
+constexpr size_t oAX = oLv + up(4 * kM);
 constexpr size_t oAY = oAX + up(8 * kM);
 constexpr size_t oAZ = oAY + up(8 * kM);
 constexpr size_t oAD = oAZ + up(8 * kM);
@@ -114,7 +115,8 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   D.c.flag = at<uint8_t>(base, oCFlag); D.c.nnz = at<uint8_t>(base, oCNnz); D.c.stat = at<uint8_t>(base, oCStat);
   D.c.f32 = at<float4>(base, oCF32); D.c.f64 = at<double4_32a>(base, oCF64);
   D.tab.e = at<unsigned long long>(base, oTab);
-  uint32_t *partial = at<uint32_t>(base, oPart);
+  D.partial = at<uint32_t>(base, oPart);
+  D.lv = at<uint32_t>(base, oLv);
 
   // Constants and cleared state: every call starts from zero, because the
   // array keeps whatever the previous call left in it.
@@ -144,7 +146,7 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   launch_bbox(D, st);
   launch_params(D, st, 1);
   launch_count(D, st, 1);
-  launch_scan(D, st, partial);
+  launch_scan(D, st);
   launch_place(D, st, 1);
   launch_force(D, st);
   // The grid's fit is known only on the device: read the error word before
