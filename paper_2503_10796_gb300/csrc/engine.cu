@@ -1000,7 +1000,7 @@ int bdm_autotune(bdm_ctx *c, int32_t iterations, bdm_tuning *chosen) {
   bdm_get_tuning(c, &best);
   float best_ms = 1e30f;
   std::vector<int> variants = {0};
-  if (c->any_fp32) variants = {0, 2, 3, 4, 5};
+  if (c->any_fp32) variants = {0, 1, 2, 3, 4, 5};
   for (int v : variants) {
     if (rc) break;
     bdm_tuning t = best;

@@ -234,84 +234,105 @@ __device__ __forceinline__ bool pair32(const DevCtx &C, int64_t p, const float4 
   return true;
 }
 
-// Batched direct loop: per stencil row the three boxes' candidates form one
-// sequence, read four records at a time with independent loads (more loads
-// in flight per thread), the next row's table words prefetched while the
-// current row is filtered; pairs that pass the FP32 filter are evaluated
-// afterwards, their records re-read from L1.
-__device__ __forceinline__ void force32_batched(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
-                                                int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
-  const float4 o0 = C.c.r0[p];
+// Direct loop with deferred pair evaluation.  The stencil walk only filters:
+// a candidate that passes the FP32 filter is queued (cell index and
+// neighbour-box code) in the thread's column of a shared-memory queue; the
+// queue is evaluated with pair32 when it is full and after the walk.  The
+// pair arithmetic, which the lanes of a warp would otherwise run one after
+// another whenever any lane finds a partner, then runs with the lanes
+// together, and the walk itself needs fewer registers.  Pairs are evaluated
+// in the walk's order, so the sums equal those of the plain direct loop.
+constexpr int kHitCap = 8;
+struct HitQueue {
+  uint32_t j[kHitCap][kThreads];
+  uint8_t b[kHitCap][kThreads];
+};
+
+// Evaluates the queued candidates in order; the agent's own cell, which the
+// walk queues rather than test every candidate against it, is skipped here.
+__device__ __forceinline__ void flush_hits(const DevCtx &C, uint32_t p, const float4 &o0, int n, const HitQueue &hq,
+                                           float Lh, float Ll, float kf, float gf, float &fx, float &fy, float &fz,
+                                           uint32_t &nnz) {
   const float4 o1 = C.c.r1[p];
-  const float Lh = s.Lh, Ll = s.Ll, marg = s.marg;
-  const float kf = sc.kf, gf = sc.gammaf;
+  for (int k = 0; k < n; ++k) {
+    const uint32_t j = hq.j[k][threadIdx.x];
+    if (j == p) continue;
+    const int b = hq.b[k][threadIdx.x];
+    const float fdx = (float)(b % 3 - 1), fdy = (float)((b / 3) % 3 - 1), fdz = (float)(b / 9 - 1);
+    pair32(C, (int64_t)p, o0, o1, (int64_t)j, C.c.r0[j], fdx, fdy, fdz, Lh, Ll, kf, gf, fx, fy, fz, nnz);
+  }
+}
+
+// kRowFlat: the three boxes of a stencil row are walked as one sequence
+// (a warp then iterates max over lanes of the row's candidates rather than
+// the sum over boxes of the per-box maxima).
+template <bool kRowFlat>
+__device__ __forceinline__ void force32_deferred(const DevCtx &C, const SimConst &sc, const SimState &s, uint32_t p,
+                                                 int64_t cx, int64_t cy, int64_t cz, uint32_t stamp,
+                                                 HitQueue &hq) {
+  const float4 o0 = C.c.r0[p];
+  const float Lh = s.Lh;
+  const float rw = __fadd_rn(o0.w, s.marg);
   const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
+  const float4 *__restrict__ r0 = C.c.r0;
   float fx = 0.f, fy = 0.f, fz = 0.f;
   uint32_t nnz = 0;
-  const int ny = t.yhi - t.ylo + 1, nz = t.zhi - t.zlo + 1, nrows = ny * nz;
-  auto row_of = [&](int r, int &dy, int &dz) {
-    dy = t.ylo + r % ny;
-    dz = t.zlo + r / ny;
-    return ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 + (uint32_t)t.cx;
-  };
-  unsigned long long ew[3];
-  {
-    int dy, dz;
-    const uint32_t row = row_of(0, dy, dz);
+  int n = 0;
+  const float sxm = __fadd_rn(o0.x, Lh), sxp = __fsub_rn(o0.x, Lh);
+  const bool x0 = t.xlo < 0, x2 = t.xhi > 0;
+  for (int dz = t.zlo; dz <= t.zhi; ++dz) {
+    const float sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
+    for (int dy = t.ylo; dy <= t.yhi; ++dy) {
+      const float sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh));
+      const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
+                           (uint32_t)t.cx;
+      const unsigned long long ew[3] = {x0 ? __ldg(t.e + row - 1) : 0ull, __ldg(t.e + row),
+                                        x2 ? __ldg(t.e + row + 1) : 0ull};
+      const int code_row = (dz + 1) * 9 + (dy + 1) * 3;
+      if constexpr (kRowFlat) {
+        const uint32_t c0 = ent_live(ew[0], stamp), c1 = ent_live(ew[1], stamp), c2 = ent_live(ew[2], stamp);
+        const uint32_t e01 = c0 + c1, tot = e01 + c2;
+        const uint32_t jb0 = ent_start(ew[0]), jb1 = ent_start(ew[1]) - c0, jb2 = ent_start(ew[2]) - e01;
+        for (uint32_t k = 0; k < tot; ++k) {
+          const bool b0 = k < c0, b1 = k < e01;
+          const uint32_t j = k + (b0 ? jb0 : (b1 ? jb1 : jb2));
+          const float sx = b0 ? sxm : (b1 ? o0.x : sxp);
+          const float4 qv = r0[j];
+          const float ddx = __fsub_rn(sx, qv.x), ddy = __fsub_rn(sy, qv.y), ddz = __fsub_rn(sz, qv.z);
+          const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+          const float Rm = __fadd_rn(rw, qv.w);
+          if (!(s2 < __fmul_rn(Rm, Rm))) continue;
+          hq.j[n][threadIdx.x] = j;
+          hq.b[n][threadIdx.x] = (uint8_t)(code_row + (b0 ? 0 : (b1 ? 1 : 2)));
+          if (++n == kHitCap) {
+            flush_hits(C, p, o0, n, hq, Lh, s.Ll, sc.kf, sc.gammaf, fx, fy, fz, nnz);
+            n = 0;
+          }
+        }
+      } else {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int dx = q - 1;
-      ew[q] = (dx >= t.xlo && dx <= t.xhi) ? __ldg(t.e + row + dx) : 0ull;
-    }
-  }
-  for (int r = 0; r < nrows; ++r) {
-    int dy, dz;
-    row_of(r, dy, dz);
-    const uint32_t c0 = ent_live(ew[0], stamp), c1 = ent_live(ew[1], stamp), c2 = ent_live(ew[2], stamp);
-    const uint32_t s0 = ent_start(ew[0]), s1 = ent_start(ew[1]), s2 = ent_start(ew[2]);
-    // prefetch the next row's table words
-    if (r + 1 < nrows) {
-      int dy2, dz2;
-      const uint32_t row2 = row_of(r + 1, dy2, dz2);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int dx = q - 1;
-        ew[q] = (dx >= t.xlo && dx <= t.xhi) ? __ldg(t.e + row2 + dx) : 0ull;
-      }
-    }
-    const float fdy = (float)dy, fdz = (float)dz;
-    const float sy = __fsub_rn(o0.y, __fmul_rn(fdy, Lh)), sz = __fsub_rn(o0.z, __fmul_rn(fdz, Lh));
-    const uint32_t total = c0 + c1 + c2;
-    for (uint32_t k0 = 0; k0 < total; k0 += 4) {
-      float4 qv[4];
-      uint32_t hits = 0;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t k = k0 + u;
-        const uint32_t j = k < c0 ? s0 + k : (k < c0 + c1 ? s1 + (k - c0) : s2 + (k - c0 - c1));
-        qv[u] = k < total ? C.c.r0[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t k = k0 + u;
-        const int dx = k < c0 ? -1 : (k < c0 + c1 ? 0 : 1);
-        const uint32_t j = k < c0 ? s0 + k : (k < c0 + c1 ? s1 + (k - c0) : s2 + (k - c0 - c1));
-        const float sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
-        const float ddx = __fsub_rn(sx, qv[u].x), ddy = __fsub_rn(sy, qv[u].y), ddz = __fsub_rn(sz, qv[u].z);
-        const float d2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
-        const float Rm = __fadd_rn(__fadd_rn(o0.w, qv[u].w), marg);
-        if (k < total && (int64_t)j != p && d2 < __fmul_rn(Rm, Rm)) hits |= 1u << u;
-      }
-      while (hits) {
-        const int u = __ffs(hits) - 1;
-        hits &= hits - 1;
-        const uint32_t k = k0 + u;
-        const int dx = k < c0 ? -1 : (k < c0 + c1 ? 0 : 1);
-        const uint32_t j = k < c0 ? s0 + k : (k < c0 + c1 ? s1 + (k - c0) : s2 + (k - c0 - c1));
-        pair32(C, p, o0, o1, j, C.c.r0[j], (float)dx, fdy, fdz, Lh, Ll, kf, gf, fx, fy, fz, nnz);
+        for (int q = 0; q < 3; ++q) {
+          const uint32_t cnt = ent_live(ew[q], stamp);
+          const uint32_t j0 = ent_start(ew[q]);
+          const float sx = q == 0 ? sxm : (q == 1 ? o0.x : sxp);
+          for (uint32_t j = j0; j < j0 + cnt; ++j) {
+            const float4 qv = r0[j];
+            const float ddx = __fsub_rn(sx, qv.x), ddy = __fsub_rn(sy, qv.y), ddz = __fsub_rn(sz, qv.z);
+            const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+            const float Rm = __fadd_rn(rw, qv.w);
+            if (!(s2 < __fmul_rn(Rm, Rm))) continue;
+            hq.j[n][threadIdx.x] = j;
+            hq.b[n][threadIdx.x] = (uint8_t)(code_row + q);
+            if (++n == kHitCap) {
+              flush_hits(C, p, o0, n, hq, Lh, s.Ll, sc.kf, sc.gammaf, fx, fy, fz, nnz);
+              n = 0;
+            }
+          }
+        }
       }
     }
   }
+  flush_hits(C, p, o0, n, hq, Lh, s.Ll, sc.kf, sc.gammaf, fx, fy, fz, nnz);
   C.c.f32[p] = make_float4(fx, fy, fz, 0.f);
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
 }
@@ -361,9 +382,7 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
 }
 
-// fp64_only: leave FP32-path simulations to another kernel; kBatched: the
-// FP32 path runs the batched loop.
-template <int kBatched>
+// fp64_only: leave FP32-path simulations to another kernel.
 __global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C, int fp64_only) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
@@ -380,10 +399,27 @@ __global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C, int fp64_only) 
   if (st) return;
   if (sc.precision == BDM_PREC_FP64)
     force64(C, sc, s, p, cx, cy, cz, stamp);
-  else if (kBatched)
-    force32_batched(C, sc, s, p, cx, cy, cz, stamp);
   else
     force32(C, sc, s, p, cx, cy, cz, stamp);
+}
+
+// FP32-path simulations only, deferred pair evaluation.
+template <bool kRowFlat>
+__global__ void __launch_bounds__(kThreads, 4) k_force32d(DevCtx C) {
+  __shared__ HitQueue hq;
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= C.g->n_cells) return;
+  int sim = C.c.sim[p];
+  const SimConst &sc = C.sc[sim];
+  const SimState &s = C.ss[sim];
+  if (!s.valid || sc.precision == BDM_PREC_FP64) return;
+  int64_t cx, cy, cz;
+  unpack_coords(C.c.pkey[p], cx, cy, cz);
+  uint32_t stamp = C.g->stamp & kStampMask;
+  bool st = is_static_cell(C, sc, s, p, cx, cy, cz, stamp);
+  C.c.stat[p] = st ? 1 : 0;
+  if (st) return;
+  force32_deferred<kRowFlat>(C, sc, s, (uint32_t)p, cx, cy, cz, stamp, hq);
 }
 
 // S5: displacement.  Static agents keep their position and nnz.
@@ -905,19 +941,19 @@ void launch_force32b(const DevCtx &C, cudaStream_t st) {
 static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
 void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64) {
-  if (variant == 2 || variant == 3 || variant == 4) {
-    if (has_fp32) {
-      if (variant == 3) launch_force32b(C, st);
-      else if (variant == 4) launch_force32rq(C, st);
-      else launch_force32q(C, st);
-    }
-    if (has_fp64) k_force<0><<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 1);
-  } else {
-    if (variant == 5)
-      k_force<1><<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 0);
-    else
-      k_force<0><<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, 0);
+  const unsigned int nb = blocks_for(C.total_slots, kThreads);
+  if (variant == 1) {
+    k_force<<<nb, kThreads, 0, st>>>(C, 0);
+    return;
   }
+  if (has_fp32) {
+    if (variant == 2) launch_force32q(C, st);
+    else if (variant == 3) launch_force32b(C, st);
+    else if (variant == 4) launch_force32rq(C, st);
+    else if (variant == 5) k_force32d<false><<<nb, kThreads, 0, st>>>(C);
+    else k_force32d<true><<<nb, kThreads, 0, st>>>(C);
+  }
+  if (has_fp64) k_force<<<nb, kThreads, 0, st>>>(C, 1);
 }
 
 void launch_displace(const DevCtx &C, cudaStream_t st) {
