@@ -236,13 +236,14 @@ __device__ __forceinline__ bool pair32(const DevCtx &C, int64_t p, const float4 
 
 // Direct loop with deferred pair evaluation.  The stencil walk only filters:
 // a candidate that passes the FP32 filter is queued (cell index and
-// neighbour-box code) in the thread's column of a shared-memory queue; the
-// queue is evaluated with pair32 when it is full and after the walk.  The
-// pair arithmetic, which the lanes of a warp would otherwise run one after
-// another whenever any lane finds a partner, then runs with the lanes
-// together, and the walk itself needs fewer registers.  Pairs are evaluated
-// in the walk's order, so the sums equal those of the plain direct loop.
-constexpr int kHitCap = 8;
+// neighbour-box code) in the thread's column of a shared-memory queue, and
+// the queue is evaluated with pair32 after the walk.  The pair arithmetic,
+// which the lanes of a warp would otherwise run one after another whenever
+// any lane finds a partner, then runs with the lanes together, and the walk
+// itself needs fewer registers.  An agent with more than kHitCap queued
+// candidates is evaluated again by the plain direct loop.  Both evaluate the
+// pairs in the walk's order, so the sums equal those of the direct loop.
+constexpr int kHitCap = 16;
 struct HitQueue {
   uint32_t j[kHitCap][kThreads];
   uint8_t b[kHitCap][kThreads];
@@ -302,12 +303,11 @@ __device__ __forceinline__ void force32_deferred(const DevCtx &C, const SimConst
           const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
           const float Rm = __fadd_rn(rw, qv.w);
           if (!(s2 < __fmul_rn(Rm, Rm))) continue;
-          hq.j[n][threadIdx.x] = j;
-          hq.b[n][threadIdx.x] = (uint8_t)(code_row + (b0 ? 0 : (b1 ? 1 : 2)));
-          if (++n == kHitCap) {
-            flush_hits(C, p, o0, n, hq, Lh, s.Ll, sc.kf, sc.gammaf, fx, fy, fz, nnz);
-            n = 0;
+          if (n < kHitCap) {
+            hq.j[n][threadIdx.x] = j;
+            hq.b[n][threadIdx.x] = (uint8_t)(code_row + (b0 ? 0 : (b1 ? 1 : 2)));
           }
+          ++n;
         }
       } else {
 #pragma unroll
@@ -321,16 +321,19 @@ __device__ __forceinline__ void force32_deferred(const DevCtx &C, const SimConst
             const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
             const float Rm = __fadd_rn(rw, qv.w);
             if (!(s2 < __fmul_rn(Rm, Rm))) continue;
-            hq.j[n][threadIdx.x] = j;
-            hq.b[n][threadIdx.x] = (uint8_t)(code_row + q);
-            if (++n == kHitCap) {
-              flush_hits(C, p, o0, n, hq, Lh, s.Ll, sc.kf, sc.gammaf, fx, fy, fz, nnz);
-              n = 0;
+            if (n < kHitCap) {
+              hq.j[n][threadIdx.x] = j;
+              hq.b[n][threadIdx.x] = (uint8_t)(code_row + q);
             }
+            ++n;
           }
         }
       }
     }
+  }
+  if (n > kHitCap) {
+    force32(C, sc, s, (int64_t)p, cx, cy, cz, stamp);
+    return;
   }
   flush_hits(C, p, o0, n, hq, Lh, s.Ll, sc.kf, sc.gammaf, fx, fy, fz, nnz);
   C.c.f32[p] = make_float4(fx, fy, fz, 0.f);

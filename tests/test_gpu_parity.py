@@ -312,11 +312,43 @@ def test_division_stops_at_capacity(orc):
     np.testing.assert_allclose(x_g, x_o, rtol=0, atol=1e-3)
 
 
+def dense_clump(n=300, side=20.0, seed=11):
+    """Heavily overlapping agents: each has far more than 16 partners, so the
+    deferred walk's queue overflows and the direct loop takes over."""
+    rng = np.random.default_rng(seed)
+    xyz = rng.uniform(0.0, side, (n, 3))
+    d = rng.uniform(8.0, 12.0, n)
+    return workloads.Population(xyz, d, workloads.SimParams(precision=1), "dense_clump")
+
+
+def test_deferred_walk_equals_direct_loop(orc):
+    """The deferred walk (queue and overflow path) and the direct loop find the
+    same interacting pairs (nnz equal) and agree to FP32 rounding.  Bitwise
+    equality is not expected: agents of one box are placed in the order their
+    atomic count arrived, which sets the order of the FP32 sum."""
+    for pop in (workloads.clustered(n_clusters=4, per_cluster=2000, side=500.0, sigma=30.0, seed=2),
+                dense_clump()):
+        _, _, smag = orc_for(pop).forces()
+        out = []
+        for variant in (0, 1, 5):
+            ctx = ctx_for(pop, precision=1, sort_interval=1)
+            ctx.set_tuning(force_variant=variant)
+            ctx.step(1)
+            ctx.sync()
+            out.append(ctx.forces(0)[:2])
+        F0, nnz0 = out[0]
+        for F, nnz in out[1:]:
+            assert np.array_equal(nnz, nnz0)
+            err = np.linalg.norm(F - F0, axis=1) / np.maximum(smag, 1e-30)
+            assert err.max() <= 1e-5, err.max()
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_force_variants_match_oracle(orc, variant):
     """Every force-kernel variant of the FP32 path meets the tolerance."""
     for pop in (workloads.plain_fp64(seed=5),
-                workloads.clustered(n_clusters=4, per_cluster=2000, side=500.0, sigma=30.0, seed=1)):
+                workloads.clustered(n_clusters=4, per_cluster=2000, side=500.0, sigma=30.0, seed=1),
+                dense_clump()):
         ctx = ctx_for(pop, precision=1, sort_interval=1)
         ctx.set_tuning(force_variant=variant)
         o = orc_for(pop)
