@@ -165,14 +165,27 @@ class Context:
     def count(self, sim: int) -> int:
         return self.stats(sim)["agents"]
 
-    def get_agents(self, sim: int):
+    def get_agents(self, sim: int, out=None):
+        """Positions (n x 3) and diameters (n) in ID order.  out: a pair of
+        C-contiguous float64 host arrays with room for the agents (pinned
+        memory makes the copy a direct DMA); views of their first n rows
+        are returned."""
         n = C.c_int64()
-        rc = self._lib.bdm_get_agents(self._h, sim, 0, None, None, C.byref(n), 0)
-        if rc not in (BDM_OK, -4):
-            self._check(rc)
-        xyz = np.empty((n.value, 3)); d = np.empty(n.value)
-        self._check(self._lib.bdm_get_agents(self._h, sim, n.value, _dptr(xyz), _dptr(d), C.byref(n), 0))
-        return xyz, d
+        if out is None:
+            rc = self._lib.bdm_get_agents(self._h, sim, 0, None, None, C.byref(n), 0)
+            if rc not in (BDM_OK, -4):
+                self._check(rc)
+            xyz = np.empty((n.value, 3)); d = np.empty(n.value)
+        else:
+            xyz, d = out
+            if xyz.dtype != np.float64 or d.dtype != np.float64 or not (
+                    xyz.flags.c_contiguous and d.flags.c_contiguous) or xyz.shape[0] != d.shape[0]:
+                raise ValueError("out must be C-contiguous float64 arrays (n x 3, n)")
+        self._check(self._lib.bdm_get_agents(self._h, sim, xyz.shape[0], _dptr(xyz), _dptr(d), C.byref(n), 0))
+        k = n.value
+        if out is not None and k == xyz.shape[0]:
+            return xyz, d
+        return xyz[:k], d[:k]
 
     def get_agents_device(self, sim: int, xyz_t, d_t):
         """Write into CUDA tensors (n x 3 and n float64) on the context stream."""

@@ -66,6 +66,9 @@ struct bdm_ctx {
   // graph of one iteration
   cudaGraphExec_t gexec = nullptr;
   bool graph_dirty = true;
+  double *d_xfer = nullptr;          // host transfer staging (grow-only)
+  size_t xfer_cap = 0;               // doubles
+  unsigned long long *d_bad = nullptr; // first invalid input row (input check)
   std::string err;
   uint32_t pending_err = 0;
 };
@@ -453,6 +456,7 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   ALLOC(D.order, (size_t)n_sims, "simulation order");
   ALLOC(c->d_partial, (size_t)(scan_tiles((int64_t)M) + 2048), "scan partials");
   ALLOC(D.lv, M, "scan leader values");
+  ALLOC(c->d_bad, 1, "input check");
   D.partial = c->d_partial;
   ALLOC(D.a.x, M, "x"); ALLOC(D.a.y, M, "y"); ALLOC(D.a.z, M, "z"); ALLOC(D.a.d, M, "diameter");
   ALLOC(D.a.v, M, "volume"); ALLOC(D.a.id, M, "ids"); ALLOC(D.a.sim, M, "slot simulation");
@@ -507,60 +511,71 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   return BDM_OK;
 }
 
+// Grow-only staging buffer for host transfers (no allocation per call once
+// it holds the largest population seen).
+static int ensure_xfer(bdm_ctx *c, size_t doubles) {
+  if (c->xfer_cap >= doubles) return BDM_OK;
+  size_t want = std::max(doubles, c->xfer_cap + c->xfer_cap / 4);
+  if (c->d_xfer) {
+    dfree(c, c->d_xfer);
+    c->d_xfer = nullptr;
+    c->xfer_cap = 0;
+  }
+  int rc = dalloc(c, &c->d_xfer, want, "host transfer buffer");
+  if (rc) return rc;
+  c->xfer_cap = want;
+  return BDM_OK;
+}
+
 int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const double *diameter, int32_t flags) {
   int rc = check_sim(c, sim);
   if (rc) return rc;
   if (n < 0 || (n > 0 && (!xyz || !diameter))) return fail(c, BDM_E_INVAL, "n < 0 or NULL input");
   bool dev = (flags & BDM_DEVICE_PTRS) != 0;
-  if (!dev) {
-    for (int64_t i = 0; i < n; ++i) {
-      if (!std::isfinite(xyz[3 * i]) || !std::isfinite(xyz[3 * i + 1]) || !std::isfinite(xyz[3 * i + 2]))
-        return fail(c, BDM_E_INVAL, "non-finite position at row " + std::to_string(i));
-      if (!(diameter[i] > 0) || !std::isfinite(diameter[i]))
-        return fail(c, BDM_E_INVAL, "diameter must be finite and > 0 (row " + std::to_string(i) + ")");
-    }
-  }
   SimConst &sc = c->h_sc[sim];
   int64_t want = std::max<int64_t>(n, c->params[sim].capacity);
   if (want < 1) want = 1;
-  if (sc.base < 0) {
-    if (c->used_slots + want > c->max_total)
-      return fail(c, BDM_E_CAPACITY, "agent capacity of the context exhausted");
-    sc.base = c->used_slots;
-    sc.cap = want;
-    c->used_slots += want;
-  } else if (n > sc.cap) {
-    if (sc.base + sc.cap == c->used_slots && sc.base + want <= c->max_total) {
-      c->used_slots = sc.base + want;
-      sc.cap = want;
+  // the simulation's slot region, committed only once the input is valid
+  int64_t base = sc.base, cap = sc.cap, used = c->used_slots;
+  if (base < 0) {
+    if (used + want > c->max_total) return fail(c, BDM_E_CAPACITY, "agent capacity of the context exhausted");
+    base = used;
+    cap = want;
+    used += want;
+  } else if (n > cap) {
+    if (base + cap == used && base + want <= c->max_total) {
+      used = base + want;
+      cap = want;
     } else {
       return fail(c, BDM_E_CAPACITY, "n exceeds the capacity of this simulation's region");
     }
   }
-  c->D.total_slots = c->used_slots;
-  c->graph_dirty = true;
-  // upload
+  // upload (host input through the context's staging buffer), then check
+  // every row on the device before anything of the simulation changes
   const double *dx = xyz, *dd = diameter;
-  double *tmp = nullptr;
-  if (!dev && n > 0) {
-    rc = dalloc(c, &tmp, (size_t)(4 * n), "upload buffer");
-    if (rc) return rc;
-    cudaMemcpyAsync(tmp, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream);
-    cudaMemcpyAsync(tmp + 3 * n, diameter, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
-    dx = tmp;
-    dd = tmp + 3 * n;
-  } else if (dev && n > 0) {
-    uint32_t *bad = nullptr;
-    rc = dalloc(c, &bad, 1, "input check");
-    if (rc) return rc;
-    cudaMemsetAsync(bad, 0, sizeof(uint32_t), c->stream);
-    launch_check_input(c->stream, n, xyz, diameter, bad);
-    uint32_t hb = 0;
-    cudaMemcpyAsync(&hb, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
-    cudaStreamSynchronize(c->stream);
-    dfree(c, bad);
-    if (hb) return fail(c, BDM_E_INVAL, "non-finite position or diameter <= 0 in device input");
+  if (n > 0) {
+    if (!dev) {
+      rc = ensure_xfer(c, (size_t)(4 * n));
+      if (rc) return rc;
+      cudaMemcpyAsync(c->d_xfer, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream);
+      cudaMemcpyAsync(c->d_xfer + 3 * n, diameter, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+      dx = c->d_xfer;
+      dd = c->d_xfer + 3 * n;
+    }
+    cudaMemsetAsync(c->d_bad, 0xFF, sizeof(unsigned long long), c->stream);
+    launch_check_input(c->stream, n, dx, dd, c->d_bad);
+    unsigned long long hb = ~0ull;
+    cudaMemcpyAsync(&hb, c->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "uploading agents");
+    if (hb != ~0ull)
+      return fail(c, BDM_E_INVAL, "non-finite position, or diameter not finite and > 0, at row " + std::to_string(hb));
   }
+  sc.base = base;
+  sc.cap = cap;
+  c->used_slots = used;
+  if (c->D.total_slots != c->used_slots) c->graph_dirty = true;
+  c->D.total_slots = c->used_slots;
   upload_consts(c);
   launch_set_agents(c->D, c->stream, sim, sc.base, n, sc.cap, dx, dd);
   SimState s0;
@@ -569,7 +584,6 @@ int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const 
   for (int a = 0; a < 3; ++a) { s0.bmin[a] = ~0ull; s0.bmax[a] = 0ull; }
   cudaMemcpyAsync(&c->D.ss[sim], &s0, sizeof(SimState), cudaMemcpyHostToDevice, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (tmp) dfree(c, tmp);
   if (e != cudaSuccess) return cuda_fail(c, e, "uploading agents");
   c->n_set[sim] = n;
   // region order for the device loops
@@ -647,20 +661,20 @@ int bdm_get_agents(bdm_ctx *c, int32_t sim, int64_t cap, double *xyz, double *di
   if (s.n > cap) return fail(c, BDM_E_CAPACITY, "cap below the agent count");
   if (s.n == 0) return BDM_OK;
   bool dev = (flags & BDM_DEVICE_PTRS) != 0;
-  double *bx = xyz, *bd = diameter, *tmp = nullptr;
+  double *bx = xyz, *bd = diameter;
   if (!dev) {
-    rc = dalloc(c, &tmp, (size_t)(4 * s.n), "download buffer");
+    rc = ensure_xfer(c, (size_t)(4 * s.n));
     if (rc) return rc;
-    bx = xyz ? tmp : nullptr;
-    bd = diameter ? tmp + 3 * s.n : nullptr;
+    bx = xyz ? c->d_xfer : nullptr;
+    bd = diameter ? c->d_xfer + 3 * s.n : nullptr;
   }
   launch_gather_agents(c->D, c->stream, sim, c->h_sc[sim].base, s.n, bx, bd);
   if (!dev) {
-    if (xyz) cudaMemcpyAsync(xyz, tmp, sizeof(double) * 3 * s.n, cudaMemcpyDeviceToHost, c->stream);
-    if (diameter) cudaMemcpyAsync(diameter, tmp + 3 * s.n, sizeof(double) * s.n, cudaMemcpyDeviceToHost, c->stream);
+    if (xyz) cudaMemcpyAsync(xyz, c->d_xfer, sizeof(double) * 3 * s.n, cudaMemcpyDeviceToHost, c->stream);
+    if (diameter)
+      cudaMemcpyAsync(diameter, c->d_xfer + 3 * s.n, sizeof(double) * s.n, cudaMemcpyDeviceToHost, c->stream);
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (tmp) dfree(c, tmp);
   if (e != cudaSuccess) return cuda_fail(c, e, "downloading agents");
   return BDM_OK;
 }
@@ -1026,11 +1040,13 @@ int bdm_autotune(bdm_ctx *c, int32_t iterations, bdm_tuning *chosen) {
     }
   }
   // re-sort interval: compare the time per iteration, each trial covering
-  // two re-sorts
+  // two re-sorts.  "Never" is a candidate only when no simulation asked for
+  // re-sorting: a short trial cannot see the storage order decay.
   float best_per = best_ms / (float)iterations;
   for (int iv : {0, 5, 10, 25}) {
     if (rc) break;
     if (iv == best.sort_interval) continue;
+    if (iv == 0 && c->any_sort) continue;
     bdm_tuning t = best;
     t.sort_interval = iv;
     rc = bdm_set_tuning(c, &t);

@@ -305,15 +305,17 @@ void launch_set_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, 
   k_set_agents<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, sim, base, n, cap, xyz, diam);
 }
 
-__global__ void k_check_input(int64_t n, const double *xyz, const double *diam, uint32_t *bad) {
+// Smallest row with a non-finite coordinate or a diameter that is not
+// finite and > 0 (*bad stays all-ones when every row is valid).
+__global__ void k_check_input(int64_t n, const double *xyz, const double *diam, unsigned long long *bad) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   bool ok = isfinite(xyz[3 * i]) && isfinite(xyz[3 * i + 1]) && isfinite(xyz[3 * i + 2]) && diam[i] > 0.0 &&
             isfinite(diam[i]);
-  if (!ok) atomicOr(bad, 1u);
+  if (!ok) atomicMin(bad, (unsigned long long)i);
 }
 
-void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, uint32_t *bad) {
+void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, unsigned long long *bad) {
   if (n <= 0) return;
   k_check_input<<<blocks_for(n, kThreads), kThreads, 0, st>>>(n, xyz, diam, bad);
 }

@@ -193,6 +193,14 @@ def test_invalid_input_is_rejected(orc):
     with pytest.raises(binding.BdmError) as e:
         ctx.step(1)  # nothing set yet
     assert e.value.code == -7
+    # rejected calls reserved nothing: the full capacity is still free
+    xyz = np.arange(24, dtype=np.float64).reshape(8, 3) * 10.0
+    ctx.set_agents(0, xyz, np.ones(8))
+    got, d = ctx.get_agents(0)
+    assert np.array_equal(got, xyz) and np.array_equal(d, np.ones(8))
+    xo = np.zeros((8, 3)); do = np.zeros(8)
+    assert ctx.get_agents(0, out=(xo, do))[0] is xo
+    assert np.array_equal(xo, xyz)
 
 
 def test_batched_simulations_match_single_ones(orc):
