@@ -64,7 +64,8 @@ struct bdm_ctx {
   int64_t prof_launches[kStages] = {};
   double prof_ms[kStages] = {};
   // graph of one iteration
-  cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // one iteration without / with the re-sort
+  std::vector<int64_t> h_iter;       // per simulation: iterations since its agents were set
   bool graph_dirty = true;
   double *d_xfer = nullptr;          // host transfer staging (grow-only)
   size_t xfer_cap = 0;               // doubles
@@ -202,8 +203,20 @@ void harvest_events(bdm_ctx *c) {
   cudaGetLastError();
 }
 
+// Whether some simulation re-sorts in its next iteration (the device makes
+// the same test per simulation; the host copy only picks the graph, so that
+// iterations without a re-sort launch none of the sort kernels).
+static bool sort_due(const bdm_ctx *c) {
+  if (!c->any_sort) return false;
+  for (int s = 0; s < c->n_sims; ++s) {
+    const int iv = c->h_sc[s].sort_interval;
+    if (iv > 0 && c->h_sc[s].base >= 0 && c->h_iter[s] % iv == 0) return true;
+  }
+  return false;
+}
+
 // One iteration of every simulation.
-void launch_iteration(bdm_ctx *c) {
+void launch_iteration(bdm_ctx *c, bool sort) {
   const DevCtx &D = c->D;
   cudaStream_t st = c->stream;
   stage_begin(c, 0);
@@ -213,7 +226,7 @@ void launch_iteration(bdm_ctx *c) {
   stage_begin(c, 1);
   launch_count(D, st, 1);
   stage_end(c);
-  if (c->any_sort) {
+  if (c->any_sort && sort) {
     // re-sort by the Morton code of the boxes just counted (when due)
     stage_begin(c, 7);
     launch_morton(D, st, c->d_sort, c->sort_bytes, c->sort_key_bits, c->sort_curve);
@@ -427,6 +440,7 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   c->max_total = max_agents_total;
   c->params.assign(per_sim, per_sim + n_sims);
   c->n_set.assign(n_sims, -1);
+  c->h_iter.assign(n_sims, 0);
   for (int s = 0; s < n_sims; ++s) {
     c->h_sc.push_back(make_const(per_sim[s]));
     if (per_sim[s].precision == BDM_PREC_FP64) c->any_fp64 = true;
@@ -586,6 +600,7 @@ int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const 
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "uploading agents");
   c->n_set[sim] = n;
+  c->h_iter[sim] = 0;
   // region order for the device loops
   std::vector<int32_t> order;
   for (int s = 0; s < c->n_sims; ++s)
@@ -612,29 +627,35 @@ int bdm_step(bdm_ctx *c, int32_t n_iterations) {
     if (resized) c->graph_dirty = true;
     rc = reserve_builds(c, chunk);
     if (rc) return rc;
-    if (c->profiling) {
-      for (int i = 0; i < chunk; ++i) launch_iteration(c);
-    } else {
-      if (c->graph_dirty || !c->gexec) {
-        if (c->gexec) {
-          cudaGraphExecDestroy(c->gexec);
-          c->gexec = nullptr;
+    if (c->graph_dirty) {
+      for (auto &g : c->gexec)
+        if (g) {
+          cudaGraphExecDestroy(g);
+          g = nullptr;
         }
-        cudaGraph_t g;
-        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(c, e, "beginning graph capture");
-        launch_iteration(c);
-        e = cudaStreamEndCapture(c->stream, &g);
-        if (e != cudaSuccess) return cuda_fail(c, e, "capturing the iteration graph");
-        e = cudaGraphInstantiate(&c->gexec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(c, e, "instantiating the iteration graph");
-        c->graph_dirty = false;
-      }
-      for (int i = 0; i < chunk; ++i) {
-        cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+      c->graph_dirty = false;
+    }
+    for (int i = 0; i < chunk; ++i) {
+      const bool srt = sort_due(c);
+      if (c->profiling) {
+        launch_iteration(c, srt);
+      } else {
+        cudaGraphExec_t &gx = c->gexec[srt ? 1 : 0];
+        if (!gx) {
+          cudaGraph_t g;
+          cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+          if (e != cudaSuccess) return cuda_fail(c, e, "beginning graph capture");
+          launch_iteration(c, srt);
+          e = cudaStreamEndCapture(c->stream, &g);
+          if (e != cudaSuccess) return cuda_fail(c, e, "capturing the iteration graph");
+          e = cudaGraphInstantiate(&gx, g, 0);
+          cudaGraphDestroy(g);
+          if (e != cudaSuccess) return cuda_fail(c, e, "instantiating the iteration graph");
+        }
+        cudaError_t e = cudaGraphLaunch(gx, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "launching the iteration graph");
       }
+      for (int s = 0; s < c->n_sims; ++s) c->h_iter[s] += 1;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "launching an iteration");
@@ -926,6 +947,7 @@ struct Snapshot {
   uint64_t *pk = nullptr, *ph = nullptr;
   uint8_t *fl = nullptr, *nz = nullptr;
   std::vector<SimState> ss;
+  std::vector<int64_t> h_iter;
 };
 
 int snap_alloc(bdm_ctx *c, Snapshot &S, size_t M) {
@@ -966,9 +988,11 @@ int snap_copy(bdm_ctx *c, Snapshot &S, size_t M, bool save) {
   if (!e) e = cp(S.fl, A.flags, M);
   if (!e) e = cp(S.nz, A.nnz, M);
   if (save) {
+    S.h_iter = c->h_iter;
     S.ss.resize(c->n_sims);
     if (!e) e = cudaMemcpyAsync(S.ss.data(), c->D.ss, sizeof(SimState) * c->n_sims, cudaMemcpyDeviceToHost, c->stream);
   } else {
+    c->h_iter = S.h_iter;
     if (!e) e = cudaMemcpyAsync(c->D.ss, S.ss.data(), sizeof(SimState) * c->n_sims, cudaMemcpyHostToDevice, c->stream);
   }
   if (!e) e = cudaStreamSynchronize(c->stream);
@@ -1072,7 +1096,8 @@ void bdm_destroy(bdm_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto &e : c->evs) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : c->pool) cudaEventDestroy(e);
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (auto g : c->gexec)
+    if (g) cudaGraphExecDestroy(g);
   for (void *p : c->allocs) cudaFree(p);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(kThreads) k_displace(DevCtx C) {
 }
 
 // ---------------------------------------------------------------------------
-// FP32 path, block-staged variant (the default).
+// FP32 path, block-staged variant (variant 3).
 //
 // A block owns 256 consecutive cells; because cells follow the Morton order
 // of their boxes, they occupy a compact block of boxes.  The block stages

@@ -84,9 +84,9 @@ __global__ void __launch_bounds__(kThreads) k_bbox(DevCtx C, int64_t chunk) {
     const int s0 = C.a.sim[begin], s1 = C.a.sim[end - 1];
     if (s0 == s1 && s0 >= 0) {
       const int64_t last = C.sc[s0].base + C.ss[s0].n;
-      for (int64_t slot = begin + threadIdx.x; slot < end && slot < last; slot += blockDim.x) {
-        const unsigned long long kx = ord_key(C.a.x[slot]), ky = ord_key(C.a.y[slot]), kz = ord_key(C.a.z[slot]);
-        const unsigned long long kd = ord_key(C.a.d[slot]);
+      const int64_t stop = end < last ? end : last;
+      auto add = [&](double x, double y, double z, double d) {
+        const unsigned long long kx = ord_key(x), ky = ord_key(y), kz = ord_key(z), kd = ord_key(d);
         acc.mn[0] = kx < acc.mn[0] ? kx : acc.mn[0];
         acc.mn[1] = ky < acc.mn[1] ? ky : acc.mn[1];
         acc.mn[2] = kz < acc.mn[2] ? kz : acc.mn[2];
@@ -94,7 +94,21 @@ __global__ void __launch_bounds__(kThreads) k_bbox(DevCtx C, int64_t chunk) {
         acc.mx[1] = ky > acc.mx[1] ? ky : acc.mx[1];
         acc.mx[2] = kz > acc.mx[2] ? kz : acc.mx[2];
         acc.dm = kd > acc.dm ? kd : acc.dm;
+      };
+      // four slots per thread and round: 16 independent loads in flight
+      const int64_t step = blockDim.x;
+      int64_t slot = begin + threadIdx.x;
+      for (; slot + 3 * step < stop; slot += 4 * step) {
+        double x[4], y[4], z[4], d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          x[u] = C.a.x[slot + u * step]; y[u] = C.a.y[slot + u * step];
+          z[u] = C.a.z[slot + u * step]; d[u] = C.a.d[slot + u * step];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) add(x[u], y[u], z[u], d[u]);
       }
+      for (; slot < stop; slot += step) add(C.a.x[slot], C.a.y[slot], C.a.z[slot], C.a.d[slot]);
       flush_box(C, s0, acc, sh);
       return;
     }
