@@ -208,6 +208,24 @@ __device__ __forceinline__ void split_ff(double a, float &hi, float &lo) {
   }
 }
 
+// -c as a double for 0 <= c < 2^32, built from its bits (the FP64 pipe of
+// this part is 1/64 of the FP32 rate; conversions would use it).
+__device__ __forceinline__ double neg_u32_to_double(uint32_t c) {
+  if (c == 0u) return -0.0;
+  const int e = 31 - __clz(c);
+  const unsigned long long m = ((unsigned long long)c << (52 - e)) & 0xFFFFFFFFFFFFFull;
+  return __longlong_as_double((long long)(0x8000000000000000ull | ((unsigned long long)(1023 + e) << 52) | m));
+}
+
+// d / 2, exact: the exponent field decremented for normal values whose half
+// is normal, an FP64 multiply otherwise.
+__device__ __forceinline__ double half_of(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned e = (unsigned)((b >> 52) & 0x7FF);
+  if (e > 1u && e < 0x7FFu) return __longlong_as_double((long long)(b - (1ull << 52)));
+  return __dmul_rn(0.5, d);
+}
+
 // Exact float -> double conversion with integer operations for normal
 // values.
 __device__ __forceinline__ double f2d(float f) {

@@ -482,38 +482,39 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(DevCtx C) {
 // Place every agent at start + rank of its box in `cells`.  fp64_records:
 // write the FP64 record whatever the simulation's precision (queries).
 __global__ void __launch_bounds__(kThreads) k_place(DevCtx C, Cells cells, int fp64_records) {
-  int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= C.total_slots) return;
-  int sim = C.a.sim[slot];
+  // every per-slot load first: they do not depend on one another
+  const int sim = C.a.sim[slot];
+  const uint64_t pk = C.a.pkey[slot];
+  const uint32_t rank = C.a.rank[slot];
+  const double pos[3] = {C.a.x[slot], C.a.y[slot], C.a.z[slot]};
+  const double dia = C.a.d[slot];
+  const uint8_t fl = cells.flag ? C.a.flags[slot] : (uint8_t)0;
+  const uint8_t nz = cells.flag ? C.a.nnz[slot] : (uint8_t)0;
   if (sim < 0) return;
   const SimConst &sc = C.sc[sim];
   const SimState &s = C.ss[sim];
   if (slot - sc.base >= s.n || !s.valid) return;
-  uint64_t pk = C.a.pkey[slot];
-  int64_t c[3];
-  unpack_coords(pk, c[0], c[1], c[2]);
-  int64_t idx = sc.table_base + linear_box(s, c[0], c[1], c[2]);
-  const unsigned long long e = C.tab.e[idx];
-  const uint32_t rank = C.a.rank[slot];
+  const uint32_t c[3] = {(uint32_t)(pk & kCoordMask), (uint32_t)((pk >> kCoordBits) & kCoordMask),
+                         (uint32_t)((pk >> (2 * kCoordBits)) & kCoordMask)};
+  const uint32_t off = c[0] + (uint32_t)s.dims[0] * (c[1] + (uint32_t)s.dims[1] * c[2]);
+  const unsigned long long e = C.tab.e[sc.table_base + off];
   if (rank >= ent_count(e)) return;  // box overflow (error latched by the count)
-  int64_t p = (int64_t)ent_start(e) + rank;
+  const int64_t p = (int64_t)ent_start(e) + rank;
   cells.slot[p] = (int32_t)slot;
   cells.sim[p] = sim;
   cells.pkey[p] = pk;
-  if (cells.flag) {
-    uint8_t fl = C.a.flags[slot];
-    cells.flag[p] = (!(fl & FLAG_CHANGED) && C.a.nnz[slot] <= 1) ? CELL_STATIC_ELIGIBLE : 0;
-  }
-  double pos[3] = {C.a.x[slot], C.a.y[slot], C.a.z[slot]};
-  double r = 0.5 * C.a.d[slot];
+  if (cells.flag) cells.flag[p] = (!(fl & FLAG_CHANGED) && nz <= 1) ? CELL_STATIC_ELIGIBLE : 0;
+  const double r = half_of(dia);
   if (fp64_records || sc.precision == BDM_PREC_FP64) {
     cells.r64[p] = make_double4_32a(pos[0], pos[1], pos[2], r);
   } else {
     float h[3], l[3], rh, rl;
     for (int a = 0; a < 3; ++a) {
-      // offset inside the own box, exact in FP64: a - c L
-      double av = __dsub_rn(pos[a], s.o[a]);
-      double w = __fma_rn(-(double)c[a], s.L, av);
+      // offset inside the own box, exact in FP64: (x - o) - c L
+      const double av = __dsub_rn(pos[a], s.o[a]);
+      const double w = __fma_rn(neg_u32_to_double(c[a]), s.L, av);
       split_ff(w, h[a], l[a]);
     }
     split_ff(r, rh, rl);
