@@ -209,11 +209,14 @@ int bdm_forces_noalloc(const bdm_params* params, int64_t n, const double* xyz, c
 /* Tuning knobs of a context.  None of them changes results beyond the
  * order of floating-point sums over neighbors. */
 typedef struct {
-  int32_t force_variant;   /* force kernel of the FP32 path: 0 direct walk, rows
-                              flattened, pair evaluation deferred (default); 1 direct
-                              loop, pairs evaluated in the walk; 2 global queue;
-                              3 block-staged; 4 row queue; 5 as 0 without row
-                              flattening. FP64 always direct */
+  int32_t force_variant;   /* force kernel of the FP32 path: 0 symmetric half
+                              stencil, each pair found once and its force added
+                              to both agents (default; 1 stands in when a
+                              simulation detects static agents); 1 direct walk,
+                              rows flattened, pair evaluation deferred; 2 direct
+                              loop, pairs evaluated in the walk; 3 global queue;
+                              4 block-staged; 5 row queue; 6 as 1 box by box.
+                              FP64 always direct */
   int32_t sort_interval;   /* -1: every simulation's own sort_interval;
                               >= 0: this re-sort interval for all simulations */
   int32_t sort_curve;      /* order the re-sort gives the storage: 0 Morton order of the

@@ -166,7 +166,7 @@ __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, con
       }
     }
   }
-  C.c.f32[p] = make_float4(fx, fy, fz, 0.f);
+  C.c.f32[p] = make_float4(fx, fy, fz, (float)nnz);
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
 }
 
@@ -336,8 +336,136 @@ __device__ __forceinline__ void force32_deferred(const DevCtx &C, const SimConst
     return;
   }
   flush_hits(C, p, o0, n, hq, Lh, s.Ll, sc.kf, sc.gammaf, fx, fy, fz, nnz);
-  C.c.f32[p] = make_float4(fx, fy, fz, 0.f);
+  C.c.f32[p] = make_float4(fx, fy, fz, (float)nnz);
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
+}
+
+// Pair force of candidate j on p as a vector (the operations of pair32);
+// false when the pair does not interact.  nz: the scalar force is not zero.
+__device__ __forceinline__ bool pair32_vec(const DevCtx &C, int64_t p, const float4 &o0, const float4 &o1,
+                                           int64_t j, const float4 &q, float fdx, float fdy, float fdz, float Lh,
+                                           float Ll, float kf, float gf, float &gx, float &gy, float &gz,
+                                           bool &nz) {
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  uint32_t n = 0;
+  const bool hit = pair32(C, p, o0, o1, j, q, fdx, fdy, fdz, Lh, Ll, kf, gf, fx, fy, fz, n);
+  gx = fx; gy = fy; gz = fz;
+  nz = n != 0u;
+  return hit;
+}
+
+// Symmetric half-stencil walk (FP32 path, simulations without static
+// detection).  Every interacting pair is found once: by the agent whose own
+// box comes first in the order (z, y, x), or, inside one box, by the agent
+// with the lower cell index.  The walk covers the agent's own box after its
+// cell and the 13 neighbour boxes ahead of it (5 stencil rows instead of 9);
+// the pair force goes to both agents, to the partner (and to the agent
+// itself) by vector atomic adds onto forces the placement zeroed.  The w
+// component counts the non-zero pair forces.  Candidates that pass the
+// filter are queued as in the deferred walk; an agent with more than
+// kHitCap of them evaluates its pairs during a second walk instead.
+template <bool kQueue>
+__device__ __forceinline__ uint32_t sym_walk(const DevCtx &C, const SimConst &sc, const SimState &s, uint32_t p,
+                                             const float4 &o0, const Stencil &t, uint32_t stamp, HitQueue &hq,
+                                             float &fx, float &fy, float &fz, uint32_t &nnz) {
+  const float Lh = s.Lh;
+  const float rw = __fadd_rn(o0.w, s.marg);
+  const float4 *__restrict__ r0 = C.c.r0;
+  const float sxm = __fadd_rn(o0.x, Lh), sxp = __fsub_rn(o0.x, Lh);
+  const bool x0 = t.xlo < 0, x2 = t.xhi > 0;
+  float4 o1 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if constexpr (!kQueue) o1 = C.c.r1[p];
+  uint32_t n = 0;
+  for (int r = 0; r < 5; ++r) {
+    const int dz = r < 2 ? 0 : 1;
+    const int dy = r == 0 ? 0 : (r == 1 ? 1 : r - 3);
+    if (dy < t.ylo || dy > t.yhi || dz > t.zhi) continue;
+    const float sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
+    const float sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh));
+    const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
+                         (uint32_t)t.cx;
+    const int code_row = (dz + 1) * 9 + (dy + 1) * 3;
+    // three segments A, B, C of candidates, walked as one sequence
+    uint32_t cA, cB, cC, jA, jB, jC;
+    float sA, sB, sC;
+    int kA, kB, kC;
+    if (r == 0) {
+      const unsigned long long eo = __ldg(t.e + row);
+      const unsigned long long ep = x2 ? __ldg(t.e + row + 1) : 0ull;
+      // own box: the cells after p (none unless p lies in the box)
+      const uint32_t os = ent_start(eo), oc = ent_live(eo, stamp);
+      cA = (p >= os && p - os < oc) ? os + oc - (p + 1u) : 0u;
+      jA = p + 1u; sA = o0.x; kA = code_row + 1;
+      cB = ent_live(ep, stamp); jB = ent_start(ep); sB = sxp; kB = code_row + 2;
+      cC = 0u; jC = 0u; sC = 0.f; kC = 0;
+    } else {
+      const unsigned long long em = x0 ? __ldg(t.e + row - 1) : 0ull;
+      const unsigned long long eo = __ldg(t.e + row);
+      const unsigned long long ep = x2 ? __ldg(t.e + row + 1) : 0ull;
+      cA = ent_live(em, stamp); jA = ent_start(em); sA = sxm; kA = code_row;
+      cB = ent_live(eo, stamp); jB = ent_start(eo); sB = o0.x; kB = code_row + 1;
+      cC = ent_live(ep, stamp); jC = ent_start(ep); sC = sxp; kC = code_row + 2;
+    }
+    const uint32_t eAB = cA + cB, tot = eAB + cC;
+    const uint32_t bA = jA, bB = jB - cA, bC = jC - eAB;
+    for (uint32_t k = 0; k < tot; ++k) {
+      const bool inA = k < cA, inB = k < eAB;
+      const uint32_t j = k + (inA ? bA : (inB ? bB : bC));
+      const float sx = inA ? sA : (inB ? sB : sC);
+      const float4 qv = r0[j];
+      const float ddx = __fsub_rn(sx, qv.x), ddy = __fsub_rn(sy, qv.y), ddz = __fsub_rn(sz, qv.z);
+      const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+      const float Rm = __fadd_rn(rw, qv.w);
+      if (!(s2 < __fmul_rn(Rm, Rm))) continue;
+      const int code = inA ? kA : (inB ? kB : kC);
+      if constexpr (kQueue) {
+        if (n < (uint32_t)kHitCap) {
+          hq.j[n][threadIdx.x] = j;
+          hq.b[n][threadIdx.x] = (uint8_t)code;
+        }
+        ++n;
+      } else {
+        float gx, gy, gz;
+        bool nz;
+        const float fdx = (float)(code % 3 - 1), fdy = (float)((code / 3) % 3 - 1), fdz = (float)(code / 9 - 1);
+        if (pair32_vec(C, (int64_t)p, o0, o1, (int64_t)j, qv, fdx, fdy, fdz, Lh, s.Ll, sc.kf, sc.gammaf, gx, gy,
+                       gz, nz)) {
+          fx = __fadd_rn(fx, gx); fy = __fadd_rn(fy, gy); fz = __fadd_rn(fz, gz);
+          nnz += nz ? 1u : 0u;
+          atomicAdd(&C.c.f32[j], make_float4(-gx, -gy, -gz, nz ? 1.f : 0.f));
+        }
+      }
+    }
+  }
+  return n;
+}
+
+__device__ __forceinline__ void force32_sym(const DevCtx &C, const SimConst &sc, const SimState &s, uint32_t p,
+                                            int64_t cx, int64_t cy, int64_t cz, uint32_t stamp, HitQueue &hq) {
+  const float4 o0 = C.c.r0[p];
+  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  uint32_t nnz = 0;
+  const uint32_t n = sym_walk<true>(C, sc, s, p, o0, t, stamp, hq, fx, fy, fz, nnz);
+  if (n > (uint32_t)kHitCap) {
+    sym_walk<false>(C, sc, s, p, o0, t, stamp, hq, fx, fy, fz, nnz);
+  } else {
+    const float4 o1 = C.c.r1[p];
+    for (uint32_t k = 0; k < n; ++k) {
+      const uint32_t j = hq.j[k][threadIdx.x];
+      const int b = hq.b[k][threadIdx.x];
+      const float fdx = (float)(b % 3 - 1), fdy = (float)((b / 3) % 3 - 1), fdz = (float)(b / 9 - 1);
+      float gx, gy, gz;
+      bool nz;
+      if (pair32_vec(C, (int64_t)p, o0, o1, (int64_t)j, C.c.r0[j], fdx, fdy, fdz, s.Lh, s.Ll, sc.kf, sc.gammaf,
+                     gx, gy, gz, nz)) {
+        fx = __fadd_rn(fx, gx); fy = __fadd_rn(fy, gy); fz = __fadd_rn(fz, gz);
+        nnz += nz ? 1u : 0u;
+        atomicAdd(&C.c.f32[j], make_float4(-gx, -gy, -gz, nz ? 1.f : 0.f));
+      }
+    }
+  }
+  atomicAdd(&C.c.f32[p], make_float4(fx, fy, fz, (float)nnz));
 }
 
 __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
@@ -387,6 +515,7 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
 
 // fp64_only: leave FP32-path simulations to another kernel.
 __global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C, int fp64_only) {
+  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
   int sim = C.c.sim[p];
@@ -410,6 +539,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C, int fp64_only) 
 template <bool kRowFlat>
 __global__ void __launch_bounds__(kThreads, 4) k_force32d(DevCtx C) {
   __shared__ HitQueue hq;
+  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
   int sim = C.c.sim[p];
@@ -425,8 +555,26 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32d(DevCtx C) {
   force32_deferred<kRowFlat>(C, sc, s, (uint32_t)p, cx, cy, cz, stamp, hq);
 }
 
+// FP32-path simulations only (none with static detection), symmetric
+// half-stencil walk; the forces were zeroed by the placement.
+__global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
+  __shared__ HitQueue hq;
+  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= C.g->n_cells) return;
+  int sim = C.c.sim[p];
+  const SimConst &sc = C.sc[sim];
+  const SimState &s = C.ss[sim];
+  if (!s.valid || sc.precision == BDM_PREC_FP64) return;
+  int64_t cx, cy, cz;
+  unpack_coords(C.c.pkey[p], cx, cy, cz);
+  C.c.stat[p] = 0;
+  force32_sym(C, sc, s, (uint32_t)p, cx, cy, cz, C.g->stamp & kStampMask, hq);
+}
+
 // S5: displacement.  Static agents keep their position and nnz.
 __global__ void __launch_bounds__(kThreads) k_displace(DevCtx C) {
+  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
   int sim = C.c.sim[p];
@@ -437,9 +585,9 @@ __global__ void __launch_bounds__(kThreads) k_displace(DevCtx C) {
     C.a.flags[slot] = FLAG_STATIC;
     return;
   }
-  C.a.nnz[slot] = C.c.nnz[p];
   bool moved = false, bad = false;
   if (sc.precision == BDM_PREC_FP64) {
+    C.a.nnz[slot] = C.c.nnz[p];
     double4_32a F = C.c.f64[p];
     double fn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(F.x, F.x), __dmul_rn(F.y, F.y)), __dmul_rn(F.z, F.z)));
     bad = !isfinite(fn);
@@ -459,6 +607,8 @@ __global__ void __launch_bounds__(kThreads) k_displace(DevCtx C) {
     }
   } else {
     float4 F = C.c.f32[p];
+    // FP32 path: w carries the count of non-zero pair forces
+    C.a.nnz[slot] = (uint8_t)(F.w > 255.f ? 255u : (unsigned)F.w);
     float f2 = __fmaf_rn(F.z, F.z, __fmaf_rn(F.y, F.y, __fmul_rn(F.x, F.x)));
     bad = !isfinite(f2);
     if (f2 > sc.adherence2f) {
@@ -481,7 +631,7 @@ __global__ void __launch_bounds__(kThreads) k_displace(DevCtx C) {
 }
 
 // ---------------------------------------------------------------------------
-// FP32 path, block-staged variant (variant 3).
+// FP32 path, block-staged variant (variant 4).
 //
 // A block owns 256 consecutive cells; because cells follow the Morton order
 // of their boxes, they occupy a compact block of boxes.  The block stages
@@ -570,6 +720,7 @@ __device__ __forceinline__ void eval_ff(const DevCtx &C, BlockStage &S, uint2 qe
 }
 
 __global__ void __launch_bounds__(kBT, 4) k_force32b(DevCtx C) {
+  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockStage &S = *reinterpret_cast<BlockStage *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -758,14 +909,14 @@ __global__ void __launch_bounds__(kBT, 4) k_force32b(DevCtx C) {
   if (lane < qn) eval_ff(C, S, S.q[warp][lane], p0, warp);
   __syncwarp();
   if (active) {
-    C.c.f32[p] = make_float4(S.acc[0][tid], S.acc[1][tid], S.acc[2][tid], 0.f);
     const float nz = S.acc[3][tid];
+    C.c.f32[p] = make_float4(S.acc[0][tid], S.acc[1][tid], S.acc[2][tid], nz);
     C.c.nnz[p] = (uint8_t)(nz > 255.f ? 255u : (unsigned)nz);
   }
 }
 
 // ---------------------------------------------------------------------------
-// FP32 path, row-queue variant: the direct loop's row-batched table loads,
+// FP32 path, row-queue variant (variant 5): the direct loop's row-batched table loads,
 // one flattened loop over the candidates of the three boxes of a row (no
 // reloads), and the pairs that pass the FP32 filter queued per warp and
 // evaluated 32 at a time by the full warp (float-float overlap), results
@@ -833,6 +984,7 @@ __device__ __forceinline__ void eval_rq(const DevCtx &C, RowQueueSmem &S, uint2 
 }
 
 __global__ void __launch_bounds__(kBT, 4) k_force32rq(DevCtx C) {
+  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   __shared__ RowQueueSmem S;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned FULL = 0xffffffffu;
@@ -924,8 +1076,8 @@ __global__ void __launch_bounds__(kBT, 4) k_force32rq(DevCtx C) {
   if (lane < qn) eval_rq(C, S, S.q[warp][lane], p0, warp);
   __syncwarp();
   if (active) {
-    C.c.f32[p] = make_float4(S.acc[0][tid], S.acc[1][tid], S.acc[2][tid], 0.f);
     const float nz = S.acc[3][tid];
+    C.c.f32[p] = make_float4(S.acc[0][tid], S.acc[1][tid], S.acc[2][tid], nz);
     C.c.nnz[p] = (uint8_t)(nz > 255.f ? 255u : (unsigned)nz);
   }
 }
@@ -943,17 +1095,22 @@ void launch_force32b(const DevCtx &C, cudaStream_t st) {
 
 static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
+// Variants of the FP32 path: 0 symmetric half stencil, 1 deferred walk with
+// rows flattened, 2 direct loop, 3 global queue, 4 block-staged, 5 row
+// queue, 6 deferred walk box by box.  FP64 simulations always take the
+// direct loop.
 void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64) {
   const unsigned int nb = blocks_for(C.total_slots, kThreads);
-  if (variant == 1) {
+  if (variant == 2) {
     k_force<<<nb, kThreads, 0, st>>>(C, 0);
     return;
   }
   if (has_fp32) {
-    if (variant == 2) launch_force32q(C, st);
-    else if (variant == 3) launch_force32b(C, st);
-    else if (variant == 4) launch_force32rq(C, st);
-    else if (variant == 5) k_force32d<false><<<nb, kThreads, 0, st>>>(C);
+    if (variant == 0) k_force32s<<<nb, kThreads, 0, st>>>(C);
+    else if (variant == 3) launch_force32q(C, st);
+    else if (variant == 4) launch_force32b(C, st);
+    else if (variant == 5) launch_force32rq(C, st);
+    else if (variant == 6) k_force32d<false><<<nb, kThreads, 0, st>>>(C);
     else k_force32d<true><<<nb, kThreads, 0, st>>>(C);
   }
   if (has_fp64) k_force<<<nb, kThreads, 0, st>>>(C, 1);

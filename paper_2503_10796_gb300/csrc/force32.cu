@@ -103,6 +103,7 @@ __device__ __forceinline__ void eval_pair(const DevCtx &C, Force32Smem &S, int w
 }
 
 __global__ void __launch_bounds__(kFT, 3) k_force32q(DevCtx C) {
+  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Force32Smem &S = *reinterpret_cast<Force32Smem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -228,8 +229,8 @@ __global__ void __launch_bounds__(kFT, 3) k_force32q(DevCtx C) {
   }
   __syncwarp();
   if (active) {
-    C.c.f32[p] = make_float4(S.acc[0][tid], S.acc[1][tid], S.acc[2][tid], 0.f);
     float nz = S.acc[3][tid];
+    C.c.f32[p] = make_float4(S.acc[0][tid], S.acc[1][tid], S.acc[2][tid], nz);
     C.c.nnz[p] = (uint8_t)(nz > 255.f ? 255u : (unsigned)nz);
   }
   (void)kf;

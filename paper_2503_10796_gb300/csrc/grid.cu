@@ -481,7 +481,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(DevCtx C) {
 
 // Place every agent at start + rank of its box in `cells`.  fp64_records:
 // write the FP64 record whatever the simulation's precision (queries).
-__global__ void __launch_bounds__(kThreads) k_place(DevCtx C, Cells cells, int fp64_records) {
+// zero_f32: clear the FP32 force of every placed FP32-path agent (the
+// symmetric force walk adds into it).
+__global__ void __launch_bounds__(kThreads) k_place(DevCtx C, Cells cells, int fp64_records, int zero_f32) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= C.total_slots) return;
   // every per-slot load first: they do not depend on one another
@@ -520,6 +522,7 @@ __global__ void __launch_bounds__(kThreads) k_place(DevCtx C, Cells cells, int f
     split_ff(r, rh, rl);
     cells.r0[p] = make_float4(h[0], h[1], h[2], rh);
     cells.r1[p] = make_float4(l[0], l[1], l[2], rl);
+    if (zero_f32) cells.f32[p] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -554,8 +557,9 @@ void launch_scan(const DevCtx &C, cudaStream_t st) {
   k_scan_down<<<(unsigned int)G, kScanThreads, 0, st>>>(C);
 }
 
-void launch_place(const DevCtx &C, cudaStream_t st, int step) {
-  k_place<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, step ? C.c : C.q, step ? 0 : 1);
+void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32) {
+  k_place<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, step ? C.c : C.q, step ? 0 : 1,
+                                                                     step ? zero_f32 : 0);
 }
 
 }  // namespace bdm

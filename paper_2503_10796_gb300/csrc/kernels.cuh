@@ -13,7 +13,7 @@ void launch_count(const DevCtx &C, cudaStream_t st, int step);
 // partial (scan_tiles(total_slots) entries).
 int64_t scan_tiles(int64_t total_slots);
 void launch_scan(const DevCtx &C, cudaStream_t st);
-void launch_place(const DevCtx &C, cudaStream_t st, int step);
+void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32 = 0);
 
 // force.cu, force32.cu
 // variant 0 (default) or 1: the direct kernel for both paths (force.cu);

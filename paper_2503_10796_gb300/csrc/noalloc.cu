@@ -147,8 +147,11 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   launch_params(D, st, 1);
   launch_count(D, st, 1);
   launch_scan(D, st);
-  launch_place(D, st, 1);
-  launch_force(D, st);
+  // symmetric force walk (forces zeroed by the placement), unless static
+  // agents are detected
+  const int variant = (p.precision != BDM_PREC_FP64 && p.detect_static) ? 1 : 0;
+  launch_place(D, st, 1, variant == 0 ? 1 : 0);
+  launch_force(D, st, variant);
   // The grid's fit is known only on the device: read the error word before
   // the results are gathered into the caller's buffers.
   uint32_t err = 0;

@@ -229,21 +229,27 @@ __global__ void k_gather_forces(DevCtx C, int sim, int64_t cell_base, int64_t n,
   int64_t id = C.a.id[C.c.slot[p]];
   bool st = C.c.stat[p] != 0;
   double f[3] = {0.0, 0.0, 0.0};
+  int32_t nz = 0;
   if (!st) {
     if (C.sc[sim].precision == BDM_PREC_FP64) {
       double4_32a F = C.c.f64[p];
       f[0] = F.x; f[1] = F.y; f[2] = F.z;
+      nz = (int32_t)C.c.nnz[p];
     } else {
+      // FP32 path: w carries the count of non-zero pair forces
       float4 F = C.c.f32[p];
       f[0] = F.x; f[1] = F.y; f[2] = F.z;
+      nz = (int32_t)(F.w > 255.f ? 255.f : F.w);
     }
+  } else {
+    nz = (int32_t)C.a.nnz[C.c.slot[p]];
   }
   if (force) {
     force[3 * id] = f[0];
     force[3 * id + 1] = f[1];
     force[3 * id + 2] = f[2];
   }
-  if (nnz) nnz[id] = st ? (int32_t)C.a.nnz[C.c.slot[p]] : (int32_t)C.c.nnz[p];
+  if (nnz) nnz[id] = nz;
   if (stat) stat[id] = st ? 1 : 0;
 }
 

@@ -322,7 +322,8 @@ def test_division_stops_at_capacity(orc):
 
 def dense_clump(n=300, side=20.0, seed=11):
     """Heavily overlapping agents: each has far more than 16 partners, so the
-    deferred walk's queue overflows and the direct loop takes over."""
+    queues of the deferred and symmetric walks overflow and their second,
+    evaluating walks take over."""
     rng = np.random.default_rng(seed)
     xyz = rng.uniform(0.0, side, (n, 3))
     d = rng.uniform(8.0, 12.0, n)
@@ -330,15 +331,17 @@ def dense_clump(n=300, side=20.0, seed=11):
 
 
 def test_deferred_walk_equals_direct_loop(orc):
-    """The deferred walk (queue and overflow path) and the direct loop find the
-    same interacting pairs (nnz equal) and agree to FP32 rounding.  Bitwise
+    """The deferred walk (queue and overflow path), the symmetric half-stencil
+    walk (queue and overflow path) and the direct loop find the same
+    interacting pairs (nnz equal) and agree to FP32 rounding.  Bitwise
     equality is not expected: agents of one box are placed in the order their
-    atomic count arrived, which sets the order of the FP32 sum."""
+    atomic count arrived, and the symmetric walk adds pair forces by atomics,
+    which both set the order of the FP32 sum."""
     for pop in (workloads.clustered(n_clusters=4, per_cluster=2000, side=500.0, sigma=30.0, seed=2),
                 dense_clump()):
         _, _, smag = orc_for(pop).forces()
         out = []
-        for variant in (0, 1, 5):
+        for variant in (1, 0, 2, 6):
             ctx = ctx_for(pop, precision=1, sort_interval=1)
             ctx.set_tuning(force_variant=variant)
             ctx.step(1)
@@ -351,7 +354,7 @@ def test_deferred_walk_equals_direct_loop(orc):
             assert err.max() <= 1e-5, err.max()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_force_variants_match_oracle(orc, variant):
     """Every force-kernel variant of the FP32 path meets the tolerance."""
     for pop in (workloads.plain_fp64(seed=5),
@@ -377,7 +380,7 @@ def test_autotune_restores_state(orc):
     b.step(3)
     x_before, _ = a.get_agents(0)
     chosen = a.autotune(3)
-    assert chosen["force_variant"] in (0, 1, 2, 3, 4, 5)
+    assert chosen["force_variant"] in (0, 1, 2, 3, 4, 5, 6)
     x_after, _ = a.get_agents(0)
     assert np.array_equal(x_before, x_after)
     assert a.stats(0)["iterations"] == 3
