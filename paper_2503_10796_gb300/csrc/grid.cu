@@ -290,20 +290,28 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
   const bool valid = in && sim >= 0 && sl - sc.base < s.n && s.valid;
   const unsigned vmask = __ballot_sync(0xffffffffu, valid);
   if (!valid) return;
-  int64_t c[3];
-  for (int a = 0; a < 3; ++a) {
-    double av = __dsub_rn(p[a], s.o[a]);
-    float ah, al;
-    split_ff(av, ah, al);
-    int64_t ca = box_coord(av, ah, al, s.ilh, s.ill, s.L);
-    c[a] = ca < 0 ? 0 : (ca >= s.dims[a] ? s.dims[a] - 1 : ca);
+  const bool changed = hist && (fl & FLAG_CHANGED) != 0;
+  uint32_t c[3];
+  if (hist && s.same_grid && !changed) {
+    // unchanged agent, unchanged grid: the box of the last iteration
+    c[0] = (uint32_t)(pk_prev_in & kCoordMask);
+    c[1] = (uint32_t)((pk_prev_in >> kCoordBits) & kCoordMask);
+    c[2] = (uint32_t)((pk_prev_in >> (2 * kCoordBits)) & kCoordMask);
+  } else {
+    for (int a = 0; a < 3; ++a) {
+      double av = __dsub_rn(p[a], s.o[a]);
+      float ah, al;
+      split_ff(av, ah, al);
+      int64_t ca = box_coord(av, ah, al, s.ilh, s.ill, s.L);
+      c[a] = (uint32_t)(ca < 0 ? 0 : (ca >= s.dims[a] ? s.dims[a] - 1 : ca));
+    }
   }
-  const uint64_t pk = pack_coords(c[0], c[1], c[2]);
-  const int64_t idx = sc.table_base + linear_box(s, c[0], c[1], c[2]);
+  const uint64_t pk = (uint64_t)c[0] | ((uint64_t)c[1] << kCoordBits) | ((uint64_t)c[2] << (2 * kCoordBits));
+  const int64_t idx =
+      sc.table_base + (int64_t)(c[0] + (uint32_t)s.dims[0] * (c[1] + (uint32_t)s.dims[1] * c[2]));
   // Lanes of a warp that share a box add their count with one atomic
   // (neighbouring slots mostly share boxes once the storage is sorted).
   const unsigned peers = __match_any_sync(vmask, (unsigned long long)idx);
-  const bool changed = hist && (fl & FLAG_CHANGED) != 0;
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
   const unsigned dirty_any = __reduce_or_sync(peers, changed ? 1u : 0u);
