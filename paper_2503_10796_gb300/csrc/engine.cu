@@ -909,8 +909,8 @@ int bdm_get_profile(bdm_ctx *c, int64_t launches[BDM_NUM_STAGES], double ms[BDM_
 
 int bdm_set_tuning(bdm_ctx *c, const bdm_tuning *t) {
   if (!c || !t) return BDM_E_INVAL;
-  if (t->force_variant < 0 || t->force_variant > 6)
-    return fail(c, BDM_E_INVAL, "force_variant must be 0 to 6");
+  if (t->force_variant < 0 || t->force_variant > 3)
+    return fail(c, BDM_E_INVAL, "force_variant must be 0 to 3");
   if (t->sort_interval < -1) return fail(c, BDM_E_INVAL, "sort_interval must be >= -1");
   if (t->sort_curve != 0 && t->sort_curve != 1) return fail(c, BDM_E_INVAL, "sort_curve must be 0 or 1");
   for (int k = 0; k < 5; ++k)
@@ -1044,7 +1044,7 @@ int bdm_autotune(bdm_ctx *c, int32_t iterations, bdm_tuning *chosen) {
   bdm_get_tuning(c, &best);
   float best_ms = 1e30f;
   std::vector<int> variants = {0};
-  if (c->any_fp32) variants = {0, 1, 2, 3, 4, 5, 6};
+  if (c->any_fp32) variants = {0, 1, 2, 3};
   for (int v : variants) {
     if (rc) break;
     bdm_tuning t = best;

@@ -630,475 +630,11 @@ __global__ void __launch_bounds__(kThreads) k_displace(DevCtx C) {
   C.a.flags[slot] = moved ? FLAG_CHANGED : 0;
 }
 
-// ---------------------------------------------------------------------------
-// FP32 path, block-staged variant (variant 4).
-//
-// A block owns 256 consecutive cells; because cells follow the Morton order
-// of their boxes, they occupy a compact block of boxes.  The block stages
-// the table words and FP32 records of that box block plus a one-box halo in
-// shared memory -- two rounds of independent loads, table words then
-// records -- and every thread then walks the candidates of its 27-box
-// stencil out of shared memory in one flattened loop.  Pairs that pass the
-// FP32 filter are queued per warp (ballot + popc) and evaluated 32 at a
-// time by the full warp with the float-float overlap; results go to the
-// owning thread's accumulator with shared-memory atomics.  Blocks whose
-// region has more than kBRB boxes or kBRK records (sparse regions where 256
-// cells span a long Morton range, or very dense boxes) run the reference
-// loop above instead.
-// ---------------------------------------------------------------------------
-constexpr int kBT = 256;
-constexpr int kBRB = 1024;
-constexpr int kBRK = 1536;
-constexpr int kBQ = 64;
-
-struct BlockStage {
-  uint16_t rcnt[kBRB];
-  uint16_t roff[kBRB];
-  uint32_t rstart[kBRB];
-  float4 rec[kBRK];
-  uint32_t ridx[kBRK];
-  uint2 q[kBT / 32][kBQ];
-  float acc[4][kBT];
-  unsigned red[8];
-  uint32_t wsum[kBT / 32 + 1];
-};
-
-__device__ __forceinline__ void eval_ff(const DevCtx &C, BlockStage &S, uint2 qe, int64_t block_p0, int warp) {
-  const int owner = warp * 32 + (int)(qe.y & 31u);
-  const int code = (int)(qe.y >> 8);
-  const uint32_t j = qe.x;
-  const int64_t po = block_p0 + owner;
-  const int sim = C.c.sim[po];
-  const SimConst &sc = C.sc[sim];
-  const SimState &s = C.ss[sim];
-  const float4 o0 = C.c.r0[po], o1 = C.c.r1[po];
-  const float4 q0 = C.c.r0[j], q1 = C.c.r1[j];
-  const float fdx = (float)(code % 3 - 1), fdy = (float)((code / 3) % 3 - 1), fdz = (float)(code / 9 - 1);
-  float xh, xl, yh, yl, zh, zl;
-  ff_diff(o0.x, o1.x, q0.x, q1.x, __fmul_rn(fdx, s.Lh), __fmul_rn(fdx, s.Ll), xh, xl);
-  ff_diff(o0.y, o1.y, q0.y, q1.y, __fmul_rn(fdy, s.Lh), __fmul_rn(fdy, s.Ll), yh, yl);
-  ff_diff(o0.z, o1.z, q0.z, q1.z, __fmul_rn(fdz, s.Lh), __fmul_rn(fdz, s.Ll), zh, zl);
-  float p0, e0, p1, e1, p2, e2;
-  two_prod(xh, xh, p0, e0);
-  e0 = __fmaf_rn(__fmul_rn(2.f, xh), xl, e0);
-  two_prod(yh, yh, p1, e1);
-  e1 = __fmaf_rn(__fmul_rn(2.f, yh), yl, e1);
-  two_prod(zh, zh, p2, e2);
-  e2 = __fmaf_rn(__fmul_rn(2.f, zh), zl, e2);
-  float Sa, Sea, Sb, Seb;
-  two_sum(p0, p1, Sa, Sea);
-  two_sum(Sa, p2, Sb, Seb);
-  const float sl = __fadd_rn(__fadd_rn(Sea, Seb), __fadd_rn(__fadd_rn(e0, e1), e2));
-  float sh, sll;
-  fast_two_sum(Sb, sl, sh, sll);
-  float Rh, Rl;
-  two_sum(o0.w, q0.w, Rh, Rl);
-  Rl = __fadd_rn(Rl, __fadd_rn(o1.w, q1.w));
-  float Qh, Ql;
-  two_prod(Rh, Rh, Qh, Ql);
-  Ql = __fmaf_rn(__fmul_rn(2.f, Rh), Rl, Ql);
-  const float num = __fadd_rn(__fsub_rn(Qh, sh), __fsub_rn(Ql, sll));
-  const float dist = sqrtf(sh);
-  float del;
-  if (fabsf(num) < kTinyNum) {
-    const double d64 = exact_delta(C, C.c.slot[po], C.c.slot[j]);
-    if (!(d64 > 0.0)) return;
-    del = (float)d64;
-  } else {
-    if (!(num > 0.f)) return;
-    del = __fdividef(num, __fadd_rn(Rh, dist));
-  }
-  const float rr = __fdividef(__fmul_rn(o0.w, q0.w), Rh);
-  const float fn = __fsub_rn(__fmul_rn(sc.kf, del), __fmul_rn(sc.gammaf, sqrtf(__fmul_rn(rr, del))));
-  if (fn != 0.f) atomicAdd(&S.acc[3][owner], 1.0f);
-  if (dist > 0.f) {
-    const float f = __fdividef(fn, dist);
-    atomicAdd(&S.acc[0][owner], __fmul_rn(f, xh));
-    atomicAdd(&S.acc[1][owner], __fmul_rn(f, yh));
-    atomicAdd(&S.acc[2][owner], __fmul_rn(f, zh));
-  }
-}
-
-__global__ void __launch_bounds__(kBT, 4) k_force32b(DevCtx C) {
-  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  BlockStage &S = *reinterpret_cast<BlockStage *>(smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned FULL = 0xffffffffu;
-  const int64_t p0 = (int64_t)blockIdx.x * kBT;
-  const int64_t p = p0 + tid;
-  const int64_t ncell = C.g->n_cells;
-  if (p0 >= ncell) return;
-  const uint32_t stamp = C.g->stamp & kStampMask;
-  bool active = p < ncell;
-  const int sim = active ? C.c.sim[p] : 0;
-  const SimConst &sc = C.sc[sim];
-  const SimState &s = C.ss[sim];
-  if (active && (!s.valid || sc.precision != BDM_PREC_FP32_FORCE)) active = false;
-  int64_t cx = 0, cy = 0, cz = 0;
-  if (active) {
-    unpack_coords(C.c.pkey[p], cx, cy, cz);
-    const bool st = is_static_cell(C, sc, s, p, cx, cy, cz, stamp);
-    C.c.stat[p] = st ? 1 : 0;
-    if (st) active = false;
-  }
-  S.acc[0][tid] = 0.f; S.acc[1][tid] = 0.f; S.acc[2][tid] = 0.f; S.acc[3][tid] = 0.f;
-  // block bounding box of the active cells' boxes and their simulation
-  if (tid < 8) S.red[tid] = (tid & 1) ? 0u : 0xFFFFFFFFu;
-  __syncthreads();
-  {
-    const unsigned v[8] = {active ? (unsigned)sim : 0xFFFFFFFFu, active ? (unsigned)sim : 0u,
-                           active ? (unsigned)cx : 0xFFFFFFFFu, active ? (unsigned)cx : 0u,
-                           active ? (unsigned)cy : 0xFFFFFFFFu, active ? (unsigned)cy : 0u,
-                           active ? (unsigned)cz : 0xFFFFFFFFu, active ? (unsigned)cz : 0u};
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const unsigned r = (k & 1) ? __reduce_max_sync(FULL, v[k]) : __reduce_min_sync(FULL, v[k]);
-      if (lane == 0) {
-        if (k & 1) atomicMax(&S.red[k], r);
-        else atomicMin(&S.red[k], r);
-      }
-    }
-  }
-  __syncthreads();
-  const bool any = S.red[1] >= S.red[0] && S.red[0] != 0xFFFFFFFFu;
-  if (!any) return;  // block-uniform: nothing to compute here
-  const int us = (int)S.red[0];
-  const bool uniform = S.red[0] == S.red[1];
-  const SimState &su = C.ss[us];
-  const SimConst &scu = C.sc[us];
-  const int64_t lox = S.red[2] > 0 ? (int64_t)S.red[2] - 1 : 0;
-  const int64_t loy = S.red[4] > 0 ? (int64_t)S.red[4] - 1 : 0;
-  const int64_t loz = S.red[6] > 0 ? (int64_t)S.red[6] - 1 : 0;
-  const int64_t hix = (int64_t)S.red[3] + 1 < su.dims[0] ? (int64_t)S.red[3] + 1 : su.dims[0] - 1;
-  const int64_t hiy = (int64_t)S.red[5] + 1 < su.dims[1] ? (int64_t)S.red[5] + 1 : su.dims[1] - 1;
-  const int64_t hiz = (int64_t)S.red[7] + 1 < su.dims[2] ? (int64_t)S.red[7] + 1 : su.dims[2] - 1;
-  const int64_t rx = hix - lox + 1, ry = hiy - loy + 1, rz = hiz - loz + 1;
-  const int64_t V = rx * ry * rz;
-  bool staged = uniform && V <= kBRB;
-  if (staged) {
-    // round 1: table words of the region
-    bool over = false;
-    const int irx = (int)rx, irxy = (int)(rx * ry);
-    for (int b = tid; b < (int)V; b += kBT) {
-      const int bz_ = b / irxy, rem = b - bz_ * irxy, by_ = rem / irx, bx_ = rem - by_ * irx;
-      const int64_t bx = lox + bx_, by = loy + by_, bz = loz + bz_;
-      const int64_t idx = scu.table_base + bx + su.dims[0] * (by + su.dims[1] * bz);
-      const unsigned long long e = C.tab.e[idx];
-      uint32_t c = ent_live(e, stamp);
-      if (c > (uint32_t)kBRK) { over = true; c = 0; }
-      S.rcnt[b] = (uint16_t)c;
-      S.rstart[b] = c ? ent_start(e) : 0u;
-    }
-    over = __syncthreads_or(over);
-    // exclusive prefix over the region's counts: 4 boxes per thread
-    uint32_t loc[4], tsum = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int b = tid * 4 + k;
-      loc[k] = b < (int)V ? S.rcnt[b] : 0u;
-      tsum += loc[k];
-    }
-    uint32_t inc = tsum;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane == 31) S.wsum[warp] = inc;
-    __syncthreads();
-    if (tid == 0) {
-      uint32_t run = 0;
-      for (int w = 0; w < kBT / 32; ++w) {
-        const uint32_t t = S.wsum[w];
-        S.wsum[w] = run;
-        run += t;
-      }
-      S.wsum[kBT / 32] = run;
-    }
-    __syncthreads();
-    uint32_t off = S.wsum[warp] + inc - tsum;
-    const uint32_t K = S.wsum[kBT / 32];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int b = tid * 4 + k;
-      if (b < (int)V) S.roff[b] = (uint16_t)(off > 0xFFFFu ? 0xFFFFu : off);
-      off += loc[k];
-    }
-    staged = !over && K <= (uint32_t)kBRK;
-    __syncthreads();
-    if (staged) {
-      // round 2: records, flattened over the region
-      for (int r = tid; r < (int)K; r += kBT) {
-        int lo = 0, hi = (int)V - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (S.roff[mid] <= (uint32_t)r) lo = mid; else hi = mid - 1;
-        }
-        const uint32_t cell = S.rstart[lo] + ((uint32_t)r - S.roff[lo]);
-        S.rec[r] = C.c.r0[cell];
-        S.ridx[r] = cell;
-      }
-    }
-    __syncthreads();
-  }
-  if (!staged) {
-    if (active) force32(C, sc, s, p, cx, cy, cz, stamp);
-    return;
-  }
-
-  // Candidate loop out of shared memory.
-  const float4 o0 = active ? C.c.r0[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float Lh = s.Lh, marg = s.marg;
-  int box = 0;
-  uint32_t k = 0, kend = 0;
-  int code = 13;
-  float sx = o0.x, sy = o0.y, sz = o0.z;
-  int qn = 0;
-  const unsigned lt = (1u << lane) - 1u;
-  const int lxo = (int)(cx - lox), lyo = (int)(cy - loy), lzo = (int)(cz - loz);
-  while (true) {
-    bool have = false;
-    if (active) {
-      while (k == kend && box < 27) {
-        const int dx = box % 3 - 1, dy = (box / 3) % 3 - 1, dz = box / 9 - 1;
-        const int bx = lxo + dx, by = lyo + dy, bz = lzo + dz;
-        const int bcode = box;
-        ++box;
-        if (cx + dx < 0 || cy + dy < 0 || cz + dz < 0 || cx + dx >= s.dims[0] || cy + dy >= s.dims[1] ||
-            cz + dz >= s.dims[2])
-          continue;
-        const int lb = bx + (int)rx * (by + (int)ry * bz);
-        k = S.roff[lb];
-        kend = k + S.rcnt[lb];
-        code = bcode;
-        sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
-        sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh));
-        sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
-      }
-      have = k < kend;
-    }
-    if (!__any_sync(FULL, have)) break;
-    bool hit = false;
-    uint32_t cell = 0;
-    if (have) {
-      const float4 q = S.rec[k];
-      cell = S.ridx[k];
-      ++k;
-      if ((int64_t)cell != p) {
-        const float ddx = __fsub_rn(sx, q.x), ddy = __fsub_rn(sy, q.y), ddz = __fsub_rn(sz, q.z);
-        const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
-        const float Rm = __fadd_rn(__fadd_rn(o0.w, q.w), marg);
-        hit = s2 < __fmul_rn(Rm, Rm);
-      }
-    }
-    const unsigned bal = __ballot_sync(FULL, hit);
-    if (bal) {
-      if (hit) S.q[warp][qn + __popc(bal & lt)] = make_uint2(cell, (uint32_t)lane | ((uint32_t)code << 8));
-      qn += __popc(bal);
-      if (qn >= 32) {
-        __syncwarp();
-        eval_ff(C, S, S.q[warp][lane], p0, warp);
-        __syncwarp();
-        if (lane < qn - 32) S.q[warp][lane] = S.q[warp][32 + lane];
-        __syncwarp();
-        qn -= 32;
-      }
-    }
-  }
-  __syncwarp();
-  if (lane < qn) eval_ff(C, S, S.q[warp][lane], p0, warp);
-  __syncwarp();
-  if (active) {
-    const float nz = S.acc[3][tid];
-    C.c.f32[p] = make_float4(S.acc[0][tid], S.acc[1][tid], S.acc[2][tid], nz);
-    C.c.nnz[p] = (uint8_t)(nz > 255.f ? 255u : (unsigned)nz);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// FP32 path, row-queue variant (variant 5): the direct loop's row-batched table loads,
-// one flattened loop over the candidates of the three boxes of a row (no
-// reloads), and the pairs that pass the FP32 filter queued per warp and
-// evaluated 32 at a time by the full warp (float-float overlap), results
-// added to the owner's accumulator in shared memory.
-// ---------------------------------------------------------------------------
-struct RowQueueSmem {
-  uint2 q[kBT / 32][kBQ];
-  float acc[4][kBT];
-};
-
-__device__ __forceinline__ void eval_rq(const DevCtx &C, RowQueueSmem &S, uint2 qe, int64_t block_p0, int warp) {
-  const int owner = warp * 32 + (int)(qe.y & 31u);
-  const int code = (int)(qe.y >> 8);
-  const uint32_t j = qe.x;
-  const int64_t po = block_p0 + owner;
-  const int sim = C.c.sim[po];
-  const SimConst &sc = C.sc[sim];
-  const SimState &s = C.ss[sim];
-  const float4 o0 = C.c.r0[po], o1 = C.c.r1[po];
-  const float4 q0 = C.c.r0[j], q1 = C.c.r1[j];
-  const float fdx = (float)(code % 3 - 1), fdy = (float)((code / 3) % 3 - 1), fdz = (float)(code / 9 - 1);
-  float xh, xl, yh, yl, zh, zl;
-  ff_diff(o0.x, o1.x, q0.x, q1.x, __fmul_rn(fdx, s.Lh), __fmul_rn(fdx, s.Ll), xh, xl);
-  ff_diff(o0.y, o1.y, q0.y, q1.y, __fmul_rn(fdy, s.Lh), __fmul_rn(fdy, s.Ll), yh, yl);
-  ff_diff(o0.z, o1.z, q0.z, q1.z, __fmul_rn(fdz, s.Lh), __fmul_rn(fdz, s.Ll), zh, zl);
-  float p0, e0, p1, e1, p2, e2;
-  two_prod(xh, xh, p0, e0);
-  e0 = __fmaf_rn(__fmul_rn(2.f, xh), xl, e0);
-  two_prod(yh, yh, p1, e1);
-  e1 = __fmaf_rn(__fmul_rn(2.f, yh), yl, e1);
-  two_prod(zh, zh, p2, e2);
-  e2 = __fmaf_rn(__fmul_rn(2.f, zh), zl, e2);
-  float Sa, Sea, Sb, Seb;
-  two_sum(p0, p1, Sa, Sea);
-  two_sum(Sa, p2, Sb, Seb);
-  const float sl = __fadd_rn(__fadd_rn(Sea, Seb), __fadd_rn(__fadd_rn(e0, e1), e2));
-  float sh, sll;
-  fast_two_sum(Sb, sl, sh, sll);
-  float Rh, Rl;
-  two_sum(o0.w, q0.w, Rh, Rl);
-  Rl = __fadd_rn(Rl, __fadd_rn(o1.w, q1.w));
-  float Qh, Ql;
-  two_prod(Rh, Rh, Qh, Ql);
-  Ql = __fmaf_rn(__fmul_rn(2.f, Rh), Rl, Ql);
-  const float num = __fadd_rn(__fsub_rn(Qh, sh), __fsub_rn(Ql, sll));
-  const float dist = sqrtf(sh);
-  float del;
-  if (fabsf(num) < kTinyNum) {
-    const double d64 = exact_delta(C, C.c.slot[po], C.c.slot[j]);
-    if (!(d64 > 0.0)) return;
-    del = (float)d64;
-  } else {
-    if (!(num > 0.f)) return;
-    del = __fdividef(num, __fadd_rn(Rh, dist));
-  }
-  const float rr = __fdividef(__fmul_rn(o0.w, q0.w), Rh);
-  const float fn = __fsub_rn(__fmul_rn(sc.kf, del), __fmul_rn(sc.gammaf, sqrtf(__fmul_rn(rr, del))));
-  if (fn != 0.f) atomicAdd(&S.acc[3][owner], 1.0f);
-  if (dist > 0.f) {
-    const float f = __fdividef(fn, dist);
-    atomicAdd(&S.acc[0][owner], __fmul_rn(f, xh));
-    atomicAdd(&S.acc[1][owner], __fmul_rn(f, yh));
-    atomicAdd(&S.acc[2][owner], __fmul_rn(f, zh));
-  }
-}
-
-__global__ void __launch_bounds__(kBT, 4) k_force32rq(DevCtx C) {
-  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
-  __shared__ RowQueueSmem S;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const unsigned FULL = 0xffffffffu;
-  const int64_t p0 = (int64_t)blockIdx.x * kBT;
-  const int64_t p = p0 + tid;
-  const int64_t ncell = C.g->n_cells;
-  if (p0 >= ncell) return;
-  const uint32_t stamp = C.g->stamp & kStampMask;
-  bool active = p < ncell;
-  const int sim = active ? C.c.sim[p] : 0;
-  const SimConst &sc = C.sc[sim];
-  const SimState &s = C.ss[sim];
-  if (active && (!s.valid || sc.precision != BDM_PREC_FP32_FORCE)) active = false;
-  int64_t cx = 0, cy = 0, cz = 0;
-  if (active) {
-    unpack_coords(C.c.pkey[p], cx, cy, cz);
-    const bool st = is_static_cell(C, sc, s, p, cx, cy, cz, stamp);
-    C.c.stat[p] = st ? 1 : 0;
-    if (st) active = false;
-  }
-  S.acc[0][tid] = 0.f; S.acc[1][tid] = 0.f; S.acc[2][tid] = 0.f; S.acc[3][tid] = 0.f;
-  __syncwarp();
-  if (!__any_sync(FULL, active)) return;
-  const float4 o0 = active ? C.c.r0[p] : make_float4(0.f, 0.f, 0.f, 0.f);
-  const float Lh = active ? s.Lh : 0.f, marg = active ? s.marg : 0.f;
-  Stencil t;
-  if (active) t = make_stencil(C, sc, s, cx, cy, cz);
-  const float sx0 = __fadd_rn(o0.x, Lh), sx1 = o0.x, sx2 = __fsub_rn(o0.x, Lh);
-  int qn = 0;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int r = 0; r < 9; ++r) {
-    const int dy = r % 3 - 1, dz = r / 3 - 1;
-    uint32_t c[3] = {0u, 0u, 0u}, sw[3] = {0u, 0u, 0u};
-    float sy = 0.f, sz = 0.f;
-    if (active && dy >= t.ylo && dy <= t.yhi && dz >= t.zlo && dz <= t.zhi) {
-      const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
-                           (uint32_t)t.cx;
-      unsigned long long ew[3];
-#pragma unroll
-      for (int qq = 0; qq < 3; ++qq) {
-        const int dx = qq - 1;
-        const bool in = dx >= t.xlo && dx <= t.xhi;
-        ew[qq] = in ? __ldg(t.e + row + dx) : 0ull;
-      }
-#pragma unroll
-      for (int qq = 0; qq < 3; ++qq) {
-        c[qq] = ent_live(ew[qq], stamp);
-        sw[qq] = ent_start(ew[qq]);
-      }
-      sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh));
-      sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
-    }
-    const uint32_t total = c[0] + c[1] + c[2];
-    const uint32_t kmax = __reduce_max_sync(FULL, total);
-    for (uint32_t k = 0; k < kmax; ++k) {
-      bool hit = false;
-      uint32_t j = 0;
-      int code = 0;
-      if (k < total) {
-        const int qq = k < c[0] ? 0 : (k < c[0] + c[1] ? 1 : 2);
-        const uint32_t m = qq == 0 ? k : (qq == 1 ? k - c[0] : k - c[0] - c[1]);
-        j = sw[qq] + m;
-        code = (dz + 1) * 9 + (dy + 1) * 3 + qq;
-        if ((int64_t)j != p) {
-          const float4 qv = C.c.r0[j];
-          const float sx = qq == 0 ? sx0 : (qq == 1 ? sx1 : sx2);
-          const float ddx = __fsub_rn(sx, qv.x), ddy = __fsub_rn(sy, qv.y), ddz = __fsub_rn(sz, qv.z);
-          const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
-          const float Rm = __fadd_rn(__fadd_rn(o0.w, qv.w), marg);
-          hit = s2 < __fmul_rn(Rm, Rm);
-        }
-      }
-      const unsigned bal = __ballot_sync(FULL, hit);
-      if (bal) {
-        if (hit) S.q[warp][qn + __popc(bal & lt)] = make_uint2(j, (uint32_t)lane | ((uint32_t)code << 8));
-        qn += __popc(bal);
-        if (qn >= 32) {
-          __syncwarp();
-          eval_rq(C, S, S.q[warp][lane], p0, warp);
-          __syncwarp();
-          if (lane < qn - 32) S.q[warp][lane] = S.q[warp][32 + lane];
-          __syncwarp();
-          qn -= 32;
-        }
-      }
-    }
-  }
-  __syncwarp();
-  if (lane < qn) eval_rq(C, S, S.q[warp][lane], p0, warp);
-  __syncwarp();
-  if (active) {
-    const float nz = S.acc[3][tid];
-    C.c.f32[p] = make_float4(S.acc[0][tid], S.acc[1][tid], S.acc[2][tid], nz);
-    C.c.nnz[p] = (uint8_t)(nz > 255.f ? 255u : (unsigned)nz);
-  }
-}
-
-void launch_force32rq(const DevCtx &C, cudaStream_t st) {
-  const unsigned int nb = (unsigned int)((C.total_slots + kBT - 1) / kBT);
-  k_force32rq<<<nb, kBT, 0, st>>>(C);
-}
-
-void launch_force32b(const DevCtx &C, cudaStream_t st) {
-  cudaFuncSetAttribute(k_force32b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BlockStage));
-  const unsigned int nb = (unsigned int)((C.total_slots + kBT - 1) / kBT);
-  k_force32b<<<nb, kBT, sizeof(BlockStage), st>>>(C);
-}
-
 static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
 // Variants of the FP32 path: 0 symmetric half stencil, 1 deferred walk with
-// rows flattened, 2 direct loop, 3 global queue, 4 block-staged, 5 row
-// queue, 6 deferred walk box by box.  FP64 simulations always take the
-// direct loop.
+// rows flattened, 2 direct loop, 3 deferred walk box by box.  FP64
+// simulations always take the direct loop.
 void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64) {
   const unsigned int nb = blocks_for(C.total_slots, kThreads);
   if (variant == 2) {
@@ -1107,10 +643,7 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, 
   }
   if (has_fp32) {
     if (variant == 0) k_force32s<<<nb, kThreads, 0, st>>>(C);
-    else if (variant == 3) launch_force32q(C, st);
-    else if (variant == 4) launch_force32b(C, st);
-    else if (variant == 5) launch_force32rq(C, st);
-    else if (variant == 6) k_force32d<false><<<nb, kThreads, 0, st>>>(C);
+    else if (variant == 3) k_force32d<false><<<nb, kThreads, 0, st>>>(C);
     else k_force32d<true><<<nb, kThreads, 0, st>>>(C);
   }
   if (has_fp64) k_force<<<nb, kThreads, 0, st>>>(C, 1);

@@ -15,16 +15,11 @@ int64_t scan_tiles(int64_t total_slots);
 void launch_scan(const DevCtx &C, cudaStream_t st);
 void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32 = 0);
 
-// force.cu, force32.cu
-// variant 0 (default) or 1: the direct kernel for both paths (force.cu);
-// variant 2: the FP32 path by the global-memory queue kernel (force32.cu);
-// variant 3: the FP32 path by the block-staged kernel (force.cu); variant 4:
-// the FP32 path by the row-queue kernel (force.cu).  The FP64 path always
-// runs the direct kernel.
+// force.cu
+// FP32 path: variant 0 symmetric half stencil (needs the forces zeroed by
+// the placement), 1 deferred walk with rows flattened, 2 direct loop, 3
+// deferred walk box by box.  The FP64 path always runs the direct loop.
 void launch_force(const DevCtx &C, cudaStream_t st, int variant = 0, bool has_fp32 = true, bool has_fp64 = true);
-void launch_force32q(const DevCtx &C, cudaStream_t st);
-void launch_force32b(const DevCtx &C, cudaStream_t st);
-void launch_force32rq(const DevCtx &C, cudaStream_t st);
 void launch_displace(const DevCtx &C, cudaStream_t st);
 
 // query.cu
