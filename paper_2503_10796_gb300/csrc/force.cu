@@ -440,34 +440,6 @@ __device__ __forceinline__ uint32_t sym_walk(const DevCtx &C, const SimConst &sc
   return n;
 }
 
-__device__ __forceinline__ void force32_sym(const DevCtx &C, const SimConst &sc, const SimState &s, uint32_t p,
-                                            int64_t cx, int64_t cy, int64_t cz, uint32_t stamp, HitQueue &hq) {
-  const float4 o0 = C.c.r0[p];
-  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
-  float fx = 0.f, fy = 0.f, fz = 0.f;
-  uint32_t nnz = 0;
-  const uint32_t n = sym_walk<true>(C, sc, s, p, o0, t, stamp, hq, fx, fy, fz, nnz);
-  if (n > (uint32_t)kHitCap) {
-    sym_walk<false>(C, sc, s, p, o0, t, stamp, hq, fx, fy, fz, nnz);
-  } else {
-    const float4 o1 = C.c.r1[p];
-    for (uint32_t k = 0; k < n; ++k) {
-      const uint32_t j = hq.j[k][threadIdx.x];
-      const int b = hq.b[k][threadIdx.x];
-      const float fdx = (float)(b % 3 - 1), fdy = (float)((b / 3) % 3 - 1), fdz = (float)(b / 9 - 1);
-      float gx, gy, gz;
-      bool nz;
-      if (pair32_vec(C, (int64_t)p, o0, o1, (int64_t)j, C.c.r0[j], fdx, fdy, fdz, s.Lh, s.Ll, sc.kf, sc.gammaf,
-                     gx, gy, gz, nz)) {
-        fx = __fadd_rn(fx, gx); fy = __fadd_rn(fy, gy); fz = __fadd_rn(fz, gz);
-        nnz += nz ? 1u : 0u;
-        atomicAdd(&C.c.f32[j], make_float4(-gx, -gy, -gz, nz ? 1.f : 0.f));
-      }
-    }
-  }
-  atomicAdd(&C.c.f32[p], make_float4(fx, fy, fz, (float)nnz));
-}
-
 __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
                                         int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
   const double4_32a o = C.c.r64[p];
@@ -557,19 +529,87 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32d(DevCtx C) {
 
 // FP32-path simulations only (none with static detection), symmetric
 // half-stencil walk; the forces were zeroed by the placement.
+// Warp-wide evaluation of the queued pairs: the lanes' queues are laid end
+// to end and every lane takes one pair per round, so the warp runs
+// ceil(total / 32) rounds instead of its longest queue.  A pair is added to
+// its owner and, negated, to its partner by vector atomics.  mine: this
+// lane's queue length (0 for a lane without queued pairs).
+__device__ __forceinline__ void warp_flush(const DevCtx &C, const HitQueue &hq, uint32_t mine, int64_t p) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+  uint32_t incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t excl = incl - mine;
+  const uint32_t total = __shfl_sync(FULL, incl, 31);
+  const int64_t p0 = p - lane;  // cell of lane 0 (the warp's cells are consecutive)
+  for (uint32_t base = 0; base < total; base += 32) {
+    const uint32_t k = base + (uint32_t)lane;
+    // owner: the first lane whose inclusive prefix exceeds k
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {
+      const uint32_t v = __shfl_sync(FULL, incl, o + step - 1);
+      if (v <= k) o += step;
+    }
+    const uint32_t ex = __shfl_sync(FULL, excl, o);
+    if (k < total) {
+      const uint32_t slot = k - ex;
+      const uint32_t j = hq.j[slot][wbase + o];
+      const int b = hq.b[slot][wbase + o];
+      const int64_t po = p0 + o;
+      const int so = C.c.sim[po];
+      const SimConst &sco = C.sc[so];
+      const SimState &sso = C.ss[so];
+      const float4 a0 = C.c.r0[po], a1 = C.c.r1[po];
+      const float fdx = (float)(b % 3 - 1), fdy = (float)((b / 3) % 3 - 1), fdz = (float)(b / 9 - 1);
+      float gx, gy, gz;
+      bool nz;
+      if (pair32_vec(C, po, a0, a1, (int64_t)j, C.c.r0[j], fdx, fdy, fdz, sso.Lh, sso.Ll, sco.kf, sco.gammaf, gx,
+                     gy, gz, nz)) {
+        const float w = nz ? 1.f : 0.f;
+        atomicAdd(&C.c.f32[po], make_float4(gx, gy, gz, w));
+        atomicAdd(&C.c.f32[j], make_float4(-gx, -gy, -gz, w));
+      }
+    }
+  }
+}
+
+// FP32-path simulations only (none with static detection), symmetric
+// half-stencil walk; the forces were zeroed by the placement.  Queued pairs
+// are evaluated warp-wide; an agent whose queue overflowed evaluates its
+// pairs in a second walk.
 __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
   __shared__ HitQueue hq;
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= C.g->n_cells) return;
-  int sim = C.c.sim[p];
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool active = p < C.g->n_cells;
+  const int sim = active ? C.c.sim[p] : 0;
   const SimConst &sc = C.sc[sim];
   const SimState &s = C.ss[sim];
-  if (!s.valid || sc.precision == BDM_PREC_FP64) return;
-  int64_t cx, cy, cz;
-  unpack_coords(C.c.pkey[p], cx, cy, cz);
-  C.c.stat[p] = 0;
-  force32_sym(C, sc, s, (uint32_t)p, cx, cy, cz, C.g->stamp & kStampMask, hq);
+  active = active && s.valid && sc.precision != BDM_PREC_FP64;
+  uint32_t mine = 0;
+  if (active) {
+    int64_t cx, cy, cz;
+    unpack_coords(C.c.pkey[p], cx, cy, cz);
+    C.c.stat[p] = 0;
+    const uint32_t stamp = C.g->stamp & kStampMask;
+    const float4 o0 = C.c.r0[p];
+    const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    uint32_t nnz = 0;
+    const uint32_t n = sym_walk<true>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, nnz);
+    if (n > (uint32_t)kHitCap) {
+      sym_walk<false>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, nnz);
+      atomicAdd(&C.c.f32[p], make_float4(fx, fy, fz, (float)nnz));
+    } else {
+      mine = n;
+    }
+  }
+  warp_flush(C, hq, mine, p);
 }
 
 // S5: displacement.  Static agents keep their position and nnz.
