@@ -77,6 +77,8 @@ struct Globals {
   uint32_t err;               // latched error bits
   int64_t n_cells;            // agents over all simulations
   int64_t n_new;              // agents created in the current division round
+  uint32_t tile_ticket;       // scan tiles claimed in this build (reset by k_params)
+  uint32_t pad;
 };
 
 struct Agents {               // storage arrays (per slot)
@@ -134,8 +136,7 @@ struct DevCtx {
   Cells q;                    // cells of the last neighbor query
   Table tab;
   int32_t *order;             // simulations in slot-region order (-1 padded)
-  uint32_t *lv;               // per slot: box count + 1 for box leaders, else 0 (scan)
-  uint32_t *partial;          // per scan tile: leader sum, then its exclusive prefix
+  unsigned long long *tstat;  // per scan tile: stamp << 34 | state << 32 | sum (look-back)
   int32_t n_sims;
   int64_t total_slots;
 };

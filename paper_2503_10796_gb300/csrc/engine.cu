@@ -45,6 +45,7 @@ struct bdm_ctx {
   bool any_fp32 = false, any_fp64 = false, any_grow = false, any_sort = false;
   DevCtx D{};
   uint32_t *d_partial = nullptr;
+  size_t tstat_words = 0;           // scan tile words (cleared with the table)
   int64_t table_entries = 0;
   int64_t builds = 0;        // grid builds since the box table was last cleared
   void *d_sort = nullptr;
@@ -362,6 +363,7 @@ int reserve_builds(bdm_ctx *c, int64_t n) {
   if (c->builds + n + 2 >= (int64_t)kStampMask) {
     cudaError_t e = cudaMemsetAsync(c->D.tab.e, 0, sizeof(unsigned long long) * (size_t)c->table_entries, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(&c->D.g->stamp, 0, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->D.tstat, 0, sizeof(unsigned long long) * c->tstat_words, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "clearing the box table");
     c->builds = 0;
   }
@@ -475,9 +477,9 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   ALLOC(D.g, 1, "globals");
   ALLOC(D.order, (size_t)n_sims, "simulation order");
   ALLOC(c->d_partial, (size_t)(scan_tiles((int64_t)M) + 2048), "scan partials");
-  ALLOC(D.lv, M, "scan leader values");
+  ALLOC(D.tstat, (size_t)scan_tiles((int64_t)M) + 1, "scan tile words");
+  c->tstat_words = (size_t)scan_tiles((int64_t)M) + 1;
   ALLOC(c->d_bad, 1, "input check");
-  D.partial = c->d_partial;
   ALLOC(D.a.x, M, "x"); ALLOC(D.a.y, M, "y"); ALLOC(D.a.z, M, "z"); ALLOC(D.a.d, M, "diameter");
   ALLOC(D.a.v, M, "volume"); ALLOC(D.a.id, M, "ids"); ALLOC(D.a.sim, M, "slot simulation");
   ALLOC(D.a.pkey, M, "box keys"); ALLOC(D.a.pkey_hist, M, "box history"); ALLOC(D.a.rank, M, "ranks");

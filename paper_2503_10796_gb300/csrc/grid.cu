@@ -229,6 +229,7 @@ __global__ void k_params(DevCtx C, int32_t step) {
   __syncthreads();
   if (threadIdx.x == 0) {
     g->stamp += 1u;
+    g->tile_ticket = 0u;
     int64_t cells = 0;
     for (int k = 0; k < C.n_sims; ++k) {
       const int s = C.order[k];
@@ -380,12 +381,29 @@ __device__ __forceinline__ uint32_t block_exscan_u32(uint32_t v, uint32_t *sh, u
   return r;
 }
 
-// Pass 1: each thread takes kScanItems slots of its tile (strided, so that
-// loads coalesce), issues all their loads before any is used, records the
-// leader value count + 1 (0 for non-leaders) and sums the counts per tile.
-__global__ void __launch_bounds__(kScanThreads) k_scan_up(DevCtx C) {
+// One pass with decoupled look-back.  A block claims the next tile through
+// a ticket (so every earlier tile belongs to a block that is already
+// running), sums its leaders' counts, publishes that sum, and walks back
+// over the earlier tiles' published values until it meets an inclusive
+// prefix; it then publishes its own inclusive prefix.  Each thread takes
+// kScanItems slots of the tile (strided, so that loads coalesce) and issues
+// all their loads before any is used.  Every wait is bounded: a tile that
+// never publishes latches ERR_TIMEOUT.  Tile words carry the build's stamp,
+// so they need no clearing between builds.
+constexpr uint32_t kLookSpin = 1u << 20;
+
+__device__ __forceinline__ void tile_publish(unsigned long long *w, uint32_t stamp, uint32_t state, uint32_t v) {
+  *(volatile unsigned long long *)w =
+      ((unsigned long long)stamp << 34) | ((unsigned long long)state << 32) | (unsigned long long)v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C) {
   __shared__ uint32_t sh[33];
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+  __shared__ uint32_t s_tile, s_base;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&C.g->tile_ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t base = (int64_t)tile * kScanTile + threadIdx.x;
   uint32_t rank[kScanItems];
   uint64_t pk[kScanItems];
   int sim[kScanItems];
@@ -398,11 +416,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_up(DevCtx C) {
     sim[i] = slot < C.total_slots ? C.a.sim[sl] : -1;
   }
   unsigned long long e[kScanItems];
-  bool lead[kScanItems];
+  int64_t idx[kScanItems];
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const int64_t slot = base + (int64_t)i * kScanThreads;
-    lead[i] = false;
+    idx[i] = -1;
     e[i] = 0ull;
     if (sim[i] >= 0) {
       const SimConst &sc = C.sc[sim[i]];
@@ -410,74 +428,70 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_up(DevCtx C) {
       if (slot - sc.base < s.n && s.valid && rank[i] == 0u) {
         int64_t cx, cy, cz;
         unpack_coords(pk[i], cx, cy, cz);
-        e[i] = C.tab.e[sc.table_base + linear_box(s, cx, cy, cz)];
-        lead[i] = true;
+        idx[i] = sc.table_base + linear_box(s, cx, cy, cz);
+        e[i] = C.tab.e[idx[i]];
       }
     }
   }
-  uint32_t sum = 0;
+  uint32_t cnt[kScanItems], sum = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    const int64_t slot = base + (int64_t)i * kScanThreads;
-    const uint32_t cnt = lead[i] ? ent_count(e[i]) : 0u;
-    if (slot < C.total_slots) C.lv[slot] = lead[i] ? cnt + 1u : 0u;
-    sum += cnt;
+    cnt[i] = idx[i] >= 0 ? ent_count(e[i]) : 0u;
+    sum += cnt[i];
   }
-  const uint32_t t = block_sum_u32(sum, sh);
-  if (threadIdx.x == 0) C.partial[blockIdx.x] = t;
-}
-
-// Exclusive scan of the n tile sums in one block; each thread takes a
-// contiguous run of them.
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t *partial, int64_t n) {
-  __shared__ uint32_t sh[33];
-  const int64_t per = (n + kScanThreads - 1) / kScanThreads;
-  const int64_t b = (int64_t)threadIdx.x * per;
-  const int64_t e = b + per < n ? b + per : n;
-  uint32_t sum = 0;
-  for (int64_t i = b; i < e; ++i) sum += partial[i];
-  uint32_t total;
-  uint32_t run = block_exscan_u32(sum, sh, &total);
-  for (int64_t i = b; i < e; ++i) {
-    const uint32_t v = partial[i];
-    partial[i] = run;
-    run += v;
-  }
-}
-
-// Pass 2: exclusive prefix of the leader counts in slot order; each leader
-// writes its box's first cell into the low half of the table word (a 32-bit
-// store: the high half, stamp | dirty | count, stays as the count left it).
-// After a table error every leader writes an empty current word instead, so
-// that placement, forces and queries see no agents in any box of the build.
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(DevCtx C) {
-  __shared__ uint32_t sh[33];
-  const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
-  uint32_t v[kScanItems];
-  uint64_t pk[kScanItems];
-  int sim[kScanItems];
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const int64_t slot = base + (int64_t)i * kScanThreads;
-    const int64_t sl = slot < C.total_slots ? slot : C.total_slots - 1;
-    v[i] = slot < C.total_slots ? C.lv[sl] : 0u;
-    pk[i] = C.a.pkey[sl];
-    sim[i] = C.a.sim[sl];
-  }
-  const bool bad = (C.g->err & ERR_TABLE) != 0u;
+  const uint32_t agg = block_sum_u32(sum, sh);  // valid in warp 0
   const uint32_t stamp = C.g->stamp & kStampMask;
-  uint32_t off = C.partial[blockIdx.x];
+  if (threadIdx.x < 32) {
+    // warp 0 looks back 32 tiles at a time: the nearest inclusive prefix
+    // ends the walk, the aggregates before it are added
+    const int lane = threadIdx.x;
+    uint32_t run = 0;
+    if (tile == 0) {
+      if (lane == 0) tile_publish(&C.tstat[0], stamp, 2u, agg);
+    } else {
+      if (lane == 0) tile_publish(&C.tstat[tile], stamp, 1u, agg);
+      for (int64_t j = (int64_t)tile - 1 - lane;; j -= 32) {
+        uint32_t state = 2u, v = 0u;
+        if (j >= 0) {
+          unsigned long long w = 0;
+          uint32_t spins = 0;
+          for (;;) {
+            w = *(volatile unsigned long long *)&C.tstat[j];
+            if ((uint32_t)(w >> 34) == stamp && ((w >> 32) & 3ull) != 0ull) break;
+            if (++spins >= kLookSpin) break;
+            __nanosleep(32);
+          }
+          if (spins >= kLookSpin) {
+            set_err(C.g, ERR_TIMEOUT);
+            w = 2ull << 32;  // give up: treat as a prefix of 0
+          }
+          state = (uint32_t)(w >> 32) & 3u;
+          v = (uint32_t)w;
+        }
+        const unsigned pm = __ballot_sync(0xffffffffu, state == 2u);
+        const int first = pm ? __ffs(pm) - 1 : 31;
+        run += __reduce_add_sync(0xffffffffu, lane <= first ? v : 0u);
+        if (pm) break;
+      }
+      if (lane == 0) tile_publish(&C.tstat[tile], stamp, 2u, run + agg);
+    }
+    if (lane == 0) s_base = run;
+  }
+  __syncthreads();
+  // exclusive prefix of the leader counts in slot order; each leader writes
+  // its box's first cell into the low half of the table word (a 32-bit
+  // store: the high half, stamp | dirty | count, stays as the count left
+  // it).  After a table error every leader writes an empty current word
+  // instead, so that placement, forces and queries see no agents in any box
+  // of the build.
+  const bool bad = (C.g->err & ERR_TABLE) != 0u;
+  uint32_t off = s_base;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     uint32_t total;
-    const uint32_t cnt = v[i] ? v[i] - 1u : 0u;
-    const uint32_t ex = block_exscan_u32(cnt, sh, &total);
-    if (v[i]) {
-      const SimConst &sc = C.sc[sim[i]];
-      const SimState &s = C.ss[sim[i]];
-      int64_t cx, cy, cz;
-      unpack_coords(pk[i], cx, cy, cz);
-      unsigned long long *w = &C.tab.e[sc.table_base + linear_box(s, cx, cy, cz)];
+    const uint32_t ex = block_exscan_u32(cnt[i], sh, &total);
+    if (idx[i] >= 0) {
+      unsigned long long *w = &C.tab.e[idx[i]];
       if (bad)
         *w = (unsigned long long)stamp << 43;
       else
@@ -487,8 +501,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(DevCtx C) {
   }
 }
 
-// Place every agent at start + rank of its box in `cells`.  fp64_records:
-// write the FP64 record whatever the simulation's precision (queries).
 // zero_f32: clear the FP32 force of every placed FP32-path agent (the
 // symmetric force walk adds into it).
 __global__ void __launch_bounds__(kThreads) k_place(DevCtx C, Cells cells, int fp64_records, int zero_f32) {
@@ -560,9 +572,7 @@ int64_t scan_tiles(int64_t total_slots) { return (total_slots + kScanTile - 1) /
 
 void launch_scan(const DevCtx &C, cudaStream_t st) {
   const int64_t G = scan_tiles(C.total_slots);
-  k_scan_up<<<(unsigned int)G, kScanThreads, 0, st>>>(C);
-  k_scan_top<<<1, kScanThreads, 0, st>>>(C.partial, G);
-  k_scan_down<<<(unsigned int)G, kScanThreads, 0, st>>>(C);
+  k_scan<<<(unsigned int)G, kScanThreads, 0, st>>>(C);
 }
 
 void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32) {

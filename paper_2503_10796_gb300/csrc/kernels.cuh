@@ -9,8 +9,8 @@ namespace bdm {
 void launch_bbox(const DevCtx &C, cudaStream_t st);
 void launch_params(const DevCtx &C, cudaStream_t st, int step);
 void launch_count(const DevCtx &C, cudaStream_t st, int step);
-// Scratch the scan needs in the context: lv (one uint32 per slot) and
-// partial (scan_tiles(total_slots) entries).
+// The scan needs tstat in the context: scan_tiles(total_slots) words,
+// cleared whenever the build stamp restarts.
 int64_t scan_tiles(int64_t total_slots);
 void launch_scan(const DevCtx &C, cudaStream_t st);
 void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32 = 0);

@@ -28,8 +28,9 @@ constexpr size_t oSS = oSC + up(sizeof(SimConst));
 constexpr size_t oG = oSS + up(sizeof(SimState));
 constexpr size_t oOrder = oG + up(sizeof(Globals));
 constexpr size_t oPart = oOrder + up(sizeof(int32_t));
-constexpr size_t oLv = oPart + up(2048 * sizeof(uint32_t));
-constexpr size_t oAX = oLv + up(4 * kM);
+constexpr size_t oTstat = oPart + up(2048 * sizeof(uint32_t));
+constexpr size_t kTstatWords = kM / 4096 + 2;
+constexpr size_t oAX = oTstat + up(8 * kTstatWords);
 constexpr size_t oAY = oAX + up(8 * kM);
 constexpr size_t oAZ = oAY + up(8 * kM);
 constexpr size_t oAD = oAZ + up(8 * kM);
@@ -115,8 +116,7 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   D.c.flag = at<uint8_t>(base, oCFlag); D.c.nnz = at<uint8_t>(base, oCNnz); D.c.stat = at<uint8_t>(base, oCStat);
   D.c.f32 = at<float4>(base, oCF32); D.c.f64 = at<double4_32a>(base, oCF64);
   D.tab.e = at<unsigned long long>(base, oTab);
-  D.partial = at<uint32_t>(base, oPart);
-  D.lv = at<uint32_t>(base, oLv);
+  D.tstat = at<unsigned long long>(base, oTstat);
 
   // Constants and cleared state: every call starts from zero, because the
   // array keeps whatever the previous call left in it.
@@ -138,6 +138,7 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   if (e == cudaSuccess) e = cudaMemcpyAsync(D.order, &order0, sizeof(order0), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(D.g, 0, sizeof(Globals), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(D.tab.e, 0, sizeof(unsigned long long) * (size_t)kMaxBoxes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(D.tstat, 0, sizeof(unsigned long long) * kTstatWords, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return BDM_E_CUDA;
