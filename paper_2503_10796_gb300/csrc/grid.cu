@@ -289,11 +289,10 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
   const SimConst &sc = C.sc[sim < 0 ? 0 : sim];
   const SimState &s = C.ss[sim < 0 ? 0 : sim];
   const bool valid = in && sim >= 0 && sl - sc.base < s.n && s.valid;
-  const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-  if (!valid) return;
-  const bool changed = hist && (fl & FLAG_CHANGED) != 0;
-  uint32_t c[3];
-  if (hist && s.same_grid && !changed) {
+  const bool changed = valid && hist && (fl & FLAG_CHANGED) != 0;
+  uint32_t c[3] = {0u, 0u, 0u};
+  if (!valid) {
+  } else if (hist && s.same_grid && !changed) {
     // unchanged agent, unchanged grid: the box of the last iteration
     c[0] = (uint32_t)(pk_prev_in & kCoordMask);
     c[1] = (uint32_t)((pk_prev_in >> kCoordBits) & kCoordMask);
@@ -310,14 +309,25 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
   const uint64_t pk = (uint64_t)c[0] | ((uint64_t)c[1] << kCoordBits) | ((uint64_t)c[2] << (2 * kCoordBits));
   const int64_t idx =
       sc.table_base + (int64_t)(c[0] + (uint32_t)s.dims[0] * (c[1] + (uint32_t)s.dims[1] * c[2]));
-  // Lanes of a warp that share a box add their count with one atomic
-  // (neighbouring slots mostly share boxes once the storage is sorted).
-  const unsigned peers = __match_any_sync(vmask, (unsigned long long)idx);
+  // Runs of neighbouring lanes in one box add their count with one atomic
+  // (agents of a box are neighbours once the storage is sorted; a box met
+  // in two runs takes two atomics).  Lanes without an agent get keys of
+  // their own.
+  const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  const unsigned dirty_any = __reduce_or_sync(peers, changed ? 1u : 0u);
+  const unsigned long long key = valid ? (unsigned long long)idx : (0xFFFFFFFF00000000ull | (unsigned)lane);
+  const unsigned long long prev = __shfl_up_sync(FULL, key, 1);
+  const unsigned H = __ballot_sync(FULL, lane == 0 || prev != key);
+  const int start = 31 - __clz(H & (FULL >> (31 - lane)));
+  const unsigned above = H & ~(FULL >> (31 - lane));
+  const int end = above ? __ffs(above) - 2 : 31;
+  const unsigned run = (end == 31 ? FULL : ((1u << (end + 1)) - 1u)) & ~((1u << start) - 1u);
+  const unsigned dirty_any = __ballot_sync(FULL, changed) & run;
   uint32_t base = 0;
-  if (lane == leader) base = tab_add(&C.tab.e[idx], stamp, dirty_any != 0, (uint32_t)__popc(peers), C.g);
+  if (valid && lane == start)
+    base = tab_add(&C.tab.e[idx], stamp, dirty_any != 0u, (uint32_t)(end - start + 1), C.g);
+  base = __shfl_sync(FULL, base, start);
+  if (!valid) return;
   C.a.pkey[slot] = pk;
   if (hist) hist[slot] = pk;
   if (changed && s.same_grid && pk_prev_in != pk) {
@@ -326,8 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
     if (px < s.dims[0] && py < s.dims[1] && pz < s.dims[2])
       tab_mark_dirty(&C.tab.e[sc.table_base + linear_box(s, px, py, pz)], stamp);
   }
-  base = __shfl_sync(peers, base, leader);
-  C.a.rank[slot] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+  C.a.rank[slot] = base + (uint32_t)(lane - start);
 }
 
 // ---------------------------------------------------------------------------
