@@ -219,7 +219,15 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(DevCtx C, SortBuf
     uint64_t key = act ? kin[i] : 0ull;
     int32_t val = act ? vin[i] : 0;
     uint32_t dg = act ? (uint32_t)((key >> shift) & 0xFF) : 0xFFFFFFFFu;
-    unsigned int peers = __match_any_sync(0xffffffffu, dg);
+    // lanes holding the same digit: one ballot per digit bit (and one for
+    // the active lanes), which is cheaper than a match instruction
+    const unsigned int am = __ballot_sync(0xffffffffu, act);
+    unsigned int peers = act ? am : ~am;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const unsigned int B = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
+      peers &= ((dg >> b) & 1u) ? B : ~B;
+    }
     unsigned int lt = (1u << lane) - 1u;
     uint32_t r_in_warp = __popc(peers & lt);
     if (act && r_in_warp == 0) wcnt[warp][dg] = __popc(peers);
