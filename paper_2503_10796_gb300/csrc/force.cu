@@ -243,11 +243,16 @@ __device__ __forceinline__ bool pair32(const DevCtx &C, int64_t p, const float4 
 // itself needs fewer registers.  An agent with more than kHitCap queued
 // candidates is evaluated again by the plain direct loop.  Both evaluate the
 // pairs in the walk's order, so the sums equal those of the direct loop.
-constexpr int kHitCap = 16;
-struct HitQueue {
-  uint32_t j[kHitCap][kThreads];
-  uint8_t b[kHitCap][kThreads];
+constexpr int kHitCap = 16;  // deferred walk (full stencil)
+constexpr int kSymCap = 8;   // symmetric walk (half stencil: about half the pairs)
+template <int N>
+struct HitQueueN {
+  static constexpr int kCap = N;
+  uint32_t j[N][kThreads];
+  uint8_t b[N][kThreads];
 };
+using HitQueue = HitQueueN<kHitCap>;
+using SymQueue = HitQueueN<kSymCap>;
 
 // Evaluates the queued candidates in order; the agent's own cell, which the
 // walk queues rather than test every candidate against it, is skipped here.
@@ -363,10 +368,10 @@ __device__ __forceinline__ bool pair32_vec(const DevCtx &C, int64_t p, const flo
 // itself) by vector atomic adds onto forces the placement zeroed.  The w
 // component counts the non-zero pair forces.  Candidates that pass the
 // filter are queued as in the deferred walk; an agent with more than
-// kHitCap of them evaluates its pairs during a second walk instead.
+// kSymCap of them evaluates its pairs during a second walk instead.
 template <bool kQueue>
 __device__ __forceinline__ uint32_t sym_walk(const DevCtx &C, const SimConst &sc, const SimState &s, uint32_t p,
-                                             const float4 &o0, const Stencil &t, uint32_t stamp, HitQueue &hq,
+                                             const float4 &o0, const Stencil &t, uint32_t stamp, SymQueue &hq,
                                              float &fx, float &fy, float &fz, uint32_t &nnz) {
   const float Lh = s.Lh;
   const float rw = __fadd_rn(o0.w, s.marg);
@@ -419,7 +424,7 @@ __device__ __forceinline__ uint32_t sym_walk(const DevCtx &C, const SimConst &sc
       if (!(s2 < __fmul_rn(Rm, Rm))) continue;
       const int code = inA ? kA : (inB ? kB : kC);
       if constexpr (kQueue) {
-        if (n < (uint32_t)kHitCap) {
+        if (n < (uint32_t)kSymCap) {
           hq.j[n][threadIdx.x] = j;
           hq.b[n][threadIdx.x] = (uint8_t)code;
         }
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32d(DevCtx C) {
 // ceil(total / 32) rounds instead of its longest queue.  A pair is added to
 // its owner and, negated, to its partner by vector atomics.  mine: this
 // lane's queue length (0 for a lane without queued pairs).
-__device__ __forceinline__ void warp_flush(const DevCtx &C, const HitQueue &hq, uint32_t mine, int64_t p) {
+__device__ __forceinline__ void warp_flush(const DevCtx &C, const SymQueue &hq, uint32_t mine, int64_t p) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
   uint32_t incl = mine;
@@ -583,7 +588,7 @@ __device__ __forceinline__ void warp_flush(const DevCtx &C, const HitQueue &hq, 
 // are evaluated warp-wide; an agent whose queue overflowed evaluates its
 // pairs in a second walk.
 __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
-  __shared__ HitQueue hq;
+  __shared__ SymQueue hq;
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool active = p < C.g->n_cells;
@@ -602,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
     float fx = 0.f, fy = 0.f, fz = 0.f;
     uint32_t nnz = 0;
     const uint32_t n = sym_walk<true>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, nnz);
-    if (n > (uint32_t)kHitCap) {
+    if (n > (uint32_t)kSymCap) {
       sym_walk<false>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, nnz);
       atomicAdd(&C.c.f32[p], make_float4(fx, fy, fz, (float)nnz));
     } else {
