@@ -215,7 +215,8 @@ typedef struct {
                               simulation detects static agents); 1 direct walk,
                               rows flattened, pair evaluation deferred; 2 direct
                               loop, pairs evaluated in the walk; 3 as 1 box by
-                              box. FP64 always direct */
+                              box; 4 as 0 with every pair evaluated in the walk
+                              (crowded agents). FP64 always direct */
   int32_t sort_interval;   /* -1: every simulation's own sort_interval;
                               >= 0: this re-sort interval for all simulations */
   int32_t sort_curve;      /* order the re-sort gives the storage: 0 Morton order of the

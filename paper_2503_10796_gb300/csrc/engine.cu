@@ -239,11 +239,11 @@ void launch_iteration(bdm_ctx *c, bool sort) {
   // the symmetric walk (variant 0) needs every FP32-path simulation to run
   // without static detection; otherwise the deferred walk (1) stands in
   int variant = c->force_variant;
-  if (variant == 0)
+  if (variant == 0 || variant == 4)
     for (int s = 0; s < c->n_sims; ++s)
       if (c->params[s].precision != BDM_PREC_FP64 && c->params[s].detect_static) variant = 1;
   stage_begin(c, 3);
-  launch_place(D, st, 1, variant == 0 ? 1 : 0);
+  launch_place(D, st, 1, (variant == 0 || variant == 4) ? 1 : 0);
   stage_end(c);
   stage_begin(c, 4);
   launch_force(D, st, variant, c->any_fp32, c->any_fp64);
@@ -911,8 +911,8 @@ int bdm_get_profile(bdm_ctx *c, int64_t launches[BDM_NUM_STAGES], double ms[BDM_
 
 int bdm_set_tuning(bdm_ctx *c, const bdm_tuning *t) {
   if (!c || !t) return BDM_E_INVAL;
-  if (t->force_variant < 0 || t->force_variant > 3)
-    return fail(c, BDM_E_INVAL, "force_variant must be 0 to 3");
+  if (t->force_variant < 0 || t->force_variant > 4)
+    return fail(c, BDM_E_INVAL, "force_variant must be 0 to 4");
   if (t->sort_interval < -1) return fail(c, BDM_E_INVAL, "sort_interval must be >= -1");
   if (t->sort_curve != 0 && t->sort_curve != 1) return fail(c, BDM_E_INVAL, "sort_curve must be 0 or 1");
   for (int k = 0; k < 5; ++k)
@@ -1046,7 +1046,7 @@ int bdm_autotune(bdm_ctx *c, int32_t iterations, bdm_tuning *chosen) {
   bdm_get_tuning(c, &best);
   float best_ms = 1e30f;
   std::vector<int> variants = {0};
-  if (c->any_fp32) variants = {0, 1, 2, 3};
+  if (c->any_fp32) variants = {0, 1, 2, 3, 4};
   for (int v : variants) {
     if (rc) break;
     bdm_tuning t = best;

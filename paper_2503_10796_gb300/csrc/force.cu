@@ -586,7 +586,9 @@ __device__ __forceinline__ void warp_flush(const DevCtx &C, const SymQueue &hq, 
 // FP32-path simulations only (none with static detection), symmetric
 // half-stencil walk; the forces were zeroed by the placement.  Queued pairs
 // are evaluated warp-wide; an agent whose queue overflowed evaluates its
-// pairs in a second walk.
+// pairs in a second walk.  kDirect: no queue, every pair evaluated in the
+// walk (for crowded agents, whose queues would overflow).
+template <bool kDirect>
 __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
   __shared__ SymQueue hq;
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
@@ -606,7 +608,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
     const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
     float fx = 0.f, fy = 0.f, fz = 0.f;
     uint32_t nnz = 0;
-    const uint32_t n = sym_walk<true>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, nnz);
+    const uint32_t n = kDirect ? (uint32_t)kSymCap + 1u
+                               : sym_walk<true>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, nnz);
     if (n > (uint32_t)kSymCap) {
       sym_walk<false>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, nnz);
       atomicAdd(&C.c.f32[p], make_float4(fx, fy, fz, (float)nnz));
@@ -614,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
       mine = n;
     }
   }
-  warp_flush(C, hq, mine, p);
+  if constexpr (!kDirect) warp_flush(C, hq, mine, p);
 }
 
 // S5: displacement.  Static agents keep their position and nnz.
@@ -680,18 +683,29 @@ static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)(
 // Variants of the FP32 path: 0 symmetric half stencil, 1 deferred walk with
 // rows flattened, 2 direct loop, 3 deferred walk box by box.  FP64
 // simulations always take the direct loop.
+// Threads per block of the force kernels: kThreads, or fewer (down to one
+// warp) for small populations, so that the blocks still cover the 152 SMs
+// twice (the FP64 pipe of each SM is the limit of the FP64 path).
+static inline int force_threads(int64_t n) {
+  const int64_t want = (n + 2 * 152 - 1) / (2 * 152);
+  int t = (int)((want + 31) / 32 * 32);
+  return t < 32 ? 32 : (t > kThreads ? kThreads : t);
+}
+
 void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64) {
-  const unsigned int nb = blocks_for(C.total_slots, kThreads);
+  const int th = force_threads(C.total_slots);
+  const unsigned int nb = blocks_for(C.total_slots, th);
   if (variant == 2) {
-    k_force<<<nb, kThreads, 0, st>>>(C, 0);
+    k_force<<<nb, th, 0, st>>>(C, 0);
     return;
   }
   if (has_fp32) {
-    if (variant == 0) k_force32s<<<nb, kThreads, 0, st>>>(C);
-    else if (variant == 3) k_force32d<false><<<nb, kThreads, 0, st>>>(C);
-    else k_force32d<true><<<nb, kThreads, 0, st>>>(C);
+    if (variant == 0) k_force32s<false><<<nb, th, 0, st>>>(C);
+    else if (variant == 4) k_force32s<true><<<nb, th, 0, st>>>(C);
+    else if (variant == 3) k_force32d<false><<<nb, th, 0, st>>>(C);
+    else k_force32d<true><<<nb, th, 0, st>>>(C);
   }
-  if (has_fp64) k_force<<<nb, kThreads, 0, st>>>(C, 1);
+  if (has_fp64) k_force<<<nb, th, 0, st>>>(C, 1);
 }
 
 void launch_displace(const DevCtx &C, cudaStream_t st) {

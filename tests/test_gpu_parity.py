@@ -341,7 +341,7 @@ def test_deferred_walk_equals_direct_loop(orc):
                 dense_clump()):
         _, _, smag = orc_for(pop).forces()
         out = []
-        for variant in (1, 0, 2, 3):
+        for variant in (1, 0, 2, 3, 4):
             ctx = ctx_for(pop, precision=1, sort_interval=1)
             ctx.set_tuning(force_variant=variant)
             ctx.step(1)
@@ -354,7 +354,7 @@ def test_deferred_walk_equals_direct_loop(orc):
             assert err.max() <= 1e-5, err.max()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_force_variants_match_oracle(orc, variant):
     """Every force-kernel variant of the FP32 path meets the tolerance."""
     for pop in (workloads.plain_fp64(seed=5),
@@ -380,7 +380,7 @@ def test_autotune_restores_state(orc):
     b.step(3)
     x_before, _ = a.get_agents(0)
     chosen = a.autotune(3)
-    assert chosen["force_variant"] in (0, 1, 2, 3)
+    assert chosen["force_variant"] in (0, 1, 2, 3, 4)
     x_after, _ = a.get_agents(0)
     assert np.array_equal(x_before, x_after)
     assert a.stats(0)["iterations"] == 3
