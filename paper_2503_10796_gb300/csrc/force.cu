@@ -171,65 +171,59 @@ __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, con
 }
 
 // Contribution of candidate j (record q, neighbour-box offset (fdx, fdy,
-// fdz)) to the force on p: FP32 overlap for deep pairs, float-float for
-// shallow ones, the FP64 definition when the float-float numerator is
-// within rounding of zero.  Returns false when the pair does not interact.
+// fdz)) to the force on p, from the float-float records: the overlap
+// delta = (R^2 - s) / (R + dist) keeps its relative accuracy at any depth,
+// and the FP64 definition decides when the numerator is within rounding of
+// zero.  (One path for every pair: in a warp that evaluates many pairs at
+// once, a plain FP32 path for deep pairs beside it cost more than it saved.)
+// Returns false when the pair does not interact.
 __device__ __forceinline__ bool pair32(const DevCtx &C, int64_t p, const float4 &o0, const float4 &o1, int64_t j,
                                        const float4 &q, float fdx, float fdy, float fdz, float Lh, float Ll,
                                        float kf, float gf, float &fx, float &fy, float &fz, uint32_t &nnz) {
-  const float sx = __fsub_rn(o0.x, __fmul_rn(fdx, Lh)), sy = __fsub_rn(o0.y, __fmul_rn(fdy, Lh)),
-              sz = __fsub_rn(o0.z, __fmul_rn(fdz, Lh));
-  const float ddx = __fsub_rn(sx, q.x), ddy = __fsub_rn(sy, q.y), ddz = __fsub_rn(sz, q.z);
-  const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
   const float R = __fadd_rn(o0.w, q.w);
-  float dist = sqrtf(s2);
-  float del = __fsub_rn(R, dist);
-  float ux = ddx, uy = ddy, uz = ddz;
-  if (!(del > kFastDelta)) {
-    const float4 q1 = C.c.r1[j];
-    float xh, xl, yh, yl, zh, zl;
-    ff_diff(o0.x, o1.x, q.x, q1.x, __fmul_rn(fdx, Lh), __fmul_rn(fdx, Ll), xh, xl);
-    ff_diff(o0.y, o1.y, q.y, q1.y, __fmul_rn(fdy, Lh), __fmul_rn(fdy, Ll), yh, yl);
-    ff_diff(o0.z, o1.z, q.z, q1.z, __fmul_rn(fdz, Lh), __fmul_rn(fdz, Ll), zh, zl);
-    float p0, e0, p1, e1, p2, e2;
-    two_prod(xh, xh, p0, e0);
-    e0 = __fmaf_rn(__fmul_rn(2.f, xh), xl, e0);
-    two_prod(yh, yh, p1, e1);
-    e1 = __fmaf_rn(__fmul_rn(2.f, yh), yl, e1);
-    two_prod(zh, zh, p2, e2);
-    e2 = __fmaf_rn(__fmul_rn(2.f, zh), zl, e2);
-    float Sa, Sea, Sb, Seb;
-    two_sum(p0, p1, Sa, Sea);
-    two_sum(Sa, p2, Sb, Seb);
-    const float sl = __fadd_rn(__fadd_rn(Sea, Seb), __fadd_rn(__fadd_rn(e0, e1), e2));
-    float sh, sll;
-    fast_two_sum(Sb, sl, sh, sll);
-    float Rh, Rl;
-    two_sum(o0.w, q.w, Rh, Rl);
-    Rl = __fadd_rn(Rl, __fadd_rn(o1.w, q1.w));
-    float Qh, Ql;
-    two_prod(Rh, Rh, Qh, Ql);
-    Ql = __fmaf_rn(__fmul_rn(2.f, Rh), Rl, Ql);
-    const float num = __fadd_rn(__fsub_rn(Qh, sh), __fsub_rn(Ql, sll));
-    dist = sqrtf(sh);
-    if (fabsf(num) < kTinyNum) {
-      const double d64 = exact_delta(C, C.c.slot[p], C.c.slot[j]);
-      if (!(d64 > 0.0)) return false;
-      del = (float)d64;
-    } else {
-      if (!(num > 0.f)) return false;
-      del = __fdividef(num, __fadd_rn(Rh, dist));
-    }
-    ux = xh; uy = yh; uz = zh;
+  const float4 q1 = C.c.r1[j];
+  float xh, xl, yh, yl, zh, zl;
+  ff_diff(o0.x, o1.x, q.x, q1.x, __fmul_rn(fdx, Lh), __fmul_rn(fdx, Ll), xh, xl);
+  ff_diff(o0.y, o1.y, q.y, q1.y, __fmul_rn(fdy, Lh), __fmul_rn(fdy, Ll), yh, yl);
+  ff_diff(o0.z, o1.z, q.z, q1.z, __fmul_rn(fdz, Lh), __fmul_rn(fdz, Ll), zh, zl);
+  float p0, e0, p1, e1, p2, e2;
+  two_prod(xh, xh, p0, e0);
+  e0 = __fmaf_rn(__fmul_rn(2.f, xh), xl, e0);
+  two_prod(yh, yh, p1, e1);
+  e1 = __fmaf_rn(__fmul_rn(2.f, yh), yl, e1);
+  two_prod(zh, zh, p2, e2);
+  e2 = __fmaf_rn(__fmul_rn(2.f, zh), zl, e2);
+  float Sa, Sea, Sb, Seb;
+  two_sum(p0, p1, Sa, Sea);
+  two_sum(Sa, p2, Sb, Seb);
+  const float sl = __fadd_rn(__fadd_rn(Sea, Seb), __fadd_rn(__fadd_rn(e0, e1), e2));
+  float sh, sll;
+  fast_two_sum(Sb, sl, sh, sll);
+  float Rh, Rl;
+  two_sum(o0.w, q.w, Rh, Rl);
+  Rl = __fadd_rn(Rl, __fadd_rn(o1.w, q1.w));
+  float Qh, Ql;
+  two_prod(Rh, Rh, Qh, Ql);
+  Ql = __fmaf_rn(__fmul_rn(2.f, Rh), Rl, Ql);
+  const float num = __fadd_rn(__fsub_rn(Qh, sh), __fsub_rn(Ql, sll));
+  const float dist = sqrtf(sh);
+  float del;
+  if (fabsf(num) < kTinyNum) {
+    const double d64 = exact_delta(C, C.c.slot[p], C.c.slot[j]);
+    if (!(d64 > 0.0)) return false;
+    del = (float)d64;
+  } else {
+    if (!(num > 0.f)) return false;
+    del = __fdividef(num, __fadd_rn(Rh, dist));
   }
   const float rr = __fdividef(__fmul_rn(o0.w, q.w), R);
   const float fn = __fsub_rn(__fmul_rn(kf, del), __fmul_rn(gf, sqrtf(__fmul_rn(rr, del))));
   nnz += (fn != 0.f);
   if (dist > 0.f) {
     const float f = __fdividef(fn, dist);
-    fx = __fmaf_rn(f, ux, fx);
-    fy = __fmaf_rn(f, uy, fy);
-    fz = __fmaf_rn(f, uz, fz);
+    fx = __fmaf_rn(f, xh, fx);
+    fy = __fmaf_rn(f, yh, fy);
+    fz = __fmaf_rn(f, zh, fz);
   }
   return true;
 }
@@ -242,7 +236,7 @@ __device__ __forceinline__ bool pair32(const DevCtx &C, int64_t p, const float4 
 // any lane finds a partner, then runs with the lanes together, and the walk
 // itself needs fewer registers.  An agent with more than kHitCap queued
 // candidates is evaluated again by the plain direct loop.  Both evaluate the
-// pairs in the walk's order, so the sums equal those of the direct loop.
+// pairs in the walk's order.
 constexpr int kHitCap = 16;  // deferred walk (full stencil)
 constexpr int kSymCap = 8;   // symmetric walk (half stencil: about half the pairs)
 template <int N>
