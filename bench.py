@@ -37,6 +37,13 @@ UNIT = "agent-updates/s"
 # path: FP64 diameter (8 B) and FP64 force (24 B).
 ALG_BYTES_AGENT = {1: 42.0, 0: 58.0}
 ALG_BYTES_BOX = 8.0
+# DRAM bytes (read + write) per agent of the default force kernel
+# (k_force32s, variant 0), from the ncu capture of clustered_1M summarised in
+# profiles/k_force32s_clustered_1M.md; scaled by the agents of a launch for
+# the clustered workloads (same per-cluster shape), null elsewhere or when
+# another kernel runs.
+FORCE_TRAFFIC_B_PER_AGENT = {"k_force32s": 109.8}
+FORCE_KERNEL = {0: "k_force32s", 1: "k_force32d", 2: "k_force", 3: "k_force32d", 4: "k_force32s (direct)"}
 
 
 def parse():
@@ -312,6 +319,13 @@ def main():
     prec = args.precision
     alg = ALG_BYTES_AGENT[prec] * (n_agents - st_static) + ALG_BYTES_BOX * occupied
     peak, peak_kind = peaks()
+    variant = (tuning or {}).get("force_variant", 0) if prec == 1 else 2
+    if args.static and variant in (0, 4):
+        variant = 1  # the symmetric walks do not run with static detection
+    kernel = FORCE_KERNEL.get(variant, "k_force")
+    traffic = None
+    if kernel in FORCE_TRAFFIC_B_PER_AGENT and args.workload.startswith("clustered"):
+        traffic = FORCE_TRAFFIC_B_PER_AGENT[kernel] * (n_agents - st_static)
     achieved = alg / (force_ms * 1e-3) / 1e9
     launches_per_iter = 9 + (1 if any(p.params.sort_interval > 0 for p in pops) else 0) + (
         1 if any(p.params.growth_rate > 0 for p in pops) else 0)
@@ -370,7 +384,7 @@ def main():
             "dtype": "f32-force/f64-position" if prec == 1 else "f64", "data": "synthetic",
             "config": dict(desc, parallelism=parallelism, settle_iterations=args.settle),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_force",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
                          "peak_source": f"{peak_kind} hbm_gbs", "force_ms_per_launch": force_ms,
                          "alg_bytes_per_launch": alg},
             "stages_ms_per_iter": {k: v["ms"] / max(v["launches"], 1) for k, v in prof.items() if v["launches"]},
