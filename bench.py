@@ -330,38 +330,40 @@ def main():
     launches_per_iter = 9 + (1 if any(p.params.sort_interval > 0 for p in pops) else 0) + (
         1 if any(p.params.growth_rate > 0 for p in pops) else 0)
 
-    # end to end through the public API with host buffers: every step
-    # uploads the current population from pinned host memory, steps once and
-    # reads the positions back into pinned host memory
+    # end to end through the public API with host buffers: every step moves
+    # the current population's positions from pinned host memory to the
+    # device (bdm_update_agents; diameters too where agents grow), steps
+    # once and reads the new positions back into pinned host memory
     e2e = None
     if args.e2e_steps > 0:
-        xs, ds = [], []
+        grows = [p.params.growth_rate > 0 for p in pops]
+        bufs = []
         for s in range(len(pops)):
             room = max(pops[s].params.capacity, ctx.count(s), 1)
             xp = torch.empty((room, 3), dtype=torch.float64, pin_memory=True).numpy()
             dp = torch.empty((room,), dtype=torch.float64, pin_memory=True).numpy()
-            x, d = ctx.get_agents(s, out=(xp, dp))
-            xs.append((xp, dp, x.shape[0]))
+            x, _ = ctx.get_agents(s, out=(xp, dp))
+            bufs.append([xp, dp, x.shape[0]])
         h2d = d2h = 0
+        stepped = 0
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             for s in range(len(pops)):
-                xp, dp, k = xs[s]
-                ctx.set_agents(s, xp[:k], dp[:k])
-                h2d += 32 * k
+                xp, dp, k = bufs[s]
+                ctx.update_agents(s, xp[:k], dp[:k] if grows[s] else None)
+                h2d += (32 if grows[s] else 24) * k
+                stepped += k
             ctx.step(1)
             for s in range(len(pops)):
-                xp, dp, _ = xs[s]
-                x, _ = ctx.get_agents(s, out=(xp, dp))
-                xs[s] = (xp, dp, x.shape[0])
-                d2h += 32 * x.shape[0]
+                xp, dp, _ = bufs[s]
+                x, _ = ctx.get_agents(s, out=(xp, dp if grows[s] else None))
+                bufs[s][2] = x.shape[0]
+                d2h += (32 if grows[s] else 24) * x.shape[0]
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        # set_agents restarts the per-simulation counters: count the agents
-        # stepped directly
-        e2e_updates = float(h2d // 32)
+        e2e_updates = float(stepped)
         if world > 1:
             t = torch.tensor([dt, e2e_updates], device="cuda", dtype=torch.float64)
             tm = t[:1].clone()
@@ -371,7 +373,9 @@ def main():
             dt, e2e_updates = float(tm.item()), float(tu.item())
         e2e = {"value": e2e_updates / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d // args.e2e_steps), "d2h_bytes_per_step": int(d2h // args.e2e_steps),
-               "steps": args.e2e_steps, "host_memory": "pinned"}
+               "steps": args.e2e_steps, "host_memory": "pinned",
+               "per_step": "bdm_update_agents (positions; diameters where agents grow) + bdm_step(1) + "
+                           "bdm_get_agents"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -114,6 +114,19 @@ int bdm_create(const bdm_params* per_sim, int32_t n_sims, int64_t max_agents_tot
 int bdm_set_agents(bdm_ctx* ctx, int32_t sim, int64_t n, const double* xyz,
                    const double* diameter, int32_t flags);
 
+/* Give the current agents of simulation `sim` new positions and, when
+ * `diameter` is not NULL, new diameters: row i of xyz (n x 3, row-major)
+ * and of diameter belongs to agent ID i, and n must equal the agent count.
+ * Unlike bdm_set_agents this keeps the simulation: storage order, iteration
+ * counter and history stay, and agents whose values change count as changed
+ * in the next iteration (static detection).  Meant for callers that move
+ * agents between steps (coupling to another code).  The thesis has no
+ * counterpart.  Errors: BDM_E_INVAL (n differs from the count, non-finite
+ * value, diameter <= 0), BDM_E_STATE (no agents set), latched device
+ * errors as bdm_sync. */
+int bdm_update_agents(bdm_ctx* ctx, int32_t sim, int64_t n, const double* xyz,
+                      const double* diameter, int32_t flags);
+
 /* Run n_iterations iterations of every simulation (S0-S7), asynchronously
  * on the context's stream.  Errors: BDM_E_STATE (a simulation has no
  * agents set), BDM_E_NOMEM (box table growth failed), BDM_E_CUDA. */

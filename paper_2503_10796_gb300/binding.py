@@ -49,6 +49,7 @@ class BdmTuning(C.Structure):
 SIGNATURES = {
     "bdm_create": (C.c_int, [_P(BdmParams), _i32, _i64, _i32, _vp, _P(_vp)]),
     "bdm_set_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _i32]),
+    "bdm_update_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _i32]),
     "bdm_step": (C.c_int, [_vp, _i32]),
     "bdm_sync": (C.c_int, [_vp]),
     "bdm_get_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _P(_i64), _i32]),
@@ -156,6 +157,18 @@ class Context:
             raise ValueError("xyz and diameter differ in length")
         self._check(self._lib.bdm_set_agents(self._h, sim, xyz.shape[0], _dptr(xyz), _dptr(d), 0))
 
+    def update_agents(self, sim: int, xyz, diameter=None):
+        """New positions (n x 3, by ID) and optionally diameters of the current
+        agents, keeping storage order, iteration counter and history."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        d = None
+        if diameter is not None:
+            d = np.ascontiguousarray(diameter, dtype=np.float64).reshape(-1)
+            if d.shape[0] != xyz.shape[0]:
+                raise ValueError("xyz and diameter differ in length")
+        self._check(self._lib.bdm_update_agents(self._h, sim, xyz.shape[0], _dptr(xyz),
+                                                _dptr(d) if d is not None else None, 0))
+
     def step(self, iterations: int = 1):
         self._check(self._lib.bdm_step(self._h, int(iterations)))
 
@@ -178,14 +191,15 @@ class Context:
             xyz = np.empty((n.value, 3)); d = np.empty(n.value)
         else:
             xyz, d = out
-            if xyz.dtype != np.float64 or d.dtype != np.float64 or not (
-                    xyz.flags.c_contiguous and d.flags.c_contiguous) or xyz.shape[0] != d.shape[0]:
-                raise ValueError("out must be C-contiguous float64 arrays (n x 3, n)")
-        self._check(self._lib.bdm_get_agents(self._h, sim, xyz.shape[0], _dptr(xyz), _dptr(d), C.byref(n), 0))
+            if xyz.dtype != np.float64 or not xyz.flags.c_contiguous or (d is not None and (
+                    d.dtype != np.float64 or not d.flags.c_contiguous or xyz.shape[0] != d.shape[0])):
+                raise ValueError("out must be C-contiguous float64 arrays (n x 3, n), d may be None")
+        self._check(self._lib.bdm_get_agents(self._h, sim, xyz.shape[0], _dptr(xyz),
+                                             _dptr(d) if d is not None else None, C.byref(n), 0))
         k = n.value
         if out is not None and k == xyz.shape[0]:
             return xyz, d
-        return xyz[:k], d[:k]
+        return xyz[:k], (d[:k] if d is not None else None)
 
     def get_agents_device(self, sim: int, xyz_t, d_t):
         """Write into CUDA tensors (n x 3 and n float64) on the context stream."""

@@ -621,6 +621,44 @@ int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const 
   return BDM_OK;
 }
 
+int bdm_update_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const double *diameter, int32_t flags) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
+  if (n < 0 || (n > 0 && !xyz)) return fail(c, BDM_E_INVAL, "n < 0 or NULL positions");
+  rc = latched_error(c);
+  if (rc) return rc;
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  if (n != s.n) return fail(c, BDM_E_INVAL, "n differs from the agent count " + std::to_string(s.n));
+  if (n == 0) return BDM_OK;
+  const bool dev = (flags & BDM_DEVICE_PTRS) != 0;
+  const double *dx = xyz, *dd = diameter;
+  if (!dev) {
+    rc = ensure_xfer(c, (size_t)(4 * n));
+    if (rc) return rc;
+    cudaMemcpyAsync(c->d_xfer, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream);
+    dx = c->d_xfer;
+    if (diameter) {
+      cudaMemcpyAsync(c->d_xfer + 3 * n, diameter, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+      dd = c->d_xfer + 3 * n;
+    }
+  }
+  cudaMemsetAsync(c->d_bad, 0xFF, sizeof(unsigned long long), c->stream);
+  launch_check_input(c->stream, n, dx, dd, c->d_bad);
+  unsigned long long hb = ~0ull;
+  cudaMemcpyAsync(&hb, c->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "uploading agents");
+  if (hb != ~0ull)
+    return fail(c, BDM_E_INVAL, "non-finite position, or diameter not finite and > 0, at row " + std::to_string(hb));
+  launch_update_agents(c->D, c->stream, c->h_sc[sim].base, n, dx, dd);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "updating agents");
+  return BDM_OK;
+}
+
 int bdm_step(bdm_ctx *c, int32_t n_iterations) {
   if (!c) return BDM_E_INVAL;
   if (n_iterations < 0) return fail(c, BDM_E_INVAL, "n_iterations < 0");

@@ -35,6 +35,8 @@ void launch_count_flags(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_
                         unsigned long long *counts2);
 void launch_set_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, int64_t cap,
                        const double *xyz, const double *diam);
+void launch_update_agents(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const double *xyz,
+                          const double *diam);
 void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, unsigned long long *bad);
 
 // sort.cu

@@ -311,13 +311,44 @@ void launch_set_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, 
   k_set_agents<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, sim, base, n, cap, xyz, diam);
 }
 
-// Smallest row with a non-finite coordinate or a diameter that is not
-// finite and > 0 (*bad stays all-ones when every row is valid).
+// New positions (and, when diam is given, diameters) of the agents of a
+// simulation, by ID, keeping the storage order and the history; an agent
+// whose values change is marked changed (static detection, box reuse).
+__global__ void k_update_agents(DevCtx C, int64_t base, int64_t n, const double *xyz, const double *diam) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t slot = base + i;
+  const int64_t id = C.a.id[slot];
+  const double x = xyz[3 * id], y = xyz[3 * id + 1], z = xyz[3 * id + 2];
+  bool changed = x != C.a.x[slot] || y != C.a.y[slot] || z != C.a.z[slot];
+  if (changed) {
+    C.a.x[slot] = x; C.a.y[slot] = y; C.a.z[slot] = z;
+  }
+  if (diam) {
+    const double d = diam[id];
+    if (d != C.a.d[slot]) {
+      C.a.d[slot] = d;
+      // volume of a sphere of diameter d: (pi * ((d * d) * d)) / 6
+      C.a.v[slot] = __ddiv_rn(__dmul_rn(3.141592653589793, __dmul_rn(__dmul_rn(d, d), d)), 6.0);
+      changed = true;
+    }
+  }
+  if (changed) C.a.flags[slot] |= FLAG_CHANGED;
+}
+
+void launch_update_agents(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const double *xyz,
+                          const double *diam) {
+  if (n <= 0) return;
+  k_update_agents<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, xyz, diam);
+}
+
+// Smallest row with a non-finite coordinate or (diam given) a diameter that
+// is not finite and > 0 (*bad stays all-ones when every row is valid).
 __global__ void k_check_input(int64_t n, const double *xyz, const double *diam, unsigned long long *bad) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  bool ok = isfinite(xyz[3 * i]) && isfinite(xyz[3 * i + 1]) && isfinite(xyz[3 * i + 2]) && diam[i] > 0.0 &&
-            isfinite(diam[i]);
+  bool ok = isfinite(xyz[3 * i]) && isfinite(xyz[3 * i + 1]) && isfinite(xyz[3 * i + 2]) &&
+            (!diam || (diam[i] > 0.0 && isfinite(diam[i])));
   if (!ok) atomicMin(bad, (unsigned long long)i);
 }
 

@@ -415,3 +415,39 @@ def test_box_overflow_is_reported(orc):
     with pytest.raises(binding.BdmError) as e:
         ctx.sync()
     assert e.value.code == -4
+
+
+def test_update_agents_keeps_the_simulation(orc):
+    """bdm_update_agents moves agents by ID without resetting the simulation:
+    the forces of the next step equal those of a fresh context set to the
+    same positions, IDs are kept, and n must match the agent count."""
+    from paper_2503_10796_gb300 import binding
+    pop = workloads.clustered(n_clusters=3, per_cluster=3000, side=500.0, sigma=30.0, seed=4)
+    a = ctx_for(pop, sort_interval=1)
+    a.step(3)
+    x, d = a.get_agents(0)
+    rng = np.random.default_rng(1)
+    x2 = x + rng.uniform(-0.5, 0.5, x.shape)
+    a.update_agents(0, x2)                       # positions only: diameters kept
+    assert a.stats(0)["iterations"] == 3
+    got, gd = a.get_agents(0)
+    assert np.array_equal(got, x2) and np.array_equal(gd, d)
+    b = ctx_for(workloads.Population(x2, d, pop.params, "moved"), sort_interval=1)
+    a.step(1)
+    b.step(1)
+    a.sync()
+    b.sync()
+    Fa, na, _ = a.forces(0)
+    Fb, nb, _ = b.forces(0)
+    _, _, smag = orc_for(workloads.Population(x2, d, pop.params, "moved")).forces()
+    assert np.array_equal(na, nb)
+    err = np.linalg.norm(Fa - Fb, axis=1) / np.maximum(smag, 1e-30)
+    assert err.max() <= 2e-5
+    with pytest.raises(binding.BdmError) as e:
+        a.update_agents(0, x2[:-1])
+    assert e.value.code == -1
+    bad = x2.copy()
+    bad[7, 1] = np.inf
+    with pytest.raises(binding.BdmError) as e:
+        a.update_agents(0, bad)
+    assert e.value.code == -1
