@@ -65,7 +65,7 @@ struct bdm_ctx {
   int64_t prof_launches[kStages] = {};
   double prof_ms[kStages] = {};
   // graph of one iteration
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // one iteration without / with the re-sort
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // one iteration by sort_mode
   std::vector<int64_t> h_iter;       // per simulation: iterations since its agents were set
   bool graph_dirty = true;
   double *d_xfer = nullptr;          // host transfer staging (grow-only)
@@ -207,17 +207,23 @@ void harvest_events(bdm_ctx *c) {
 // Whether some simulation re-sorts in its next iteration (the device makes
 // the same test per simulation; the host copy only picks the graph, so that
 // iterations without a re-sort launch none of the sort kernels).
-static bool sort_due(const bdm_ctx *c) {
-  if (!c->any_sort) return false;
+// 0: no re-sort in this iteration; 1: Morton radix sort after the count
+// (a simulation re-sorts in its first iteration since its agents were set:
+// the storage is in ID order); 2: permutation into the cell order at the
+// end of the iteration (every later re-sort: the storage is already sorted
+// and the cells keep its order).
+static int sort_mode(const bdm_ctx *c) {
+  if (!c->any_sort) return 0;
+  int mode = 0;
   for (int s = 0; s < c->n_sims; ++s) {
     const int iv = c->h_sc[s].sort_interval;
-    if (iv > 0 && c->h_sc[s].base >= 0 && c->h_iter[s] % iv == 0) return true;
+    if (iv > 0 && c->h_sc[s].base >= 0 && c->h_iter[s] % iv == 0) mode = c->h_iter[s] == 0 ? 1 : (mode ? mode : 2);
   }
-  return false;
+  return mode;
 }
 
 // One iteration of every simulation.
-void launch_iteration(bdm_ctx *c, bool sort) {
+void launch_iteration(bdm_ctx *c, int sort) {
   const DevCtx &D = c->D;
   cudaStream_t st = c->stream;
   stage_begin(c, 0);
@@ -227,7 +233,7 @@ void launch_iteration(bdm_ctx *c, bool sort) {
   stage_begin(c, 1);
   launch_count(D, st, 1);
   stage_end(c);
-  if (c->any_sort && sort) {
+  if (c->any_sort && sort == 1) {
     // re-sort by the Morton code of the boxes just counted (when due)
     stage_begin(c, 7);
     launch_morton(D, st, c->d_sort, c->sort_bytes, c->sort_key_bits, c->sort_curve);
@@ -254,6 +260,11 @@ void launch_iteration(bdm_ctx *c, bool sort) {
   if (c->any_grow) {
     stage_begin(c, 6);
     launch_growth(D, st, c->d_grow, c->grow_bytes);
+    stage_end(c);
+  }
+  if (c->any_sort && sort == 2) {
+    stage_begin(c, 7);
+    launch_cell_order(D, st, c->d_sort);
     stage_end(c);
   }
 }
@@ -682,11 +693,11 @@ int bdm_step(bdm_ctx *c, int32_t n_iterations) {
       c->graph_dirty = false;
     }
     for (int i = 0; i < chunk; ++i) {
-      const bool srt = sort_due(c);
+      const int srt = sort_mode(c);
       if (c->profiling) {
         launch_iteration(c, srt);
       } else {
-        cudaGraphExec_t &gx = c->gexec[srt ? 1 : 0];
+        cudaGraphExec_t &gx = c->gexec[srt];
         if (!gx) {
           cudaGraph_t g;
           cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);

@@ -40,6 +40,7 @@ void launch_update_agents(const DevCtx &C, cudaStream_t st, int64_t base, int64_
 void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, unsigned long long *bad);
 
 // sort.cu
+void launch_cell_order(const DevCtx &C, cudaStream_t st, void *scratch);
 void launch_morton(const DevCtx &C, cudaStream_t st, void *scratch, size_t scratch_bytes, int key_bits,
                    int curve = 0);
 size_t morton_scratch_bytes(int64_t total_slots);

@@ -269,12 +269,15 @@ __global__ void k_sort_gather(DevCtx C, SortBufs B, const int32_t *perm) {
   B.nnz[k] = C.a.nnz[src];
 }
 
-__global__ void k_sort_writeback(DevCtx C, SortBufs B, const int32_t *perm) {
+// cells: the permutation is the cell order (perm = the cells' slots), and
+// each cell's slot becomes its new one.
+__global__ void k_sort_writeback(DevCtx C, SortBufs B, const int32_t *perm, int cells) {
   if (!B.flag[0]) return;
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= C.g->n_cells) return;
   int s = C.a.sim[perm[k]];
   int64_t dst = C.sc[s].base + (k - C.ss[s].cell_base);
+  if (cells) C.c.slot[k] = (int32_t)dst;
   C.a.x[dst] = B.x[k];
   C.a.y[dst] = B.y[k];
   C.a.z[dst] = B.z[k];
@@ -322,7 +325,23 @@ void launch_morton(const DevCtx &C, cudaStream_t st, void *scratch, size_t scrat
     int32_t *tv = vin; vin = vout; vout = tv;
   }
   k_sort_gather<<<nb, kSortThreads, 0, st>>>(C, B, vin);
-  k_sort_writeback<<<nb, kSortThreads, 0, st>>>(C, B, vin);
+  k_sort_writeback<<<nb, kSortThreads, 0, st>>>(C, B, vin, 0);
+}
+
+// Re-sort without a sort: the cells of the iteration just computed list
+// every box's agents together, boxes in the storage order of their first
+// agent (the order of the last sort, kept as agents move); permuting the
+// storage into cell order keeps boxes contiguous and that order.  Runs at
+// the end of an iteration (after displacement and division), when the cells
+// still map onto the storage.
+void launch_cell_order(const DevCtx &C, cudaStream_t st, void *scratch) {
+  int64_t M = C.total_slots;
+  if (M <= 0) return;
+  SortBufs B = carve(scratch, M);
+  cudaMemsetAsync(B.flag, 1, sizeof(uint32_t), st);  // non-zero: due (a memset node in a graph)
+  unsigned int nb = (unsigned int)((M + kSortThreads - 1) / kSortThreads);
+  k_sort_gather<<<nb, kSortThreads, 0, st>>>(C, B, C.c.slot);
+  k_sort_writeback<<<nb, kSortThreads, 0, st>>>(C, B, C.c.slot, 1);
 }
 
 }  // namespace bdm

@@ -271,6 +271,23 @@ def test_morton_sort_orders_storage(orc, n_sims):
         assert np.array_equal(x, p.xyz)
 
 
+def test_later_resorts_keep_morton_order(orc):
+    """Re-sorts after the first permute the storage into the cell order; with
+    no movement the storage stays in Morton order of boxes, every agent once,
+    and the results stay the same."""
+    pop = workloads.clustered(n_clusters=3, per_cluster=1200, side=500.0, sigma=30.0, seed=6)
+    ctx = ctx_for(pop, adherence=1e9, sort_interval=1)
+    ctx.step(4)
+    order = ctx.storage_order(0)
+    assert np.array_equal(np.sort(order), np.arange(pop.n))
+    box, _, dims = ctx.grid(0)
+    codes = morton_codes(box, dims)
+    seq = codes[order]
+    assert np.array_equal(seq, codes[orc_for(pop).morton_agent_order()])
+    x, _ = ctx.get_agents(0)
+    assert np.array_equal(x, pop.xyz)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_sorting_does_not_change_results(orc, precision):
     pop = workloads.plain_fp64()
