@@ -484,6 +484,93 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
 }
 
+// FP64 path with a thread per stencil row: 9 threads per agent, 32 agents
+// per block.  Each thread sums its row's pairs (the definition operation by
+// operation, as force64); the agent's first thread adds the nine row sums
+// in row order.  Nine times the threads of force64 hide the latency of the
+// FP64 divisions and square roots, which run at a small fraction of the
+// FP32 rate on this part.
+constexpr int kRowAgents = 32;
+constexpr int kRowThreads = kRowAgents * 9;
+
+__global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
+  __shared__ double part[kRowThreads][3];
+  __shared__ uint32_t pnz[kRowThreads];
+  __shared__ uint8_t skip[kRowAgents];
+  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
+  const int a = threadIdx.x / 9, r = threadIdx.x % 9;
+  const int64_t p = (int64_t)blockIdx.x * kRowAgents + a;
+  bool active = p < C.g->n_cells;
+  const int sim = active ? C.c.sim[p] : 0;
+  const SimConst &sc = C.sc[sim];
+  const SimState &s = C.ss[sim];
+  active = active && s.valid && sc.precision == BDM_PREC_FP64;
+  int64_t cx = 0, cy = 0, cz = 0;
+  if (active) unpack_coords(C.c.pkey[p], cx, cy, cz);
+  const uint32_t stamp = C.g->stamp & kStampMask;
+  if (r == 0) {
+    bool st = false;
+    if (active) {
+      st = is_static_cell(C, sc, s, p, cx, cy, cz, stamp);
+      C.c.stat[p] = st ? 1 : 0;
+    }
+    skip[a] = (!active || st) ? 1 : 0;
+  }
+  __syncthreads();
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  uint32_t nnz = 0;
+  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
+  const int dz = r / 3 - 1, dy = r % 3 - 1;
+  if (!skip[a] && dz >= t.zlo && dz <= t.zhi && dy >= t.ylo && dy <= t.yhi) {
+    const double4_32a o = C.c.r64[p];
+    const double k = sc.k, gam = sc.gamma;
+    const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
+                         (uint32_t)t.cx;
+    for (int dx = t.xlo; dx <= t.xhi; ++dx) {
+      const unsigned long long e = t.e[row + dx];
+      const uint32_t cnt = ent_live(e, stamp);
+      const int64_t j0 = ent_start(e);
+      for (uint32_t m = 0; m < cnt; ++m) {
+        const int64_t j = j0 + m;
+        if (j == p) continue;
+        const double4_32a q = C.c.r64[j];
+        const double ddx = __dsub_rn(o.x, q.x), ddy = __dsub_rn(o.y, q.y), ddz = __dsub_rn(o.z, q.z);
+        const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+        const double R = __dadd_rn(o.w, q.w);
+        if (!(s2 < __dmul_rn(R, R) * 1.0000001)) continue;  // cheap reject far beyond contact
+        const double dist = __dsqrt_rn(s2);
+        const double del = __dsub_rn(R, dist);
+        if (!(del > 0.0)) continue;
+        const double rr = __ddiv_rn(__dmul_rn(o.w, q.w), R);
+        const double rep = __dmul_rn(k, del);
+        const double adh = __dmul_rn(gam, __dsqrt_rn(__dmul_rn(rr, del)));
+        const double fn = __dsub_rn(rep, adh);
+        nnz += (fn != 0.0);
+        if (dist > 0.0) {
+          fx = __dadd_rn(fx, __dmul_rn(fn, __ddiv_rn(ddx, dist)));
+          fy = __dadd_rn(fy, __dmul_rn(fn, __ddiv_rn(ddy, dist)));
+          fz = __dadd_rn(fz, __dmul_rn(fn, __ddiv_rn(ddz, dist)));
+        }
+      }
+    }
+  }
+  part[threadIdx.x][0] = fx; part[threadIdx.x][1] = fy; part[threadIdx.x][2] = fz;
+  pnz[threadIdx.x] = nnz;
+  __syncthreads();
+  if (r == 0 && !skip[a]) {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    uint32_t sn = 0;
+    for (int q = 0; q < 9; ++q) {
+      sx = __dadd_rn(sx, part[threadIdx.x + q][0]);
+      sy = __dadd_rn(sy, part[threadIdx.x + q][1]);
+      sz = __dadd_rn(sz, part[threadIdx.x + q][2]);
+      sn += pnz[threadIdx.x + q];
+    }
+    C.c.f64[p] = make_double4_32a(sx, sy, sz, 0.0);
+    C.c.nnz[p] = (uint8_t)(sn > 255u ? 255u : sn);
+  }
+}
+
 // fp64_only: leave FP32-path simulations to another kernel.
 __global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C, int fp64_only) {
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
@@ -699,7 +786,8 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, 
     else if (variant == 3) k_force32d<false><<<nb, th, 0, st>>>(C);
     else k_force32d<true><<<nb, th, 0, st>>>(C);
   }
-  if (has_fp64) k_force<<<nb, th, 0, st>>>(C, 1);
+  if (has_fp64)
+    k_force64r<<<(unsigned int)((C.total_slots + kRowAgents - 1) / kRowAgents), kRowThreads, 0, st>>>(C);
 }
 
 void launch_displace(const DevCtx &C, cudaStream_t st) {
