@@ -85,8 +85,8 @@ struct Agents {               // storage arrays (per slot)
   double *x, *y, *z, *d, *v;
   int32_t *id;                // caller ID
   int32_t *sim;               // owning simulation (every slot of a region)
-  uint64_t *pkey;             // packed box coordinates c_x | c_y << 21 | c_z << 42
-  uint64_t *pkey_hist;        // box coordinates in the last iteration's grid
+  uint64_t *pkey;             // packed box coordinates c_x | c_y << 21 | c_z << 42 of the last
+                              // step's grid (a step reads them as history, then rewrites them)
   uint32_t *rank;             // position inside the box
   uint8_t *flags;
   uint8_t *nnz;               // non-zero pair forces of the last evaluation (saturating)
@@ -137,6 +137,7 @@ struct DevCtx {
   Table tab;
   int32_t *order;             // simulations in slot-region order (-1 padded)
   unsigned long long *tstat;  // per scan tile: stamp << 34 | state << 32 | sum (look-back)
+  uint64_t *qkey;             // per slot: packed box of the last query build (queries only)
   int32_t n_sims;
   int64_t total_slots;
 };

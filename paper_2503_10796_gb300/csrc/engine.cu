@@ -429,7 +429,7 @@ int query_grid(bdm_ctx *c, bool with_cells, const std::vector<double> *boxes) {
   launch_params(c->D, c->stream, 0);
   if (with_cells) {
     launch_count(c->D, c->stream, 0);
-    launch_scan(c->D, c->stream);
+    launch_scan(c->D, c->stream, 0);
     launch_place(c->D, c->stream, 0);
   }
   if (boxes) upload_consts(c);
@@ -493,7 +493,7 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   ALLOC(c->d_bad, 1, "input check");
   ALLOC(D.a.x, M, "x"); ALLOC(D.a.y, M, "y"); ALLOC(D.a.z, M, "z"); ALLOC(D.a.d, M, "diameter");
   ALLOC(D.a.v, M, "volume"); ALLOC(D.a.id, M, "ids"); ALLOC(D.a.sim, M, "slot simulation");
-  ALLOC(D.a.pkey, M, "box keys"); ALLOC(D.a.pkey_hist, M, "box history"); ALLOC(D.a.rank, M, "ranks");
+  ALLOC(D.a.pkey, M, "box keys"); ALLOC(D.a.rank, M, "ranks");
   ALLOC(D.a.flags, M, "flags"); ALLOC(D.a.nnz, M, "nnz");
   ALLOC(D.c.slot, M, "cell slots"); ALLOC(D.c.sim, M, "cell sims"); ALLOC(D.c.pkey, M, "cell keys");
   ALLOC(D.c.flag, M, "cell flags"); ALLOC(D.c.nnz, M, "cell nnz"); ALLOC(D.c.stat, M, "cell static");
@@ -798,6 +798,7 @@ int bdm_neighbors(bdm_ctx *c, int32_t sim, double radius, int64_t cap, int64_t *
     if (!r2) r2 = dalloc(c, &c->D.q.sim, M, "query sims");
     if (!r2) r2 = dalloc(c, &c->D.q.pkey, M, "query keys");
     if (!r2) r2 = dalloc(c, &c->D.q.r64, M, "query records");
+    if (!r2) r2 = dalloc(c, &c->D.qkey, M, "query box keys");
     if (r2) return r2;
     cudaMemsetAsync(c->D.q.slot, 0, sizeof(int32_t) * M, c->stream);
     cudaMemsetAsync(c->D.q.sim, 0, sizeof(int32_t) * M, c->stream);
@@ -1001,7 +1002,7 @@ namespace {
 struct Snapshot {
   double *x = nullptr, *y = nullptr, *z = nullptr, *d = nullptr, *v = nullptr;
   int32_t *id = nullptr;
-  uint64_t *pk = nullptr, *ph = nullptr;
+  uint64_t *pk = nullptr;
   uint8_t *fl = nullptr, *nz = nullptr;
   std::vector<SimState> ss;
   std::vector<int64_t> h_iter;
@@ -1016,7 +1017,6 @@ int snap_alloc(bdm_ctx *c, Snapshot &S, size_t M) {
   if (!rc) rc = dalloc(c, &S.v, M, "snapshot v");
   if (!rc) rc = dalloc(c, &S.id, M, "snapshot id");
   if (!rc) rc = dalloc(c, &S.pk, M, "snapshot keys");
-  if (!rc) rc = dalloc(c, &S.ph, M, "snapshot key history");
   if (!rc) rc = dalloc(c, &S.fl, M, "snapshot flags");
   if (!rc) rc = dalloc(c, &S.nz, M, "snapshot nnz");
   return rc;
@@ -1024,7 +1024,7 @@ int snap_alloc(bdm_ctx *c, Snapshot &S, size_t M) {
 
 void snap_free(bdm_ctx *c, Snapshot &S) {
   dfree(c, S.x); dfree(c, S.y); dfree(c, S.z); dfree(c, S.d); dfree(c, S.v);
-  dfree(c, S.id); dfree(c, S.pk); dfree(c, S.ph); dfree(c, S.fl); dfree(c, S.nz);
+  dfree(c, S.id); dfree(c, S.pk); dfree(c, S.fl); dfree(c, S.nz);
 }
 
 int snap_copy(bdm_ctx *c, Snapshot &S, size_t M, bool save) {
@@ -1041,7 +1041,6 @@ int snap_copy(bdm_ctx *c, Snapshot &S, size_t M, bool save) {
   if (!e) e = cp(S.v, A.v, 8 * M);
   if (!e) e = cp(S.id, A.id, 4 * M);
   if (!e) e = cp(S.pk, A.pkey, 8 * M);
-  if (!e) e = cp(S.ph, A.pkey_hist, 8 * M);
   if (!e) e = cp(S.fl, A.flags, M);
   if (!e) e = cp(S.nz, A.nnz, M);
   if (save) {

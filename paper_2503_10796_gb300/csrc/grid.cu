@@ -273,26 +273,28 @@ __device__ __forceinline__ void tab_mark_dirty(unsigned long long *e, uint32_t s
   atomicOr(e, 1ull << 42);
 }
 
-// hist: the per-slot box history (the step passes it; queries pass null so
-// that the history of the last iteration survives them).  Every load that
-// does not depend on another is issued before the first test, so that one
-// thread waits for few round trips in a row.
-__global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
+// step: the step's build, which reads each agent's box of the last step
+// (the history of static detection and of the unchanged-agent shortcut)
+// before it rewrites it; a query build (step = 0) writes its boxes to the
+// query keys and leaves the history alone.  Every load that does not depend
+// on another is issued before the first test, so that one thread waits for
+// few round trips in a row.
+__global__ void __launch_bounds__(kThreads) k_count(DevCtx C, int step) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool in = slot < C.total_slots;
   const int64_t sl = in ? slot : C.total_slots - 1;
   const int sim = C.a.sim[sl];
   const double p[3] = {C.a.x[sl], C.a.y[sl], C.a.z[sl]};
-  const uint64_t pk_prev_in = hist ? hist[sl] : 0ull;
-  const uint8_t fl = hist ? C.a.flags[sl] : (uint8_t)0;
+  const uint64_t pk_prev_in = step ? C.a.pkey[sl] : 0ull;
+  const uint8_t fl = step ? C.a.flags[sl] : (uint8_t)0;
   const uint32_t stamp = C.g->stamp & kStampMask;
   const SimConst &sc = C.sc[sim < 0 ? 0 : sim];
   const SimState &s = C.ss[sim < 0 ? 0 : sim];
   const bool valid = in && sim >= 0 && sl - sc.base < s.n && s.valid;
-  const bool changed = valid && hist && (fl & FLAG_CHANGED) != 0;
+  const bool changed = valid && step && (fl & FLAG_CHANGED) != 0;
   uint32_t c[3] = {0u, 0u, 0u};
   if (!valid) {
-  } else if (hist && s.same_grid && !changed) {
+  } else if (step && s.same_grid && !changed) {
     // unchanged agent, unchanged grid: the box of the last iteration
     c[0] = (uint32_t)(pk_prev_in & kCoordMask);
     c[1] = (uint32_t)((pk_prev_in >> kCoordBits) & kCoordMask);
@@ -328,8 +330,10 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, uint64_t *hist) {
     base = tab_add(&C.tab.e[idx], stamp, dirty_any != 0u, (uint32_t)(end - start + 1), C.g);
   base = __shfl_sync(FULL, base, start);
   if (!valid) return;
-  C.a.pkey[slot] = pk;
-  if (hist) hist[slot] = pk;
+  if (step)
+    C.a.pkey[slot] = pk;
+  else
+    C.qkey[slot] = pk;
   if (changed && s.same_grid && pk_prev_in != pk) {
     int64_t px, py, pz;
     unpack_coords(pk_prev_in, px, py, pz);
@@ -406,7 +410,7 @@ __device__ __forceinline__ void tile_publish(unsigned long long *w, uint32_t sta
       ((unsigned long long)stamp << 34) | ((unsigned long long)state << 32) | (unsigned long long)v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C) {
+__global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t *keys) {
   __shared__ uint32_t sh[33];
   __shared__ uint32_t s_tile, s_base;
   if (threadIdx.x == 0) s_tile = atomicAdd(&C.g->tile_ticket, 1u);
@@ -421,7 +425,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C) {
     const int64_t slot = base + (int64_t)i * kScanThreads;
     const int64_t sl = slot < C.total_slots ? slot : C.total_slots - 1;
     rank[i] = C.a.rank[sl];
-    pk[i] = C.a.pkey[sl];
+    pk[i] = keys[sl];
     sim[i] = slot < C.total_slots ? C.a.sim[sl] : -1;
   }
   unsigned long long e[kScanItems];
@@ -512,12 +516,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C) {
 
 // zero_f32: clear the FP32 force of every placed FP32-path agent (the
 // symmetric force walk adds into it).
-__global__ void __launch_bounds__(kThreads) k_place(DevCtx C, Cells cells, int fp64_records, int zero_f32) {
+__global__ void __launch_bounds__(kThreads) k_place(DevCtx C, Cells cells, const uint64_t *keys, int fp64_records,
+                                                   int zero_f32) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= C.total_slots) return;
   // every per-slot load first: they do not depend on one another
   const int sim = C.a.sim[slot];
-  const uint64_t pk = C.a.pkey[slot];
+  const uint64_t pk = keys[slot];
   const uint32_t rank = C.a.rank[slot];
   const double pos[3] = {C.a.x[slot], C.a.y[slot], C.a.z[slot]};
   const double dia = C.a.d[slot];
@@ -574,19 +579,19 @@ void launch_bbox(const DevCtx &C, cudaStream_t st) {
 void launch_params(const DevCtx &C, cudaStream_t st, int step) { k_params<<<1, 256, 0, st>>>(C, step); }
 
 void launch_count(const DevCtx &C, cudaStream_t st, int step) {
-  k_count<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, step ? C.a.pkey_hist : nullptr);
+  k_count<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, step);
 }
 
 int64_t scan_tiles(int64_t total_slots) { return (total_slots + kScanTile - 1) / kScanTile; }
 
-void launch_scan(const DevCtx &C, cudaStream_t st) {
+void launch_scan(const DevCtx &C, cudaStream_t st, int step) {
   const int64_t G = scan_tiles(C.total_slots);
-  k_scan<<<(unsigned int)G, kScanThreads, 0, st>>>(C);
+  k_scan<<<(unsigned int)G, kScanThreads, 0, st>>>(C, step ? C.a.pkey : C.qkey);
 }
 
 void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32) {
-  k_place<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, step ? C.c : C.q, step ? 0 : 1,
-                                                                     step ? zero_f32 : 0);
+  k_place<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, step ? C.c : C.q, step ? C.a.pkey : C.qkey,
+                                                                     step ? 0 : 1, step ? zero_f32 : 0);
 }
 
 }  // namespace bdm

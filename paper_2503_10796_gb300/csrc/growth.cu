@@ -302,7 +302,6 @@ __global__ void k_divide(DevCtx C, GrowBufs B) {
   C.a.nnz[j] = 0;
   C.a.id[j] = (int32_t)(n0 + r);
   C.a.pkey[j] = C.a.pkey[slot];
-  C.a.pkey_hist[j] = C.a.pkey_hist[slot];
   C.a.rank[j] = 0;
 }
 

@@ -109,7 +109,7 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   D.a.x = at<double>(base, oAX); D.a.y = at<double>(base, oAY); D.a.z = at<double>(base, oAZ);
   D.a.d = at<double>(base, oAD); D.a.v = at<double>(base, oAV);
   D.a.id = at<int32_t>(base, oAId); D.a.sim = at<int32_t>(base, oASim);
-  D.a.pkey = at<uint64_t>(base, oAKey); D.a.pkey_hist = at<uint64_t>(base, oAHist);
+  D.a.pkey = at<uint64_t>(base, oAKey);
   D.a.rank = at<uint32_t>(base, oARank); D.a.flags = at<uint8_t>(base, oAFlags); D.a.nnz = at<uint8_t>(base, oANnz);
   D.c.slot = at<int32_t>(base, oCSlot); D.c.sim = at<int32_t>(base, oCSim); D.c.pkey = at<uint64_t>(base, oCKey);
   D.c.r0 = at<float4>(base, oCR0); D.c.r1 = at<float4>(base, oCR1); D.c.r64 = at<double4_32a>(base, oCR64);

@@ -301,7 +301,6 @@ __global__ void k_set_agents(DevCtx C, int sim, int64_t base, int64_t n, int64_t
   C.a.flags[slot] = FLAG_CHANGED;
   C.a.nnz[slot] = 0;
   C.a.pkey[slot] = 0;
-  C.a.pkey_hist[slot] = 0;
   C.a.rank[slot] = 0;
 }
 

@@ -42,7 +42,7 @@ struct SortBufs {
   // permutation scratch
   double *x, *y, *z, *d, *v;
   int32_t *id;
-  uint64_t *pkey, *pkey_hist;
+  uint64_t *pkey;
   uint32_t *rank;
   uint8_t *flags, *nnz;
 };
@@ -71,7 +71,6 @@ static SortBufs carve(void *scratch, int64_t M) {
   b.v = (double *)take(8 * M);
   b.id = (int32_t *)take(4 * M);
   b.pkey = (uint64_t *)take(8 * M);
-  b.pkey_hist = (uint64_t *)take(8 * M);
   b.rank = (uint32_t *)take(4 * M);
   b.flags = (uint8_t *)take(M);
   b.nnz = (uint8_t *)take(M);
@@ -83,7 +82,7 @@ size_t morton_scratch_bytes(int64_t total_slots) {
   size_t b = 0;
   for (size_t s : {8 * M, 8 * M, 4 * M, 4 * M, (size_t)4 * kDigits * 2048, (size_t)4 * kDigits, (size_t)16, 8 * M,
                    8 * M, 8 * M,
-                   8 * M, 8 * M, 4 * M, 8 * M, 8 * M, 4 * M, M, M})
+                   8 * M, 8 * M, 4 * M, 8 * M, 4 * M, M, M})
     b += align256(s);
   return b;
 }
@@ -263,7 +262,6 @@ __global__ void k_sort_gather(DevCtx C, SortBufs B, const int32_t *perm) {
   B.v[k] = C.a.v[src];
   B.id[k] = C.a.id[src];
   B.pkey[k] = C.a.pkey[src];
-  B.pkey_hist[k] = C.a.pkey_hist[src];
   B.rank[k] = C.a.rank[src];
   B.flags[k] = C.a.flags[src];
   B.nnz[k] = C.a.nnz[src];
@@ -285,7 +283,6 @@ __global__ void k_sort_writeback(DevCtx C, SortBufs B, const int32_t *perm, int 
   C.a.v[dst] = B.v[k];
   C.a.id[dst] = B.id[k];
   C.a.pkey[dst] = B.pkey[k];
-  C.a.pkey_hist[dst] = B.pkey_hist[k];
   C.a.rank[dst] = B.rank[k];
   C.a.flags[dst] = B.flags[k];
   C.a.nnz[dst] = B.nnz[k];
