@@ -416,23 +416,34 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
   if (threadIdx.x == 0) s_tile = atomicAdd(&C.g->tile_ticket, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const int64_t base = (int64_t)tile * kScanTile + threadIdx.x;
+  // each thread takes kScanItems consecutive slots (vector loads)
+  const int64_t base = (int64_t)tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
   uint32_t rank[kScanItems];
   uint64_t pk[kScanItems];
   int sim[kScanItems];
+  if (base + kScanItems <= C.total_slots) {
+    const uint4 r4 = *reinterpret_cast<const uint4 *>(C.a.rank + base);
+    const int4 s4 = *reinterpret_cast<const int4 *>(C.a.sim + base);
+    const ulonglong2 k01 = *reinterpret_cast<const ulonglong2 *>(keys + base);
+    const ulonglong2 k23 = *reinterpret_cast<const ulonglong2 *>(keys + base + 2);
+    rank[0] = r4.x; rank[1] = r4.y; rank[2] = r4.z; rank[3] = r4.w;
+    sim[0] = s4.x; sim[1] = s4.y; sim[2] = s4.z; sim[3] = s4.w;
+    pk[0] = k01.x; pk[1] = k01.y; pk[2] = k23.x; pk[3] = k23.y;
+  } else {
 #pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const int64_t slot = base + (int64_t)i * kScanThreads;
-    const int64_t sl = slot < C.total_slots ? slot : C.total_slots - 1;
-    rank[i] = C.a.rank[sl];
-    pk[i] = keys[sl];
-    sim[i] = slot < C.total_slots ? C.a.sim[sl] : -1;
+    for (int i = 0; i < kScanItems; ++i) {
+      const int64_t slot = base + i;
+      const int64_t sl = slot < C.total_slots ? slot : C.total_slots - 1;
+      rank[i] = C.a.rank[sl];
+      pk[i] = keys[sl];
+      sim[i] = slot < C.total_slots ? C.a.sim[sl] : -1;
+    }
   }
   unsigned long long e[kScanItems];
   int64_t idx[kScanItems];
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    const int64_t slot = base + (int64_t)i * kScanThreads;
+    const int64_t slot = base + i;
     idx[i] = -1;
     e[i] = 0ull;
     if (sim[i] >= 0) {
@@ -446,13 +457,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
       }
     }
   }
-  uint32_t cnt[kScanItems], sum = 0;
+  uint32_t loc[kScanItems], sum = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    cnt[i] = idx[i] >= 0 ? ent_count(e[i]) : 0u;
-    sum += cnt[i];
+    loc[i] = sum;
+    sum += idx[i] >= 0 ? ent_count(e[i]) : 0u;
   }
-  const uint32_t agg = block_sum_u32(sum, sh);  // valid in warp 0
+  uint32_t agg;
+  const uint32_t ex = block_exscan_u32(sum, sh, &agg);
   const uint32_t stamp = C.g->stamp & kStampMask;
   if (threadIdx.x < 32) {
     // warp 0 looks back 32 tiles at a time: the nearest inclusive prefix
@@ -491,26 +503,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
     if (lane == 0) s_base = run;
   }
   __syncthreads();
-  // exclusive prefix of the leader counts in slot order; each leader writes
-  // its box's first cell into the low half of the table word (a 32-bit
-  // store: the high half, stamp | dirty | count, stays as the count left
-  // it).  After a table error every leader writes an empty current word
-  // instead, so that placement, forces and queries see no agents in any box
-  // of the build.
+  // each leader writes its box's first cell into the low half of the table
+  // word (a 32-bit store: the high half, stamp | dirty | count, stays as the
+  // count left it).  After a table error every leader writes an empty
+  // current word instead, so that placement, forces and queries see no
+  // agents in any box of the build.
   const bool bad = (C.g->err & ERR_TABLE) != 0u;
-  uint32_t off = s_base;
+  const uint32_t off = s_base + ex;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    uint32_t total;
-    const uint32_t ex = block_exscan_u32(cnt[i], sh, &total);
     if (idx[i] >= 0) {
       unsigned long long *w = &C.tab.e[idx[i]];
       if (bad)
         *w = (unsigned long long)stamp << 43;
       else
-        *reinterpret_cast<uint32_t *>(w) = off + ex;
+        *reinterpret_cast<uint32_t *>(w) = off + loc[i];
     }
-    off += total;
   }
 }
 
