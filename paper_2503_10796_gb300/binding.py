@@ -128,6 +128,13 @@ class Context:
         self._h = h
         self.n_sims = len(plist)
 
+    def _check_size_query(self, rc, n):
+        # BDM_E_CAPACITY with a count is the answer to a size query (cap 0);
+        # without one it is an error latched on the device
+        if rc == BDM_OK or (rc == -4 and n.value > 0):
+            return
+        self._check(rc)
+
     def _check(self, rc):
         if rc != BDM_OK:
             raise BdmError(rc, self._lib.bdm_last_error(self._h).decode())
@@ -186,8 +193,7 @@ class Context:
         n = C.c_int64()
         if out is None:
             rc = self._lib.bdm_get_agents(self._h, sim, 0, None, None, C.byref(n), 0)
-            if rc not in (BDM_OK, -4):
-                self._check(rc)
+            self._check_size_query(rc, n)
             xyz = np.empty((n.value, 3)); d = np.empty(n.value)
         else:
             xyz, d = out
@@ -212,8 +218,7 @@ class Context:
     def neighbors(self, sim: int, radius: float) -> np.ndarray:
         n = C.c_int64()
         rc = self._lib.bdm_neighbors(self._h, sim, float(radius), 0, None, C.byref(n))
-        if rc not in (BDM_OK, -4):
-            self._check(rc)
+        self._check_size_query(rc, n)
         out = np.empty((max(n.value, 1), 2), np.int64)
         self._check(self._lib.bdm_neighbors(self._h, sim, float(radius), n.value, _dptr(out), C.byref(n)))
         return out[: n.value]
@@ -228,8 +233,7 @@ class Context:
     def forces(self, sim: int):
         n = C.c_int64()
         rc = self._lib.bdm_get_forces(self._h, sim, 0, None, None, None, C.byref(n))
-        if rc not in (BDM_OK, -4):
-            self._check(rc)
+        self._check_size_query(rc, n)
         m = max(n.value, 1)
         F = np.empty((m, 3)); nnz = np.empty(m, np.int32); st = np.empty(m, np.uint8)
         self._check(self._lib.bdm_get_forces(self._h, sim, m, _dptr(F), _dptr(nnz), _dptr(st), C.byref(n)))
@@ -239,8 +243,7 @@ class Context:
     def storage_order(self, sim: int) -> np.ndarray:
         n = C.c_int64()
         rc = self._lib.bdm_get_storage_order(self._h, sim, 0, None, C.byref(n))
-        if rc not in (BDM_OK, -4):
-            self._check(rc)
+        self._check_size_query(rc, n)
         out = np.empty(max(n.value, 1), np.int64)
         self._check(self._lib.bdm_get_storage_order(self._h, sim, n.value, _dptr(out), C.byref(n)))
         return out[: n.value]
