@@ -468,3 +468,37 @@ def test_update_agents_keeps_the_simulation(orc):
     with pytest.raises(binding.BdmError) as e:
         a.update_agents(0, bad)
     assert e.value.code == -1
+
+
+def test_update_agents_with_static_detection_and_diameters(orc):
+    """Agents moved by bdm_update_agents count as changed: with static
+    detection on, the trajectory equals the one without it (the oracle's
+    static rules are exact), and new diameters change the grid's box length."""
+    from tests.test_oracle_pins import perturbed_scene
+    xyz, d = perturbed_scene()
+    pop = workloads.Population(xyz, d, workloads.SimParams(dt=0.05, precision=0))
+    on = ctx_for(pop, detect_static=1)
+    off = ctx_for(pop, detect_static=0)
+    for _ in range(6):
+        on.step(1)
+        off.step(1)
+    x, dd = on.get_agents(0)
+    x2 = x.copy()
+    x2[:5] += 0.25                      # disturb a few agents between steps
+    on.update_agents(0, x2)
+    off.update_agents(0, x2)
+    for _ in range(6):
+        on.step(1)
+        off.step(1)
+    a, _ = on.get_agents(0)
+    b, _ = off.get_agents(0)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-10)
+    # larger diameters: the next grid's box length is the new largest one
+    d2 = dd * 1.1
+    on.update_agents(0, a, d2)
+    on.step(1)
+    on.sync()
+    st = on.stats(0)
+    assert st["origin_len"][3] == d2.max()
+    _, gd = on.get_agents(0)
+    assert np.array_equal(gd, d2)
