@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) k_count(DevCtx C, int step) {
 // contributes the box's count), in slot order, giving every box its first
 // cell position; then placement of every agent at start + rank.
 // ---------------------------------------------------------------------------
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 512;
 constexpr int kScanItems = 4;
 constexpr int64_t kScanTile = (int64_t)kScanThreads * kScanItems;
 

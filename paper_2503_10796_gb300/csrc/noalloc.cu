@@ -29,7 +29,7 @@ constexpr size_t oG = oSS + up(sizeof(SimState));
 constexpr size_t oOrder = oG + up(sizeof(Globals));
 constexpr size_t oPart = oOrder + up(sizeof(int32_t));
 constexpr size_t oTstat = oPart + up(2048 * sizeof(uint32_t));
-constexpr size_t kTstatWords = kM / 4096 + 2;
+constexpr size_t kTstatWords = kM / 2048 + 2;  // scan tiles of 2,048 slots
 constexpr size_t oAX = oTstat + up(8 * kTstatWords);
 constexpr size_t oAY = oAX + up(8 * kM);
 constexpr size_t oAZ = oAY + up(8 * kM);
