@@ -299,5 +299,8 @@ __device__ __forceinline__ bool is_static_cell(const DevCtx &C, const SimConst &
 
 // Grid-stride helpers sized for 152 SMs.
 constexpr int kThreads = 256;
+// Block size of the one-agent-per-thread passes of the grid build and the
+// displacement (measured faster than 256 or 512 on this part).
+constexpr int kAgentThreads = 128;
 
 }  // namespace bdm

@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
 }
 
 // S5: displacement.  Static agents keep their position and nnz.
-__global__ void __launch_bounds__(kThreads) k_displace(DevCtx C) {
+__global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
@@ -791,7 +791,7 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, 
 }
 
 void launch_displace(const DevCtx &C, cudaStream_t st) {
-  k_displace<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C);
+  k_displace<<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
 }
 
 }  // namespace bdm

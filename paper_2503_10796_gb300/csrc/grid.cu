@@ -279,7 +279,7 @@ __device__ __forceinline__ void tab_mark_dirty(unsigned long long *e, uint32_t s
 // query keys and leaves the history alone.  Every load that does not depend
 // on another is issued before the first test, so that one thread waits for
 // few round trips in a row.
-__global__ void __launch_bounds__(kThreads) k_count(DevCtx C, int step) {
+__global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool in = slot < C.total_slots;
   const int64_t sl = in ? slot : C.total_slots - 1;
@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
 
 // zero_f32: clear the FP32 force of every placed FP32-path agent (the
 // symmetric force walk adds into it).
-__global__ void __launch_bounds__(kThreads) k_place(DevCtx C, Cells cells, const uint64_t *keys, int fp64_records,
+__global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, const uint64_t *keys, int fp64_records,
                                                    int zero_f32) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= C.total_slots) return;
@@ -587,7 +587,7 @@ void launch_bbox(const DevCtx &C, cudaStream_t st) {
 void launch_params(const DevCtx &C, cudaStream_t st, int step) { k_params<<<1, 256, 0, st>>>(C, step); }
 
 void launch_count(const DevCtx &C, cudaStream_t st, int step) {
-  k_count<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, step);
+  k_count<<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C, step);
 }
 
 int64_t scan_tiles(int64_t total_slots) { return (total_slots + kScanTile - 1) / kScanTile; }
@@ -598,7 +598,7 @@ void launch_scan(const DevCtx &C, cudaStream_t st, int step) {
 }
 
 void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32) {
-  k_place<<<blocks_for(C.total_slots, kThreads), kThreads, 0, st>>>(C, step ? C.c : C.q, step ? C.a.pkey : C.qkey,
+  k_place<<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C, step ? C.c : C.q, step ? C.a.pkey : C.qkey,
                                                                      step ? 0 : 1, step ? zero_f32 : 0);
 }
 
