@@ -55,12 +55,17 @@ def parse():
     ap.add_argument("--workload", default="clustered_8M")
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--static", type=int, default=0)
-    ap.add_argument("--settle", type=int, default=50, help="untimed iterations before warm-up")
+    ap.add_argument("--settle", type=int, default=-1,
+                    help="untimed iterations before warm-up; -1: 65 for the growth workload (its capacity "
+                         "holds from the 65th iteration on), else 50")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--force-variant", type=int, default=-1, help="-1: autotune; else the variant")
     ap.add_argument("--sort-interval", type=int, default=-2, help="-2: autotune/workload default")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.settle < 0:
+        args.settle = 65 if args.workload == "growth_division_65536" else 50
+    return args
 
 
 def make_workload(name: str, precision: int, static: int):
@@ -94,7 +99,7 @@ def make_workload(name: str, precision: int, static: int):
     for p in pops:
         p.params.detect_static = static
     desc.update(precision="fp32-force/fp64-position" if precision == 1 else "fp64", static_skip=bool(static),
-                l2="inputs larger than L2 (no flush needed)" if sum(p.n for p in pops) > 1_000_000 else
+                l2="inputs larger than L2 (no flush needed)" if sum(max(p.n, p.params.capacity) for p in pops) > 1_000_000 else
                 "working set inside L2")
     return pops, desc
 

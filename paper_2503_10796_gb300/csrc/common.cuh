@@ -241,27 +241,54 @@ __device__ __forceinline__ double f2d(float f) {
 }
 
 // floor(fl64(a / L)) for a >= 0, exactly as IEEE FP64 division and floor
-// give it.  (ah, al) split a; (ilh, ill) is 1/L as float-float.  The
-// float-float quotient decides unless it lies within a relative 2^-36 of
-// an integer; only then is the FP64 division evaluated.
-__device__ __forceinline__ int64_t box_coord(double a, float ah, float al, float ilh, float ill,
-                                             double L) {
+// give it, from float-float operands: (ah, al) approximates a and (ilh, ill)
+// is 1/L to 2^-47 relative.  p + e = ah ilh + ah ill + al ilh, with
+// |e| < 5 p 2^-24 (the product's rounding and the two tails, each below
+// 2^-23 of its head).  A fraction of p at least p 2^-20 + 2^-10 away from 0
+// and 1 decides at once; otherwise the fraction corrected by e decides
+// unless it lies within p 2^-36 + 2^-40 of the integer (far above the
+// remaining error, about p 2^-44, and the FP64 rounding of x - o and of the
+// quotient).  False: undecided, the caller divides in FP64.
+__device__ __forceinline__ bool box_coord_ff(float ah, float al, float ilh, float ill, int &out) {
   float p, e;
   two_prod(ah, ilh, p, e);
   e = __fadd_rn(e, __fadd_rn(__fmul_rn(ah, ill), __fmul_rn(al, ilh)));
-  float c = floorf(p);
-  float g = __fsub_rn(p, c);  // exact: fractional bits of p
-  float m = __fmaf_rn(p, 0x1p-36f, 0x1p-40f);
-  if (g >= 0x1p-10f && g <= 1.0f - 0x1p-10f) return (int64_t)c;
-  float t = (g < 0.5f) ? __fadd_rn(g, e) : __fadd_rn(__fsub_rn(g, 1.0f), e);
-  if (g < 0.5f) {
-    if (t >= m) return (int64_t)c;
-    if (t <= -m) return (int64_t)c - 1;
-  } else {
-    if (t <= -m) return (int64_t)c;
-    if (t >= m) return (int64_t)c + 1;
+  const float c = floorf(p);
+  const float g = __fsub_rn(p, c);  // exact: fractional bits of p
+  const int ci = __float2int_rz(c);
+  const float mg = __fmaf_rn(p, 0x1p-20f, 0x1p-10f);
+  if (g >= mg && g <= 1.0f - mg) {
+    out = ci;
+    return true;
   }
-  return (int64_t)floor(__ddiv_rn(a, L));
+  const float m = __fmaf_rn(p, 0x1p-36f, 0x1p-40f);
+  if (g < 0.5f) {
+    const float t = __fadd_rn(g, e);
+    if (t >= m) { out = ci; return true; }
+    if (t <= -m) { out = ci - 1; return true; }
+  } else {
+    const float t = __fadd_rn(__fsub_rn(g, 1.0f), e);
+    if (t <= -m) { out = ci; return true; }
+    if (t >= m) { out = ci + 1; return true; }
+  }
+  return false;
+}
+
+// Box coordinate of centre coordinate x on axis a (§4.4.3:
+// floor((x - o_a) / L) with IEEE FP64 subtraction, division and floor),
+// clamped to the grid.  The FP64 division runs only for undecided
+// quotients.
+__device__ __forceinline__ uint32_t grid_coord(const SimState &s, double x, int a) {
+  const double av = __dsub_rn(x, s.o[a]);
+  float ah, al;
+  split_ff(av, ah, al);
+  int c;
+  int64_t cl;
+  if (box_coord_ff(ah, al, s.ilh, s.ill, c))
+    cl = c;
+  else
+    cl = (int64_t)floor(__ddiv_rn(av, s.L));
+  return (uint32_t)(cl < 0 ? 0 : (cl >= s.dims[a] ? s.dims[a] - 1 : cl));
 }
 
 // Warp-aggregated atomic add of a per-lane count into *dst.

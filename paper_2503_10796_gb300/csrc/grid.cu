@@ -300,13 +300,7 @@ __global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
     c[1] = (uint32_t)((pk_prev_in >> kCoordBits) & kCoordMask);
     c[2] = (uint32_t)((pk_prev_in >> (2 * kCoordBits)) & kCoordMask);
   } else {
-    for (int a = 0; a < 3; ++a) {
-      double av = __dsub_rn(p[a], s.o[a]);
-      float ah, al;
-      split_ff(av, ah, al);
-      int64_t ca = box_coord(av, ah, al, s.ilh, s.ill, s.L);
-      c[a] = (uint32_t)(ca < 0 ? 0 : (ca >= s.dims[a] ? s.dims[a] - 1 : ca));
-    }
+    for (int a = 0; a < 3; ++a) c[a] = grid_coord(s, p[a], a);
   }
   const uint64_t pk = (uint64_t)c[0] | ((uint64_t)c[1] << kCoordBits) | ((uint64_t)c[2] << (2 * kCoordBits));
   const int64_t idx =

@@ -21,13 +21,7 @@ __global__ void k_boxids(DevCtx C, int sim, int64_t *out) {
   }
   double p[3] = {C.a.x[slot], C.a.y[slot], C.a.z[slot]};
   int64_t c[3];
-  for (int a = 0; a < 3; ++a) {
-    double av = __dsub_rn(p[a], s.o[a]);
-    float ah, al;
-    split_ff(av, ah, al);
-    int64_t ca = box_coord(av, ah, al, s.ilh, s.ill, s.L);
-    c[a] = ca < 0 ? 0 : (ca >= s.dims[a] ? s.dims[a] - 1 : ca);
-  }
+  for (int a = 0; a < 3; ++a) c[a] = grid_coord(s, p[a], a);  // as the step's count
   out[id] = linear_box(s, c[0], c[1], c[2]);
 }
 

@@ -67,6 +67,67 @@ def test_grid_boundary_cases(orc):
     assert np.array_equal(box, obox) and np.array_equal(dims, odims)
 
 
+def boundary_values(rng, origin, L, span, n_edges):
+    """Coordinates on box boundaries origin + k L, one to three ulps either
+    side of them, and uniform ones, none below the origin."""
+    k = np.sort(rng.choice(span, min(span, n_edges), replace=False)).astype(np.float64)
+    edge = origin + k * L
+    pts = [edge]
+    for u in (1, 2, 3):
+        lo = edge.copy()
+        hi = edge.copy()
+        for _ in range(u):
+            lo = np.nextafter(lo, -np.inf)
+            hi = np.nextafter(hi, np.inf)
+        pts += [lo, hi]
+    v = np.concatenate(pts + [origin + rng.uniform(0, span * L, 3 * n_edges)])
+    v = np.clip(v, origin, None)
+    v[0] = origin  # the grid origin is the smallest coordinate
+    return v
+
+
+def boundary_population(origin, L, span, const_x=None):
+    """Boundary coordinates along a wide axis (x, or y when x is held at
+    const_x) and along narrow ones (20 boxes), so that the dense box table
+    stays small."""
+    rng = np.random.default_rng(1)
+    wide = boundary_values(rng, origin, L, span, 600)
+    m = wide.size
+    narrow = [rng.choice(boundary_values(rng, origin, L, 20, 20), m) for _ in range(2)]
+    for v in narrow:
+        v[0] = origin
+    if const_x is None:
+        xyz = np.stack([wide, narrow[0], narrow[1]], axis=1)
+    else:
+        xyz = np.stack([np.full(m, const_x), wide, narrow[0]], axis=1)
+    # a clamp of one box length keeps the table's allowance for movement small
+    return workloads.Population(xyz, np.full(m, 0.5 * L), workloads.SimParams(box_length=L, max_displacement=L))
+
+
+@pytest.mark.parametrize("origin,L,span,const_x", [(-123456.789, 10.3, 3000, None), (9.87654321e8, 0.7, 5000, None),
+                                                   (-2.5e-3, 1e-3, 40000, None), (0.0, 10.0, 3000, 1e28)])
+def test_grid_boundaries_far_from_zero(orc, origin, L, span, const_x):
+    """Box indices on and next to box boundaries with the origin far from
+    zero and grids thousands of boxes wide; with x at 1e28 (box length 10)
+    the coordinates are too large for the integer grid frame and the FP64
+    route computes every index."""
+    pop = boundary_population(origin, L, span, const_x)
+    ctx = ctx_for(pop)
+    box, ol, dims = ctx.grid(0)
+    obox, ool, odims = orc_for(pop).grid()
+    assert np.array_equal(ol, ool) and np.array_equal(dims, odims)
+    assert np.array_equal(box, obox)
+
+
+@pytest.mark.parametrize("shift", [1.0e6, -3.0e7])
+def test_forces_far_from_zero(orc, shift):
+    """Clusters a million and thirty million length units from zero: the
+    box-relative FP32 records keep the force within the FP32 tolerance."""
+    base = small_pops()[2]
+    pop = workloads.Population(base.xyz + shift, base.diameter, workloads.SimParams(precision=1))
+    check_forces(pop, 1)
+
+
 @pytest.mark.parametrize("k", range(3))
 @pytest.mark.parametrize("radius", [-1.0, 6.0, 25.0])
 def test_neighbor_pairs_bit_exact(orc, k, radius):
@@ -134,6 +195,54 @@ def test_multi_step_trajectory(orc, precision):
         assert err <= 1e-9 * L, err
     else:
         assert err <= 1e-4 * L, err
+
+
+def test_fp32_error_growth_is_bounded(orc):
+    """FP32-force path over 40 iterations of the plain workload: the position
+    error against the oracle at every fifth iteration, reported, and bounded
+    well below a box length (agents whose force sits at the adherence
+    threshold may take the other branch, a jump of up to dt * |F|)."""
+    pop = workloads.plain_fp64()
+    ctx = ctx_for(pop, precision=1)
+    o = orc_for(pop)
+    L = pop.diameter.max()
+    errs = []
+    for t in range(8):
+        ctx.step(5)
+        o.step(5)
+        x_g, _ = ctx.get_agents(0)
+        x_o, _, _ = o.get()
+        e = np.abs(x_g - x_o).max(axis=1)
+        errs.append((5 * (t + 1), e.max() / L, np.quantile(e, 0.999) / L))
+    print("GROWTH " + " ".join(f"t={t}: max {a:.2e} p99.9 {b:.2e}" for t, a, b in errs))
+    assert errs[1][1] <= 1e-4
+    assert all(a <= 1e-2 for _, a, _ in errs)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cluster_statistics_match_oracle(orc, precision):
+    """20 iterations of five dense clusters with static detection on: per
+    cluster the radius of gyration, and over all agents the mean contact
+    count and the static fraction, within 1% of the oracle's."""
+    base = small_pops()[2]
+    p = workloads.SimParams(precision=precision, detect_static=1)
+    pop = workloads.Population(base.xyz, base.diameter, p, "clusters_static")
+    ctx = ctx_for(pop)
+    o = orc_for(pop)
+    ctx.step(20)
+    o.step(20)
+    x_g, _ = ctx.get_agents(0)
+    x_o, _, _ = o.get()
+    _, nnz_g, st_g = ctx.forces(0)
+    _, _, nnz_o, st_o, _ = o.last()
+    for c in range(5):
+        sl = slice(700 * c, 700 * (c + 1))
+        rg = [np.sqrt(((x[sl] - x[sl].mean(axis=0)) ** 2).sum(axis=1).mean()) for x in (x_g, x_o)]
+        assert abs(rg[0] - rg[1]) <= 0.01 * rg[1], (c, rg)
+    assert abs(nnz_g.mean() - nnz_o.mean()) <= 0.01 * nnz_o.mean()
+    assert abs(st_g.mean() - st_o.astype(bool).mean()) <= 0.01
+    print(f"CLUSTERS precision {precision}: contacts {nnz_g.mean():.4f} / {nnz_o.mean():.4f}, "
+          f"static {st_g.mean():.4f} / {st_o.astype(bool).mean():.4f}")
 
 
 def test_two_sphere_closed_form_on_gpu(orc):
