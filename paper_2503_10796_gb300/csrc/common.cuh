@@ -64,6 +64,7 @@ struct SimState {
   double prev_o[3], prev_L;
   int64_t prev_dims[3];
   int64_t cell_base;
+  unsigned long long cell_cursor;  // next unclaimed cell of the build (unordered scan)
   int64_t ncell;              // agents placed in the cells of the last build
   int64_t t;                  // iterations completed
   int64_t it;                 // index of the iteration being computed

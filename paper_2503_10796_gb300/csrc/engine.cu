@@ -240,7 +240,9 @@ void launch_iteration(bdm_ctx *c, int sort) {
     stage_end(c);
   }
   stage_begin(c, 2);
-  launch_scan(D, st);
+  // the cell order reaches the storage only when this iteration re-sorts
+  // into it: only then must it follow the leaders' storage order
+  launch_scan(D, st, 1, (c->any_sort && sort == 2) ? 1 : 0);
   stage_end(c);
   // the symmetric walk (variant 0) needs every FP32-path simulation to run
   // without static detection; otherwise the deferred walk (1) stands in

@@ -235,6 +235,7 @@ __global__ void k_params(DevCtx C, int32_t step) {
       const int s = C.order[k];
       if (s < 0) break;
       C.ss[s].cell_base = cells;
+      C.ss[s].cell_cursor = (unsigned long long)cells;
       cells += C.ss[s].n;
     }
     g->n_cells = cells;
@@ -388,11 +389,19 @@ __device__ __forceinline__ uint32_t block_exscan_u32(uint32_t v, uint32_t *sh, u
   return r;
 }
 
-// One pass with decoupled look-back.  A block claims the next tile through
-// a ticket (so every earlier tile belongs to a block that is already
-// running), sums its leaders' counts, publishes that sum, and walks back
-// over the earlier tiles' published values until it meets an inclusive
-// prefix; it then publishes its own inclusive prefix.  Each thread takes
+// Box starts: every box's leader (the agent of rank 0) receives the first
+// cell of its box.  kOrdered: one pass with decoupled look-back, so that the
+// boxes' ranges follow the storage order of their leaders.  A block claims
+// the next tile through a ticket (so every earlier tile belongs to a block
+// that is already running), sums its leaders' counts, publishes that sum,
+// and walks back over the earlier tiles' published values until it meets an
+// inclusive prefix; it then publishes its own inclusive prefix.  Otherwise a
+// block claims its leaders' cells with one atomic add on its simulation's
+// cell cursor (or, in a block that holds leaders of several simulations,
+// one per leader): no block waits for another, and the tiles' ranges follow
+// the order in which the blocks finish.  The iterations that re-sort the
+// storage into cell order take the ordered scan, so that arrival order
+// never reaches the storage.  Each thread takes
 // kScanItems slots of the tile (strided, so that loads coalesce) and issues
 // all their loads before any is used.  Every wait is bounded: a tile that
 // never publishes latches ERR_TIMEOUT.  Tile words carry the build's stamp,
@@ -404,10 +413,17 @@ __device__ __forceinline__ void tile_publish(unsigned long long *w, uint32_t sta
       ((unsigned long long)stamp << 34) | ((unsigned long long)state << 32) | (unsigned long long)v;
 }
 
+template <bool kOrdered>
 __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t *keys) {
   __shared__ uint32_t sh[33];
   __shared__ uint32_t s_tile, s_base;
-  if (threadIdx.x == 0) s_tile = atomicAdd(&C.g->tile_ticket, 1u);
+  __shared__ int s_lo, s_hi;
+  if (threadIdx.x == 0) {
+    s_tile = kOrdered ? atomicAdd(&C.g->tile_ticket, 1u) : blockIdx.x;
+    s_base = 0u;
+    s_lo = 0x7fffffff;
+    s_hi = -1;
+  }
   __syncthreads();
   const uint32_t tile = s_tile;
   // each thread takes kScanItems consecutive slots (vector loads)
@@ -460,7 +476,26 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
   uint32_t agg;
   const uint32_t ex = block_exscan_u32(sum, sh, &agg);
   const uint32_t stamp = C.g->stamp & kStampMask;
-  if (threadIdx.x < 32) {
+  bool one = true;  // unordered: the block's leaders belong to one simulation
+  if (!kOrdered) {
+    int smin = 0x7fffffff, smax = -1;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+      if (idx[i] >= 0) {
+        smin = sim[i] < smin ? sim[i] : smin;
+        smax = sim[i] > smax ? sim[i] : smax;
+      }
+    smin = __reduce_min_sync(0xffffffffu, smin);
+    smax = __reduce_max_sync(0xffffffffu, smax);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&s_lo, smin);
+      atomicMax(&s_hi, smax);
+    }
+    __syncthreads();
+    one = s_lo == s_hi;
+    if (one && threadIdx.x == 0 && agg)
+      s_base = (uint32_t)atomicAdd(&C.ss[s_lo].cell_cursor, (unsigned long long)agg);
+  } else if (threadIdx.x < 32) {
     // warp 0 looks back 32 tiles at a time: the nearest inclusive prefix
     // ends the walk, the aggregates before it are added
     const int lane = threadIdx.x;
@@ -510,8 +545,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
       unsigned long long *w = &C.tab.e[idx[i]];
       if (bad)
         *w = (unsigned long long)stamp << 43;
-      else
+      else if (one)
         *reinterpret_cast<uint32_t *>(w) = off + loc[i];
+      else
+        *reinterpret_cast<uint32_t *>(w) =
+            (uint32_t)atomicAdd(&C.ss[sim[i]].cell_cursor, (unsigned long long)ent_count(e[i]));
     }
   }
 }
@@ -586,9 +624,12 @@ void launch_count(const DevCtx &C, cudaStream_t st, int step) {
 
 int64_t scan_tiles(int64_t total_slots) { return (total_slots + kScanTile - 1) / kScanTile; }
 
-void launch_scan(const DevCtx &C, cudaStream_t st, int step) {
+void launch_scan(const DevCtx &C, cudaStream_t st, int step, int ordered) {
   const int64_t G = scan_tiles(C.total_slots);
-  k_scan<<<(unsigned int)G, kScanThreads, 0, st>>>(C, step ? C.a.pkey : C.qkey);
+  if (ordered)
+    k_scan<true><<<(unsigned int)G, kScanThreads, 0, st>>>(C, step ? C.a.pkey : C.qkey);
+  else
+    k_scan<false><<<(unsigned int)G, kScanThreads, 0, st>>>(C, step ? C.a.pkey : C.qkey);
 }
 
 void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32) {

@@ -12,7 +12,9 @@ void launch_count(const DevCtx &C, cudaStream_t st, int step);
 // The scan needs tstat in the context: scan_tiles(total_slots) words,
 // cleared whenever the build stamp restarts.
 int64_t scan_tiles(int64_t total_slots);
-void launch_scan(const DevCtx &C, cudaStream_t st, int step = 1);
+// ordered: box ranges in the storage order of the leaders (decoupled
+// look-back); otherwise in the order the scan's blocks finish
+void launch_scan(const DevCtx &C, cudaStream_t st, int step = 1, int ordered = 1);
 void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32 = 0);
 
 // force.cu
