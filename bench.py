@@ -42,7 +42,7 @@ ALG_BYTES_BOX = 8.0
 # profiles/k_force32s_clustered_1M.md; scaled by the agents of a launch for
 # the clustered workloads (same per-cluster shape), null elsewhere or when
 # another kernel runs.
-FORCE_TRAFFIC_B_PER_AGENT = {"k_force32s": 109.5}
+FORCE_TRAFFIC_B_PER_AGENT = {"k_force32s": 112.6}
 FORCE_KERNEL = {0: "k_force32s", 1: "k_force32d", 2: "k_force", 3: "k_force32d", 4: "k_force32s (direct)"}
 
 
