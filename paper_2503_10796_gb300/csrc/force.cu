@@ -484,18 +484,51 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
 }
 
+// Pair force of the FP64 path, the definition operation by operation (Eq.
+// 4.1/4.2 and the unit vector from j to i): false when the pair does not
+// overlap.  nz: the scalar force is not zero.
+__device__ __forceinline__ bool pair64(const double4_32a &o, const double4_32a &q, double k, double gam, double &gx,
+                                       double &gy, double &gz, bool &nz) {
+  const double ddx = __dsub_rn(o.x, q.x), ddy = __dsub_rn(o.y, q.y), ddz = __dsub_rn(o.z, q.z);
+  const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+  const double R = __dadd_rn(o.w, q.w);
+  const double dist = __dsqrt_rn(s2);
+  const double del = __dsub_rn(R, dist);
+  gx = gy = gz = 0.0;
+  nz = false;
+  if (!(del > 0.0)) return false;
+  const double rr = __ddiv_rn(__dmul_rn(o.w, q.w), R);
+  const double rep = __dmul_rn(k, del);
+  const double adh = __dmul_rn(gam, __dsqrt_rn(__dmul_rn(rr, del)));
+  const double fn = __dsub_rn(rep, adh);
+  nz = fn != 0.0;
+  if (dist > 0.0) {
+    gx = __dmul_rn(fn, __ddiv_rn(ddx, dist));
+    gy = __dmul_rn(fn, __ddiv_rn(ddy, dist));
+    gz = __dmul_rn(fn, __ddiv_rn(ddz, dist));
+  }
+  return true;
+}
+
 // FP64 path with a thread per stencil row: 9 threads per agent, 32 agents
-// per block.  Each thread sums its row's pairs (the definition operation by
-// operation, as force64); the agent's first thread adds the nine row sums
-// in row order.  Nine times the threads of force64 hide the latency of the
-// FP64 divisions and square roots, which run at a small fraction of the
-// FP32 rate on this part.
+// per block.  A thread walks its row with the cheap filter only and queues
+// the candidates that pass (in walk order); the warp then evaluates the
+// queued pairs together, one per lane and round, and every thread adds its
+// own pairs' forces in queue order, so that each row sums its pairs in the
+// walk's order.  The FP64 square roots and divisions of a pair run at a
+// small fraction of the FP32 rate on this part; evaluated in the walk they
+// ran once for every candidate step in which any lane of the warp had a
+// partner.  A row with more than kRowCap queued candidates is evaluated
+// again in place.  The agent's first thread adds the nine row sums in row
+// order.
 constexpr int kRowAgents = 32;
 constexpr int kRowThreads = kRowAgents * 9;
+constexpr int kRowCap = 4;
 
 __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
   __shared__ double part[kRowThreads][3];
   __shared__ uint32_t pnz[kRowThreads];
+  __shared__ uint32_t rq[kRowCap][kRowThreads];
   __shared__ uint8_t skip[kRowAgents];
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   const int a = threadIdx.x / 9, r = threadIdx.x % 9;
@@ -518,14 +551,16 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
   }
   __syncthreads();
   double fx = 0.0, fy = 0.0, fz = 0.0;
-  uint32_t nnz = 0;
+  uint32_t nnz = 0, n = 0;
   const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
   const int dz = r / 3 - 1, dy = r % 3 - 1;
-  if (!skip[a] && dz >= t.zlo && dz <= t.zhi && dy >= t.ylo && dy <= t.yhi) {
-    const double4_32a o = C.c.r64[p];
-    const double k = sc.k, gam = sc.gamma;
-    const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
-                         (uint32_t)t.cx;
+  const bool walk = !skip[a] && dz >= t.zlo && dz <= t.zhi && dy >= t.ylo && dy <= t.yhi;
+  const uint32_t row = walk ? ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
+                                  (uint32_t)t.cx
+                            : 0u;
+  double4_32a o = {};
+  if (walk) {
+    o = C.c.r64[p];
     for (int dx = t.xlo; dx <= t.xhi; ++dx) {
       const unsigned long long e = t.e[row + dx];
       const uint32_t cnt = ent_live(e, stamp);
@@ -538,18 +573,73 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
         const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
         const double R = __dadd_rn(o.w, q.w);
         if (!(s2 < __dmul_rn(R, R) * 1.0000001)) continue;  // cheap reject far beyond contact
-        const double dist = __dsqrt_rn(s2);
-        const double del = __dsub_rn(R, dist);
-        if (!(del > 0.0)) continue;
-        const double rr = __ddiv_rn(__dmul_rn(o.w, q.w), R);
-        const double rep = __dmul_rn(k, del);
-        const double adh = __dmul_rn(gam, __dsqrt_rn(__dmul_rn(rr, del)));
-        const double fn = __dsub_rn(rep, adh);
-        nnz += (fn != 0.0);
-        if (dist > 0.0) {
-          fx = __dadd_rn(fx, __dmul_rn(fn, __ddiv_rn(ddx, dist)));
-          fy = __dadd_rn(fy, __dmul_rn(fn, __ddiv_rn(ddy, dist)));
-          fz = __dadd_rn(fz, __dmul_rn(fn, __ddiv_rn(ddz, dist)));
+        if (n < (uint32_t)kRowCap) rq[n][threadIdx.x] = (uint32_t)j;
+        ++n;
+      }
+    }
+  }
+  uint32_t mine = n;
+  if (n > (uint32_t)kRowCap) {
+    // crowded row: evaluate it in place, in walk order
+    mine = 0;
+    const double k = sc.k, gam = sc.gamma;
+    for (int dx = t.xlo; dx <= t.xhi; ++dx) {
+      const unsigned long long e = t.e[row + dx];
+      const uint32_t cnt = ent_live(e, stamp);
+      const int64_t j0 = ent_start(e);
+      for (uint32_t m = 0; m < cnt; ++m) {
+        const int64_t j = j0 + m;
+        if (j == p) continue;
+        double gx, gy, gz;
+        bool nz;
+        if (pair64(o, C.c.r64[j], k, gam, gx, gy, gz, nz)) {
+          fx = __dadd_rn(fx, gx); fy = __dadd_rn(fy, gy); fz = __dadd_rn(fz, gz);
+          nnz += nz ? 1u : 0u;
+        }
+      }
+    }
+  }
+  // warp-wide evaluation of the queues laid end to end
+  {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+    uint32_t incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const uint32_t excl = incl - mine;
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    for (uint32_t base = 0; base < total; base += 32) {
+      const uint32_t kk = base + (uint32_t)lane;
+      int ow = 0;  // owner: the first lane whose inclusive prefix exceeds kk
+#pragma unroll
+      for (int step = 16; step; step >>= 1) {
+        const uint32_t v = __shfl_sync(FULL, incl, ow + step - 1);
+        if (v <= kk) ow += step;
+      }
+      const uint32_t ex = __shfl_sync(FULL, excl, ow);
+      double gx = 0.0, gy = 0.0, gz = 0.0;
+      bool nz = false, hit = false;
+      if (kk < total) {
+        const int to = wbase + ow;  // the owner's thread in the block
+        const int64_t po = (int64_t)blockIdx.x * kRowAgents + to / 9;
+        const SimConst &so = C.sc[C.c.sim[po]];
+        hit = pair64(C.c.r64[po], C.c.r64[rq[kk - ex][to]], so.k, so.gamma, gx, gy, gz, nz);
+      }
+      // every owner adds its pairs of this round (consecutive lanes) in order
+      const int first = (int)(excl > base ? excl - base : 0u);
+      const int last = (int)((incl > base ? incl - base : 0u) < 32u ? (incl > base ? incl - base : 0u) : 32u);
+      for (int l = 0; l < kRowCap; ++l) {
+        const int src = first + l;
+        const double ax = __shfl_sync(FULL, gx, src & 31), ay = __shfl_sync(FULL, gy, src & 31),
+                     az = __shfl_sync(FULL, gz, src & 31);
+        const bool ah = __shfl_sync(FULL, hit ? 1 : 0, src & 31) != 0;
+        const bool an = __shfl_sync(FULL, nz ? 1 : 0, src & 31) != 0;
+        if (src < last && ah) {
+          fx = __dadd_rn(fx, ax); fy = __dadd_rn(fy, ay); fz = __dadd_rn(fz, az);
+          nnz += an ? 1u : 0u;
         }
       }
     }
