@@ -499,8 +499,11 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   ALLOC(D.a.flags, M, "flags"); ALLOC(D.a.nnz, M, "nnz");
   ALLOC(D.c.slot, M, "cell slots"); ALLOC(D.c.sim, M, "cell sims"); ALLOC(D.c.pkey, M, "cell keys");
   ALLOC(D.c.flag, M, "cell flags"); ALLOC(D.c.nnz, M, "cell nnz"); ALLOC(D.c.stat, M, "cell static");
+  // the leading float parts of the box-relative records are the candidate
+  // filter of both force paths
+  ALLOC(D.c.r0, M, "FP32 records hi");
   if (c->any_fp32) {
-    ALLOC(D.c.r0, M, "FP32 records hi"); ALLOC(D.c.r1, M, "FP32 records lo"); ALLOC(D.c.f32, M, "FP32 forces");
+    ALLOC(D.c.r1, M, "FP32 records lo"); ALLOC(D.c.f32, M, "FP32 forces");
   }
   if (c->any_fp64) {
     ALLOC(D.c.r64, M, "FP64 records"); ALLOC(D.c.f64, M, "FP64 forces");

@@ -511,8 +511,10 @@ __device__ __forceinline__ bool pair64(const double4_32a &o, const double4_32a &
 }
 
 // FP64 path with a thread per stencil row: 9 threads per agent, 32 agents
-// per block.  A thread walks its row with the cheap filter only and queues
-// the candidates that pass (in walk order); the warp then evaluates the
+// per block.  A thread walks its row with the FP32 filter of the FP32 path
+// (box-relative leading parts, a margin above their error, so that every
+// pair that overlaps in FP64 passes) and queues the candidates that pass
+// (in walk order); the warp then evaluates the
 // queued pairs together, one per lane and round, and every thread adds its
 // own pairs' forces in queue order, so that each row sums its pairs in the
 // walk's order.  The FP64 square roots and divisions of a pair run at a
@@ -561,18 +563,22 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
   double4_32a o = {};
   if (walk) {
     o = C.c.r64[p];
+    const float4 o0 = C.c.r0[p];
+    const float Lh = s.Lh, marg = s.marg;
+    const float sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh)), sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
     for (int dx = t.xlo; dx <= t.xhi; ++dx) {
       const unsigned long long e = t.e[row + dx];
       const uint32_t cnt = ent_live(e, stamp);
       const int64_t j0 = ent_start(e);
+      const float sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
       for (uint32_t m = 0; m < cnt; ++m) {
         const int64_t j = j0 + m;
         if (j == p) continue;
-        const double4_32a q = C.c.r64[j];
-        const double ddx = __dsub_rn(o.x, q.x), ddy = __dsub_rn(o.y, q.y), ddz = __dsub_rn(o.z, q.z);
-        const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-        const double R = __dadd_rn(o.w, q.w);
-        if (!(s2 < __dmul_rn(R, R) * 1.0000001)) continue;  // cheap reject far beyond contact
+        const float4 q = C.c.r0[j];
+        const float ddx = __fsub_rn(sx, q.x), ddy = __fsub_rn(sy, q.y), ddz = __fsub_rn(sz, q.z);
+        const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+        const float Rm = __fadd_rn(__fadd_rn(o0.w, q.w), marg);
+        if (!(s2 < __fmul_rn(Rm, Rm))) continue;
         if (n < (uint32_t)kRowCap) rq[n][threadIdx.x] = (uint32_t)j;
         ++n;
       }

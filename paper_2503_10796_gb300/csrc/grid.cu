@@ -583,9 +583,12 @@ __global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, 
   cells.pkey[p] = pk;
   if (cells.flag) cells.flag[p] = (!(fl & FLAG_CHANGED) && nz <= 1) ? CELL_STATIC_ELIGIBLE : 0;
   const double r = half_of(dia);
-  if (fp64_records || sc.precision == BDM_PREC_FP64) {
-    cells.r64[p] = make_double4_32a(pos[0], pos[1], pos[2], r);
-  } else {
+  const bool fp64 = sc.precision == BDM_PREC_FP64;
+  if (fp64_records || fp64) cells.r64[p] = make_double4_32a(pos[0], pos[1], pos[2], r);
+  if (!fp64_records) {
+    // the step's build: box-relative float-float records, whose leading
+    // parts are the candidate filter of both paths (the FP64 path needs no
+    // tails)
     float h[3], l[3], rh, rl;
     for (int a = 0; a < 3; ++a) {
       // offset inside the own box, exact in FP64: (x - o) - c L
@@ -595,8 +598,10 @@ __global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, 
     }
     split_ff(r, rh, rl);
     cells.r0[p] = make_float4(h[0], h[1], h[2], rh);
-    cells.r1[p] = make_float4(l[0], l[1], l[2], rl);
-    if (zero_f32) cells.f32[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!fp64) {
+      cells.r1[p] = make_float4(l[0], l[1], l[2], rl);
+      if (zero_f32) cells.f32[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
 }
 
