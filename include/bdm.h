@@ -13,7 +13,8 @@
  *   S1  box index per agent: c_a = floor((x_a - o_a) / L) in IEEE FP64,
  *       index c_x + n_x (c_y + n_y c_z) (§5.3.1, Fig 5.4B).
  *   S2  grid build with per-box timestamps, so that empty boxes are never
- *       cleared (§5.3.1): count, prefix sum over box leaders, placement.
+ *       cleared (§5.3.1): count, a contiguous cell range per box (prefix
+ *       sum over the box leaders, or ranges claimed by atomics), placement.
  *   S3  Morton re-sort of the agent storage every `sort_interval`
  *       iterations (§5.4.2, Fig 5.4); results never depend on it.
  *   S4  pairwise force over the 27-box stencil, Eq 4.1 / Eq 4.2 (§4.5.1):

@@ -339,9 +339,10 @@ __global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
 }
 
 // ---------------------------------------------------------------------------
-// S2: exclusive prefix sum over box leaders (the rank-0 agent of each box
-// contributes the box's count), in slot order, giving every box its first
-// cell position; then placement of every agent at start + rank.
+// S2: every box gets a contiguous range of cells, claimed by its leader
+// (the rank-0 agent, which contributes the box's count): an exclusive
+// prefix sum over the leaders in slot order, or ranges claimed by atomics
+// (see k_scan); then placement of every agent at start + rank.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 4;
