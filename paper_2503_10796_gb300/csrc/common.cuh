@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "bdm.h"
+#include "ffmath.cuh"
 
 namespace bdm {
 
@@ -168,111 +169,6 @@ __device__ __forceinline__ void unpack_coords(uint64_t p, int64_t &cx, int64_t &
 
 __device__ __forceinline__ int64_t linear_box(const SimState &s, int64_t cx, int64_t cy, int64_t cz) {
   return cx + s.dims[0] * (cy + s.dims[1] * cz);
-}
-
-// Error-free transformations in FP32 (Knuth two-sum, fma two-product).
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
-__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
-  p = __fmul_rn(a, b);
-  e = __fmaf_rn(a, b, -p);
-}
-
-// 2^k as a float for -126 <= k <= 127.
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
-
-// Split a finite double into hi + lo floats (hi: leading 24 significant bits,
-// truncated; lo: the remaining 29 bits rounded to 24).  Integer operations
-// only, except for zero, tiny or huge magnitudes.
-__device__ __forceinline__ void split_ff(double a, float &hi, float &lo) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(a);
-  int e = (int)((b >> 52) & 0x7FF);
-  unsigned int sign = (unsigned int)(b >> 63) << 31;
-  if (e >= 1023 - 126 + 52 && e <= 1023 + 127) {
-    unsigned int hb = sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)((b >> 29) & 0x7FFFFF);
-    hi = __uint_as_float(hb);
-    float l = __fmul_rn(__uint2float_rn((unsigned int)(b & 0x1FFFFFFF)), pow2f(e - 1075));
-    lo = sign ? -l : l;
-  } else if (a == 0.0) {
-    hi = 0.0f;
-    lo = 0.0f;
-  } else {
-    hi = __double2float_rn(a);
-    lo = __double2float_rn(__dsub_rn(a, (double)hi));
-  }
-}
-
-// -c as a double for 0 <= c < 2^32, built from its bits (the FP64 pipe of
-// this part is 1/64 of the FP32 rate; conversions would use it).
-__device__ __forceinline__ double neg_u32_to_double(uint32_t c) {
-  if (c == 0u) return -0.0;
-  const int e = 31 - __clz(c);
-  const unsigned long long m = ((unsigned long long)c << (52 - e)) & 0xFFFFFFFFFFFFFull;
-  return __longlong_as_double((long long)(0x8000000000000000ull | ((unsigned long long)(1023 + e) << 52) | m));
-}
-
-// d / 2, exact: the exponent field decremented for normal values whose half
-// is normal, an FP64 multiply otherwise.
-__device__ __forceinline__ double half_of(double d) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-  const unsigned e = (unsigned)((b >> 52) & 0x7FF);
-  if (e > 1u && e < 0x7FFu) return __longlong_as_double((long long)(b - (1ull << 52)));
-  return __dmul_rn(0.5, d);
-}
-
-// Exact float -> double conversion with integer operations for normal
-// values.
-__device__ __forceinline__ double f2d(float f) {
-  unsigned int u = __float_as_uint(f);
-  unsigned int e = (u >> 23) & 0xFF;
-  if (e == 0 || e == 0xFF) return (double)f;
-  unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
-                         ((unsigned long long)(e + (1023 - 127)) << 52) |
-                         ((unsigned long long)(u & 0x7FFFFF) << 29);
-  return __longlong_as_double((long long)b);
-}
-
-// floor(fl64(a / L)) for a >= 0, exactly as IEEE FP64 division and floor
-// give it, from float-float operands: (ah, al) approximates a and (ilh, ill)
-// is 1/L to 2^-47 relative.  p + e = ah ilh + ah ill + al ilh, with
-// |e| < 5 p 2^-24 (the product's rounding and the two tails, each below
-// 2^-23 of its head).  A fraction of p at least p 2^-20 + 2^-10 away from 0
-// and 1 decides at once; otherwise the fraction corrected by e decides
-// unless it lies within p 2^-36 + 2^-40 of the integer (far above the
-// remaining error, about p 2^-44, and the FP64 rounding of x - o and of the
-// quotient).  False: undecided, the caller divides in FP64.
-__device__ __forceinline__ bool box_coord_ff(float ah, float al, float ilh, float ill, int &out) {
-  float p, e;
-  two_prod(ah, ilh, p, e);
-  e = __fadd_rn(e, __fadd_rn(__fmul_rn(ah, ill), __fmul_rn(al, ilh)));
-  const float c = floorf(p);
-  const float g = __fsub_rn(p, c);  // exact: fractional bits of p
-  const int ci = __float2int_rz(c);
-  const float mg = __fmaf_rn(p, 0x1p-20f, 0x1p-10f);
-  if (g >= mg && g <= 1.0f - mg) {
-    out = ci;
-    return true;
-  }
-  const float m = __fmaf_rn(p, 0x1p-36f, 0x1p-40f);
-  if (g < 0.5f) {
-    const float t = __fadd_rn(g, e);
-    if (t >= m) { out = ci; return true; }
-    if (t <= -m) { out = ci - 1; return true; }
-  } else {
-    const float t = __fadd_rn(__fsub_rn(g, 1.0f), e);
-    if (t <= -m) { out = ci; return true; }
-    if (t >= m) { out = ci + 1; return true; }
-  }
-  return false;
 }
 
 // Box coordinate of centre coordinate x on axis a (§4.4.3:
