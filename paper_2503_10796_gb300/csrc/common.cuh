@@ -157,10 +157,6 @@ __device__ __forceinline__ double ord_val(unsigned long long k) {
   return __longlong_as_double((long long)b);
 }
 
-__device__ __forceinline__ uint64_t pack_coords(int64_t cx, int64_t cy, int64_t cz) {
-  return (uint64_t)cx | ((uint64_t)cy << kCoordBits) | ((uint64_t)cz << (2 * kCoordBits));
-}
-
 __device__ __forceinline__ void unpack_coords(uint64_t p, int64_t &cx, int64_t &cy, int64_t &cz) {
   cx = (int64_t)(p & kCoordMask);
   cy = (int64_t)((p >> kCoordBits) & kCoordMask);
@@ -186,14 +182,6 @@ __device__ __forceinline__ uint32_t grid_coord(const SimState &s, double x, int 
   else
     cl = (int64_t)floor(__ddiv_rn(av, s.L));
   return (uint32_t)(cl < 0 ? 0 : (cl >= s.dims[a] ? s.dims[a] - 1 : cl));
-}
-
-// Warp-aggregated atomic add of a per-lane count into *dst.
-__device__ __forceinline__ void warp_add(unsigned long long *dst, unsigned int v) {
-  unsigned int mask = __activemask();
-  unsigned int s = __reduce_add_sync(mask, v);
-  int leader = __ffs(mask) - 1;
-  if ((int)(threadIdx.x & 31) == leader && s) atomicAdd(dst, (unsigned long long)s);
 }
 
 __device__ __forceinline__ void set_err(Globals *g, uint32_t bits) { atomicOr(&g->err, bits); }

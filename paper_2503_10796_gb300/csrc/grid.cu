@@ -348,20 +348,6 @@ constexpr int kScanThreads = 512;
 constexpr int kScanItems = 4;
 constexpr int64_t kScanTile = (int64_t)kScanThreads * kScanItems;
 
-__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *sh) {
-  v = __reduce_add_sync(0xffffffffu, v);
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  uint32_t t = 0;
-  if (warp == 0) {
-    t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
-    t = __reduce_add_sync(0xffffffffu, t);
-  }
-  __syncthreads();
-  return t;  // valid in warp 0
-}
-
 // Exclusive scan inside the block; *total receives the block total.
 __device__ __forceinline__ uint32_t block_exscan_u32(uint32_t v, uint32_t *sh, uint32_t *total) {
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
