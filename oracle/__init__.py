@@ -1,11 +1,12 @@
-"""Python handle on the plain FP64 CPU oracle (``bdm_oracle.c``).
+"""Python handle on the plain FP64 CPU oracle (``bdm_oracle.c``: the
+mechanics step; ``diffusion_oracle.c``: diffusion, secretion, chemotaxis).
 
 TEST INFRASTRUCTURE ONLY: imported by the test suite, by the smoke check of
 ``__graft_entry__`` and by the CPU-baseline leg of ``bench.py``.  The
 library path never imports this package.
 
-``build()`` compiles ``bdm_oracle.c`` with gcc (``-O2 -ffp-contract=off``,
-no fused multiply-add) into ``oracle/_build/libbdm_oracle.so``.
+``build()`` compiles both C files with gcc (``-O2 -ffp-contract=off``, no
+fused multiply-add) into ``oracle/_build/libbdm_oracle.so``.
 """
 from __future__ import annotations
 
@@ -18,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bdm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "diffusion_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libbdm_oracle.so")
 _lock = threading.Lock()
@@ -39,12 +41,12 @@ def build(force: bool = False) -> str:
     """Compile the oracle if its library is missing or older than the source."""
     with _lock:
         if (not force and os.path.exists(_LIB_PATH)
-                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+                and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
             return _LIB_PATH
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-std=gnu11", "-Wall", "-o", tmp, _SRC, "-lm"]
+               "-std=gnu11", "-Wall", "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
@@ -90,6 +92,14 @@ def lib():
         L.orc_diameter_of_volume.argtypes = [C.c_double]
         L.orc_volume_of_diameter.restype = C.c_double
         L.orc_volume_of_diameter.argtypes = [C.c_double]
+        L.orc_diffuse.restype = C.c_int
+        L.orc_diffuse.argtypes = [i64p, dp, C.c_double, C.c_double, C.c_double, C.c_int32, dp]
+        L.orc_secrete.restype = C.c_int
+        L.orc_secrete.argtypes = [dp, dp, i64p, dp, C.c_int64, dp, C.c_double]
+        L.orc_gradient.restype = C.c_int
+        L.orc_gradient.argtypes = [dp, dp, i64p, dp, C.c_int64, dp, dp]
+        L.orc_chemotaxis.restype = C.c_int
+        L.orc_chemotaxis.argtypes = [dp, dp, i64p, dp, C.c_int64, dp, C.c_double]
         _lib = L
     return _lib
 
@@ -247,3 +257,54 @@ def diameter_of_volume(v: float) -> float:
 
 def volume_of_diameter(d: float) -> float:
     return float(lib().orc_volume_of_diameter(float(d)))
+
+
+# --------------------------------------------------- diffusion slice ----
+# Grids are numpy arrays of shape (n_z, n_y, n_x), C order (x fastest), the
+# layout of the C functions.  lo, h: 3-vectors (x, y, z).
+
+def _grid_args(u, lo=None, h=None):
+    if u.dtype != np.float64 or not u.flags.c_contiguous or u.ndim != 3:
+        raise ValueError("u must be a C-contiguous float64 array of shape (nz, ny, nx)")
+    n = np.array([u.shape[2], u.shape[1], u.shape[0]], dtype=np.int64)
+    lo = np.ascontiguousarray(lo if lo is not None else np.zeros(3), dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    return n, lo, h
+
+
+def diffuse(u, h, nu: float, mu: float, dt: float, steps: int = 1):
+    """Eq 4.3 applied `steps` times to u in place (zero outside the grid)."""
+    n, _, h = _grid_args(u, None, h)
+    rc = lib().orc_diffuse(_ptr(n, C.c_int64), _ptr(h, C.c_double), float(nu), float(mu), float(dt),
+                           int(steps), _ptr(u, C.c_double))
+    if rc:
+        raise RuntimeError(f"oracle diffusion failed ({rc})")
+    return u
+
+
+def secrete(u, lo, h, xyz, quantity: float):
+    """Algorithm 6: each agent adds `quantity` to the box of its center."""
+    n, lo, h = _grid_args(u, lo, h)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    lib().orc_secrete(_ptr(lo, C.c_double), _ptr(h, C.c_double), _ptr(n, C.c_int64), _ptr(u, C.c_double),
+                      xyz.shape[0], _ptr(xyz, C.c_double), float(quantity))
+    return u
+
+
+def gradient(u, lo, h, xyz):
+    """Normalized central-difference gradient of each position's box."""
+    n, lo, h = _grid_args(u, lo, h)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    g = np.empty_like(xyz)
+    lib().orc_gradient(_ptr(lo, C.c_double), _ptr(h, C.c_double), _ptr(n, C.c_int64), _ptr(u, C.c_double),
+                       xyz.shape[0], _ptr(xyz, C.c_double), _ptr(g, C.c_double))
+    return g
+
+
+def chemotaxis(u, lo, h, xyz, weight: float):
+    """Algorithm 7: positions moved by weight x normalized gradient (a copy)."""
+    n, lo, h = _grid_args(u, lo, h)
+    x = np.array(xyz, dtype=np.float64).reshape(-1, 3)
+    lib().orc_chemotaxis(_ptr(lo, C.c_double), _ptr(h, C.c_double), _ptr(n, C.c_int64), _ptr(u, C.c_double),
+                         x.shape[0], _ptr(x, C.c_double), float(weight))
+    return x
