@@ -249,6 +249,48 @@ int bdm_get_tuning(bdm_ctx* ctx, bdm_tuning* tuning);
  * The agents' state after the call equals the state before it. */
 int bdm_autotune(bdm_ctx* ctx, int32_t iterations, bdm_tuning* chosen);
 
+/* ---- Soma-clustering slice: diffusion, secretion, chemotaxis ----------
+ *
+ * A diffusion grid of n[0] x n[1] x n[2] FP64 concentrations (§4.5.2),
+ * point (i, j, k) stored at i + n[0] (j + n[1] k).  Point (i, j, k) stands
+ * for the box [lo + (i, j, k) h, lo + (i + 1, j + 1, k + 1) h) per axis; a
+ * position belongs to the box floor((x - lo) / h) (IEEE FP64).  Outside the
+ * grid the concentration is zero (substances diffuse out of the space).
+ * The concentrations are host memory (copied in and out on every call) or,
+ * with BDM_DEVICE_PTRS, device memory read and written on the context's
+ * stream.  Errors: BDM_E_INVAL for a NULL grid or array, n < 1 on an axis,
+ * more than 2^40 points, h not finite and > 0, lo not finite, or (per call)
+ * parameters below; BDM_E_NOMEM when scratch memory cannot be had; a
+ * latched device error is reported first. */
+typedef struct {
+  double lo[3];   /* lower corner of box (0, 0, 0) */
+  double h[3];    /* box size per axis */
+  int64_t n[3];   /* points per axis */
+} bdm_diffusion_grid;
+
+/* Eq 4.3 (§4.5.2): n_steps explicit steps
+ *   u' = u (1 - mu dt) + nu dt / hx^2 (u[i+1] - 2u + u[i-1]) + (y) + (z),
+ * evaluated term by term in that order.  nu >= 0 (diffusion coefficient),
+ * mu >= 0 (decay), dt >= 0, n_steps >= 0, all finite.  Stability
+ * (nu dt (1/hx^2 + 1/hy^2 + 1/hz^2) <= 1/2) is the caller's choice. */
+int bdm_diffuse(bdm_ctx* ctx, const bdm_diffusion_grid* grid, double* u, double nu, double mu, double dt,
+                int32_t n_steps, int32_t flags);
+
+/* Algorithm 6: every agent of simulation `sim` whose center lies inside the
+ * grid adds `quantity` (finite) to the concentration of its box.
+ * BDM_E_STATE when the simulation has no agents set. */
+int bdm_secrete(bdm_ctx* ctx, int32_t sim, const bdm_diffusion_grid* grid, double* u, double quantity,
+                int32_t flags);
+
+/* Algorithm 7: every agent of simulation `sim` whose center lies inside the
+ * grid moves by weight (finite) times the normalized gradient of its box:
+ * g_a = (u[+1] - u[-1]) / (2 h_a) per axis, divided by
+ * |g| = sqrt((gx gx + gy gy) + gz gz); no move where |g| = 0.  u is only
+ * read.  Moved agents count as changed for static detection.
+ * BDM_E_STATE when the simulation has no agents set. */
+int bdm_chemotaxis(bdm_ctx* ctx, int32_t sim, const bdm_diffusion_grid* grid, const double* u, double weight,
+                   int32_t flags);
+
 /* Release everything the context owns. */
 void bdm_destroy(bdm_ctx* ctx);
 

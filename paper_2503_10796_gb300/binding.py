@@ -46,6 +46,10 @@ class BdmTuning(C.Structure):
                 ("reserved", C.c_int32 * 5)]
 
 
+class BdmDiffusionGrid(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("h", C.c_double * 3), ("n", C.c_int64 * 3)]
+
+
 SIGNATURES = {
     "bdm_create": (C.c_int, [_P(BdmParams), _i32, _i64, _i32, _vp, _P(_vp)]),
     "bdm_set_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _i32]),
@@ -64,6 +68,9 @@ SIGNATURES = {
     "bdm_get_tuning": (C.c_int, [_vp, _P(BdmTuning)]),
     "bdm_autotune": (C.c_int, [_vp, _i32, _P(BdmTuning)]),
     "bdm_forces_noalloc": (C.c_int, [_P(BdmParams), _i64, _vp, _vp, _vp, _vp, _vp]),
+    "bdm_diffuse": (C.c_int, [_vp, _P(BdmDiffusionGrid), _vp, _dbl, _dbl, _dbl, _i32, _i32]),
+    "bdm_secrete": (C.c_int, [_vp, _i32, _P(BdmDiffusionGrid), _vp, _dbl, _i32]),
+    "bdm_chemotaxis": (C.c_int, [_vp, _i32, _P(BdmDiffusionGrid), _vp, _dbl, _i32]),
     "bdm_destroy": (None, [_vp]),
     "bdm_last_error": (C.c_char_p, [_vp]),
 }
@@ -254,6 +261,41 @@ class Context:
         return dict(agents=s.agents, iterations=s.iterations, static_agents=s.static_agents,
                     moved_agents=s.moved_agents, origin_len=list(s.origin_len), dims=list(s.dims),
                     agent_updates=s.agent_updates)
+
+    # -- diffusion slice (§4.5.2, Algorithms 6 and 7) ------------------------
+    @staticmethod
+    def _diffusion_grid(u, lo, h):
+        """Grid descriptor for a concentration array of shape (nz, ny, nx)
+        (numpy float64, C order, or a CUDA torch tensor); flags for it."""
+        if hasattr(u, "data_ptr") and getattr(u, "is_cuda", False):
+            if u.dim() != 3 or not u.is_contiguous() or str(u.dtype) != "torch.float64":
+                raise ValueError("u must be a contiguous float64 CUDA tensor of shape (nz, ny, nx)")
+            shape, ptr, flags = tuple(u.shape), C.c_void_p(u.data_ptr()), DEVICE_PTRS
+        else:
+            if not isinstance(u, np.ndarray) or u.dtype != np.float64 or not u.flags.c_contiguous or u.ndim != 3:
+                raise ValueError("u must be a C-contiguous float64 array of shape (nz, ny, nx)")
+            shape, ptr, flags = u.shape, _dptr(u), 0
+        g = BdmDiffusionGrid((C.c_double * 3)(*[float(v) for v in lo]), (C.c_double * 3)(*[float(v) for v in h]),
+                             (C.c_int64 * 3)(shape[2], shape[1], shape[0]))
+        return g, ptr, flags
+
+    def diffuse(self, u, lo, h, nu: float, mu: float, dt: float, steps: int = 1):
+        """Eq 4.3, `steps` explicit steps of u in place."""
+        g, ptr, flags = self._diffusion_grid(u, lo, h)
+        self._check(self._lib.bdm_diffuse(self._h, C.byref(g), ptr, float(nu), float(mu), float(dt), int(steps),
+                                          flags))
+        return u
+
+    def secrete(self, sim: int, u, lo, h, quantity: float):
+        """Algorithm 6 for the agents of `sim`, into u in place."""
+        g, ptr, flags = self._diffusion_grid(u, lo, h)
+        self._check(self._lib.bdm_secrete(self._h, sim, C.byref(g), ptr, float(quantity), flags))
+        return u
+
+    def chemotaxis(self, sim: int, u, lo, h, weight: float):
+        """Algorithm 7: moves the agents of `sim` up the gradient of u."""
+        g, ptr, flags = self._diffusion_grid(u, lo, h)
+        self._check(self._lib.bdm_chemotaxis(self._h, sim, C.byref(g), ptr, float(weight), flags))
 
     # -- tuning ------------------------------------------------------------
     def set_tuning(self, force_variant: int = 0, sort_interval: int = -1, sort_curve: int = 0):

@@ -440,6 +440,47 @@ int query_grid(bdm_ctx *c, bool with_cells, const std::vector<double> *boxes) {
   return BDM_OK;
 }
 
+// soma-clustering slice helpers
+bool fin(double v) { return std::isfinite(v); }
+
+// Points of a valid grid (> 0), or a negative error code with the reason.
+int64_t check_grid(bdm_ctx *c, const bdm_diffusion_grid *g, const void *u) {
+  if (!g || !u) return fail(c, BDM_E_INVAL, "NULL grid or concentrations");
+  int64_t total = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (g->n[a] < 1) return fail(c, BDM_E_INVAL, "grid needs at least one point per axis");
+    if (!fin(g->h[a]) || !(g->h[a] > 0.0)) return fail(c, BDM_E_INVAL, "grid spacing not finite and > 0");
+    if (!fin(g->lo[a])) return fail(c, BDM_E_INVAL, "grid corner not finite");
+    if (g->n[a] > (1ll << 40) || total > (1ll << 40) / g->n[a]) return fail(c, BDM_E_INVAL, "more than 2^40 grid points");
+    total *= g->n[a];
+  }
+  return total;
+}
+
+// The concentrations on the device: the caller's array, or a scratch copy
+// of the host array.  *scratch receives what the call must free.
+int grid_on_device(bdm_ctx *c, const double *u, int64_t total, int32_t flags, double **dev, double **scratch) {
+  *scratch = nullptr;
+  if (flags & BDM_DEVICE_PTRS) {
+    *dev = const_cast<double *>(u);
+    return BDM_OK;
+  }
+  int rc = dalloc(c, scratch, (size_t)total, "diffusion grid");
+  if (rc) return rc;
+  cudaMemcpyAsync(*scratch, u, sizeof(double) * (size_t)total, cudaMemcpyHostToDevice, c->stream);
+  *dev = *scratch;
+  return BDM_OK;
+}
+
+int agents_ready(bdm_ctx *c, int32_t sim, SimState *s) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
+  rc = latched_error(c);
+  if (rc) return rc;
+  return read_state(c, sim, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -759,6 +800,85 @@ int bdm_get_agents(bdm_ctx *c, int32_t sim, int64_t cap, double *xyz, double *di
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "downloading agents");
+  return BDM_OK;
+}
+
+// ---- soma-clustering slice (§4.5.2, Algorithms 6 and 7) ------------------
+int bdm_diffuse(bdm_ctx *c, const bdm_diffusion_grid *g, double *u, double nu, double mu, double dt, int32_t n_steps,
+                int32_t flags) {
+  if (!c) return BDM_E_INVAL;
+  const int64_t total = check_grid(c, g, u);
+  if (total < 0) return (int)total;
+  if (!fin(nu) || !fin(mu) || !fin(dt) || nu < 0 || mu < 0 || dt < 0 || n_steps < 0)
+    return fail(c, BDM_E_INVAL, "nu, mu, dt must be finite and >= 0, n_steps >= 0");
+  int rc = latched_error(c);
+  if (rc) return rc;
+  if (n_steps == 0) return BDM_OK;
+  double *a = nullptr, *own = nullptr, *b = nullptr;
+  rc = grid_on_device(c, u, total, flags, &a, &own);
+  if (rc) return rc;
+  rc = dalloc(c, &b, (size_t)total, "diffusion scratch");
+  if (rc) {
+    dfree(c, own);
+    return rc;
+  }
+  double *in = a, *out = b;
+  for (int32_t t = 0; t < n_steps; ++t) {
+    launch_diffuse_step(c->stream, in, out, *g, nu, mu, dt);
+    std::swap(in, out);
+  }
+  // `in` holds the result
+  if (flags & BDM_DEVICE_PTRS) {
+    if (in != u) cudaMemcpyAsync(u, in, sizeof(double) * (size_t)total, cudaMemcpyDeviceToDevice, c->stream);
+  } else {
+    cudaMemcpyAsync(u, in, sizeof(double) * (size_t)total, cudaMemcpyDeviceToHost, c->stream);
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  dfree(c, b);
+  dfree(c, own);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "diffusion");
+  return BDM_OK;
+}
+
+int bdm_secrete(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, double *u, double quantity, int32_t flags) {
+  if (!c) return BDM_E_INVAL;
+  const int64_t total = check_grid(c, g, u);
+  if (total < 0) return (int)total;
+  if (!fin(quantity)) return fail(c, BDM_E_INVAL, "quantity not finite");
+  SimState s;
+  int rc = agents_ready(c, sim, &s);
+  if (rc) return rc;
+  double *dev = nullptr, *own = nullptr;
+  rc = grid_on_device(c, u, total, flags, &dev, &own);
+  if (rc) return rc;
+  launch_secrete(c->D, c->stream, c->h_sc[sim].base, s.n, *g, dev, quantity);
+  if (!(flags & BDM_DEVICE_PTRS))
+    cudaMemcpyAsync(u, dev, sizeof(double) * (size_t)total, cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  dfree(c, own);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "secretion");
+  return BDM_OK;
+}
+
+int bdm_chemotaxis(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, const double *u, double weight,
+                   int32_t flags) {
+  if (!c) return BDM_E_INVAL;
+  const int64_t total = check_grid(c, g, u);
+  if (total < 0) return (int)total;
+  if (!fin(weight)) return fail(c, BDM_E_INVAL, "weight not finite");
+  SimState s;
+  int rc = agents_ready(c, sim, &s);
+  if (rc) return rc;
+  double *dev = nullptr, *own = nullptr;
+  rc = grid_on_device(c, u, total, flags, &dev, &own);
+  if (rc) return rc;
+  launch_chemotaxis(c->D, c->stream, c->h_sc[sim].base, s.n, *g, dev, weight);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  dfree(c, own);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "chemotaxis");
   return BDM_OK;
 }
 

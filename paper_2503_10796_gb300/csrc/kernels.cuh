@@ -24,6 +24,15 @@ void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32 = 0);
 void launch_force(const DevCtx &C, cudaStream_t st, int variant = 0, bool has_fp32 = true, bool has_fp64 = true);
 void launch_displace(const DevCtx &C, cudaStream_t st);
 
+// diffusion.cu (soma-clustering slice)
+typedef bdm_diffusion_grid DiffGrid;
+void launch_diffuse_step(cudaStream_t st, const double *in, double *out, const DiffGrid &g, double nu, double mu,
+                         double dt);
+void launch_secrete(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const DiffGrid &g, double *u,
+                    double quantity);
+void launch_chemotaxis(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const DiffGrid &g, const double *u,
+                       double weight);
+
 // query.cu
 void launch_boxids(const DevCtx &C, cudaStream_t st, int sim, int64_t *out_by_id);
 int64_t launch_pairs(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, double radius,
