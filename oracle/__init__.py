@@ -1,5 +1,6 @@
 """Python handle on the plain FP64 CPU oracle (``bdm_oracle.c``: the
-mechanics step; ``diffusion_oracle.c``: diffusion, secretion, chemotaxis).
+mechanics step; ``diffusion_oracle.c``: diffusion, secretion, chemotaxis;
+``sir_oracle.c``: the epidemiology use case).
 
 TEST INFRASTRUCTURE ONLY: imported by the test suite, by the smoke check of
 ``__graft_entry__`` and by the CPU-baseline leg of ``bench.py``.  The
@@ -19,7 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bdm_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "diffusion_oracle.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "diffusion_oracle.c"), os.path.join(_HERE, "sir_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libbdm_oracle.so")
 _lock = threading.Lock()
@@ -35,6 +36,11 @@ class OrcParams(C.Structure):
         ("sort_interval", C.c_int32), ("reserved", C.c_int32),
         ("seed", C.c_uint64), ("capacity", C.c_int64),
     ]
+
+
+class SirParams(C.Structure):
+    _fields_ = [("radius", C.c_double), ("p_infect", C.c_double), ("p_recover", C.c_double),
+                ("speed", C.c_double), ("length", C.c_double), ("seed", C.c_uint64)]
 
 
 def build(force: bool = False) -> str:
@@ -100,6 +106,8 @@ def lib():
         L.orc_gradient.argtypes = [dp, dp, i64p, dp, C.c_int64, dp, dp]
         L.orc_chemotaxis.restype = C.c_int
         L.orc_chemotaxis.argtypes = [dp, dp, i64p, dp, C.c_int64, dp, C.c_double]
+        L.orc_sir_step.restype = C.c_int
+        L.orc_sir_step.argtypes = [P(SirParams), C.c_int64, dp, u8p, C.c_int64, C.c_int32]
         _lib = L
     return _lib
 
@@ -308,3 +316,21 @@ def chemotaxis(u, lo, h, xyz, weight: float):
     lib().orc_chemotaxis(_ptr(lo, C.c_double), _ptr(h, C.c_double), _ptr(n, C.c_int64), _ptr(u, C.c_double),
                          x.shape[0], _ptr(x, C.c_double), float(weight))
     return x
+
+
+# ------------------------------------------------------- epidemiology ----
+SUSCEPTIBLE, INFECTED, RECOVERED = 0, 1, 2
+
+
+def sir_step(xyz, state, radius: float, p_infect: float, p_recover: float, speed: float, length: float,
+             seed: int = 0, t0: int = 0, steps: int = 1):
+    """Algorithms 3-5 for `steps` steps from step t0, on copies of xyz
+    (n x 3) and state (n, uint8: 0 S, 1 I, 2 R); returns (xyz, state)."""
+    x = np.array(xyz, dtype=np.float64).reshape(-1, 3)
+    st = np.array(state, dtype=np.uint8).reshape(-1)
+    prm = SirParams(float(radius), float(p_infect), float(p_recover), float(speed), float(length), int(seed))
+    rc = lib().orc_sir_step(C.byref(prm), x.shape[0], _ptr(x, C.c_double), _ptr(st, C.c_uint8), int(t0),
+                            int(steps))
+    if rc:
+        raise RuntimeError(f"oracle SIR step failed ({rc})")
+    return x, st
