@@ -68,7 +68,9 @@ def parse():
     return args
 
 
-def make_workload(name: str, precision: int, static: int):
+def make_workload(name: str, precision: int, static: int, build: bool = True):
+    """(populations, description); build=False describes the 200M-agent
+    workload without generating it (populations None)."""
     from paper_2503_10796_gb300 import workloads as W
     if name == "clustered_8M":
         pops = [W.clustered(precision=precision, detect_static=static, sort_interval=10)]
@@ -89,18 +91,18 @@ def make_workload(name: str, precision: int, static: int):
         pops = [W.plain_fp64(precision=precision)]
         desc = dict(workload="plain_4096", agents=4096, side=160.0, diameters="U[8,12]")
     elif name == "uniform_200M":
-        pops = [W.uniform_fraction(200_000_000, precision=precision, sort_interval=10)]
+        pops = [W.uniform_fraction(200_000_000, precision=precision, sort_interval=10)] if build else None
         desc = dict(workload="uniform_200M", agents=200_000_000, volume_fraction=0.3)
     elif name == "batched_sweep_256":
         pops = W.batched_sweep(precision=precision)
         desc = dict(workload="batched_sweep_256", sims=256, agents=int(sum(p.n for p in pops)))
     else:
         raise SystemExit(f"unknown workload {name}")
-    for p in pops:
+    for p in pops or []:
         p.params.detect_static = static
+    slots = sum(max(p.n, p.params.capacity) for p in pops) if pops is not None else desc["agents"]
     desc.update(precision="fp32-force/fp64-position" if precision == 1 else "fp64", static_skip=bool(static),
-                l2="inputs larger than L2 (no flush needed)" if sum(max(p.n, p.params.capacity) for p in pops) > 1_000_000 else
-                "working set inside L2")
+                l2="inputs larger than L2 (no flush needed)" if slots > 1_000_000 else "working set inside L2")
     return pops, desc
 
 
@@ -193,6 +195,17 @@ def cpu_baseline(name: str):
             "seconds": dt}
 
 
+def parallelism_of(workload: str, world: int) -> str:
+    if world > 1 and workload == "batched_sweep_256":
+        return f"{world} ranks, simulations sharded (longest-processing-time)"
+    return f"{world} independent replicas" if world > 1 else "1 GPU"
+
+
+def arm_config(desc: dict, parallelism: str, args) -> dict:
+    """The `config` of a JSON line, the same for both arms."""
+    return dict(desc, parallelism=parallelism, settle_iterations=args.settle)
+
+
 def reference_arm(args):
     """--impl reference: the oracle on the host cores, one bounded sample per step."""
     import oracle
@@ -219,12 +232,12 @@ def reference_arm(args):
         s.step(1)
     dt = time.perf_counter() - t0
     v = pop.n * args.steps / dt
-    _, desc = make_workload(args.workload, args.precision, args.static) if args.workload != "uniform_200M" else (
-        None, dict(workload="uniform_200M"))
+    _, desc = make_workload(args.workload, args.precision, args.static, build=False)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": desc,
+            "data": "synthetic", "config": arm_config(desc, parallelism_of(args.workload, world), args),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -256,11 +269,7 @@ def main():
         # independent simulations: shard them, no exchange on the data path
         from paper_2503_10796_gb300 import sharding
         _, pops = sharding.shard(pops, [p.n for p in pops], rank, world)
-        parallelism = f"{world} ranks, simulations sharded (longest-processing-time)"
-    elif world > 1:
-        parallelism = f"{world} independent replicas"
-    else:
-        parallelism = "1 GPU"
+    parallelism = parallelism_of(args.workload, world)
     total_agents = sum(max(p.n, p.params.capacity) for p in pops)
     # a dedicated stream: the library captures CUDA graphs on it, which the
     # legacy default stream does not allow
@@ -391,7 +400,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32-force/f64-position" if prec == 1 else "f64", "data": "synthetic",
-            "config": dict(desc, parallelism=parallelism, settle_iterations=args.settle),
+            "config": arm_config(desc, parallelism, args),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
                          "peak_source": f"{peak_kind} hbm_gbs", "force_ms_per_launch": force_ms,

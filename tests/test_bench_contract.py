@@ -1,0 +1,45 @@
+"""The benchmark's JSON line on the host: the reference arm (the oracle on
+the CPU) prints the contract's keys, and its `config` is the one the GPU
+arm prints for the same workload and launch."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_line(orc):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                          "plain_fp64_4096", "--precision", "0", "--steps", "3", "--warmup", "3"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT, check=True)
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 3 and line["warmup"] == 3
+    assert line["higher_is_better"] is True and line["vs_baseline"] is None and line["n_gpus"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["e2e"]["value"] == line["value"]
+
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+    _, desc = bench.make_workload("plain_fp64_4096", 0, 0)
+    args = argparse.Namespace(settle=line["config"]["settle_iterations"])
+    assert line["config"] == bench.arm_config(desc, bench.parallelism_of("plain_fp64_4096", 1), args)
+
+
+def test_settle_defaults():
+    sys.path.insert(0, ROOT)
+    import bench
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py", "--workload", "growth_division_65536"]
+        assert bench.parse().settle == 65
+        sys.argv = ["bench.py"]
+        assert bench.parse().settle == 50
+    finally:
+        sys.argv = argv
