@@ -291,6 +291,36 @@ int bdm_secrete(bdm_ctx* ctx, int32_t sim, const bdm_diffusion_grid* grid, doubl
 int bdm_chemotaxis(bdm_ctx* ctx, int32_t sim, const bdm_diffusion_grid* grid, const double* u, double weight,
                    int32_t flags);
 
+/* ---- Epidemiology use case (§4.6.3) ------------------------------------
+ * Persons are the agents of a simulation (their diameters play no part);
+ * each has a state 0 susceptible, 1 infected, 2 recovered, in a uint8
+ * array by agent ID (host memory, or device memory with BDM_DEVICE_PTRS).
+ * One step, all persons reading the states and positions at its start:
+ *   Algorithm 3: a susceptible person draws u0; if u0 < p_infect and any
+ *     other person infected at the start of the step lies within radius
+ *     (squared distance (dx dx + dy dy) + dz dz below radius * radius), it
+ *     becomes infected;
+ *   Algorithm 4: an infected person (also one infected in this step) draws
+ *     u1 and recovers if u1 < p_recover;
+ *   Algorithm 5: every person moves by speed along the normalized vector of
+ *     three uniforms in [-1, 1) (no move for the zero vector), and every
+ *     coordinate is wrapped into [0, length) (a torus).
+ * Uniforms: Philox4x64-10 with key {seed, 1}, counter {ID, t, 0, 0}
+ * (words 0, 1: u0, u1) and {ID, t, 1, 0} (words 0-2: movement), each the
+ * top 53 bits of a word times 2^-53; t counts steps from t0.
+ * Errors: BDM_E_INVAL for a NULL argument, n_steps < 0, t0 < 0, radius,
+ * speed or length not finite and >= 0 (length > 0), probabilities outside
+ * [0, 1], a state outside {0, 1, 2}; BDM_E_STATE when the simulation has
+ * no agents set; BDM_E_NOMEM for scratch memory.  Moved persons count as
+ * changed for the mechanics step. */
+typedef struct {
+  double radius, p_infect, p_recover, speed, length;
+  uint64_t seed;
+} bdm_sir_params;
+
+int bdm_sir_step(bdm_ctx* ctx, int32_t sim, const bdm_sir_params* params, uint8_t* state, int64_t t0,
+                 int32_t n_steps, int32_t flags);
+
 /* Release everything the context owns. */
 void bdm_destroy(bdm_ctx* ctx);
 

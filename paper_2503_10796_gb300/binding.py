@@ -50,6 +50,11 @@ class BdmDiffusionGrid(C.Structure):
     _fields_ = [("lo", C.c_double * 3), ("h", C.c_double * 3), ("n", C.c_int64 * 3)]
 
 
+class BdmSirParams(C.Structure):
+    _fields_ = [("radius", C.c_double), ("p_infect", C.c_double), ("p_recover", C.c_double),
+                ("speed", C.c_double), ("length", C.c_double), ("seed", C.c_uint64)]
+
+
 SIGNATURES = {
     "bdm_create": (C.c_int, [_P(BdmParams), _i32, _i64, _i32, _vp, _P(_vp)]),
     "bdm_set_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _i32]),
@@ -71,6 +76,7 @@ SIGNATURES = {
     "bdm_diffuse": (C.c_int, [_vp, _P(BdmDiffusionGrid), _vp, _dbl, _dbl, _dbl, _i32, _i32]),
     "bdm_secrete": (C.c_int, [_vp, _i32, _P(BdmDiffusionGrid), _vp, _dbl, _i32]),
     "bdm_chemotaxis": (C.c_int, [_vp, _i32, _P(BdmDiffusionGrid), _vp, _dbl, _i32]),
+    "bdm_sir_step": (C.c_int, [_vp, _i32, _P(BdmSirParams), _vp, _i64, _i32, _i32]),
     "bdm_destroy": (None, [_vp]),
     "bdm_last_error": (C.c_char_p, [_vp]),
 }
@@ -296,6 +302,22 @@ class Context:
         """Algorithm 7: moves the agents of `sim` up the gradient of u."""
         g, ptr, flags = self._diffusion_grid(u, lo, h)
         self._check(self._lib.bdm_chemotaxis(self._h, sim, C.byref(g), ptr, float(weight), flags))
+
+    # -- epidemiology (§4.6.3, Algorithms 3-5) -------------------------------
+    def sir_step(self, sim: int, state, radius: float, p_infect: float, p_recover: float, speed: float,
+                 length: float, seed: int = 0, t0: int = 0, steps: int = 1):
+        """`steps` steps of the persons of `sim` from step t0; state (uint8
+        by agent ID: 0 S, 1 I, 2 R; numpy, or a CUDA torch tensor) is
+        updated in place."""
+        prm = BdmSirParams(float(radius), float(p_infect), float(p_recover), float(speed), float(length), int(seed))
+        if hasattr(state, "data_ptr") and getattr(state, "is_cuda", False):
+            ptr, flags = C.c_void_p(state.data_ptr()), DEVICE_PTRS
+        else:
+            if not isinstance(state, np.ndarray) or state.dtype != np.uint8 or not state.flags.c_contiguous:
+                raise ValueError("state must be a C-contiguous uint8 array")
+            ptr, flags = _dptr(state), 0
+        self._check(self._lib.bdm_sir_step(self._h, sim, C.byref(prm), ptr, int(t0), int(steps), flags))
+        return state
 
     # -- tuning ------------------------------------------------------------
     def set_tuning(self, force_variant: int = 0, sort_interval: int = -1, sort_curve: int = 0):

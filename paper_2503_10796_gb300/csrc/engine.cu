@@ -481,6 +481,36 @@ int agents_ready(bdm_ctx *c, int32_t sim, SimState *s) {
   return read_state(c, sim, s);
 }
 
+// Query cells of every simulation (FP64 records), the box length of `sim`
+// at least `radius` (the step's box length, or the radius when larger);
+// *s receives the simulation's state of that build.
+int radius_cells(bdm_ctx *c, int32_t sim, double radius, SimState *s) {
+  const size_t M = (size_t)c->max_total;
+  if (!c->D.q.r64) {
+    int r2 = BDM_OK;
+    if (!r2) r2 = dalloc(c, &c->D.q.slot, M, "query slots");
+    if (!r2) r2 = dalloc(c, &c->D.q.sim, M, "query sims");
+    if (!r2) r2 = dalloc(c, &c->D.q.pkey, M, "query keys");
+    if (!r2) r2 = dalloc(c, &c->D.q.r64, M, "query records");
+    if (!r2) r2 = dalloc(c, &c->D.qkey, M, "query box keys");
+    if (r2) return r2;
+    cudaMemsetAsync(c->D.q.slot, 0, sizeof(int32_t) * M, c->stream);
+    cudaMemsetAsync(c->D.q.sim, 0, sizeof(int32_t) * M, c->stream);
+    cudaMemsetAsync(c->D.q.pkey, 0, sizeof(uint64_t) * M, c->stream);
+    c->graph_dirty = true;
+  }
+  int rc = query_grid(c, false, nullptr);
+  if (rc) return rc;
+  rc = read_state(c, sim, s);
+  if (rc) return rc;
+  std::vector<double> boxes(c->n_sims);
+  for (int k = 0; k < c->n_sims; ++k) boxes[k] = c->h_sc[k].box_length;
+  if (radius >= 0 && radius > s->L) boxes[sim] = radius;
+  rc = query_grid(c, true, &boxes);
+  if (rc) return rc;
+  return read_state(c, sim, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -882,6 +912,62 @@ int bdm_chemotaxis(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, const d
   return BDM_OK;
 }
 
+// ---- epidemiology use case (§4.6.3, Algorithms 3-5) ----------------------
+int bdm_sir_step(bdm_ctx *c, int32_t sim, const bdm_sir_params *p, uint8_t *state, int64_t t0, int32_t n_steps,
+                 int32_t flags) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  if (!p || !state) return fail(c, BDM_E_INVAL, "NULL parameters or states");
+  if (n_steps < 0 || t0 < 0) return fail(c, BDM_E_INVAL, "n_steps and t0 must be >= 0");
+  if (!fin(p->radius) || p->radius < 0 || !fin(p->speed) || p->speed < 0 || !fin(p->length) || !(p->length > 0) ||
+      !(p->p_infect >= 0 && p->p_infect <= 1) || !(p->p_recover >= 0 && p->p_recover <= 1))
+    return fail(c, BDM_E_INVAL, "radius, speed >= 0, length > 0 finite; probabilities in [0, 1]");
+  if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
+  rc = latched_error(c);
+  if (rc) return rc;
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  const int64_t n = s.n;
+  if (n == 0 || n_steps == 0) return BDM_OK;
+  const bool dev = (flags & BDM_DEVICE_PTRS) != 0;
+  uint8_t *a = nullptr, *b = nullptr;
+  double *nxyz = nullptr;
+  rc = dalloc(c, &a, (size_t)n, "states");
+  if (!rc) rc = dalloc(c, &b, (size_t)n, "states");
+  if (!rc) rc = dalloc(c, &nxyz, (size_t)(3 * n), "new positions");
+  if (rc) {
+    dfree(c, a); dfree(c, b); dfree(c, nxyz);
+    return rc;
+  }
+  cudaMemcpyAsync(a, state, (size_t)n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  std::vector<uint8_t> check((size_t)n);
+  cudaMemcpyAsync(check.data(), a, (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) {
+    for (uint8_t v : check)
+      if (v > 2) {
+        dfree(c, a); dfree(c, b); dfree(c, nxyz);
+        return fail(c, BDM_E_INVAL, "a state outside {0, 1, 2}");
+      }
+  }
+  for (int32_t k = 0; k < n_steps && e == cudaSuccess; ++k) {
+    rc = radius_cells(c, sim, p->radius, &s);
+    if (rc) break;
+    launch_sir_step(c->D, c->stream, sim, s.cell_base, n, c->h_sc[sim].base, a, b, nxyz, *p, (long long)(t0 + k));
+    std::swap(a, b);
+    e = cudaGetLastError();
+  }
+  if (!rc && e == cudaSuccess) {
+    cudaMemcpyAsync(state, a, (size_t)n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+  }
+  dfree(c, a); dfree(c, b); dfree(c, nxyz);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(c, e, "epidemiology step");
+  return latched_error(c);
+}
+
 int bdm_get_grid(bdm_ctx *c, int32_t sim, int64_t cap, int64_t *box_id, double origin_len[4], int64_t dims[3]) {
   int rc = check_sim(c, sim);
   if (rc) return rc;
@@ -916,32 +1002,8 @@ int bdm_neighbors(bdm_ctx *c, int32_t sim, double radius, int64_t cap, int64_t *
   if (rc) return rc;
   if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
   if (!std::isfinite(radius)) return fail(c, BDM_E_INVAL, "radius must be finite");
-  size_t M = (size_t)c->max_total;
-  if (!c->D.q.r64) {
-    int r2 = BDM_OK;
-    if (!r2) r2 = dalloc(c, &c->D.q.slot, M, "query slots");
-    if (!r2) r2 = dalloc(c, &c->D.q.sim, M, "query sims");
-    if (!r2) r2 = dalloc(c, &c->D.q.pkey, M, "query keys");
-    if (!r2) r2 = dalloc(c, &c->D.q.r64, M, "query records");
-    if (!r2) r2 = dalloc(c, &c->D.qkey, M, "query box keys");
-    if (r2) return r2;
-    cudaMemsetAsync(c->D.q.slot, 0, sizeof(int32_t) * M, c->stream);
-    cudaMemsetAsync(c->D.q.sim, 0, sizeof(int32_t) * M, c->stream);
-    cudaMemsetAsync(c->D.q.pkey, 0, sizeof(uint64_t) * M, c->stream);
-    c->graph_dirty = true;
-  }
-  // Box length for the query: the step's, or the radius when larger.
   SimState s;
-  rc = query_grid(c, false, nullptr);
-  if (rc) return rc;
-  rc = read_state(c, sim, &s);
-  if (rc) return rc;
-  std::vector<double> boxes(c->n_sims);
-  for (int k = 0; k < c->n_sims; ++k) boxes[k] = c->h_sc[k].box_length;
-  if (radius >= 0 && radius > s.L) boxes[sim] = radius;
-  rc = query_grid(c, true, &boxes);
-  if (rc) return rc;
-  rc = read_state(c, sim, &s);
+  rc = radius_cells(c, sim, radius, &s);
   if (rc) return rc;
   int64_t n = s.n;
   int64_t *counts = nullptr, *offsets = nullptr;

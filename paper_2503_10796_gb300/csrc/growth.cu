@@ -12,6 +12,7 @@
 //               attempt, 0} and key {seed, 0}: the counter-based generator
 //               that §7.1.4 proposes for reproducible runs.
 #include "kernels.cuh"
+#include "philox.cuh"
 
 namespace bdm {
 
@@ -120,23 +121,6 @@ __device__ double cbrt_rn(double x) {
 
 __device__ __forceinline__ double diameter_of_volume(double V) {
   return cbrt_rn(__ddiv_rn(__dmul_rn(6.0, V), 3.141592653589793));
-}
-
-// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC 2011).
-__device__ void philox4x64_10(const unsigned long long ctr[4], const unsigned long long key[2],
-                              unsigned long long out[4]) {
-  const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-  const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-  unsigned long long c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
-  unsigned long long k0 = key[0], k1 = key[1];
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) { k0 += W0; k1 += W1; }
-    unsigned long long lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
-    unsigned long long lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
-    unsigned long long n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
-    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
-  }
-  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
 __device__ void division_axis(unsigned long long seed, long long id, long long t, double u[3]) {

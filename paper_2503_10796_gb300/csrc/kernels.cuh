@@ -33,6 +33,10 @@ void launch_secrete(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, c
 void launch_chemotaxis(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const DiffGrid &g, const double *u,
                        double weight);
 
+// sir.cu (epidemiology use case): one step on the query cells of `sim`
+void launch_sir_step(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, int64_t base,
+                     const uint8_t *st_in, uint8_t *st_out, double *nxyz, const bdm_sir_params &prm, long long t);
+
 // query.cu
 void launch_boxids(const DevCtx &C, cudaStream_t st, int sim, int64_t *out_by_id);
 int64_t launch_pairs(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, double radius,
