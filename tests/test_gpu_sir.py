@@ -4,8 +4,6 @@ same counter-based draws on both sides."""
 import numpy as np
 import pytest
 
-from paper_2503_10796_gb300 import workloads
-
 pytestmark = pytest.mark.gpu
 
 S, I, R = 0, 1, 2

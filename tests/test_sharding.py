@@ -5,7 +5,6 @@ import os
 import socket
 
 import numpy as np
-import pytest
 
 from paper_2503_10796_gb300 import sharding, workloads
 

@@ -4,7 +4,6 @@ recovery rule and its rate, movement by exactly the speed on the torus, and
 agreement with the SIR model the thesis compares against (measles
 parameters of Table 4.3, Fig 4.17A)."""
 import numpy as np
-import pytest
 
 S, I, R = 0, 1, 2
 
