@@ -43,3 +43,17 @@ def test_settle_defaults():
         assert bench.parse().settle == 50
     finally:
         sys.argv = argv
+
+
+def test_clock_summary():
+    sys.path.insert(0, ROOT)
+    import bench
+    lines = ["0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "0, 1995, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+             "0, 2070, 2070, 1100.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "garbage", ""]
+    out = bench.ClockSampler.summarize(lines)
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+    hot = bench.ClockSampler.summarize(["0, 1500, 2070, 1400, 0x8, Active, Not Active, Active, Not Active"])
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
