@@ -5,13 +5,25 @@ roofline fraction, an end-to-end figure through the C ABI with host
 buffers, and the CPU oracle timed on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
-                    [--workload clustered_8M|plain_fp64_4096|uniform_200M|batched_sweep_256]
-                    [--precision 1|0] [--static 0|1]
+                    [--workload clustered_8M|plain_fp64_4096|uniform_200M|batched_sweep_256|
+                                growth_division_65536|clustered_1M]
+                    [--precision 1|0] [--static 0|1] [--static-leg 0|1]
 
-One step = one iteration of every simulation of the workload.  Under
-torchrun (N > 1) every rank steps its own replica of the workload (the
-single-domain workloads do not shard) and the value is the whole-job
-aggregate over ranks; timing is the maximum over ranks.
+One step = one iteration of every simulation of the workload.  The timed
+region replays the library's CUDA graphs (the production path); a profiled
+pass of as many iterations right after it brackets every stage with CUDA
+events on the library's stream, which gives the stage times and the force
+kernel's launch duration of the roofline.  Under torchrun (N > 1) every rank
+steps its own replica of the workload (the single-domain workloads do not
+shard) or, for the parameter sweep, its share of the simulations; the value
+is the whole-job aggregate over ranks and timing is the maximum over ranks.
+
+The clustered 8M workload keeps its stated re-sort settings (Morton order
+every 10 iterations); the autotuner picks only the force kernel, the box
+length and the iterations per graph there.  Its line also carries a static-
+skip leg: static detection on and off from the same input, settled until
+the static fraction changes by less than 0.5% over 10 iterations (at most
+500), then 100 timed iterations each.
 """
 from __future__ import annotations
 
@@ -19,6 +31,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -37,13 +50,16 @@ UNIT = "agent-updates/s"
 # path: FP64 diameter (8 B) and FP64 force (24 B).
 ALG_BYTES_AGENT = {1: 42.0, 0: 58.0}
 ALG_BYTES_BOX = 8.0
-# DRAM bytes (read + write) per agent of the default force kernel
-# (k_force32s, variant 0), from the ncu capture of clustered_1M summarised in
-# profiles/k_force32s_clustered_1M.md; scaled by the agents of a launch for
-# the clustered workloads (same per-cluster shape), null elsewhere or when
-# another kernel runs.
-FORCE_TRAFFIC_B_PER_AGENT = {"k_force32s": 112.6}
-FORCE_KERNEL = {0: "k_force32s", 1: "k_force32d", 2: "k_force", 3: "k_force32d", 4: "k_force32s (direct)"}
+# DRAM bytes (read + write) per agent of a force kernel, from an ncu capture
+# of the 1M-agent clustered case (the per-cluster shape of the 8M case),
+# scaled by the agents of a launch for the clustered workloads and null
+# elsewhere.  An entry holds only while the kernel is the one captured.
+FORCE_TRAFFIC_B_PER_AGENT: dict = {}
+FORCE_KERNEL = {0: "k_force32s", 1: "k_force32d", 2: "k_force", 3: "k_force32d", 4: "k_force32s (direct)",
+                5: "k_force32w", 6: "k_static + k_force32w"}
+# Workloads whose configuration fixes the re-sort (interval, curve): the
+# autotuner leaves those two knobs alone there.
+FIXED_SORT = {"clustered_8M": (10, 0), "clustered_1M": (10, 0)}
 
 
 def parse():
@@ -62,6 +78,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--force-variant", type=int, default=-1, help="-1: autotune; else the variant")
     ap.add_argument("--sort-interval", type=int, default=-2, help="-2: autotune/workload default")
+    ap.add_argument("--static-leg", type=int, default=-1,
+                    help="static detection on/off leg; -1: on for the clustered 8M workload")
+    ap.add_argument("--static-steps", type=int, default=100)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default tuning (with the fixed settings), e.g. for a profiler capture")
     args = ap.parse_args()
     if args.settle < 0:
         args.settle = 65 if args.workload == "growth_division_65536" else 50
@@ -101,9 +122,24 @@ def make_workload(name: str, precision: int, static: int, build: bool = True):
     for p in pops or []:
         p.params.detect_static = static
     slots = sum(max(p.n, p.params.capacity) for p in pops) if pops is not None else desc["agents"]
-    desc.update(precision="fp32-force/fp64-position" if precision == 1 else "fp64", static_skip=bool(static),
+    desc.update(static_skip=bool(static),
                 l2="inputs larger than L2 (no flush needed)" if slots > 1_000_000 else "working set inside L2")
     return pops, desc
+
+
+def host_info() -> dict:
+    """Host cores and CPU model (the oracle runs on one of them)."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if model:
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
 
 class ClockSampler:
@@ -198,7 +234,7 @@ def cpu_baseline(name: str):
     s.step(iters)
     dt = time.perf_counter() - t0
     return {"value": pop.n * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-            "seconds": dt}
+            "seconds": dt, **host_info()}
 
 
 def parallelism_of(workload: str, world: int) -> str:
@@ -207,9 +243,14 @@ def parallelism_of(workload: str, world: int) -> str:
     return f"{world} independent replicas" if world > 1 else "1 GPU"
 
 
-def arm_config(desc: dict, parallelism: str, args) -> dict:
-    """The `config` of a JSON line, the same for both arms."""
-    return dict(desc, parallelism=parallelism, settle_iterations=args.settle)
+def arm_config(desc: dict, parallelism: str, precision: str, args) -> dict:
+    """The `config` of a JSON line: the workload (the same for both arms),
+    the arm's parallelism and the precision it computes in."""
+    return dict(desc, parallelism=parallelism, precision=precision, settle_iterations=args.settle)
+
+
+def precision_of(p: int) -> str:
+    return "fp32-force/fp64-position" if p == 1 else "fp64"
 
 
 def reference_arm(args):
@@ -243,10 +284,84 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": arm_config(desc, parallelism_of(args.workload, world), args),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic",
+            "config": arm_config(desc, "1 host core (the oracle, single-threaded)", "fp64 (the oracle)", args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             **host_info()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def settle_static(ctx, n_agents: int, limit: int = 500, window: int = 10, tol: float = 0.005):
+    """Step until the static fraction changes by less than `tol` over
+    `window` iterations (at most `limit` iterations); returns the iterations
+    stepped and the fraction trace."""
+    trace = []
+    done = 0
+    prev = None
+    while done < limit:
+        ctx.step(window)
+        done += window
+        f = ctx.stats(0)["static_agents"] / max(n_agents, 1)
+        trace.append(round(f, 5))
+        if prev is not None and abs(f - prev) < tol:
+            break
+        prev = f
+    return done, trace
+
+
+def timed_steps(ctx, stream, steps: int):
+    """CUDA-event time (ms) of `steps` iterations on the library's stream."""
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def static_leg(args, local: int, tune_knobs: int, fixed: dict):
+    """Static detection on and off on the same input: settle by the rule with
+    detection on, step the detection-off context as many iterations, then
+    time `--static-steps` iterations of each."""
+    import torch
+    from paper_2503_10796_gb300 import binding
+    out = {}
+    ctxs = {}
+    stream = torch.cuda.Stream(device=local)
+    for on in (1, 0):
+        pops, _ = make_workload(args.workload, args.precision, on)
+        p = pops[0]
+        ctxs[on] = (binding.Context([binding.make_params(p.params)], p.n + 1024, device=local,
+                                    stream=stream.cuda_stream), p.n)
+        ctxs[on][0].set_agents(0, p.xyz, p.diameter)
+    ctx_on, n = ctxs[1]
+    settled, trace = settle_static(ctx_on, n)
+    ctx_off, _ = ctxs[0]
+    ctx_off.step(settled)
+    for on in (1, 0):
+        ctx = ctxs[on][0]
+        if fixed:
+            t = ctx.get_tuning()
+            t.update(fixed)
+            ctx.set_tuning(**t)
+        tuning = ctx.autotune(3, tune_knobs) if tune_knobs else None
+        ctx.step(args.warmup)
+        ctx.sync()
+        ms = timed_steps(ctx, stream, args.static_steps)
+        st = ctx.stats(0)
+        out["on" if on else "off"] = {"value": n * args.static_steps / (ms * 1e-3), "ms_per_step": ms / args.static_steps,
+                                      "static_fraction_last_iter": st["static_agents"] / n,
+                                      "tuning": ctx.get_tuning() if tuning is None else tuning}
+    for on in (1, 0):
+        ctxs[on][0].close()
+    return {"settle_rule": "until the static fraction changes by < 0.5% over 10 iterations, at most 500",
+            "settle_iterations": settled, "static_fraction_trace_every_10": trace,
+            "timed_iterations": args.static_steps, "unit": UNIT, **out,
+            "speedup": out["on"]["value"] / out["off"]["value"]}
 
 
 def main():
@@ -284,39 +399,41 @@ def main():
                           stream=stream.cuda_stream)
     for s, p in enumerate(pops):
         ctx.set_agents(s, p.xyz, p.diameter)
-    n_agents = sum(p.n for p in pops)
     if args.settle > 0:
         ctx.step(args.settle)
-    tuning = None
-    if args.force_variant < 0:
-        tuning = ctx.autotune(3)
-    else:
-        ctx.set_tuning(force_variant=args.force_variant,
-                       sort_interval=args.sort_interval if args.sort_interval >= -1 else -1)
-        tuning = ctx.get_tuning()
+    # tuning: the workload's own re-sort settings where its configuration
+    # states them, the autotuner for the rest
+    fixed = {}
+    knobs = binding.TUNE_ALL
+    if args.workload in FIXED_SORT:
+        iv, cv = FIXED_SORT[args.workload]
+        fixed = {"sort_interval": iv, "sort_curve": cv}
+        knobs &= ~(binding.TUNE_INTERVAL | binding.TUNE_CURVE)
+    if args.sort_interval >= -1:
+        fixed["sort_interval"] = args.sort_interval
+        knobs &= ~binding.TUNE_INTERVAL
+    if args.force_variant >= 0:
+        fixed["force_variant"] = args.force_variant
+        knobs &= ~binding.TUNE_FORCE
+    if fixed:
+        t = ctx.get_tuning()
+        t.update(fixed)
+        ctx.set_tuning(**t)
+    tuning = ctx.autotune(3, knobs) if knobs and not args.no_autotune else ctx.get_tuning()
     ctx.step(args.warmup)
     ctx.sync()
-    ctx.profile(True)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     barrier()
-    torch.cuda.synchronize()
     upd0 = sum(ctx.stats(s)["agent_updates"] for s in range(len(pops)))
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ctx.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    c0 = ctx.counters()
+    ms = timed_steps(ctx, stream, args.steps)
     barrier()
-    ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     ctx.sync()
-    prof = ctx.get_profile()
-    ctx.profile(False)
+    c1 = ctx.counters()
     upd1 = sum(ctx.stats(s)["agent_updates"] for s in range(len(pops)))
-    n_agents = sum(ctx.count(s) for s in range(len(pops)))
     updates = float(upd1 - upd0)
     if world > 1:
         t = torch.tensor([ms, updates], device="cuda", dtype=torch.float64)
@@ -327,28 +444,34 @@ def main():
         ms, updates = float(tm.item()), float(tu.item())
     value = updates / (ms * 1e-3)
 
+    # profiled pass of as many iterations: CUDA events around every stage on
+    # the library's stream (stage times, the force kernel's launch duration)
+    n_agents = sum(ctx.count(s) for s in range(len(pops)))
+    st_static = sum(ctx.stats(s)["static_agents"] for s in range(len(pops)))
+    ctx.profile(True)
+    prof_ms = timed_steps(ctx, stream, args.steps)
+    ctx.sync()
+    prof = ctx.get_profile()
+    ctx.profile(False)
+
     # roofline of the force kernel
     f = prof["force"]
     force_ms = f["ms"] / max(f["launches"], 1)
     occupied = 0
-    st_static = 0
     for s in range(len(pops)):
         box, _, _ = ctx.grid(s)
         occupied += int(np.unique(box).size)
-        st_static += ctx.stats(s)["static_agents"]
     prec = args.precision
     alg = ALG_BYTES_AGENT[prec] * (n_agents - st_static) + ALG_BYTES_BOX * occupied
     peak, peak_kind = peaks()
-    variant = (tuning or {}).get("force_variant", 0) if prec == 1 else 2
+    variant = (tuning or {}).get("force_variant", 5) if prec == 1 else 2
     if args.static and variant in (0, 4):
         variant = 1  # the symmetric walks do not run with static detection
-    kernel = FORCE_KERNEL.get(variant, "k_force")
+    kernel = FORCE_KERNEL.get(variant, "k_force") if prec == 1 else "k_force64r"
     traffic = None
     if kernel in FORCE_TRAFFIC_B_PER_AGENT and args.workload.startswith("clustered"):
         traffic = FORCE_TRAFFIC_B_PER_AGENT[kernel] * (n_agents - st_static)
     achieved = alg / (force_ms * 1e-3) / 1e9
-    launches_per_iter = 9 + (1 if any(p.params.sort_interval > 0 for p in pops) else 0) + (
-        1 if any(p.params.growth_rate > 0 for p in pops) else 0)
 
     # end to end through the public API with host buffers: every step moves
     # the current population's positions from pinned host memory to the
@@ -396,6 +519,12 @@ def main():
                "steps": args.e2e_steps, "host_memory": "pinned",
                "per_step": "bdm_update_agents (positions; diameters where agents grow) + bdm_step(1) + "
                            "bdm_get_agents"}
+    ctx.close()
+
+    leg = None
+    want_leg = args.static_leg if args.static_leg >= 0 else int(args.workload == "clustered_8M" and world == 1)
+    if want_leg and len(pops) == 1:
+        leg = static_leg(args, local, knobs, {k: v for k, v in fixed.items() if k != "force_variant"})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -406,21 +535,25 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32-force/f64-position" if prec == 1 else "f64", "data": "synthetic",
-            "config": arm_config(desc, parallelism, args),
+            "config": arm_config(desc, parallelism, precision_of(prec), args),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
                          "peak_source": f"{peak_kind} hbm_gbs", "force_ms_per_launch": force_ms,
-                         "alg_bytes_per_launch": alg},
+                         "alg_bytes_per_launch": alg,
+                         "timing": "CUDA events around the force stage on the library's stream, profiled "
+                                   "pass of as many iterations right after the timed region"},
             "stages_ms_per_iter": {k: v["ms"] / max(v["launches"], 1) for k, v in prof.items() if v["launches"]},
+            "profiled_ms_per_step": prof_ms / args.steps,
             "static_agents_last_iter": st_static,
             "tuning": tuning,
             "clocks": clk,
             "e2e": e2e,
-            "gpu_launches": launches_per_iter * args.steps + math.ceil(args.steps / 256),
+            "gpu_launches": c1["kernels"] - c0["kernels"],
+            "graph_launches": c1["graph_launches"] - c0["graph_launches"],
+            "static_skip_leg": leg,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
 

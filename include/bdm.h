@@ -165,10 +165,12 @@ int bdm_get_grid(bdm_ctx* ctx, int32_t sim, int64_t cap, int64_t* box_id, double
 
 /* Per-agent results of the last iteration of `sim`, by caller ID: the
  * net force (cap x 3; zero for static agents), the number of non-zero pair
- * forces and the static flag.  Any output may be NULL.  Agents created in
- * the last iteration report zeros. */
+ * forces (saturated at 255), the static flag and the number of overlapping
+ * pairs (delta > 0, Eq 4.1; -1 for static agents, which evaluate none).
+ * Any output may be NULL.  Agents created in the last iteration report
+ * zeros (overlaps -1). */
 int bdm_get_forces(bdm_ctx* ctx, int32_t sim, int64_t cap, double* force, int32_t* nnz,
-                   uint8_t* is_static, int64_t* n_out);
+                   uint8_t* is_static, int32_t* overlaps, int64_t* n_out);
 
 /* Caller IDs of `sim` in device storage order (the order that the Morton
  * re-sort arranges). */
@@ -191,63 +193,116 @@ int bdm_get_profile(bdm_ctx* ctx, int64_t launches[BDM_NUM_STAGES], double ms[BD
 /* Net force on each of n spheres, without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc (code recorded inside a CUDA stream capture,
- * allocator-free runtimes, programs that hand out every byte of device
- * memory from their own pool).  It builds the grid of the given positions
+ * cannot call cudaMalloc (allocator-free runtimes, programs that hand out
+ * every byte of device memory from their own pool and cannot have a library
+ * allocate behind their back).  It builds the grid of the given positions
  * and evaluates the force of one iteration exactly as bdm_step does for its
  * first iteration (S0-S4), but it calls no cudaMalloc, cudaFree or
  * allocating library routine: its working memory is one fixed array of
- * about 5 MB in the library's device memory, held by every GPU that loads
+ * about 4.9 MB in the library's device memory, held by every GPU that loads
  * the library until the process exits.
  *
- * params: one parameter set (growth, static and sort fields are ignored).
+ * params: one parameter set (growth, static, sort and capacity fields are
+ * ignored: the first iteration has no static agents).
  * xyz: device pointer, n x 3 doubles, row-major; diameter: device pointer,
  * n doubles; force: device pointer, n x 3 doubles written in row order;
  * nnz: device pointer, n int32 (non-zero pair forces per agent), or NULL.
  * cuda_stream: the stream to run on (NULL: the legacy default stream).
  * The caller owns all four buffers.
  *
- * Limits: n <= 16384 and at most 131072 grid boxes; beyond them the call
- * returns BDM_E_CAPACITY (n too large: before any work; too many boxes:
- * after the run, with force contents undefined).
+ * Limits: n <= 16384, at most 131072 grid boxes and at most 1023 agents in
+ * one box; beyond them the call returns BDM_E_CAPACITY (n too large: before
+ * any work; the others: after the run, with force contents undefined).
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress while that device is current; make that first call
- * before any stream capture.  The call waits for its stream to finish.
+ * cudaGetSymbolAddress while that device is current.  The call waits for
+ * its stream to finish (it reads the device error word before it gathers
+ * the results), so it cannot be recorded into a CUDA stream capture.
  * All calls on a device share the one array: calls that overlap on the GPU
  * race and give undefined results.
  * Errors: BDM_E_INVAL (NULL pointer, n < 0, bad params), BDM_E_CAPACITY,
- * BDM_E_NONFINITE, BDM_E_CUDA. */
+ * BDM_E_NONFINITE (a position not finite, or a diameter not finite and
+ * > 0), BDM_E_CUDA. */
 int bdm_forces_noalloc(const bdm_params* params, int64_t n, const double* xyz, const double* diameter,
                        double* force, int32_t* nnz, void* cuda_stream);
 
 /* Tuning knobs of a context.  None of them changes results beyond the
  * order of floating-point sums over neighbors. */
 typedef struct {
-  int32_t force_variant;   /* force kernel of the FP32 path: 0 symmetric half
-                              stencil, each pair found once and its force added
-                              to both agents (default; 1 stands in when a
-                              simulation detects static agents); 1 direct walk,
-                              rows flattened, pair evaluation deferred; 2 direct
-                              loop, pairs evaluated in the walk; 3 as 1 box by
-                              box; 4 as 0 with every pair evaluated in the walk
-                              (crowded agents). FP64 always direct */
+  int32_t force_variant;   /* force kernel of the FP32 path (the FP64 path always
+                              runs its row kernel): 5 warp candidate stream, the
+                              stencil boxes a sphere can reach laid end to end
+                              and tested 32 at a time (default; half stencil with
+                              each pair's force added to both agents, or the full
+                              stencil when a simulation detects static agents);
+                              6 as 5, but with static detection the static flags
+                              are computed first and the half stencil is kept
+                              (static agents' forces are then computed but
+                              unused); 0 symmetric half-stencil walk, a lane per
+                              agent (1 stands in when a simulation detects static
+                              agents); 1 direct walk, rows flattened, pair
+                              evaluation deferred; 2 direct loop, pairs evaluated
+                              in the walk; 3 as 1 box by box; 4 as 0 with every
+                              pair evaluated in the walk (crowded agents) */
   int32_t sort_interval;   /* -1: every simulation's own sort_interval;
                               >= 0: this re-sort interval for all simulations */
   int32_t sort_curve;      /* order the re-sort gives the storage: 0 Morton order of the
                               boxes (default, §5.4.2); 1 row-major box order */
-  int32_t reserved[5];     /* must be 0 */
+  int32_t box_scale_pct;   /* grid box length in percent of the largest diameter, 100
+                              to 400 (0 = 100), for simulations without static
+                              detection and without a box_length of their own (a
+                              longer box keeps every interaction inside the 27-box
+                              stencil, §4.4.3; the static check's stencil would
+                              change, so those simulations keep the thesis's rule) */
+  int32_t iter_batch;      /* iterations per replayed CUDA graph, 1 to 64 (0 = 1) */
+  int32_t test_flags;      /* test hook, 0 in normal use.  1: the ordered grid scan's
+                              bounded wait looks for a word that nothing writes and
+                              gives up after 64 polls per tile, so that the next
+                              bdm_sync reports BDM_E_TIMEOUT (that iteration's
+                              results are undefined; the context stays usable) */
+  int32_t reserved[2];     /* must be 0 */
 } bdm_tuning;
 
 int bdm_set_tuning(bdm_ctx* ctx, const bdm_tuning* tuning);
 int bdm_get_tuning(bdm_ctx* ctx, bdm_tuning* tuning);
 
+/* Knobs of bdm_autotune. */
+enum {
+  BDM_TUNE_FORCE = 1,     /* force_variant */
+  BDM_TUNE_CURVE = 2,     /* sort_curve */
+  BDM_TUNE_INTERVAL = 4,  /* sort_interval */
+  BDM_TUNE_BOX = 8,       /* box_scale_pct */
+  BDM_TUNE_BATCH = 16,    /* iter_batch */
+  BDM_TUNE_ALL = 31
+};
+
 /* Autotuner (the thesis proposes automatic tuning of performance
  * parameters such as the sorting frequency, §7.1.7): from the current
- * agents, time `iterations` iterations for every force-kernel variant,
- * both storage curves and several re-sort intervals, restoring the saved state after each
- * trial, and keep the fastest setting; *chosen (may be NULL) receives it.
- * The agents' state after the call equals the state before it. */
-int bdm_autotune(bdm_ctx* ctx, int32_t iterations, bdm_tuning* chosen);
+ * agents, time the current setting and then, one knob after another, each
+ * candidate of the knobs selected in `knobs` (BDM_TUNE_* bits; the others
+ * keep their current values): every force-kernel variant, box lengths of
+ * 100, 125 and 150% of the largest diameter, both storage curves, re-sort
+ * intervals 0 (only if no simulation asked for re-sorting), 5, 10 and 25,
+ * and 1, 4 or 10 iterations per graph.  Each trial runs a whole number of
+ * re-sort periods after as many untimed iterations, the saved state is
+ * restored after each trial, and the setting with the shortest time per
+ * iteration is kept; *chosen (may be NULL) receives it.  The agents' state
+ * after the call equals the state before it.  Errors: BDM_E_INVAL
+ * (iterations < 1, unknown knob bits), BDM_E_STATE, BDM_E_NOMEM, latched
+ * device errors. */
+int bdm_autotune(bdm_ctx* ctx, int32_t iterations, int32_t knobs, bdm_tuning* chosen);
+
+/* Launch counters of a context since bdm_create: CUDA graphs replayed by
+ * bdm_step, the kernels they and bdm_step's own table sizing launched, and
+ * the iterations the graphs covered (iterations stepped while profiling is
+ * enabled launch their kernels one by one and are not counted). */
+typedef struct {
+  int64_t graph_launches;
+  int64_t kernels;
+  int64_t graph_iterations;
+  int64_t reserved[5];
+} bdm_counters;
+
+int bdm_get_counters(bdm_ctx* ctx, bdm_counters* out);
 
 /* ---- Soma-clustering slice: diffusion, secretion, chemotaxis ----------
  *

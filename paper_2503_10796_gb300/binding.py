@@ -43,7 +43,17 @@ class BdmStats(C.Structure):
 
 class BdmTuning(C.Structure):
     _fields_ = [("force_variant", C.c_int32), ("sort_interval", C.c_int32), ("sort_curve", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("box_scale_pct", C.c_int32), ("iter_batch", C.c_int32), ("test_flags", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
+
+
+TUNING_FIELDS = ("force_variant", "sort_interval", "sort_curve", "box_scale_pct", "iter_batch", "test_flags")
+TUNE_FORCE, TUNE_CURVE, TUNE_INTERVAL, TUNE_BOX, TUNE_BATCH, TUNE_ALL = 1, 2, 4, 8, 16, 31
+
+
+class BdmCounters(C.Structure):
+    _fields_ = [("graph_launches", C.c_int64), ("kernels", C.c_int64), ("graph_iterations", C.c_int64),
+                ("reserved", C.c_int64 * 5)]
 
 
 class BdmDiffusionGrid(C.Structure):
@@ -64,14 +74,15 @@ SIGNATURES = {
     "bdm_get_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _P(_i64), _i32]),
     "bdm_neighbors": (C.c_int, [_vp, _i32, _dbl, _i64, _vp, _P(_i64)]),
     "bdm_get_grid": (C.c_int, [_vp, _i32, _i64, _vp, _P(_dbl), _P(_i64)]),
-    "bdm_get_forces": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _vp, _P(_i64)]),
+    "bdm_get_forces": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _vp, _vp, _P(_i64)]),
     "bdm_get_storage_order": (C.c_int, [_vp, _i32, _i64, _vp, _P(_i64)]),
     "bdm_get_stats": (C.c_int, [_vp, _i32, _P(BdmStats)]),
     "bdm_profile": (C.c_int, [_vp, _i32]),
     "bdm_get_profile": (C.c_int, [_vp, _P(_i64), _P(_dbl), _P(C.c_char_p)]),
     "bdm_set_tuning": (C.c_int, [_vp, _P(BdmTuning)]),
     "bdm_get_tuning": (C.c_int, [_vp, _P(BdmTuning)]),
-    "bdm_autotune": (C.c_int, [_vp, _i32, _P(BdmTuning)]),
+    "bdm_autotune": (C.c_int, [_vp, _i32, _i32, _P(BdmTuning)]),
+    "bdm_get_counters": (C.c_int, [_vp, _P(BdmCounters)]),
     "bdm_forces_noalloc": (C.c_int, [_P(BdmParams), _i64, _vp, _vp, _vp, _vp, _vp]),
     "bdm_diffuse": (C.c_int, [_vp, _P(BdmDiffusionGrid), _vp, _dbl, _dbl, _dbl, _i32, _i32]),
     "bdm_secrete": (C.c_int, [_vp, _i32, _P(BdmDiffusionGrid), _vp, _dbl, _i32]),
@@ -243,14 +254,21 @@ class Context:
         self._check(self._lib.bdm_get_grid(self._h, sim, n, _dptr(box), ol, dims))
         return box[: st["agents"]], np.array(list(ol)), np.array(list(dims), np.int64)
 
-    def forces(self, sim: int):
+    def forces(self, sim: int, overlaps: bool = False):
+        """Force (n x 3), non-zero pair count and static flag per agent ID of
+        the last iteration; with overlaps=True also the overlapping-pair
+        count (delta > 0; -1 for static agents)."""
         n = C.c_int64()
-        rc = self._lib.bdm_get_forces(self._h, sim, 0, None, None, None, C.byref(n))
+        rc = self._lib.bdm_get_forces(self._h, sim, 0, None, None, None, None, C.byref(n))
         self._check_size_query(rc, n)
         m = max(n.value, 1)
         F = np.empty((m, 3)); nnz = np.empty(m, np.int32); st = np.empty(m, np.uint8)
-        self._check(self._lib.bdm_get_forces(self._h, sim, m, _dptr(F), _dptr(nnz), _dptr(st), C.byref(n)))
+        ov = np.empty(m, np.int32)
+        self._check(self._lib.bdm_get_forces(self._h, sim, m, _dptr(F), _dptr(nnz), _dptr(st), _dptr(ov),
+                                             C.byref(n)))
         k = n.value
+        if overlaps:
+            return F[:k], nnz[:k], st[:k].astype(bool), ov[:k]
         return F[:k], nnz[:k], st[:k].astype(bool)
 
     def storage_order(self, sim: int) -> np.ndarray:
@@ -320,19 +338,28 @@ class Context:
         return state
 
     # -- tuning ------------------------------------------------------------
-    def set_tuning(self, force_variant: int = 0, sort_interval: int = -1, sort_curve: int = 0):
-        t = BdmTuning(int(force_variant), int(sort_interval), int(sort_curve))
+    def set_tuning(self, force_variant: int = 0, sort_interval: int = -1, sort_curve: int = 0,
+                   box_scale_pct: int = 100, iter_batch: int = 1, test_flags: int = 0):
+        t = BdmTuning(int(force_variant), int(sort_interval), int(sort_curve), int(box_scale_pct),
+                      int(iter_batch), int(test_flags))
         self._check(self._lib.bdm_set_tuning(self._h, C.byref(t)))
 
     def get_tuning(self) -> dict:
         t = BdmTuning()
         self._check(self._lib.bdm_get_tuning(self._h, C.byref(t)))
-        return dict(force_variant=t.force_variant, sort_interval=t.sort_interval, sort_curve=t.sort_curve)
+        return {k: getattr(t, k) for k in TUNING_FIELDS}
 
-    def autotune(self, iterations: int = 5) -> dict:
+    def autotune(self, iterations: int = 5, knobs: int = TUNE_ALL) -> dict:
+        """Time the candidates of the knobs selected in `knobs` (TUNE_* bits)
+        and keep the fastest setting (bdm_autotune)."""
         t = BdmTuning()
-        self._check(self._lib.bdm_autotune(self._h, int(iterations), C.byref(t)))
-        return dict(force_variant=t.force_variant, sort_interval=t.sort_interval, sort_curve=t.sort_curve)
+        self._check(self._lib.bdm_autotune(self._h, int(iterations), int(knobs), C.byref(t)))
+        return {k: getattr(t, k) for k in TUNING_FIELDS}
+
+    def counters(self) -> dict:
+        c = BdmCounters()
+        self._check(self._lib.bdm_get_counters(self._h, C.byref(c)))
+        return dict(graph_launches=c.graph_launches, kernels=c.kernels, graph_iterations=c.graph_iterations)
 
     # -- profiling ---------------------------------------------------------
     def profile(self, enable: bool = True):

@@ -40,6 +40,7 @@ constexpr uint64_t kCoordMask = (1ull << kCoordBits) - 1ull;
 // Per-simulation constants (host-written).
 struct SimConst {
   double k, gamma, adherence, max_disp, dt, box_length, growth_rate, divide_volume;
+  double box_scale;           // box length = box_scale x largest diameter when box_length is 0
   float kf, gammaf, adherence2f, max_disp2f, max_dispf, dtf;
   int32_t precision, detect_static, sort_interval, grows;
   uint64_t seed;
@@ -59,6 +60,7 @@ struct SimState {
   float Lh, Ll;               // L as float-float
   float ilh, ill;             // 1/L as float-float
   float marg;                 // conservative margin of the FP32 pair filter
+  float rmaxf;                // largest radius of the iteration, rounded up to FP32
   int32_t same_grid;          // grid equals the previous iteration's
   int32_t valid;              // grid fits the table region
   int32_t has_prev;
@@ -80,8 +82,13 @@ struct Globals {
   int64_t n_cells;            // agents over all simulations
   int64_t n_new;              // agents created in the current division round
   uint32_t tile_ticket;       // scan tiles claimed in this build (reset by k_params)
-  uint32_t pad;
+  uint32_t test_flags;        // TEST_* hooks (host-set; 0 in normal use)
 };
+
+// Test hooks of Globals::test_flags.  TEST_SCAN_TIMEOUT: the ordered scan's
+// look-back waits for a tile word that no tile publishes and gives up after
+// kTestSpin polls, so that a test sees its bounded wait run out.
+enum : uint32_t { TEST_SCAN_TIMEOUT = 1u };
 
 struct Agents {               // storage arrays (per slot)
   double *x, *y, *z, *d, *v;

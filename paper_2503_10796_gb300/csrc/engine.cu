@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -51,9 +52,12 @@ struct bdm_ctx {
   void *d_sort = nullptr;
   size_t sort_bytes = 0;
   int sort_key_bits = 0;
-  int force_variant = 0;     // force kernel variant of the FP32 path (see launch_force)
+  int force_variant = 5;     // force kernel variant of the FP32 path (see launch_force)
   int sort_override = -1;    // -1: per-simulation sort intervals
-  int sort_curve = 0;        // 0: Morton order of boxes; 1: row-major box order     // simulation-rank bits + 3 x bits per box coordinate
+  int sort_curve = 0;        // 0: Morton order of boxes; 1: row-major box order
+  int box_scale_pct = 100;   // box length in % of the largest diameter (simulations without static detection)
+  int iter_batch = 1;        // iterations per replayed graph
+  uint32_t test_flags = 0;   // TEST_* hooks of the device globals
   void *d_grow = nullptr;
   size_t grow_bytes = 0;
   std::vector<void *> allocs;
@@ -64,10 +68,13 @@ struct bdm_ctx {
   std::vector<cudaEvent_t> pool;
   int64_t prof_launches[kStages] = {};
   double prof_ms[kStages] = {};
-  // graph of one iteration
-  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // one iteration by sort_mode
+  // graphs of iteration batches, keyed by the re-sort mode of each of
+  // their iterations; kernel nodes per graph for the launch counter
+  struct Graph { cudaGraphExec_t exec; int64_t kernels; };
+  std::map<std::string, Graph> graphs;
   std::vector<int64_t> h_iter;       // per simulation: iterations since its agents were set
   bool graph_dirty = true;
+  int64_t cnt_graphs = 0, cnt_kernels = 0, cnt_iters = 0;  // bdm_get_counters
   double *d_xfer = nullptr;          // host transfer staging (grow-only)
   size_t xfer_cap = 0;               // doubles
   unsigned long long *d_bad = nullptr; // first invalid input row (input check)
@@ -146,6 +153,7 @@ SimConst make_const(const bdm_params &p) {
   s.box_length = p.box_length;
   s.growth_rate = p.growth_rate;
   s.divide_volume = p.divide_volume;
+  s.box_scale = 1.0;
   s.kf = (float)p.k;
   s.gammaf = (float)p.gamma;
   s.adherence2f = (float)(p.adherence * p.adherence);
@@ -212,12 +220,14 @@ void harvest_events(bdm_ctx *c) {
 // the storage is in ID order); 2: permutation into the cell order at the
 // end of the iteration (every later re-sort: the storage is already sorted
 // and the cells keep its order).
-static int sort_mode(const bdm_ctx *c) {
+// ahead: the iteration `ahead` iterations after the next one.
+static int sort_mode(const bdm_ctx *c, int64_t ahead = 0) {
   if (!c->any_sort) return 0;
   int mode = 0;
   for (int s = 0; s < c->n_sims; ++s) {
     const int iv = c->h_sc[s].sort_interval;
-    if (iv > 0 && c->h_sc[s].base >= 0 && c->h_iter[s] % iv == 0) mode = c->h_iter[s] == 0 ? 1 : (mode ? mode : 2);
+    const int64_t it = c->h_iter[s] + ahead;
+    if (iv > 0 && c->h_sc[s].base >= 0 && it % iv == 0) mode = it == 0 ? 1 : (mode ? mode : 2);
   }
   return mode;
 }
@@ -230,6 +240,10 @@ void launch_iteration(bdm_ctx *c, int sort) {
   launch_bbox(D, st);
   launch_params(D, st, 1);
   stage_end(c);
+  bool any_static = false;
+  for (int s = 0; s < c->n_sims; ++s)
+    if (c->params[s].precision != BDM_PREC_FP64 && c->params[s].detect_static) any_static = true;
+  const ForcePlan pl = plan_force(c->force_variant, any_static);
   stage_begin(c, 1);
   launch_count(D, st, 1);
   stage_end(c);
@@ -242,19 +256,13 @@ void launch_iteration(bdm_ctx *c, int sort) {
   stage_begin(c, 2);
   // the cell order reaches the storage only when this iteration re-sorts
   // into it: only then must it follow the leaders' storage order
-  launch_scan(D, st, 1, (c->any_sort && sort == 2) ? 1 : 0);
+  launch_scan(D, st, 1, ((c->any_sort && sort == 2) || c->test_flags) ? 1 : 0);
   stage_end(c);
-  // the symmetric walk (variant 0) needs every FP32-path simulation to run
-  // without static detection; otherwise the deferred walk (1) stands in
-  int variant = c->force_variant;
-  if (variant == 0 || variant == 4)
-    for (int s = 0; s < c->n_sims; ++s)
-      if (c->params[s].precision != BDM_PREC_FP64 && c->params[s].detect_static) variant = 1;
   stage_begin(c, 3);
-  launch_place(D, st, 1, (variant == 0 || variant == 4) ? 1 : 0);
+  launch_place(D, st, 1, pl.zero_f32 ? 1 : 0);
   stage_end(c);
   stage_begin(c, 4);
-  launch_force(D, st, variant, c->any_fp32, c->any_fp64);
+  launch_force(D, st, pl.variant, c->any_fp32, c->any_fp64, any_static);
   stage_end(c);
   stage_begin(c, 5);
   launch_displace(D, st);
@@ -746,6 +754,36 @@ int bdm_update_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, con
   return BDM_OK;
 }
 
+static void drop_graphs(bdm_ctx *c) {
+  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  c->graphs.clear();
+}
+
+// Capture `modes.size()` iterations (re-sort mode of each) into one graph.
+static int capture_batch(bdm_ctx *c, const std::string &modes, bdm_ctx::Graph *out) {
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(c, e, "beginning graph capture");
+  for (char m : modes) launch_iteration(c, m - '0');
+  e = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "capturing the iteration graph");
+  size_t nn = 0;
+  int64_t kernels = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+      for (size_t k = 0; k < nn; ++k) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+      }
+  }
+  e = cudaGraphInstantiate(&out->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(c, e, "instantiating the iteration graph");
+  out->kernels = kernels;
+  return BDM_OK;
+}
+
 int bdm_step(bdm_ctx *c, int32_t n_iterations) {
   if (!c) return BDM_E_INVAL;
   if (n_iterations < 0) return fail(c, BDM_E_INVAL, "n_iterations < 0");
@@ -760,35 +798,37 @@ int bdm_step(bdm_ctx *c, int32_t n_iterations) {
     if (resized) c->graph_dirty = true;
     rc = reserve_builds(c, chunk);
     if (rc) return rc;
+    c->cnt_kernels += 1;  // the bounding box that sized the table
     if (c->graph_dirty) {
-      for (auto &g : c->gexec)
-        if (g) {
-          cudaGraphExecDestroy(g);
-          g = nullptr;
-        }
+      drop_graphs(c);
       c->graph_dirty = false;
     }
-    for (int i = 0; i < chunk; ++i) {
-      const int srt = sort_mode(c);
+    for (int i = 0; i < chunk;) {
       if (c->profiling) {
-        launch_iteration(c, srt);
-      } else {
-        cudaGraphExec_t &gx = c->gexec[srt];
-        if (!gx) {
-          cudaGraph_t g;
-          cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-          if (e != cudaSuccess) return cuda_fail(c, e, "beginning graph capture");
-          launch_iteration(c, srt);
-          e = cudaStreamEndCapture(c->stream, &g);
-          if (e != cudaSuccess) return cuda_fail(c, e, "capturing the iteration graph");
-          e = cudaGraphInstantiate(&gx, g, 0);
-          cudaGraphDestroy(g);
-          if (e != cudaSuccess) return cuda_fail(c, e, "instantiating the iteration graph");
-        }
-        cudaError_t e = cudaGraphLaunch(gx, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "launching the iteration graph");
+        launch_iteration(c, sort_mode(c));
+        for (int s = 0; s < c->n_sims; ++s) c->h_iter[s] += 1;
+        ++i;
+        continue;
       }
-      for (int s = 0; s < c->n_sims; ++s) c->h_iter[s] += 1;
+      // one graph for the next k iterations, keyed by their re-sort modes
+      const int k = std::min(std::max(c->iter_batch, 1), chunk - i);
+      std::string modes(k, '0');
+      for (int j = 0; j < k; ++j) modes[j] = (char)('0' + sort_mode(c, j));
+      auto it = c->graphs.find(modes);
+      if (it == c->graphs.end()) {
+        if (c->graphs.size() >= 16) drop_graphs(c);
+        bdm_ctx::Graph g{};
+        rc = capture_batch(c, modes, &g);
+        if (rc) return rc;
+        it = c->graphs.emplace(modes, g).first;
+      }
+      cudaError_t e = cudaGraphLaunch(it->second.exec, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "launching the iteration graph");
+      c->cnt_graphs += 1;
+      c->cnt_kernels += it->second.kernels;
+      c->cnt_iters += k;
+      for (int s = 0; s < c->n_sims; ++s) c->h_iter[s] += k;
+      i += k;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "launching an iteration");
@@ -1040,7 +1080,7 @@ int bdm_neighbors(bdm_ctx *c, int32_t sim, double radius, int64_t cap, int64_t *
 }
 
 int bdm_get_forces(bdm_ctx *c, int32_t sim, int64_t cap, double *force, int32_t *nnz, uint8_t *is_static,
-                   int64_t *n_out) {
+                   int32_t *overlaps, int64_t *n_out) {
   int rc = check_sim(c, sim);
   if (rc) return rc;
   rc = latched_error(c);
@@ -1054,21 +1094,24 @@ int bdm_get_forces(bdm_ctx *c, int32_t sim, int64_t cap, double *force, int32_t 
   // cells of the last iteration: [cell_base, cell_base + ncell)
   int64_t n = s.n;
   double *df = nullptr;
-  int32_t *dn = nullptr;
+  int32_t *dn = nullptr, *dv = nullptr;
   uint8_t *ds = nullptr;
   rc = dalloc(c, &df, (size_t)(3 * n), "force buffer");
   if (!rc) rc = dalloc(c, &dn, (size_t)n, "nnz buffer");
   if (!rc) rc = dalloc(c, &ds, (size_t)n, "static buffer");
-  if (rc) { dfree(c, df); dfree(c, dn); dfree(c, ds); return rc; }
+  if (!rc) rc = dalloc(c, &dv, (size_t)n, "overlap buffer");
+  if (rc) { dfree(c, df); dfree(c, dn); dfree(c, ds); dfree(c, dv); return rc; }
   cudaMemsetAsync(df, 0, sizeof(double) * 3 * n, c->stream);
   cudaMemsetAsync(dn, 0, sizeof(int32_t) * n, c->stream);
   cudaMemsetAsync(ds, 0, n, c->stream);
-  if (s.t > 0) launch_gather_forces(c->D, c->stream, sim, s.cell_base, std::min(s.ncell, n), df, dn, ds);
+  cudaMemsetAsync(dv, 0xff, sizeof(int32_t) * n, c->stream);
+  if (s.t > 0) launch_gather_forces(c->D, c->stream, sim, s.cell_base, std::min(s.ncell, n), df, dn, ds, dv);
   if (force) cudaMemcpyAsync(force, df, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream);
   if (nnz) cudaMemcpyAsync(nnz, dn, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream);
   if (is_static) cudaMemcpyAsync(is_static, ds, n, cudaMemcpyDeviceToHost, c->stream);
+  if (overlaps) cudaMemcpyAsync(overlaps, dv, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
-  dfree(c, df); dfree(c, dn); dfree(c, ds);
+  dfree(c, df); dfree(c, dn); dfree(c, ds); dfree(c, dv);
   if (e != cudaSuccess) return cuda_fail(c, e, "reading forces");
   return BDM_OK;
 }
@@ -1148,21 +1191,36 @@ int bdm_get_profile(bdm_ctx *c, int64_t launches[BDM_NUM_STAGES], double ms[BDM_
 
 int bdm_set_tuning(bdm_ctx *c, const bdm_tuning *t) {
   if (!c || !t) return BDM_E_INVAL;
-  if (t->force_variant < 0 || t->force_variant > 4)
-    return fail(c, BDM_E_INVAL, "force_variant must be 0 to 4");
+  if (t->force_variant < 0 || t->force_variant >= kForceVariants)
+    return fail(c, BDM_E_INVAL, "force_variant must be 0 to " + std::to_string(kForceVariants - 1));
   if (t->sort_interval < -1) return fail(c, BDM_E_INVAL, "sort_interval must be >= -1");
   if (t->sort_curve != 0 && t->sort_curve != 1) return fail(c, BDM_E_INVAL, "sort_curve must be 0 or 1");
-  for (int k = 0; k < 5; ++k)
+  if (t->box_scale_pct != 0 && (t->box_scale_pct < 100 || t->box_scale_pct > 400))
+    return fail(c, BDM_E_INVAL, "box_scale_pct must be 0 or 100 to 400");
+  if (t->iter_batch < 0 || t->iter_batch > 64) return fail(c, BDM_E_INVAL, "iter_batch must be 0 to 64");
+  if (t->test_flags != 0 && t->test_flags != (int32_t)TEST_SCAN_TIMEOUT)
+    return fail(c, BDM_E_INVAL, "test_flags must be 0 or 1");
+  for (int k = 0; k < 2; ++k)
     if (t->reserved[k]) return fail(c, BDM_E_INVAL, "reserved fields must be 0");
   cudaStreamSynchronize(c->stream);
   c->force_variant = t->force_variant;
   c->sort_override = t->sort_interval;
   c->sort_curve = t->sort_curve;
+  c->box_scale_pct = t->box_scale_pct ? t->box_scale_pct : 100;
+  c->iter_batch = t->iter_batch ? t->iter_batch : 1;
+  if ((uint32_t)t->test_flags != c->test_flags) {
+    c->test_flags = (uint32_t)t->test_flags;
+    cudaMemcpyAsync(&c->D.g->test_flags, &c->test_flags, sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream);
+  }
   bool any = false;
   for (int s = 0; s < c->n_sims; ++s) {
     int iv = t->sort_interval >= 0 ? t->sort_interval : c->params[s].sort_interval;
     c->h_sc[s].sort_interval = iv;
     if (iv > 0) any = true;
+    // the box length shapes the static check's stencil: only simulations
+    // without static detection (and without a box length of their own) scale it
+    const bool scalable = !c->params[s].detect_static && !(c->params[s].box_length > 0);
+    c->h_sc[s].box_scale = scalable ? c->box_scale_pct / 100.0 : 1.0;
   }
   if (any && !c->d_sort) {
     c->sort_bytes = morton_scratch_bytes(c->max_total);
@@ -1180,6 +1238,18 @@ int bdm_get_tuning(bdm_ctx *c, bdm_tuning *t) {
   t->force_variant = c->force_variant;
   t->sort_interval = c->sort_override;
   t->sort_curve = c->sort_curve;
+  t->box_scale_pct = c->box_scale_pct;
+  t->iter_batch = c->iter_batch;
+  t->test_flags = (int32_t)c->test_flags;
+  return BDM_OK;
+}
+
+int bdm_get_counters(bdm_ctx *c, bdm_counters *out) {
+  if (!c || !out) return BDM_E_INVAL;
+  memset(out, 0, sizeof(*out));
+  out->graph_launches = c->cnt_graphs;
+  out->kernels = c->cnt_kernels;
+  out->graph_iterations = c->cnt_iters;
   return BDM_OK;
 }
 
@@ -1247,8 +1317,9 @@ int timed_trial(bdm_ctx *c, int iters, float *ms) {
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  // one untimed iteration builds the graph and warms the caches
-  int rc = bdm_step(c, 1);
+  // as many untimed iterations first: they capture the graphs the timed
+  // ones replay (the same re-sort pattern comes round) and warm the caches
+  int rc = bdm_step(c, iters);
   if (!rc) {
     cudaEventRecord(a, c->stream);
     rc = bdm_step(c, iters);
@@ -1264,9 +1335,10 @@ int timed_trial(bdm_ctx *c, int iters, float *ms) {
 
 }  // namespace
 
-int bdm_autotune(bdm_ctx *c, int32_t iterations, bdm_tuning *chosen) {
+int bdm_autotune(bdm_ctx *c, int32_t iterations, int32_t knobs, bdm_tuning *chosen) {
   if (!c) return BDM_E_INVAL;
   if (iterations < 1) return fail(c, BDM_E_INVAL, "iterations must be >= 1");
+  if (knobs & ~BDM_TUNE_ALL) return fail(c, BDM_E_INVAL, "unknown knob bits");
   for (int s = 0; s < c->n_sims; ++s)
     if (c->n_set[s] < 0) return fail(c, BDM_E_STATE, "simulation " + std::to_string(s) + " has no agents set");
   int rc = latched_error(c);
@@ -1279,53 +1351,84 @@ int bdm_autotune(bdm_ctx *c, int32_t iterations, bdm_tuning *chosen) {
   if (!rc) rc = snap_copy(c, S, M, true);
   bdm_tuning best;
   bdm_get_tuning(c, &best);
-  float best_ms = 1e30f;
-  std::vector<int> variants = {0};
-  if (c->any_fp32) variants = {0, 1, 2, 3, 4};
-  for (int v : variants) {
-    if (rc) break;
-    bdm_tuning t = best;
-    t.force_variant = v;
-    rc = bdm_set_tuning(c, &t);
+  // every trial runs a whole number of re-sort periods of the longest
+  // interval in play, so that its time per iteration carries the re-sorts
+  int period = 1;
+  for (int s = 0; s < c->n_sims; ++s) period = std::max(period, c->h_sc[s].sort_interval);
+  const auto span = [&](int iv, int batch) {
+    const int p = std::max({iv, period, 1});
+    int n = std::max(iterations, batch);
+    n = (n + p - 1) / p * p;
+    return n;
+  };
+  float best_per = 1e30f;
+  auto trial = [&](const bdm_tuning &t, bool *better) {
+    *better = false;
+    int r = bdm_set_tuning(c, &t);
+    const int n = span(t.sort_interval > 0 ? t.sort_interval : 0, t.iter_batch);
     float ms = 0.f;
-    if (!rc) rc = timed_trial(c, iterations, &ms);
-    if (!rc && ms < best_ms) { best_ms = ms; best.force_variant = v; }
-    if (!rc) rc = snap_copy(c, S, M, false);
-  }
+    if (!r) r = timed_trial(c, n, &ms);
+    if (!r && ms / (float)n < best_per) {
+      best_per = ms / (float)n;
+      *better = true;
+    }
+    if (!r) r = snap_copy(c, S, M, false);
+    return r;
+  };
+  bool better = false;
+  rc = rc ? rc : trial(best, &better);  // the current setting
+  if ((knobs & BDM_TUNE_FORCE) && c->any_fp32)
+    for (int v = 0; v < kForceVariants && !rc; ++v) {
+      if (v == best.force_variant) continue;
+      bdm_tuning t = best;
+      t.force_variant = v;
+      rc = trial(t, &better);
+      if (better) best.force_variant = v;
+    }
+  bool scalable = false;
+  for (int s = 0; s < c->n_sims; ++s)
+    if (!c->params[s].detect_static && !(c->params[s].box_length > 0)) scalable = true;
+  if ((knobs & BDM_TUNE_BOX) && scalable)
+    for (int pct : {100, 125, 150}) {
+      if (rc) break;
+      if (pct == best.box_scale_pct) continue;
+      bdm_tuning t = best;
+      t.box_scale_pct = pct;
+      rc = trial(t, &better);
+      if (better) best.box_scale_pct = pct;
+    }
   // storage curve of the re-sort
-  if (c->any_sort || best.sort_interval > 0) {
+  if ((knobs & BDM_TUNE_CURVE) && (c->any_sort || best.sort_interval > 0))
     for (int cv : {0, 1}) {
       if (rc) break;
       if (cv == best.sort_curve) continue;
       bdm_tuning t = best;
       t.sort_curve = cv;
-      rc = bdm_set_tuning(c, &t);
-      float ms = 0.f;
-      if (!rc) rc = timed_trial(c, iterations, &ms);
-      if (!rc && ms < best_ms) { best_ms = ms; best.sort_curve = cv; }
-      if (!rc) rc = snap_copy(c, S, M, false);
+      rc = trial(t, &better);
+      if (better) best.sort_curve = cv;
     }
-  }
-  // re-sort interval: compare the time per iteration, each trial covering
-  // two re-sorts.  "Never" is a candidate only when no simulation asked for
-  // re-sorting: a short trial cannot see the storage order decay.
-  float best_per = best_ms / (float)iterations;
-  for (int iv : {0, 5, 10, 25}) {
-    if (rc) break;
-    if (iv == best.sort_interval) continue;
-    if (iv == 0 && c->any_sort) continue;
-    bdm_tuning t = best;
-    t.sort_interval = iv;
-    rc = bdm_set_tuning(c, &t);
-    const int n = std::max(iterations, 2 * std::max(iv, 1));
-    float ms = 0.f;
-    if (!rc) rc = timed_trial(c, n, &ms);
-    if (!rc && ms / (float)n < best_per) {
-      best_per = ms / (float)n;
-      best.sort_interval = iv;
+  // re-sort interval.  "Never" is a candidate only when no simulation asked
+  // for re-sorting: a short trial cannot see the storage order decay.
+  if (knobs & BDM_TUNE_INTERVAL)
+    for (int iv : {0, 5, 10, 25}) {
+      if (rc) break;
+      if (iv == best.sort_interval) continue;
+      if (iv == 0 && c->any_sort) continue;
+      bdm_tuning t = best;
+      t.sort_interval = iv;
+      rc = trial(t, &better);
+      if (better) best.sort_interval = iv;
     }
-    if (!rc) rc = snap_copy(c, S, M, false);
-  }
+  // iterations per replayed graph
+  if (knobs & BDM_TUNE_BATCH)
+    for (int k : {1, 4, 10}) {
+      if (rc) break;
+      if (k == best.iter_batch) continue;
+      bdm_tuning t = best;
+      t.iter_batch = k;
+      rc = trial(t, &better);
+      if (better) best.iter_batch = k;
+    }
   int rc2 = bdm_set_tuning(c, &best);
   if (!rc) rc = rc2;
   snap_free(c, S);
@@ -1339,8 +1442,7 @@ void bdm_destroy(bdm_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto &e : c->evs) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : c->pool) cudaEventDestroy(e);
-  for (auto g : c->gexec)
-    if (g) cudaGraphExecDestroy(g);
+  drop_graphs(c);
   for (void *p : c->allocs) cudaFree(p);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -1,68 +1,14 @@
 // S4 pairwise force over the 27-box stencil (Eq 4.1 / Eq 4.2, §4.5.1),
 // S5 displacement (adherence threshold, norm clamp) and the static-agent
-// skip of §5.5.
-//
-// FP32 path.  No FP64 arithmetic per pair: every agent carries its offset
-// inside its own box, w = (x - o) - c L (exact in FP64 when placed), as a
-// float-float pair.  A candidate in the neighbor box at offset dc has the
-// center difference x_i - x_j = (w_i - w_j) - dc L, so the FP32 filter and
-// the float-float refinement only ever see magnitudes below 2L.  Pairs
-// deeper than kFastDelta use the plain FP32 overlap; shallower pairs
-// recompute the overlap as (R^2 - s) / (R + dist) in float-float, which
-// keeps its relative accuracy as delta shrinks.  The float-float numerator
-// carries an absolute error near 1e-12, so when it is within 2^-19 of zero
-// (delta below about 1e-7, a rare pair) the FP64 expression of the
-// definition gives the sign and size of delta instead.
+// skip of §5.5.  The pair arithmetic of both paths is in pair.cuh; the
+// warp candidate-stream kernel of the FP32 path is in force_stream.cu.
 //
 // FP64 path.  The definition, operation by operation, with IEEE FP64
 // intrinsics (no contraction): the pair set and the per-pair forces equal
-// the definition's; only the order of the sum over neighbors differs.
-#include "kernels.cuh"
+// the definition's.
+#include "pair.cuh"
 
 namespace bdm {
-
-constexpr float kFastDelta = 0.5f;
-constexpr float kTinyNum = 0x1p-19f;
-
-__device__ __forceinline__ void ff_diff(float hi_i, float lo_i, float hi_j, float lo_j, float off_h,
-                                        float off_l, float &dh, float &dl) {
-  float s1, e1, s2, e2;
-  two_sum(hi_i, -hi_j, s1, e1);
-  two_sum(s1, -off_h, s2, e2);
-  float l = __fadd_rn(__fadd_rn(e1, e2), __fsub_rn(__fsub_rn(lo_i, lo_j), off_l));
-  fast_two_sum(s2, l, dh, dl);
-}
-
-// Overlap of two spheres from the definition in FP64 (used only to decide
-// pairs whose float-float overlap is within rounding of zero).
-__device__ __noinline__ double exact_delta(const DevCtx &C, int32_t si, int32_t sj) {
-  double dx = __dsub_rn(C.a.x[si], C.a.x[sj]);
-  double dy = __dsub_rn(C.a.y[si], C.a.y[sj]);
-  double dz = __dsub_rn(C.a.z[si], C.a.z[sj]);
-  double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-  double R = __dadd_rn(__dmul_rn(0.5, C.a.d[si]), __dmul_rn(0.5, C.a.d[sj]));
-  return __dsub_rn(R, __dsqrt_rn(s));
-}
-
-// Stencil bounds of a box: neighbor offsets that stay inside the grid.
-struct Stencil {
-  int xlo, xhi, ylo, yhi, zlo, zhi;
-  int cx, cy, cz, d0, d1;
-  const unsigned long long *e;    // this simulation's table words
-};
-
-__device__ __forceinline__ Stencil make_stencil(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t cx,
-                                                int64_t cy, int64_t cz) {
-  Stencil t;
-  t.cx = (int)cx; t.cy = (int)cy; t.cz = (int)cz;
-  t.d0 = (int)s.dims[0]; t.d1 = (int)s.dims[1];
-  const int d2 = (int)s.dims[2];
-  t.xlo = t.cx > 0 ? -1 : 0; t.xhi = t.cx < t.d0 - 1 ? 1 : 0;
-  t.ylo = t.cy > 0 ? -1 : 0; t.yhi = t.cy < t.d1 - 1 ? 1 : 0;
-  t.zlo = t.cz > 0 ? -1 : 0; t.zhi = t.cz < d2 - 1 ? 1 : 0;
-  t.e = C.tab.e + sc.table_base;
-  return t;
-}
 
 // Direct FP32 loop: per stencil box the own offset is shifted into the
 // neighbour box's frame once; per candidate the FP32 filter, and for pairs
@@ -77,7 +23,7 @@ __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, con
   const float kf = sc.kf, gf = sc.gammaf;
   const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
   float fx = 0.f, fy = 0.f, fz = 0.f;
-  uint32_t nnz = 0;
+  uint32_t nnz = 0, ovl = 0, zeros = 0;
   for (int dz = t.zlo; dz <= t.zhi; ++dz) {
     const float fdz = (float)dz;
     const float sz = __fsub_rn(o0.z, __fmul_rn(fdz, Lh));
@@ -156,6 +102,8 @@ __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, con
           const float rr = __fdividef(__fmul_rn(o0.w, q.w), R);
           const float fn = __fsub_rn(__fmul_rn(kf, del), __fmul_rn(gf, sqrtf(__fmul_rn(rr, del))));
           nnz += (fn != 0.f);
+          ++ovl;
+          zeros += (fn == 0.f);
           if (dist > 0.f) {
             const float f = __fdividef(fn, dist);
             fx = __fmaf_rn(f, ux, fx);
@@ -166,66 +114,8 @@ __device__ __forceinline__ void force32(const DevCtx &C, const SimConst &sc, con
       }
     }
   }
-  C.c.f32[p] = make_float4(fx, fy, fz, (float)nnz);
+  C.c.f32[p] = make_float4(fx, fy, fz, (float)(ovl + 65536u * zeros));
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
-}
-
-// Contribution of candidate j (record q, neighbour-box offset (fdx, fdy,
-// fdz)) to the force on p, from the float-float records: the overlap
-// delta = (R^2 - s) / (R + dist) keeps its relative accuracy at any depth,
-// and the FP64 definition decides when the numerator is within rounding of
-// zero.  (One path for every pair: in a warp that evaluates many pairs at
-// once, a plain FP32 path for deep pairs beside it cost more than it saved.)
-// Returns false when the pair does not interact.
-__device__ __forceinline__ bool pair32(const DevCtx &C, int64_t p, const float4 &o0, const float4 &o1, int64_t j,
-                                       const float4 &q, float fdx, float fdy, float fdz, float Lh, float Ll,
-                                       float kf, float gf, float &fx, float &fy, float &fz, uint32_t &nnz) {
-  const float R = __fadd_rn(o0.w, q.w);
-  const float4 q1 = C.c.r1[j];
-  float xh, xl, yh, yl, zh, zl;
-  ff_diff(o0.x, o1.x, q.x, q1.x, __fmul_rn(fdx, Lh), __fmul_rn(fdx, Ll), xh, xl);
-  ff_diff(o0.y, o1.y, q.y, q1.y, __fmul_rn(fdy, Lh), __fmul_rn(fdy, Ll), yh, yl);
-  ff_diff(o0.z, o1.z, q.z, q1.z, __fmul_rn(fdz, Lh), __fmul_rn(fdz, Ll), zh, zl);
-  float p0, e0, p1, e1, p2, e2;
-  two_prod(xh, xh, p0, e0);
-  e0 = __fmaf_rn(__fmul_rn(2.f, xh), xl, e0);
-  two_prod(yh, yh, p1, e1);
-  e1 = __fmaf_rn(__fmul_rn(2.f, yh), yl, e1);
-  two_prod(zh, zh, p2, e2);
-  e2 = __fmaf_rn(__fmul_rn(2.f, zh), zl, e2);
-  float Sa, Sea, Sb, Seb;
-  two_sum(p0, p1, Sa, Sea);
-  two_sum(Sa, p2, Sb, Seb);
-  const float sl = __fadd_rn(__fadd_rn(Sea, Seb), __fadd_rn(__fadd_rn(e0, e1), e2));
-  float sh, sll;
-  fast_two_sum(Sb, sl, sh, sll);
-  float Rh, Rl;
-  two_sum(o0.w, q.w, Rh, Rl);
-  Rl = __fadd_rn(Rl, __fadd_rn(o1.w, q1.w));
-  float Qh, Ql;
-  two_prod(Rh, Rh, Qh, Ql);
-  Ql = __fmaf_rn(__fmul_rn(2.f, Rh), Rl, Ql);
-  const float num = __fadd_rn(__fsub_rn(Qh, sh), __fsub_rn(Ql, sll));
-  const float dist = sqrtf(sh);
-  float del;
-  if (fabsf(num) < kTinyNum) {
-    const double d64 = exact_delta(C, C.c.slot[p], C.c.slot[j]);
-    if (!(d64 > 0.0)) return false;
-    del = (float)d64;
-  } else {
-    if (!(num > 0.f)) return false;
-    del = __fdividef(num, __fadd_rn(Rh, dist));
-  }
-  const float rr = __fdividef(__fmul_rn(o0.w, q.w), R);
-  const float fn = __fsub_rn(__fmul_rn(kf, del), __fmul_rn(gf, sqrtf(__fmul_rn(rr, del))));
-  nnz += (fn != 0.f);
-  if (dist > 0.f) {
-    const float f = __fdividef(fn, dist);
-    fx = __fmaf_rn(f, xh, fx);
-    fy = __fmaf_rn(f, yh, fy);
-    fz = __fmaf_rn(f, zh, fz);
-  }
-  return true;
 }
 
 // Direct loop with deferred pair evaluation.  The stencil walk only filters:
@@ -252,14 +142,14 @@ using SymQueue = HitQueueN<kSymCap>;
 // walk queues rather than test every candidate against it, is skipped here.
 __device__ __forceinline__ void flush_hits(const DevCtx &C, uint32_t p, const float4 &o0, int n, const HitQueue &hq,
                                            float Lh, float Ll, float kf, float gf, float &fx, float &fy, float &fz,
-                                           uint32_t &nnz) {
+                                           uint32_t &nnz, uint32_t &ovl) {
   const float4 o1 = C.c.r1[p];
   for (int k = 0; k < n; ++k) {
     const uint32_t j = hq.j[k][threadIdx.x];
     if (j == p) continue;
     const int b = hq.b[k][threadIdx.x];
     const float fdx = (float)(b % 3 - 1), fdy = (float)((b / 3) % 3 - 1), fdz = (float)(b / 9 - 1);
-    pair32(C, (int64_t)p, o0, o1, (int64_t)j, C.c.r0[j], fdx, fdy, fdz, Lh, Ll, kf, gf, fx, fy, fz, nnz);
+    if (pair32(C, (int64_t)p, o0, o1, (int64_t)j, C.c.r0[j], fdx, fdy, fdz, Lh, Ll, kf, gf, fx, fy, fz, nnz)) ++ovl;
   }
 }
 
@@ -334,23 +224,10 @@ __device__ __forceinline__ void force32_deferred(const DevCtx &C, const SimConst
     force32(C, sc, s, (int64_t)p, cx, cy, cz, stamp);
     return;
   }
-  flush_hits(C, p, o0, n, hq, Lh, s.Ll, sc.kf, sc.gammaf, fx, fy, fz, nnz);
-  C.c.f32[p] = make_float4(fx, fy, fz, (float)nnz);
+  uint32_t ovl = 0;
+  flush_hits(C, p, o0, n, hq, Lh, s.Ll, sc.kf, sc.gammaf, fx, fy, fz, nnz, ovl);
+  C.c.f32[p] = make_float4(fx, fy, fz, (float)(ovl + 65536u * (ovl - nnz)));
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
-}
-
-// Pair force of candidate j on p as a vector (the operations of pair32);
-// false when the pair does not interact.  nz: the scalar force is not zero.
-__device__ __forceinline__ bool pair32_vec(const DevCtx &C, int64_t p, const float4 &o0, const float4 &o1,
-                                           int64_t j, const float4 &q, float fdx, float fdy, float fdz, float Lh,
-                                           float Ll, float kf, float gf, float &gx, float &gy, float &gz,
-                                           bool &nz) {
-  float fx = 0.f, fy = 0.f, fz = 0.f;
-  uint32_t n = 0;
-  const bool hit = pair32(C, p, o0, o1, j, q, fdx, fdy, fdz, Lh, Ll, kf, gf, fx, fy, fz, n);
-  gx = fx; gy = fy; gz = fz;
-  nz = n != 0u;
-  return hit;
 }
 
 // Symmetric half-stencil walk (FP32 path, simulations without static
@@ -366,7 +243,7 @@ __device__ __forceinline__ bool pair32_vec(const DevCtx &C, int64_t p, const flo
 template <bool kQueue>
 __device__ __forceinline__ uint32_t sym_walk(const DevCtx &C, const SimConst &sc, const SimState &s, uint32_t p,
                                              const float4 &o0, const Stencil &t, uint32_t stamp, SymQueue &hq,
-                                             float &fx, float &fy, float &fz, uint32_t &nnz) {
+                                             float &fx, float &fy, float &fz, float &cw) {
   const float Lh = s.Lh;
   const float rw = __fadd_rn(o0.w, s.marg);
   const float4 *__restrict__ r0 = C.c.r0;
@@ -430,8 +307,9 @@ __device__ __forceinline__ uint32_t sym_walk(const DevCtx &C, const SimConst &sc
         if (pair32_vec(C, (int64_t)p, o0, o1, (int64_t)j, qv, fdx, fdy, fdz, Lh, s.Ll, sc.kf, sc.gammaf, gx, gy,
                        gz, nz)) {
           fx = __fadd_rn(fx, gx); fy = __fadd_rn(fy, gy); fz = __fadd_rn(fz, gz);
-          nnz += nz ? 1u : 0u;
-          atomicAdd(&C.c.f32[j], make_float4(-gx, -gy, -gz, nz ? 1.f : 0.f));
+          const float w = pair_count_word(nz);
+          cw = __fadd_rn(cw, w);
+          atomicAdd(&C.c.f32[j], make_float4(-gx, -gy, -gz, w));
         }
       }
     }
@@ -445,7 +323,7 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
   const double k = sc.k, gam = sc.gamma;
   const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
   double fx = 0.0, fy = 0.0, fz = 0.0;
-  uint32_t nnz = 0;
+  uint32_t nnz = 0, ovl = 0;
   for (int dz = t.zlo; dz <= t.zhi; ++dz) {
     for (int dy = t.ylo; dy <= t.yhi; ++dy) {
       const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
@@ -471,6 +349,7 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
           const double adh = __dmul_rn(gam, __dsqrt_rn(__dmul_rn(rr, del)));
           const double fn = __dsub_rn(rep, adh);
           nnz += (fn != 0.0);
+          ++ovl;
           if (dist > 0.0) {
             fx = __dadd_rn(fx, __dmul_rn(fn, __ddiv_rn(ddx, dist)));
             fy = __dadd_rn(fy, __dmul_rn(fn, __ddiv_rn(ddy, dist)));
@@ -480,34 +359,9 @@ __device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, con
       }
     }
   }
-  C.c.f64[p] = make_double4_32a(fx, fy, fz, 0.0);
+  // w: the number of overlapping pairs
+  C.c.f64[p] = make_double4_32a(fx, fy, fz, (double)ovl);
   C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
-}
-
-// Pair force of the FP64 path, the definition operation by operation (Eq.
-// 4.1/4.2 and the unit vector from j to i): false when the pair does not
-// overlap.  nz: the scalar force is not zero.
-__device__ __forceinline__ bool pair64(const double4_32a &o, const double4_32a &q, double k, double gam, double &gx,
-                                       double &gy, double &gz, bool &nz) {
-  const double ddx = __dsub_rn(o.x, q.x), ddy = __dsub_rn(o.y, q.y), ddz = __dsub_rn(o.z, q.z);
-  const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-  const double R = __dadd_rn(o.w, q.w);
-  const double dist = __dsqrt_rn(s2);
-  const double del = __dsub_rn(R, dist);
-  gx = gy = gz = 0.0;
-  nz = false;
-  if (!(del > 0.0)) return false;
-  const double rr = __ddiv_rn(__dmul_rn(o.w, q.w), R);
-  const double rep = __dmul_rn(k, del);
-  const double adh = __dmul_rn(gam, __dsqrt_rn(__dmul_rn(rr, del)));
-  const double fn = __dsub_rn(rep, adh);
-  nz = fn != 0.0;
-  if (dist > 0.0) {
-    gx = __dmul_rn(fn, __ddiv_rn(ddx, dist));
-    gy = __dmul_rn(fn, __ddiv_rn(ddy, dist));
-    gz = __dmul_rn(fn, __ddiv_rn(ddz, dist));
-  }
-  return true;
 }
 
 // FP64 path with a thread per stencil row: 9 threads per agent, 32 agents
@@ -600,7 +454,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
         bool nz;
         if (pair64(o, C.c.r64[j], k, gam, gx, gy, gz, nz)) {
           fx = __dadd_rn(fx, gx); fy = __dadd_rn(fy, gy); fz = __dadd_rn(fz, gz);
-          nnz += nz ? 1u : 0u;
+          nnz += (nz ? 1u : 0u) + (1u << 16);  // non-zero count | overlaps << 16
         }
       }
     }
@@ -645,7 +499,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
         const bool an = __shfl_sync(FULL, nz ? 1 : 0, src & 31) != 0;
         if (src < last && ah) {
           fx = __dadd_rn(fx, ax); fy = __dadd_rn(fy, ay); fz = __dadd_rn(fz, az);
-          nnz += an ? 1u : 0u;
+          nnz += (an ? 1u : 0u) + (1u << 16);
         }
       }
     }
@@ -662,8 +516,9 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
       sz = __dadd_rn(sz, part[threadIdx.x + q][2]);
       sn += pnz[threadIdx.x + q];
     }
-    C.c.f64[p] = make_double4_32a(sx, sy, sz, 0.0);
-    C.c.nnz[p] = (uint8_t)(sn > 255u ? 255u : sn);
+    const uint32_t nz = sn & 0xFFFFu;
+    C.c.f64[p] = make_double4_32a(sx, sy, sz, (double)(sn >> 16));  // w: overlapping pairs
+    C.c.nnz[p] = (uint8_t)(nz > 255u ? 255u : nz);
   }
 }
 
@@ -752,7 +607,7 @@ __device__ __forceinline__ void warp_flush(const DevCtx &C, const SymQueue &hq, 
       bool nz;
       if (pair32_vec(C, po, a0, a1, (int64_t)j, C.c.r0[j], fdx, fdy, fdz, sso.Lh, sso.Ll, sco.kf, sco.gammaf, gx,
                      gy, gz, nz)) {
-        const float w = nz ? 1.f : 0.f;
+        const float w = pair_count_word(nz);
         atomicAdd(&C.c.f32[po], make_float4(gx, gy, gz, w));
         atomicAdd(&C.c.f32[j], make_float4(-gx, -gy, -gz, w));
       }
@@ -783,13 +638,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
     const uint32_t stamp = C.g->stamp & kStampMask;
     const float4 o0 = C.c.r0[p];
     const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    uint32_t nnz = 0;
+    float fx = 0.f, fy = 0.f, fz = 0.f, cw = 0.f;
     const uint32_t n = kDirect ? (uint32_t)kSymCap + 1u
-                               : sym_walk<true>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, nnz);
+                               : sym_walk<true>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, cw);
     if (n > (uint32_t)kSymCap) {
-      sym_walk<false>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, nnz);
-      atomicAdd(&C.c.f32[p], make_float4(fx, fy, fz, (float)nnz));
+      sym_walk<false>(C, sc, s, (uint32_t)p, o0, t, stamp, hq, fx, fy, fz, cw);
+      atomicAdd(&C.c.f32[p], make_float4(fx, fy, fz, cw));
     } else {
       mine = n;
     }
@@ -832,8 +686,10 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
     }
   } else {
     float4 F = C.c.f32[p];
-    // FP32 path: w carries the count of non-zero pair forces
-    C.a.nnz[slot] = (uint8_t)(F.w > 255.f ? 255u : (unsigned)F.w);
+    // FP32 path: w carries the pair counts
+    uint32_t ovl, nz;
+    decode_counts(F.w, ovl, nz);
+    C.a.nnz[slot] = (uint8_t)(nz > 255u ? 255u : nz);
     float f2 = __fmaf_rn(F.z, F.z, __fmaf_rn(F.y, F.y, __fmul_rn(F.x, F.x)));
     bad = !isfinite(f2);
     if (f2 > sc.adherence2f) {
@@ -869,7 +725,17 @@ static inline int force_threads(int64_t n) {
   return t < 32 ? 32 : (t > kThreads ? kThreads : t);
 }
 
-void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64) {
+ForcePlan plan_force(int variant, bool any_static) {
+  ForcePlan pl{variant, false};
+  // the symmetric walks add pair forces to both agents: a static agent's
+  // partner would miss them, so simulations with static detection take the
+  // deferred walk instead of 0 and 4
+  if ((variant == 0 || variant == 4) && any_static) pl.variant = 1;
+  pl.zero_f32 = pl.variant == 0 || pl.variant == 4 || pl.variant == 6 || (pl.variant == 5 && !any_static);
+  return pl;
+}
+
+void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64, bool any_static) {
   const int th = force_threads(C.total_slots);
   const unsigned int nb = blocks_for(C.total_slots, th);
   if (variant == 2) {
@@ -880,6 +746,8 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, 
     if (variant == 0) k_force32s<false><<<nb, th, 0, st>>>(C);
     else if (variant == 4) k_force32s<true><<<nb, th, 0, st>>>(C);
     else if (variant == 3) k_force32d<false><<<nb, th, 0, st>>>(C);
+    else if (variant == 5) launch_force_stream(C, st, any_static ? 1 : 0, th);
+    else if (variant == 6) launch_force_stream(C, st, any_static ? 2 : 0, th);
     else k_force32d<true><<<nb, th, 0, st>>>(C);
   }
   if (has_fp64)

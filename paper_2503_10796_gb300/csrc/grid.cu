@@ -189,7 +189,9 @@ __global__ void k_params(DevCtx C, int32_t step) {
       mx[a] = ord_val(st.bmax[a]);
     }
     double dmax = ord_val(st.dmax);
-    double L = sc.box_length > 0.0 ? sc.box_length : dmax;
+    // box length: the user's value, else the largest diameter (times the
+    // tuned scale, which only simulations without static detection take)
+    double L = sc.box_length > 0.0 ? sc.box_length : (sc.box_scale > 1.0 ? __dmul_rn(dmax, sc.box_scale) : dmax);
     st.L = L;
     bool ok = L > 0.0 && isfinite(L);
     int64_t nb = 1;
@@ -217,6 +219,7 @@ __global__ void k_params(DevCtx C, int32_t step) {
     // FP32 filter margin: truncated hi parts are off by < 1 ulp of values
     // below 2L; differences and squares add a few more ulps.
     st.marg = (float)(L * 0x1p-19) + 0x1p-30f;
+    st.rmaxf = __double2float_ru(__dmul_rn(0.5, dmax));
     if (step) {
       for (int a = 0; a < 3; ++a) { st.prev_o[a] = st.o[a]; st.prev_dims[a] = st.dims[a]; }
       st.prev_L = L;
@@ -394,6 +397,7 @@ __device__ __forceinline__ uint32_t block_exscan_u32(uint32_t v, uint32_t *sh, u
 // never publishes latches ERR_TIMEOUT.  Tile words carry the build's stamp,
 // so they need no clearing between builds.
 constexpr uint32_t kLookSpin = 1u << 20;
+constexpr uint32_t kTestSpin = 64u;  // polls per awaited tile under TEST_SCAN_TIMEOUT
 
 __device__ __forceinline__ void tile_publish(unsigned long long *w, uint32_t stamp, uint32_t state, uint32_t v) {
   *(volatile unsigned long long *)w =
@@ -487,6 +491,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
     // ends the walk, the aggregates before it are added
     const int lane = threadIdx.x;
     uint32_t run = 0;
+    // under the timeout test hook the walk waits for a stamp that no tile of
+    // this build publishes, with a short bound
+    const bool test = (C.g->test_flags & TEST_SCAN_TIMEOUT) != 0u;
+    const uint32_t want = test ? ((stamp + 1u) & kStampMask) : stamp;
+    const uint32_t limit = test ? kTestSpin : kLookSpin;
     if (tile == 0) {
       if (lane == 0) tile_publish(&C.tstat[0], stamp, 2u, agg);
     } else {
@@ -498,11 +507,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
           uint32_t spins = 0;
           for (;;) {
             w = *(volatile unsigned long long *)&C.tstat[j];
-            if ((uint32_t)(w >> 34) == stamp && ((w >> 32) & 3ull) != 0ull) break;
-            if (++spins >= kLookSpin) break;
+            if ((uint32_t)(w >> 34) == want && ((w >> 32) & 3ull) != 0ull) break;
+            if (++spins >= limit) break;
             __nanosleep(32);
           }
-          if (spins >= kLookSpin) {
+          if (spins >= limit) {
             set_err(C.g, ERR_TIMEOUT);
             w = 2ull << 32;  // give up: treat as a prefix of 0
           }

@@ -20,8 +20,22 @@ void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32 = 0);
 // force.cu
 // FP32 path: variant 0 symmetric half stencil (needs the forces zeroed by
 // the placement), 1 deferred walk with rows flattened, 2 direct loop, 3
-// deferred walk box by box.  The FP64 path always runs the direct loop.
-void launch_force(const DevCtx &C, cudaStream_t st, int variant = 0, bool has_fp32 = true, bool has_fp64 = true);
+// deferred walk box by box, 4 as 0 without queue, 5 warp candidate stream
+// (force_stream.cu; half stencil, or the full one when a simulation detects
+// static agents), 6 as 5 with the static flags computed first and the half
+// stencil kept.  The FP64 path runs the row kernel.
+constexpr int kForceVariants = 7;
+struct ForcePlan {
+  int variant;      // variant that runs
+  bool zero_f32;    // the placement must zero the FP32 forces (symmetric walks)
+};
+// any_static: some FP32-path simulation detects static agents
+ForcePlan plan_force(int variant, bool any_static);
+void launch_force(const DevCtx &C, cudaStream_t st, int variant = 0, bool has_fp32 = true, bool has_fp64 = true,
+                  bool any_static = false);
+// force_stream.cu: mode 0 half stencil, 1 full stencil with static skip,
+// 2 static flags first, then the half stencil
+void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads);
 void launch_displace(const DevCtx &C, cudaStream_t st);
 
 // diffusion.cu (soma-clustering slice)
@@ -45,7 +59,7 @@ int64_t launch_pairs(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_bas
 void launch_gather_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, double *xyz,
                           double *diam);
 void launch_gather_forces(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, double *force,
-                          int32_t *nnz, uint8_t *stat);
+                          int32_t *nnz, uint8_t *stat, int32_t *overlaps = nullptr);
 void launch_count_flags(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n,
                         unsigned long long *counts2);
 void launch_set_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, int64_t cap,

@@ -1,13 +1,15 @@
 // One-shot force evaluation that allocates nothing.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA stream
-// capture that a framework records once and replays, allocator-free
-// embedded runtimes, and host programs that own every byte of device
-// memory through their own pool.  bdm_forces_noalloc serves them: it runs
-// the same grid build and force kernels as bdm_step, on caller-owned input
-// and output buffers, with all of its working memory in one file-scope
-// device array of fixed size (below).  Every GPU that loads this library
-// keeps that array until the process exits.
+// Some callers cannot call cudaMalloc: allocator-free embedded runtimes,
+// and host programs that hand out every byte of device memory from their
+// own pool, where an allocation behind their back would fail or break
+// their accounting.  bdm_forces_noalloc serves them: it runs the same grid
+// build and force kernels as bdm_step, on caller-owned input and output
+// buffers, with all of its working memory in one file-scope device array of
+// fixed size (below).  Every GPU that loads this library keeps that array
+// until the process exits.  The call waits for its stream (it reads the
+// device error word before it gathers the results), so it must not be
+// recorded into a CUDA stream capture.
 #include <mutex>
 
 #include "kernels.cuh"
@@ -27,8 +29,8 @@ constexpr size_t oSC = 0;
 constexpr size_t oSS = oSC + up(sizeof(SimConst));
 constexpr size_t oG = oSS + up(sizeof(SimState));
 constexpr size_t oOrder = oG + up(sizeof(Globals));
-constexpr size_t oPart = oOrder + up(sizeof(int32_t));
-constexpr size_t oTstat = oPart + up(2048 * sizeof(uint32_t));
+constexpr size_t oBad = oOrder + up(sizeof(int32_t));
+constexpr size_t oTstat = oBad + up(sizeof(unsigned long long));
 constexpr size_t kTstatWords = kM / 2048 + 2;  // scan tiles of 2,048 slots
 constexpr size_t oAX = oTstat + up(8 * kTstatWords);
 constexpr size_t oAY = oAX + up(8 * kM);
@@ -38,8 +40,7 @@ constexpr size_t oAV = oAD + up(8 * kM);
 constexpr size_t oAId = oAV + up(8 * kM);
 constexpr size_t oASim = oAId + up(4 * kM);
 constexpr size_t oAKey = oASim + up(4 * kM);
-constexpr size_t oAHist = oAKey + up(8 * kM);
-constexpr size_t oARank = oAHist + up(8 * kM);
+constexpr size_t oARank = oAKey + up(8 * kM);
 constexpr size_t oAFlags = oARank + up(4 * kM);
 constexpr size_t oANnz = oAFlags + up(kM);
 constexpr size_t oCSlot = oANnz + up(kM);
@@ -56,7 +57,7 @@ constexpr size_t oCF64 = oCF32 + up(16 * kM);
 constexpr size_t oTab = oCF64 + up(32 * kM);
 constexpr size_t kBytes = oTab + up(8 * (size_t)kMaxBoxes);
 
-// The working memory: about 5 MB per GPU.
+// The working memory: about 4.9 MB per GPU.
 static __device__ __align__(256) unsigned char g_scratch[kBytes];
 
 std::mutex g_mu;
@@ -123,6 +124,7 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   SimConst sc{};
   sc.k = p.k; sc.gamma = p.gamma; sc.adherence = p.adherence; sc.max_disp = p.max_displacement; sc.dt = p.dt;
   sc.box_length = p.box_length;
+  sc.box_scale = 1.0;
   sc.kf = (float)p.k; sc.gammaf = (float)p.gamma;
   sc.adherence2f = (float)(p.adherence * p.adherence);
   sc.max_disp2f = (float)(p.max_displacement * p.max_displacement);
@@ -139,31 +141,38 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   if (e == cudaSuccess) e = cudaMemsetAsync(D.g, 0, sizeof(Globals), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(D.tab.e, 0, sizeof(unsigned long long) * (size_t)kMaxBoxes, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(D.tstat, 0, sizeof(unsigned long long) * kTstatWords, st);
+  unsigned long long *bad = at<unsigned long long>(base, oBad);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0xFF, sizeof(unsigned long long), st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return BDM_E_CUDA;
   }
+  // the first invalid row (non-finite value, diameter not > 0), if any
+  launch_check_input(st, n, xyz, diameter, bad);
   launch_set_agents(D, st, 0, 0, n, n, xyz, diameter);
   launch_bbox(D, st);
   launch_params(D, st, 1);
   launch_count(D, st, 1);
   launch_scan(D, st);
-  // symmetric force walk (forces zeroed by the placement), unless static
-  // agents are detected
-  const int variant = (p.precision != BDM_PREC_FP64 && p.detect_static) ? 1 : 0;
-  launch_place(D, st, 1, variant == 0 ? 1 : 0);
-  launch_force(D, st, variant);
+  // the first iteration has no static agents (every agent is new), so the
+  // symmetric force walk always applies; the placement zeroes its forces
+  launch_place(D, st, 1, 1);
+  launch_force(D, st, 0);
   // The grid's fit is known only on the device: read the error word before
   // the results are gathered into the caller's buffers.
   uint32_t err = 0;
+  unsigned long long first_bad = ~0ull;
   e = cudaMemcpyAsync(&err, &D.g->err, sizeof(err), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&first_bad, bad, sizeof(first_bad), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return BDM_E_CUDA;
   }
-  if (err & (ERR_TABLE | ERR_COORD)) return BDM_E_CAPACITY;
+  if (first_bad != ~0ull) return BDM_E_NONFINITE;
+  // a non-finite input also makes the grid invalid (ERR_COORD): report it first
   if (err & ERR_NONFINITE) return BDM_E_NONFINITE;
+  if (err & (ERR_TABLE | ERR_COORD)) return BDM_E_CAPACITY;
   if (err & ERR_TIMEOUT) return BDM_E_TIMEOUT;
   launch_gather_forces(D, st, 0, 0, n, force, nnz, nullptr);
   e = cudaStreamSynchronize(st);

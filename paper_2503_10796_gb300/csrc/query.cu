@@ -1,7 +1,7 @@
 // Queries and transfers: box index per agent (parity hook of S1), neighbor
 // pairs (§4.4.3 ForEachNeighbor: radius query or overlap query, decided in
 // FP64 exactly as defined), gathers by caller ID, and agent upload.
-#include "kernels.cuh"
+#include "pair.cuh"
 
 namespace bdm {
 
@@ -215,7 +215,7 @@ void launch_gather_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t bas
 }
 
 __global__ void k_gather_forces(DevCtx C, int sim, int64_t cell_base, int64_t n, double *force, int32_t *nnz,
-                                uint8_t *stat) {
+                                uint8_t *stat, int32_t *overlaps) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int64_t p = cell_base + i;
@@ -223,17 +223,21 @@ __global__ void k_gather_forces(DevCtx C, int sim, int64_t cell_base, int64_t n,
   int64_t id = C.a.id[C.c.slot[p]];
   bool st = C.c.stat[p] != 0;
   double f[3] = {0.0, 0.0, 0.0};
-  int32_t nz = 0;
+  int32_t nz = 0, ov = -1;
   if (!st) {
     if (C.sc[sim].precision == BDM_PREC_FP64) {
       double4_32a F = C.c.f64[p];
       f[0] = F.x; f[1] = F.y; f[2] = F.z;
       nz = (int32_t)C.c.nnz[p];
+      ov = (int32_t)F.w;
     } else {
-      // FP32 path: w carries the count of non-zero pair forces
+      // FP32 path: w carries the pair counts
       float4 F = C.c.f32[p];
       f[0] = F.x; f[1] = F.y; f[2] = F.z;
-      nz = (int32_t)(F.w > 255.f ? 255.f : F.w);
+      uint32_t o, z;
+      decode_counts(F.w, o, z);
+      nz = (int32_t)(z > 255u ? 255u : z);
+      ov = (int32_t)o;
     }
   } else {
     nz = (int32_t)C.a.nnz[C.c.slot[p]];
@@ -245,12 +249,13 @@ __global__ void k_gather_forces(DevCtx C, int sim, int64_t cell_base, int64_t n,
   }
   if (nnz) nnz[id] = nz;
   if (stat) stat[id] = st ? 1 : 0;
+  if (overlaps) overlaps[id] = ov;
 }
 
 void launch_gather_forces(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, double *force,
-                          int32_t *nnz, uint8_t *stat) {
+                          int32_t *nnz, uint8_t *stat, int32_t *overlaps) {
   if (n <= 0) return;
-  k_gather_forces<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, sim, cell_base, n, force, nnz, stat);
+  k_gather_forces<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, sim, cell_base, n, force, nnz, stat, overlaps);
 }
 
 __global__ void k_count_flags(DevCtx C, int sim, int64_t cell_base, int64_t n, unsigned long long *counts2) {

@@ -29,7 +29,14 @@ def test_reference_arm_line(orc):
     import bench
     _, desc = bench.make_workload("plain_fp64_4096", 0, 0)
     args = argparse.Namespace(settle=line["config"]["settle_iterations"])
-    assert line["config"] == bench.arm_config(desc, bench.parallelism_of("plain_fp64_4096", 1), args)
+    own = bench.arm_config(desc, bench.parallelism_of("plain_fp64_4096", 1), bench.precision_of(0), args)
+    ref = line["config"]
+    # the same workload; parallelism and precision name what each arm runs
+    assert {k: v for k, v in ref.items() if k not in ("parallelism", "precision")} == \
+        {k: v for k, v in own.items() if k not in ("parallelism", "precision")}
+    assert ref["precision"] == "fp64 (the oracle)" and "host core" in ref["parallelism"]
+    cb = line["cpu_baseline"]
+    assert cb["nproc"] >= 1 and cb["cpu_model"]
 
 
 def test_settle_defaults():

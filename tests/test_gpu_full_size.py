@@ -25,6 +25,7 @@ import numpy as np
 import pytest
 
 from paper_2503_10796_gb300 import workloads
+from tests.pair_counts import check_nnz, overlap_counts
 
 pytestmark = pytest.mark.gpu
 
@@ -73,7 +74,7 @@ def rel_err(F, F0, smag):
     return err
 
 
-def check_region(name, pop, box_gpu, pairs_gpu, F_gpu, nnz_gpu, x_gpu, lo, hi):
+def check_region(name, pop, box_gpu, pairs_gpu, F_gpu, nnz_gpu, ov_gpu, x_gpu, lo, hi):
     """Everything the oracle can fix from one region of the population."""
     import oracle
     ids, core = region_subset(pop.xyz, pop.diameter, lo, hi)
@@ -89,14 +90,16 @@ def check_region(name, pop, box_gpu, pairs_gpu, F_gpu, nnz_gpu, x_gpu, lo, hi):
     want = want[in_core[want[:, 0]] | in_core[want[:, 1]]]
     got = pairs_gpu[in_core[pairs_gpu[:, 0]] | in_core[pairs_gpu[:, 1]]]
     assert got.shape == want.shape and np.array_equal(got, want), name
-    # forces of the core agents
+    # forces of the core agents; their overlap counts from the oracle's pairs
     loc = np.flatnonzero(core)
     F0, nnz0, smag = sub.forces(loc)
     g = ids[loc]
     err = rel_err(F_gpu[g], F0, smag)
     report(name, err)
     assert err.max() <= TOL32, (name, err.max())
-    assert np.mean(nnz_gpu[g] == nnz0) >= 0.999, name
+    sub_pairs = sub.neighbors(-1.0)
+    assert np.array_equal(ov_gpu[g], overlap_counts(ids.size, sub_pairs)[loc]), name
+    check_nnz(nnz_gpu[g], nnz0, loc, pop.xyz[ids], pop.diameter[ids], sub_pairs, pop.params.k, pop.params.gamma)
     # one step: positions of the core agents
     sub.step(1)
     x_o, _, _ = sub.get()
@@ -116,7 +119,7 @@ def test_clustered_8M_full_size(orc):
     dense centre and its flank)."""
     import oracle
     pop = workloads.clustered(sort_interval=10)
-    ctx = make_ctx([pop], force_variant=0, sort_interval=25, sort_curve=1)
+    ctx = make_ctx([pop], force_variant=5, sort_interval=10, sort_curve=0)
     try:
         box_gpu, ol, dims = ctx.grid(0)
         full = oracle.Sim(pop.xyz, pop.diameter, pop.params)
@@ -126,7 +129,7 @@ def test_clustered_8M_full_size(orc):
         pairs_gpu = ctx.neighbors(0, -1.0)
         ctx.step(1)
         ctx.sync()
-        F_gpu, nnz_gpu, st = ctx.forces(0)
+        F_gpu, nnz_gpu, st, ov_gpu = ctx.forces(0, overlaps=True)
         assert not st.any()
         x_gpu, _ = ctx.get_agents(0)
         rng = np.random.default_rng(5)
@@ -136,11 +139,14 @@ def test_clustered_8M_full_size(orc):
         err = rel_err(F_gpu[sample], F0, smag)
         report("clustered_8M sampled", err)
         assert err.max() <= TOL32
-        assert np.mean(nnz_gpu[sample] == nnz0) >= 0.999
+        # every agent's overlap count from the (bit-exact, region-checked)
+        # pair list; nnz of the sample against the oracle
+        assert np.array_equal(ov_gpu, overlap_counts(pop.n, pairs_gpu))
+        check_nnz(nnz_gpu[sample], nnz0, sample, pop.xyz, pop.diameter, pairs_gpu, pop.params.k, pop.params.gamma)
         c = pop.xyz[:131072].mean(axis=0)  # the first cluster's centre
         for name, off in (("clustered_8M centre", 0.0), ("clustered_8M flank", 300.0)):
             lo = c + np.array([off, 0.0, 0.0]) - 100.0
-            check_region(name, pop, box_gpu, pairs_gpu, F_gpu, nnz_gpu, x_gpu, lo, lo + 200.0)
+            check_region(name, pop, box_gpu, pairs_gpu, F_gpu, nnz_gpu, ov_gpu, x_gpu, lo, lo + 200.0)
     finally:
         ctx.close()
 
@@ -149,19 +155,20 @@ def test_uniform_200M_full_size(orc):
     """200M agents at volume fraction 0.3: box indices, pairs, forces and
     positions of a corner region (at the grid origin) and a central one."""
     pop = workloads.uniform_fraction(200_000_000, sort_interval=10)
-    ctx = make_ctx([pop], force_variant=0, sort_interval=-1, sort_curve=1)
+    ctx = make_ctx([pop], force_variant=5, sort_interval=-1, sort_curve=1)
     try:
         box_gpu, ol, dims = ctx.grid(0)
         assert np.array_equal(ol[:3], pop.xyz.min(axis=0)) and ol[3] == pop.diameter.max()
         pairs_gpu = ctx.neighbors(0, -1.0)
         ctx.step(1)
         ctx.sync()
-        F_gpu, nnz_gpu, st = ctx.forces(0)
+        F_gpu, nnz_gpu, st, ov_gpu = ctx.forces(0, overlaps=True)
         assert not st.any()
+        assert np.array_equal(ov_gpu, overlap_counts(pop.n, pairs_gpu))
         x_gpu, _ = ctx.get_agents(0)
         side = float(pop.xyz.max())
         for name, lo in (("uniform_200M corner", ol[:3]), ("uniform_200M centre", np.full(3, side / 2 - 75.0))):
-            check_region(name, pop, box_gpu, pairs_gpu, F_gpu, nnz_gpu, x_gpu, lo, lo + 150.0)
+            check_region(name, pop, box_gpu, pairs_gpu, F_gpu, nnz_gpu, ov_gpu, x_gpu, lo, lo + 150.0)
     finally:
         ctx.close()
 
@@ -171,7 +178,7 @@ def test_batched_sweep_256_full_size(orc):
     and four seeded picks) against the oracle in full."""
     import oracle
     pops = workloads.batched_sweep()
-    ctx = make_ctx(pops, force_variant=0, sort_interval=5, sort_curve=0)
+    ctx = make_ctx(pops, force_variant=5, sort_interval=5, sort_curve=0)
     try:
         sizes = np.array([p.n for p in pops])
         rng = np.random.default_rng(7)
@@ -190,11 +197,12 @@ def test_batched_sweep_256_full_size(orc):
             assert np.array_equal(ol, ool) and np.array_equal(dims, odims) and np.array_equal(box, obox), s
             assert np.array_equal(pairs, o.neighbors(-1.0)), s
             F0, nnz0, smag = o.forces()
-            F, nnz, st = ctx.forces(s)
+            F, nnz, st, ov = ctx.forces(s, overlaps=True)
             err = rel_err(F, F0, smag)
             report(f"batched_sweep_256 sim {s} ({pop.n} agents)", err)
             assert err.max() <= TOL32, s
-            assert np.mean(nnz == nnz0) >= 0.999, s
+            assert np.array_equal(ov, overlap_counts(pop.n, pairs)), s
+            check_nnz(nnz, nnz0, np.arange(pop.n), pop.xyz, pop.diameter, pairs, pop.params.k, pop.params.gamma)
             o.step(1)
             x_o, _, _ = o.get()
             x_g, _ = ctx.get_agents(s)

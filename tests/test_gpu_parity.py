@@ -1,14 +1,19 @@
 """Parity of the sm_103a library (through the C ABI) with the CPU oracle.
 
-Bit-exact: box indices, grid origin/length/dims, neighbor pair sets, nnz in
-the FP64 path.  Forces: |F_gpu - F_oracle| / s_i <= 1e-12 (FP64 path) or
-1e-5 (FP32-force path) with s_i = sum_j (k delta + gamma sqrt(r delta)), the
-magnitude sum of agent i's pair forces.
+Bit-exact: box indices, grid origin/length/dims, neighbor pair sets, the
+per-agent overlap count (pairs with delta > 0) in both paths, nnz in the
+FP64 path (in the FP32 path too, except at the force crossover).  Forces:
+|F_gpu - F_oracle| / s_i <= 1e-12 (FP64 path) or 1e-5 (FP32-force path) with
+s_i = sum_j (k delta + gamma sqrt(r delta)), the magnitude sum of agent i's
+pair forces.
 """
 import numpy as np
 import pytest
 
 from paper_2503_10796_gb300 import workloads
+from tests.pair_counts import check_nnz, overlap_counts
+
+VARIANTS = range(7)
 
 pytestmark = pytest.mark.gpu
 
@@ -139,13 +144,24 @@ def test_neighbor_pairs_bit_exact(orc, k, radius):
     assert np.array_equal(got, want)
 
 
-def check_forces(pop, precision, orc_sim=None):
+def check_counts(pop, ov, nnz, o, nnz0, ids=None):
+    """Overlap counts exact; nnz exact except at the force crossover."""
+    pairs = o.neighbors(-1.0)
+    want = overlap_counts(pop.n, pairs)
+    ids = np.arange(pop.n) if ids is None else ids
+    assert np.array_equal(ov, want[ids]), np.flatnonzero(ov != want[ids])[:10]
+    check_nnz(nnz, nnz0, ids, pop.xyz, pop.diameter, pairs, pop.params.k, pop.params.gamma)
+
+
+def check_forces(pop, precision, orc_sim=None, variant=None):
     ctx = ctx_for(pop, precision=precision)
+    if variant is not None:
+        ctx.set_tuning(force_variant=variant)
     o = orc_sim or orc_for(pop)
     F0, nnz0, smag = o.forces()
     ctx.step(1)
     ctx.sync()
-    F, nnz, st = ctx.forces(0)
+    F, nnz, st, ov = ctx.forces(0, overlaps=True)
     assert not st.any()
     scale = np.maximum(smag, 1e-300)
     err = np.linalg.norm(F - F0, axis=1) / scale
@@ -153,8 +169,7 @@ def check_forces(pop, precision, orc_sim=None):
     assert err.max() <= TOL[precision], (err.max(), np.argmax(err))
     if precision == 0:
         assert np.array_equal(nnz, nnz0)
-    else:
-        assert np.mean(nnz == nnz0) > 0.999
+    check_counts(pop, ov, nnz, o, nnz0)
     return ctx, o, err
 
 
@@ -219,8 +234,8 @@ def test_fp32_error_growth_is_bounded(orc):
     assert all(a <= 1e-2 for _, a, _ in errs)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_cluster_statistics_match_oracle(orc, precision):
+@pytest.mark.parametrize("precision,variant", [(0, 0), (1, 1), (1, 5), (1, 6)])
+def test_cluster_statistics_match_oracle(orc, precision, variant):
     """20 iterations of five dense clusters with static detection on: per
     cluster the radius of gyration, and over all agents the mean contact
     count and the static fraction, within 1% of the oracle's."""
@@ -228,6 +243,7 @@ def test_cluster_statistics_match_oracle(orc, precision):
     p = workloads.SimParams(precision=precision, detect_static=1)
     pop = workloads.Population(base.xyz, base.diameter, p, "clusters_static")
     ctx = ctx_for(pop)
+    ctx.set_tuning(force_variant=variant)
     o = orc_for(pop)
     ctx.step(20)
     o.step(20)
@@ -328,13 +344,15 @@ def test_batched_simulations_match_single_ones(orc):
         np.testing.assert_allclose(a, x_o, rtol=0, atol=1e-3)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_static_skip_matches_no_skip(orc, precision):
+@pytest.mark.parametrize("precision,variant", [(0, 0), (1, 1), (1, 5), (1, 6)])
+def test_static_skip_matches_no_skip(orc, precision, variant):
     from tests.test_oracle_pins import perturbed_scene
     xyz, d = perturbed_scene()
     pop = workloads.Population(xyz, d, workloads.SimParams(dt=0.05, precision=precision))
     on = ctx_for(pop, detect_static=1)
     off = ctx_for(pop, detect_static=0)
+    on.set_tuning(force_variant=variant)
+    off.set_tuning(force_variant=variant)
     o = orc_for(pop, detect_static=1)
     n_static = 0
     for _ in range(15):
@@ -467,35 +485,50 @@ def test_deferred_walk_equals_direct_loop(orc):
                 dense_clump()):
         _, _, smag = orc_for(pop).forces()
         out = []
-        for variant in (1, 0, 2, 3, 4):
+        for variant in (1, 0, 2, 3, 4, 5, 6):
             ctx = ctx_for(pop, precision=1, sort_interval=1)
             ctx.set_tuning(force_variant=variant)
             ctx.step(1)
             ctx.sync()
-            out.append(ctx.forces(0)[:2])
-        F0, nnz0 = out[0]
-        for F, nnz in out[1:]:
+            F, nnz, _, ov = ctx.forces(0, overlaps=True)
+            out.append((F, nnz, ov))
+        F0, nnz0, ov0 = out[0]
+        for F, nnz, ov in out[1:]:
             assert np.array_equal(nnz, nnz0)
+            assert np.array_equal(ov, ov0)
             err = np.linalg.norm(F - F0, axis=1) / np.maximum(smag, 1e-30)
             assert err.max() <= 1e-5, err.max()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def crowded_boxes(n=6000, seed=12):
+    """Many agents per box (about 30, like the late growth workload) and a
+    ragged tail: lanes of the stream kernel with long segments."""
+    rng = np.random.default_rng(seed)
+    xyz = rng.uniform(0.0, 60.0, (n, 3))
+    d = rng.uniform(8.0, 12.0, n)
+    return workloads.Population(xyz, d, workloads.SimParams(precision=1), "crowded")
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_force_variants_match_oracle(orc, variant):
-    """Every force-kernel variant of the FP32 path meets the tolerance."""
+    """Every force-kernel variant of the FP32 path meets the tolerance, with
+    exact overlap counts."""
     for pop in (workloads.plain_fp64(seed=5),
                 workloads.clustered(n_clusters=4, per_cluster=2000, side=500.0, sigma=30.0, seed=1),
-                dense_clump()):
+                dense_clump(), crowded_boxes(),
+                workloads.Population(*workloads.uniform_cube(33, 40.0, seed=2)),
+                workloads.Population(*workloads.uniform_cube(1, 10.0, seed=2))):
         ctx = ctx_for(pop, precision=1, sort_interval=1)
         ctx.set_tuning(force_variant=variant)
         o = orc_for(pop)
         F0, nnz0, smag = o.forces()
         ctx.step(1)
         ctx.sync()
-        F, nnz, _ = ctx.forces(0)
+        F, nnz, _, ov = ctx.forces(0, overlaps=True)
         err = np.linalg.norm(F - F0, axis=1) / np.maximum(smag, 1e-300)
         err[smag == 0] = np.linalg.norm(F[smag == 0], axis=1)
         assert err.max() <= TOL[1], (variant, err.max())
+        check_counts(pop, ov, nnz, o, nnz0)
 
 
 def test_autotune_restores_state(orc):
@@ -506,7 +539,8 @@ def test_autotune_restores_state(orc):
     b.step(3)
     x_before, _ = a.get_agents(0)
     chosen = a.autotune(3)
-    assert chosen["force_variant"] in (0, 1, 2, 3, 4)
+    assert chosen["force_variant"] in VARIANTS
+    assert chosen["sort_interval"] in (-1, 0, 5, 10, 25) and chosen["iter_batch"] in (1, 4, 10)
     x_after, _ = a.get_agents(0)
     assert np.array_equal(x_before, x_after)
     assert a.stats(0)["iterations"] == 3
