@@ -199,7 +199,7 @@ int bdm_get_profile(bdm_ctx* ctx, int64_t launches[BDM_NUM_STAGES], double ms[BD
  * and evaluates the force of one iteration exactly as bdm_step does for its
  * first iteration (S0-S4), but it calls no cudaMalloc, cudaFree or
  * allocating library routine: its working memory is one fixed array of
- * about 4.9 MB in the library's device memory, held by every GPU that loads
+ * about 5 MB in the library's device memory, held by every GPU that loads
  * the library until the process exits.
  *
  * params: one parameter set (growth, static, sort and capacity fields are

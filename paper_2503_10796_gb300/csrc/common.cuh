@@ -83,6 +83,8 @@ struct Globals {
   int64_t n_new;              // agents created in the current division round
   uint32_t tile_ticket;       // scan tiles claimed in this build (reset by k_params)
   uint32_t test_flags;        // TEST_* hooks (host-set; 0 in normal use)
+  uint32_t n_ovf;             // FP64-path agents left to the overflow kernel (reset by k_params)
+  uint32_t pad;
 };
 
 // Test hooks of Globals::test_flags.  TEST_SCAN_TIMEOUT: the ordered scan's
@@ -147,6 +149,7 @@ struct DevCtx {
   int32_t *order;             // simulations in slot-region order (-1 padded)
   unsigned long long *tstat;  // per scan tile: stamp << 34 | state << 32 | sum (look-back)
   uint64_t *qkey;             // per slot: packed box of the last query build (queries only)
+  int32_t *ovf;               // FP64 path: cells with more overlapping partners than the row kernel keeps
   int32_t n_sims;
   int64_t total_slots;
 };

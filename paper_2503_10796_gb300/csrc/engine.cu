@@ -586,6 +586,7 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   }
   if (c->any_fp64) {
     ALLOC(D.c.r64, M, "FP64 records"); ALLOC(D.c.f64, M, "FP64 forces");
+    ALLOC(D.ovf, M, "FP64 overflow list");
   }
 #undef ALLOC
   if (!rc && c->any_sort) {

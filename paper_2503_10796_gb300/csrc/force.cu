@@ -317,231 +317,23 @@ __device__ __forceinline__ uint32_t sym_walk(const DevCtx &C, const SimConst &sc
   return n;
 }
 
-__device__ __forceinline__ void force64(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
-                                        int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
-  const double4_32a o = C.c.r64[p];
-  const double k = sc.k, gam = sc.gamma;
-  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
-  double fx = 0.0, fy = 0.0, fz = 0.0;
-  uint32_t nnz = 0, ovl = 0;
-  for (int dz = t.zlo; dz <= t.zhi; ++dz) {
-    for (int dy = t.ylo; dy <= t.yhi; ++dy) {
-      const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
-                           (uint32_t)t.cx;
-      for (int dx = t.xlo; dx <= t.xhi; ++dx) {
-        const unsigned long long e = t.e[row + dx];
-        const uint32_t cnt = ent_live(e, stamp);
-        if (!cnt) continue;
-        const int64_t j0 = ent_start(e);
-        for (uint32_t m = 0; m < cnt; ++m) {
-          const int64_t j = j0 + m;
-          if (j == p) continue;
-          const double4_32a q = C.c.r64[j];
-          const double ddx = __dsub_rn(o.x, q.x), ddy = __dsub_rn(o.y, q.y), ddz = __dsub_rn(o.z, q.z);
-          const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-          const double R = __dadd_rn(o.w, q.w);
-          if (!(s2 < __dmul_rn(R, R) * 1.0000001)) continue;  // cheap reject far beyond contact
-          const double dist = __dsqrt_rn(s2);
-          const double del = __dsub_rn(R, dist);
-          if (!(del > 0.0)) continue;
-          const double rr = __ddiv_rn(__dmul_rn(o.w, q.w), R);
-          const double rep = __dmul_rn(k, del);
-          const double adh = __dmul_rn(gam, __dsqrt_rn(__dmul_rn(rr, del)));
-          const double fn = __dsub_rn(rep, adh);
-          nnz += (fn != 0.0);
-          ++ovl;
-          if (dist > 0.0) {
-            fx = __dadd_rn(fx, __dmul_rn(fn, __ddiv_rn(ddx, dist)));
-            fy = __dadd_rn(fy, __dmul_rn(fn, __ddiv_rn(ddy, dist)));
-            fz = __dadd_rn(fz, __dmul_rn(fn, __ddiv_rn(ddz, dist)));
-          }
-        }
-      }
-    }
-  }
-  // w: the number of overlapping pairs
-  C.c.f64[p] = make_double4_32a(fx, fy, fz, (double)ovl);
-  C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
-}
-
-// FP64 path with a thread per stencil row: 9 threads per agent, 32 agents
-// per block.  A thread walks its row with the FP32 filter of the FP32 path
-// (box-relative leading parts, a margin above their error, so that every
-// pair that overlaps in FP64 passes) and queues the candidates that pass
-// (in walk order); the warp then evaluates the
-// queued pairs together, one per lane and round, and every thread adds its
-// own pairs' forces in queue order, so that each row sums its pairs in the
-// walk's order.  The FP64 square roots and divisions of a pair run at a
-// small fraction of the FP32 rate on this part; evaluated in the walk they
-// ran once for every candidate step in which any lane of the warp had a
-// partner.  A row with more than kRowCap queued candidates is evaluated
-// again in place.  The agent's first thread adds the nine row sums in row
-// order.
-constexpr int kRowAgents = 32;
-constexpr int kRowThreads = kRowAgents * 9;
-constexpr int kRowCap = 4;
-
-__global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
-  __shared__ double part[kRowThreads][3];
-  __shared__ uint32_t pnz[kRowThreads];
-  __shared__ uint32_t rq[kRowCap][kRowThreads];
-  __shared__ uint8_t skip[kRowAgents];
-  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
-  const int a = threadIdx.x / 9, r = threadIdx.x % 9;
-  const int64_t p = (int64_t)blockIdx.x * kRowAgents + a;
-  bool active = p < C.g->n_cells;
-  const int sim = active ? C.c.sim[p] : 0;
-  const SimConst &sc = C.sc[sim];
-  const SimState &s = C.ss[sim];
-  active = active && s.valid && sc.precision == BDM_PREC_FP64;
-  int64_t cx = 0, cy = 0, cz = 0;
-  if (active) unpack_coords(C.c.pkey[p], cx, cy, cz);
-  const uint32_t stamp = C.g->stamp & kStampMask;
-  if (r == 0) {
-    bool st = false;
-    if (active) {
-      st = is_static_cell(C, sc, s, p, cx, cy, cz, stamp);
-      C.c.stat[p] = st ? 1 : 0;
-    }
-    skip[a] = (!active || st) ? 1 : 0;
-  }
-  __syncthreads();
-  double fx = 0.0, fy = 0.0, fz = 0.0;
-  uint32_t nnz = 0, n = 0;
-  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
-  const int dz = r / 3 - 1, dy = r % 3 - 1;
-  const bool walk = !skip[a] && dz >= t.zlo && dz <= t.zhi && dy >= t.ylo && dy <= t.yhi;
-  const uint32_t row = walk ? ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
-                                  (uint32_t)t.cx
-                            : 0u;
-  double4_32a o = {};
-  if (walk) {
-    o = C.c.r64[p];
-    const float4 o0 = C.c.r0[p];
-    const float Lh = s.Lh, marg = s.marg;
-    const float sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh)), sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
-    for (int dx = t.xlo; dx <= t.xhi; ++dx) {
-      const unsigned long long e = t.e[row + dx];
-      const uint32_t cnt = ent_live(e, stamp);
-      const int64_t j0 = ent_start(e);
-      const float sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
-      for (uint32_t m = 0; m < cnt; ++m) {
-        const int64_t j = j0 + m;
-        if (j == p) continue;
-        const float4 q = C.c.r0[j];
-        const float ddx = __fsub_rn(sx, q.x), ddy = __fsub_rn(sy, q.y), ddz = __fsub_rn(sz, q.z);
-        const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
-        const float Rm = __fadd_rn(__fadd_rn(o0.w, q.w), marg);
-        if (!(s2 < __fmul_rn(Rm, Rm))) continue;
-        if (n < (uint32_t)kRowCap) rq[n][threadIdx.x] = (uint32_t)j;
-        ++n;
-      }
-    }
-  }
-  uint32_t mine = n;
-  if (n > (uint32_t)kRowCap) {
-    // crowded row: evaluate it in place, in walk order
-    mine = 0;
-    const double k = sc.k, gam = sc.gamma;
-    for (int dx = t.xlo; dx <= t.xhi; ++dx) {
-      const unsigned long long e = t.e[row + dx];
-      const uint32_t cnt = ent_live(e, stamp);
-      const int64_t j0 = ent_start(e);
-      for (uint32_t m = 0; m < cnt; ++m) {
-        const int64_t j = j0 + m;
-        if (j == p) continue;
-        double gx, gy, gz;
-        bool nz;
-        if (pair64(o, C.c.r64[j], k, gam, gx, gy, gz, nz)) {
-          fx = __dadd_rn(fx, gx); fy = __dadd_rn(fy, gy); fz = __dadd_rn(fz, gz);
-          nnz += (nz ? 1u : 0u) + (1u << 16);  // non-zero count | overlaps << 16
-        }
-      }
-    }
-  }
-  // warp-wide evaluation of the queues laid end to end
-  {
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
-    uint32_t incl = mine;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, incl, d);
-      if (lane >= d) incl += y;
-    }
-    const uint32_t excl = incl - mine;
-    const uint32_t total = __shfl_sync(FULL, incl, 31);
-    for (uint32_t base = 0; base < total; base += 32) {
-      const uint32_t kk = base + (uint32_t)lane;
-      int ow = 0;  // owner: the first lane whose inclusive prefix exceeds kk
-#pragma unroll
-      for (int step = 16; step; step >>= 1) {
-        const uint32_t v = __shfl_sync(FULL, incl, ow + step - 1);
-        if (v <= kk) ow += step;
-      }
-      const uint32_t ex = __shfl_sync(FULL, excl, ow);
-      double gx = 0.0, gy = 0.0, gz = 0.0;
-      bool nz = false, hit = false;
-      if (kk < total) {
-        const int to = wbase + ow;  // the owner's thread in the block
-        const int64_t po = (int64_t)blockIdx.x * kRowAgents + to / 9;
-        const SimConst &so = C.sc[C.c.sim[po]];
-        hit = pair64(C.c.r64[po], C.c.r64[rq[kk - ex][to]], so.k, so.gamma, gx, gy, gz, nz);
-      }
-      // every owner adds its pairs of this round (consecutive lanes) in order
-      const int first = (int)(excl > base ? excl - base : 0u);
-      const int last = (int)((incl > base ? incl - base : 0u) < 32u ? (incl > base ? incl - base : 0u) : 32u);
-      for (int l = 0; l < kRowCap; ++l) {
-        const int src = first + l;
-        const double ax = __shfl_sync(FULL, gx, src & 31), ay = __shfl_sync(FULL, gy, src & 31),
-                     az = __shfl_sync(FULL, gz, src & 31);
-        const bool ah = __shfl_sync(FULL, hit ? 1 : 0, src & 31) != 0;
-        const bool an = __shfl_sync(FULL, nz ? 1 : 0, src & 31) != 0;
-        if (src < last && ah) {
-          fx = __dadd_rn(fx, ax); fy = __dadd_rn(fy, ay); fz = __dadd_rn(fz, az);
-          nnz += (an ? 1u : 0u) + (1u << 16);
-        }
-      }
-    }
-  }
-  part[threadIdx.x][0] = fx; part[threadIdx.x][1] = fy; part[threadIdx.x][2] = fz;
-  pnz[threadIdx.x] = nnz;
-  __syncthreads();
-  if (r == 0 && !skip[a]) {
-    double sx = 0.0, sy = 0.0, sz = 0.0;
-    uint32_t sn = 0;
-    for (int q = 0; q < 9; ++q) {
-      sx = __dadd_rn(sx, part[threadIdx.x + q][0]);
-      sy = __dadd_rn(sy, part[threadIdx.x + q][1]);
-      sz = __dadd_rn(sz, part[threadIdx.x + q][2]);
-      sn += pnz[threadIdx.x + q];
-    }
-    const uint32_t nz = sn & 0xFFFFu;
-    C.c.f64[p] = make_double4_32a(sx, sy, sz, (double)(sn >> 16));  // w: overlapping pairs
-    C.c.nnz[p] = (uint8_t)(nz > 255u ? 255u : nz);
-  }
-}
-
-// fp64_only: leave FP32-path simulations to another kernel.
-__global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C, int fp64_only) {
+// Direct loop of the FP32 path (FP64-path simulations are left to the
+// kernels of force64.cu).
+__global__ void __launch_bounds__(kThreads, 4) k_force(DevCtx C) {
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
   int sim = C.c.sim[p];
   const SimConst &sc = C.sc[sim];
   const SimState &s = C.ss[sim];
-  if (!s.valid) return;
-  if (fp64_only && sc.precision != BDM_PREC_FP64) return;
+  if (!s.valid || sc.precision == BDM_PREC_FP64) return;
   int64_t cx, cy, cz;
   unpack_coords(C.c.pkey[p], cx, cy, cz);
   uint32_t stamp = C.g->stamp & kStampMask;
   bool st = is_static_cell(C, sc, s, p, cx, cy, cz, stamp);
   C.c.stat[p] = st ? 1 : 0;
   if (st) return;
-  if (sc.precision == BDM_PREC_FP64)
-    force64(C, sc, s, p, cx, cy, cz, stamp);
-  else
-    force32(C, sc, s, p, cx, cy, cz, stamp);
+  force32(C, sc, s, p, cx, cy, cz, stamp);
 }
 
 // FP32-path simulations only, deferred pair evaluation.
@@ -738,20 +530,16 @@ ForcePlan plan_force(int variant, bool any_static) {
 void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64, bool any_static) {
   const int th = force_threads(C.total_slots);
   const unsigned int nb = blocks_for(C.total_slots, th);
-  if (variant == 2) {
-    k_force<<<nb, th, 0, st>>>(C, 0);
-    return;
-  }
   if (has_fp32) {
-    if (variant == 0) k_force32s<false><<<nb, th, 0, st>>>(C);
+    if (variant == 2) k_force<<<nb, th, 0, st>>>(C);
+    else if (variant == 0) k_force32s<false><<<nb, th, 0, st>>>(C);
     else if (variant == 4) k_force32s<true><<<nb, th, 0, st>>>(C);
     else if (variant == 3) k_force32d<false><<<nb, th, 0, st>>>(C);
     else if (variant == 5) launch_force_stream(C, st, any_static ? 1 : 0, th);
     else if (variant == 6) launch_force_stream(C, st, any_static ? 2 : 0, th);
     else k_force32d<true><<<nb, th, 0, st>>>(C);
   }
-  if (has_fp64)
-    k_force64r<<<(unsigned int)((C.total_slots + kRowAgents - 1) / kRowAgents), kRowThreads, 0, st>>>(C);
+  if (has_fp64) launch_force64(C, st);
 }
 
 void launch_displace(const DevCtx &C, cudaStream_t st) {

@@ -233,6 +233,7 @@ __global__ void k_params(DevCtx C, int32_t step) {
   if (threadIdx.x == 0) {
     g->stamp += 1u;
     g->tile_ticket = 0u;
+    g->n_ovf = 0u;
     int64_t cells = 0;
     for (int k = 0; k < C.n_sims; ++k) {
       const int s = C.order[k];

@@ -33,6 +33,8 @@ struct ForcePlan {
 ForcePlan plan_force(int variant, bool any_static);
 void launch_force(const DevCtx &C, cudaStream_t st, int variant = 0, bool has_fp32 = true, bool has_fp64 = true,
                   bool any_static = false);
+// force64.cu: the FP64 path (row kernel, overflow kernel)
+void launch_force64(const DevCtx &C, cudaStream_t st);
 // force_stream.cu: mode 0 half stencil, 1 full stencil with static skip,
 // 2 static flags first, then the half stencil
 void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads);

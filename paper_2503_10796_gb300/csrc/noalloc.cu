@@ -54,10 +54,11 @@ constexpr size_t oCNnz = oCFlag + up(kM);
 constexpr size_t oCStat = oCNnz + up(kM);
 constexpr size_t oCF32 = oCStat + up(kM);
 constexpr size_t oCF64 = oCF32 + up(16 * kM);
-constexpr size_t oTab = oCF64 + up(32 * kM);
+constexpr size_t oOvf = oCF64 + up(32 * kM);
+constexpr size_t oTab = oOvf + up(4 * kM);
 constexpr size_t kBytes = oTab + up(8 * (size_t)kMaxBoxes);
 
-// The working memory: about 4.9 MB per GPU.
+// The working memory: about 5 MB per GPU.
 static __device__ __align__(256) unsigned char g_scratch[kBytes];
 
 std::mutex g_mu;
@@ -117,6 +118,7 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   D.c.flag = at<uint8_t>(base, oCFlag); D.c.nnz = at<uint8_t>(base, oCNnz); D.c.stat = at<uint8_t>(base, oCStat);
   D.c.f32 = at<float4>(base, oCF32); D.c.f64 = at<double4_32a>(base, oCF64);
   D.tab.e = at<unsigned long long>(base, oTab);
+  D.ovf = at<int32_t>(base, oOvf);
   D.tstat = at<unsigned long long>(base, oTstat);
 
   // Constants and cleared state: every call starts from zero, because the

@@ -139,7 +139,7 @@ __device__ __forceinline__ bool pair32_vec(const DevCtx &C, int64_t p, const flo
 // 4.1/4.2 and the unit vector from j to i): false when the pair does not
 // overlap.  nz: the scalar force is not zero.
 __device__ __forceinline__ bool pair64(const double4_32a &o, const double4_32a &q, double k, double gam, double &gx,
-                                       double &gy, double &gz, bool &nz) {
+                                       double &gy, double &gz, bool &nz, bool &dir) {
   const double ddx = __dsub_rn(o.x, q.x), ddy = __dsub_rn(o.y, q.y), ddz = __dsub_rn(o.z, q.z);
   const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
   const double R = __dadd_rn(o.w, q.w);
@@ -147,6 +147,7 @@ __device__ __forceinline__ bool pair64(const double4_32a &o, const double4_32a &
   const double del = __dsub_rn(R, dist);
   gx = gy = gz = 0.0;
   nz = false;
+  dir = dist > 0.0;  // coincident centres: no direction, no force (counted in nnz)
   if (!(del > 0.0)) return false;
   const double rr = __ddiv_rn(__dmul_rn(o.w, q.w), R);
   const double rep = __dmul_rn(k, del);

@@ -362,9 +362,12 @@ def test_static_skip_matches_no_skip(orc, precision, variant):
     a, _ = on.get_agents(0)
     b, _ = off.get_agents(0)
     c, _, _ = o.get()
-    tol = 1e-12 if precision == 0 else 1e-5
-    np.testing.assert_allclose(a, b, rtol=0, atol=tol * 100)
-    np.testing.assert_allclose(a, c, rtol=0, atol=tol * 100)
+    if precision == 0:
+        # FP64 path: on, off and the oracle bit for bit
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+    else:
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-3)
+        np.testing.assert_allclose(a, c, rtol=0, atol=1e-3)
     assert n_static > 0
     assert on.stats(0)["static_agents"] >= 0
 
@@ -645,3 +648,71 @@ def test_update_agents_with_static_detection_and_diameters(orc):
     assert st["origin_len"][3] == d2.max()
     _, gd = on.get_agents(0)
     assert np.array_equal(gd, d2)
+
+
+# ---- FP64 path: bit-exact trajectories -------------------------------------
+# The FP64 path evaluates every definition with IEEE operations in the
+# oracle's order and adds each agent's pair forces in ascending partner ID,
+# so positions, static flags and nnz equal the oracle's bit for bit at every
+# iteration, whatever the storage order.
+
+def fp64_scenes():
+    from tests.test_oracle_pins import perturbed_scene
+    xyz, d = perturbed_scene()
+    base = small_pops()[2]
+    return [
+        ("plain_4096", workloads.plain_fp64()),
+        ("perturbed", workloads.Population(xyz, d, workloads.SimParams(dt=0.05, precision=0))),
+        ("clusters", workloads.Population(base.xyz, base.diameter, workloads.SimParams(precision=0))),
+        ("dense_clump", workloads.Population(dense_clump().xyz, dense_clump().diameter,
+                                             workloads.SimParams(precision=0))),
+    ]
+
+
+@pytest.mark.parametrize("static", [0, 1])
+@pytest.mark.parametrize("sort_interval", [0, 3])
+@pytest.mark.parametrize("scene", range(4))
+def test_fp64_trajectory_bit_exact(orc, static, sort_interval, scene):
+    name, pop = fp64_scenes()[scene]
+    ctx = ctx_for(pop, precision=0, detect_static=static, sort_interval=sort_interval)
+    o = orc_for(pop, detect_static=static)
+    n_static = 0
+    for t in range(16):
+        ctx.step(1)
+        o.step(1)
+        x_g, _ = ctx.get_agents(0)
+        x_o, _, _ = o.get()
+        assert np.array_equal(x_g, x_o), (name, t, np.abs(x_g - x_o).max())
+        F_g, nnz_g, st_g = ctx.forces(0)
+        F_o, _, nnz_o, st_o, _ = o.last()
+        assert np.array_equal(st_g, st_o), (name, t)
+        assert np.array_equal(nnz_g, np.minimum(nnz_o, 255)), (name, t)  # stored saturated at 255
+        assert np.array_equal(F_g, F_o), (name, t)
+        n_static += int(st_g.sum())
+    if static and name in ("perturbed", "clusters"):
+        assert n_static > 0
+    print(f"FP64 BITWISE {name} static={static} sort={sort_interval}: 16 iterations, {n_static} static agent-steps")
+
+
+def test_fp64_growth_division_bit_exact(orc):
+    pop = workloads.growth_division(shape=(4, 4, 4), cap_factor=8, precision=0)
+    ctx = ctx_for(pop)
+    o = orc_for(pop)
+    for t in range(45):
+        ctx.step(1)
+        o.step(1)
+        x_g, d_g = ctx.get_agents(0)
+        x_o, d_o, _ = o.get()
+        assert np.array_equal(d_g, d_o) and np.array_equal(x_g, x_o), t
+
+
+def test_fp64_batched_simulations_bit_exact(orc):
+    pops = workloads.batched_sweep(n_sims=5, lo=50, hi=3000, seed=9, precision=0)
+    ctx = ctx_for(pops)
+    ctx.step(8)
+    for s, p in enumerate(pops):
+        o = orc_for(p)
+        o.step(8)
+        x_o, _, _ = o.get()
+        x_g, _ = ctx.get_agents(s)
+        assert np.array_equal(x_g, x_o), s
