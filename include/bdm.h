@@ -128,6 +128,27 @@ int bdm_set_agents(bdm_ctx* ctx, int32_t sim, int64_t n, const double* xyz,
 int bdm_update_agents(bdm_ctx* ctx, int32_t sim, int64_t n, const double* xyz,
                       const double* diameter, int32_t flags);
 
+/* Checkpoint of simulation `sim` for a resume that continues bit for bit
+ * (the thesis backs simulations up at an interval, §4.3.5; this is the state
+ * one iteration reads).  bdm_get_state writes *size_out and, when cap_bytes
+ * is at least that, the state into buf (host memory): a 144-byte header
+ * (the magic "BDMSTATE", version 1, the agent count, the iterations done,
+ * which are also the counter of the division axes' random numbers, the
+ * agent-update counter and the grid of the last iteration) and, by caller
+ * ID, positions, diameters, volumes, the box of the last grid, the changed
+ * and static flags and the non-zero pair counts.  BDM_E_CAPACITY (nothing
+ * written) when cap_bytes is too small, BDM_E_STATE when no agents are set.
+ * bdm_set_state replaces the agents of `sim` by such a state (of this or
+ * another context or simulation; the parameters are the receiving
+ * simulation's): the next iterations then equal, in the FP64 path bit for
+ * bit, those the saved simulation would have run.  Storage order is not part
+ * of the state (the next due re-sort sorts again).  Errors: BDM_E_INVAL (not
+ * a state of this version, size or header inconsistent, an agent value not
+ * finite or a diameter or volume not > 0), BDM_E_CAPACITY (as
+ * bdm_set_agents). */
+int bdm_get_state(bdm_ctx* ctx, int32_t sim, void* buf, int64_t cap_bytes, int64_t* size_out);
+int bdm_set_state(bdm_ctx* ctx, int32_t sim, const void* buf, int64_t size_bytes);
+
 /* Run n_iterations iterations of every simulation (S0-S7), asynchronously
  * on the context's stream.  Errors: BDM_E_STATE (a simulation has no
  * agents set), BDM_E_NOMEM (box table growth failed), BDM_E_CUDA. */

@@ -70,6 +70,8 @@ SIGNATURES = {
     "bdm_set_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _i32]),
     "bdm_update_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _i32]),
     "bdm_step": (C.c_int, [_vp, _i32]),
+    "bdm_get_state": (C.c_int, [_vp, _i32, _vp, _i64, _P(_i64)]),
+    "bdm_set_state": (C.c_int, [_vp, _i32, _vp, _i64]),
     "bdm_sync": (C.c_int, [_vp]),
     "bdm_get_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _P(_i64), _i32]),
     "bdm_neighbors": (C.c_int, [_vp, _i32, _dbl, _i64, _vp, _P(_i64)]),
@@ -199,6 +201,20 @@ class Context:
                 raise ValueError("xyz and diameter differ in length")
         self._check(self._lib.bdm_update_agents(self._h, sim, xyz.shape[0], _dptr(xyz),
                                                 _dptr(d) if d is not None else None, 0))
+
+    def get_state(self, sim: int) -> bytes:
+        """Checkpoint of simulation `sim` (bdm_get_state) as bytes."""
+        n = C.c_int64()
+        rc = self._lib.bdm_get_state(self._h, sim, None, 0, C.byref(n))
+        self._check_size_query(rc, n)
+        buf = C.create_string_buffer(n.value)
+        self._check(self._lib.bdm_get_state(self._h, sim, buf, n.value, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def set_state(self, sim: int, state: bytes):
+        """Replace simulation `sim` by a checkpoint (bdm_set_state)."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        self._check(self._lib.bdm_set_state(self._h, sim, buf, len(state)))
 
     def step(self, iterations: int = 1):
         self._check(self._lib.bdm_step(self._h, int(iterations)))

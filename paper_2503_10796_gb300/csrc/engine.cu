@@ -73,6 +73,7 @@ struct bdm_ctx {
   struct Graph { cudaGraphExec_t exec; int64_t kernels; };
   std::map<std::string, Graph> graphs;
   std::vector<int64_t> h_iter;       // per simulation: iterations since its agents were set
+  std::vector<char> need_radix;      // per simulation: storage not in a sorted order (set, restored)
   bool graph_dirty = true;
   int64_t cnt_graphs = 0, cnt_kernels = 0, cnt_iters = 0;  // bdm_get_counters
   double *d_xfer = nullptr;          // host transfer staging (grow-only)
@@ -220,15 +221,19 @@ void harvest_events(bdm_ctx *c) {
 // the storage is in ID order); 2: permutation into the cell order at the
 // end of the iteration (every later re-sort: the storage is already sorted
 // and the cells keep its order).
-// ahead: the iteration `ahead` iterations after the next one.
-static int sort_mode(const bdm_ctx *c, int64_t ahead = 0) {
+// ahead: the iteration `ahead` iterations after the next one; radix: per
+// simulation, whether its storage still needs the radix sort (after
+// bdm_set_agents or bdm_set_state it is in ID order).  A radix-sort
+// iteration sorts every simulation's storage, so it clears every flag.
+static int sort_mode(const bdm_ctx *c, int64_t ahead, std::vector<char> &radix) {
   if (!c->any_sort) return 0;
   int mode = 0;
   for (int s = 0; s < c->n_sims; ++s) {
     const int iv = c->h_sc[s].sort_interval;
     const int64_t it = c->h_iter[s] + ahead;
-    if (iv > 0 && c->h_sc[s].base >= 0 && it % iv == 0) mode = it == 0 ? 1 : (mode ? mode : 2);
+    if (iv > 0 && c->h_sc[s].base >= 0 && it % iv == 0) mode = (it == 0 || radix[s]) ? 1 : (mode ? mode : 2);
   }
+  if (mode == 1) std::fill(radix.begin(), radix.end(), 0);
   return mode;
 }
 
@@ -541,6 +546,7 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   c->params.assign(per_sim, per_sim + n_sims);
   c->n_set.assign(n_sims, -1);
   c->h_iter.assign(n_sims, 0);
+  c->need_radix.assign(n_sims, 1);
   for (int s = 0; s < n_sims; ++s) {
     c->h_sc.push_back(make_const(per_sim[s]));
     if (per_sim[s].precision == BDM_PREC_FP64) c->any_fp64 = true;
@@ -629,6 +635,45 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   return BDM_OK;
 }
 
+// Region order for the device loops (simulations by slot base).
+static int upload_order(bdm_ctx *c) {
+  std::vector<int32_t> order;
+  for (int s = 0; s < c->n_sims; ++s)
+    if (c->h_sc[s].base >= 0) order.push_back(s);
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return c->h_sc[a].base < c->h_sc[b].base; });
+  while ((int)order.size() < c->n_sims) order.push_back(-1);
+  cudaMemcpyAsync(c->D.order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "uploading the simulation order");
+  return BDM_OK;
+}
+
+// The slot region that simulation `sim` needs for n agents: its current
+// one, grown at the end of the used slots, or a new one.  Nothing is
+// committed here.
+static int plan_region(bdm_ctx *c, int32_t sim, int64_t n, int64_t *base, int64_t *cap, int64_t *used) {
+  const SimConst &sc = c->h_sc[sim];
+  int64_t want = std::max<int64_t>(n, c->params[sim].capacity);
+  if (want < 1) want = 1;
+  *base = sc.base;
+  *cap = sc.cap;
+  *used = c->used_slots;
+  if (*base < 0) {
+    if (*used + want > c->max_total) return fail(c, BDM_E_CAPACITY, "agent capacity of the context exhausted");
+    *base = *used;
+    *cap = want;
+    *used += want;
+  } else if (n > *cap) {
+    if (*base + *cap == *used && *base + want <= c->max_total) {
+      *used = *base + want;
+      *cap = want;
+    } else {
+      return fail(c, BDM_E_CAPACITY, "n exceeds the capacity of this simulation's region");
+    }
+  }
+  return BDM_OK;
+}
+
 // Grow-only staging buffer for host transfers (no allocation per call once
 // it holds the largest population seen).
 static int ensure_xfer(bdm_ctx *c, size_t doubles) {
@@ -651,23 +696,10 @@ int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const 
   if (n < 0 || (n > 0 && (!xyz || !diameter))) return fail(c, BDM_E_INVAL, "n < 0 or NULL input");
   bool dev = (flags & BDM_DEVICE_PTRS) != 0;
   SimConst &sc = c->h_sc[sim];
-  int64_t want = std::max<int64_t>(n, c->params[sim].capacity);
-  if (want < 1) want = 1;
   // the simulation's slot region, committed only once the input is valid
-  int64_t base = sc.base, cap = sc.cap, used = c->used_slots;
-  if (base < 0) {
-    if (used + want > c->max_total) return fail(c, BDM_E_CAPACITY, "agent capacity of the context exhausted");
-    base = used;
-    cap = want;
-    used += want;
-  } else if (n > cap) {
-    if (base + cap == used && base + want <= c->max_total) {
-      used = base + want;
-      cap = want;
-    } else {
-      return fail(c, BDM_E_CAPACITY, "n exceeds the capacity of this simulation's region");
-    }
-  }
+  int64_t base, cap, used;
+  rc = plan_region(c, sim, n, &base, &cap, &used);
+  if (rc) return rc;
   // upload (host input through the context's staging buffer), then check
   // every row on the device before anything of the simulation changes
   const double *dx = xyz, *dd = diameter;
@@ -705,16 +737,8 @@ int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const 
   if (e != cudaSuccess) return cuda_fail(c, e, "uploading agents");
   c->n_set[sim] = n;
   c->h_iter[sim] = 0;
-  // region order for the device loops
-  std::vector<int32_t> order;
-  for (int s = 0; s < c->n_sims; ++s)
-    if (c->h_sc[s].base >= 0) order.push_back(s);
-  std::sort(order.begin(), order.end(), [&](int a, int b) { return c->h_sc[a].base < c->h_sc[b].base; });
-  while ((int)order.size() < c->n_sims) order.push_back(-1);
-  cudaMemcpyAsync(c->D.order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, c->stream);
-  e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "uploading agents");
-  return BDM_OK;
+  c->need_radix[sim] = 1;
+  return upload_order(c);
 }
 
 int bdm_update_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const double *diameter, int32_t flags) {
@@ -785,6 +809,132 @@ static int capture_batch(bdm_ctx *c, const std::string &modes, bdm_ctx::Graph *o
   return BDM_OK;
 }
 
+// ---- checkpoint state ------------------------------------------------------
+// Header of a state blob, followed by the agent arrays by caller ID (see
+// state_array_bytes): x, y, z, diameter, volume (doubles), box key of the
+// last grid (uint64), flags, nnz (bytes).
+namespace {
+constexpr char kStateMagic[8] = {'B', 'D', 'M', 'S', 'T', 'A', 'T', 'E'};
+constexpr uint32_t kStateVersion = 1;
+struct StateHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t header_bytes;
+  int64_t n;                // agents
+  int64_t t;                // iterations completed (the division axes' counter)
+  int64_t updates;          // agent-updates counted since the agents were set
+  int32_t has_prev;         // a grid of the last iteration exists
+  int32_t reserved0;
+  double prev_o[3], prev_L; // that grid
+  int64_t prev_dims[3];
+  int64_t reserved[5];
+};
+static_assert(sizeof(StateHeader) == 144, "state header layout");
+int64_t state_bytes(int64_t n) { return (int64_t)sizeof(StateHeader) + (state_array_bytes(n) + 7) / 8 * 8; }
+}  // namespace
+
+int bdm_get_state(bdm_ctx *c, int32_t sim, void *buf, int64_t cap_bytes, int64_t *size_out) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
+  rc = latched_error(c);
+  if (rc) return rc;
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  const int64_t size = state_bytes(s.n);
+  if (size_out) *size_out = size;
+  if (cap_bytes < size || !buf) return fail(c, BDM_E_CAPACITY, "buffer smaller than the state");
+  StateHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kStateMagic, 8);
+  h.version = kStateVersion;
+  h.header_bytes = (uint32_t)sizeof(StateHeader);
+  h.n = s.n;
+  h.t = s.t;
+  h.updates = (int64_t)s.updates;
+  h.has_prev = s.has_prev;
+  for (int a = 0; a < 3; ++a) { h.prev_o[a] = s.prev_o[a]; h.prev_dims[a] = s.prev_dims[a]; }
+  h.prev_L = s.prev_L;
+  memcpy(buf, &h, sizeof(h));
+  if (s.n > 0) {
+    const int64_t ab = state_array_bytes(s.n);
+    rc = ensure_xfer(c, (size_t)((ab + 7) / 8));
+    if (rc) return rc;
+    launch_state_gather(c->D, c->stream, c->h_sc[sim].base, s.n, c->d_xfer);
+    cudaMemcpyAsync((char *)buf + sizeof(h), c->d_xfer, (size_t)ab, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reading the state");
+  }
+  return BDM_OK;
+}
+
+int bdm_set_state(bdm_ctx *c, int32_t sim, const void *buf, int64_t size_bytes) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  if (!buf || size_bytes < (int64_t)sizeof(StateHeader)) return fail(c, BDM_E_INVAL, "state buffer too small");
+  StateHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (memcmp(h.magic, kStateMagic, 8) != 0 || h.version != kStateVersion || h.header_bytes != sizeof(StateHeader))
+    return fail(c, BDM_E_INVAL, "not a state of this library version");
+  if (h.n < 0 || h.n > (1ll << 31) - 1 || size_bytes != state_bytes(h.n) || h.t < 0 || h.updates < 0 ||
+      (h.has_prev != 0 && h.has_prev != 1))
+    return fail(c, BDM_E_INVAL, "inconsistent state header");
+  if (h.has_prev) {
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(h.prev_o[a]) || h.prev_dims[a] < 1 || h.prev_dims[a] >= (1ll << kCoordBits))
+        return fail(c, BDM_E_INVAL, "inconsistent state header");
+    if (!std::isfinite(h.prev_L) || !(h.prev_L > 0)) return fail(c, BDM_E_INVAL, "inconsistent state header");
+  }
+  rc = latched_error(c);
+  if (rc) return rc;
+  int64_t base, cap, used;
+  rc = plan_region(c, sim, h.n, &base, &cap, &used);
+  if (rc) return rc;
+  const int64_t ab = state_array_bytes(h.n);
+  if (h.n > 0) {
+    rc = ensure_xfer(c, (size_t)((ab + 7) / 8));
+    if (rc) return rc;
+    cudaMemcpyAsync(c->d_xfer, (const char *)buf + sizeof(h), (size_t)ab, cudaMemcpyHostToDevice, c->stream);
+    cudaMemsetAsync(c->d_bad, 0xFF, sizeof(unsigned long long), c->stream);
+    launch_state_check(c->stream, h.n, c->d_xfer, c->d_bad);
+    unsigned long long hb = ~0ull;
+    cudaMemcpyAsync(&hb, c->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "uploading the state");
+    if (hb != ~0ull) return fail(c, BDM_E_INVAL, "invalid agent in the state at row " + std::to_string(hb));
+  }
+  // commit: the region, the agents in ID order, the simulation's counters
+  SimConst &sc = c->h_sc[sim];
+  sc.base = base;
+  sc.cap = cap;
+  c->used_slots = used;
+  if (c->D.total_slots != c->used_slots) c->graph_dirty = true;
+  c->D.total_slots = c->used_slots;
+  upload_consts(c);
+  launch_state_scatter(c->D, c->stream, sim, base, h.n, cap, c->d_xfer);
+  SimState s0;
+  memset(&s0, 0, sizeof(s0));
+  s0.n = h.n;
+  s0.t = h.t;
+  s0.updates = (unsigned long long)h.updates;
+  s0.has_prev = h.has_prev;
+  for (int a = 0; a < 3; ++a) {
+    s0.bmin[a] = ~0ull;
+    s0.bmax[a] = 0ull;
+    s0.prev_o[a] = h.prev_o[a];
+    s0.prev_dims[a] = h.prev_dims[a];
+  }
+  s0.prev_L = h.prev_L;
+  cudaMemcpyAsync(&c->D.ss[sim], &s0, sizeof(SimState), cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "restoring the state");
+  c->n_set[sim] = h.n;
+  c->h_iter[sim] = h.t;
+  c->need_radix[sim] = 1;
+  return upload_order(c);
+}
+
 int bdm_step(bdm_ctx *c, int32_t n_iterations) {
   if (!c) return BDM_E_INVAL;
   if (n_iterations < 0) return fail(c, BDM_E_INVAL, "n_iterations < 0");
@@ -806,7 +956,7 @@ int bdm_step(bdm_ctx *c, int32_t n_iterations) {
     }
     for (int i = 0; i < chunk;) {
       if (c->profiling) {
-        launch_iteration(c, sort_mode(c));
+        launch_iteration(c, sort_mode(c, 0, c->need_radix));
         for (int s = 0; s < c->n_sims; ++s) c->h_iter[s] += 1;
         ++i;
         continue;
@@ -814,7 +964,7 @@ int bdm_step(bdm_ctx *c, int32_t n_iterations) {
       // one graph for the next k iterations, keyed by their re-sort modes
       const int k = std::min(std::max(c->iter_batch, 1), chunk - i);
       std::string modes(k, '0');
-      for (int j = 0; j < k; ++j) modes[j] = (char)('0' + sort_mode(c, j));
+      for (int j = 0; j < k; ++j) modes[j] = (char)('0' + sort_mode(c, j, c->need_radix));
       auto it = c->graphs.find(modes);
       if (it == c->graphs.end()) {
         if (c->graphs.size() >= 16) drop_graphs(c);
@@ -1264,6 +1414,7 @@ struct Snapshot {
   uint8_t *fl = nullptr, *nz = nullptr;
   std::vector<SimState> ss;
   std::vector<int64_t> h_iter;
+  std::vector<char> need_radix;
 };
 
 int snap_alloc(bdm_ctx *c, Snapshot &S, size_t M) {
@@ -1303,10 +1454,12 @@ int snap_copy(bdm_ctx *c, Snapshot &S, size_t M, bool save) {
   if (!e) e = cp(S.nz, A.nnz, M);
   if (save) {
     S.h_iter = c->h_iter;
+    S.need_radix = c->need_radix;
     S.ss.resize(c->n_sims);
     if (!e) e = cudaMemcpyAsync(S.ss.data(), c->D.ss, sizeof(SimState) * c->n_sims, cudaMemcpyDeviceToHost, c->stream);
   } else {
     c->h_iter = S.h_iter;
+    c->need_radix = S.need_radix;
     if (!e) e = cudaMemcpyAsync(c->D.ss, S.ss.data(), sizeof(SimState) * c->n_sims, cudaMemcpyHostToDevice, c->stream);
   }
   if (!e) e = cudaStreamSynchronize(c->stream);

@@ -70,6 +70,14 @@ void launch_update_agents(const DevCtx &C, cudaStream_t st, int64_t base, int64_
                           const double *diam);
 void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, unsigned long long *bad);
 
+// query.cu: checkpoint state arrays (by caller ID) in device staging memory
+int64_t state_array_bytes(int64_t n);
+void launch_state_gather(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, void *staging);
+// first invalid row into *bad (set to ~0 by the caller)
+void launch_state_check(cudaStream_t st, int64_t n, const void *staging, unsigned long long *bad);
+void launch_state_scatter(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, int64_t cap,
+                          const void *staging);
+
 // sort.cu
 void launch_cell_order(const DevCtx &C, cudaStream_t st, void *scratch);
 void launch_morton(const DevCtx &C, cudaStream_t st, void *scratch, size_t scratch_bytes, int key_bits,

@@ -355,4 +355,83 @@ void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const dou
   k_check_input<<<blocks_for(n, kThreads), kThreads, 0, st>>>(n, xyz, diam, bad);
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint state (bdm_get_state / bdm_set_state): per-agent arrays by
+// caller ID, laid out as x, y, z, d, v (doubles), box key (uint64), flags,
+// nnz (bytes), each array n long, in device staging memory.
+// ---------------------------------------------------------------------------
+struct StateArrays {
+  double *x, *y, *z, *d, *v;
+  uint64_t *pkey;
+  uint8_t *flags, *nnz;
+};
+
+__host__ __device__ inline StateArrays state_arrays(void *base, int64_t n) {
+  StateArrays a;
+  char *b = (char *)base;
+  a.x = (double *)b; a.y = a.x + n; a.z = a.y + n; a.d = a.z + n; a.v = a.d + n;
+  a.pkey = (uint64_t *)(a.v + n);
+  a.flags = (uint8_t *)(a.pkey + n);
+  a.nnz = a.flags + n;
+  return a;
+}
+
+int64_t state_array_bytes(int64_t n) { return n * (5 * 8 + 8 + 1 + 1); }
+
+__global__ void k_state_gather(DevCtx C, int64_t base, int64_t n, StateArrays o) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t slot = base + i;
+  const int64_t id = C.a.id[slot];
+  o.x[id] = C.a.x[slot]; o.y[id] = C.a.y[slot]; o.z[id] = C.a.z[slot];
+  o.d[id] = C.a.d[slot]; o.v[id] = C.a.v[slot];
+  o.pkey[id] = C.a.pkey[slot];
+  o.flags[id] = C.a.flags[slot];
+  o.nnz[id] = C.a.nnz[slot];
+}
+
+// Rows in ID order into the slots of `sim` (the rest of its region is
+// marked as owned and empty).
+__global__ void k_state_scatter(DevCtx C, int sim, int64_t base, int64_t n, int64_t cap, StateArrays a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap) return;
+  const int64_t slot = base + i;
+  C.a.sim[slot] = sim;
+  if (i >= n) return;
+  C.a.x[slot] = a.x[i]; C.a.y[slot] = a.y[i]; C.a.z[slot] = a.z[i];
+  C.a.d[slot] = a.d[i]; C.a.v[slot] = a.v[i];
+  C.a.id[slot] = (int32_t)i;
+  C.a.pkey[slot] = a.pkey[i];
+  C.a.flags[slot] = a.flags[i];
+  C.a.nnz[slot] = a.nnz[i];
+  C.a.rank[slot] = 0;
+}
+
+// The first invalid row of restored arrays (a position not finite, a
+// diameter or volume not finite and > 0, a flag outside the defined bits).
+__global__ void k_state_check(int64_t n, StateArrays a, unsigned long long *bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool ok = isfinite(a.x[i]) && isfinite(a.y[i]) && isfinite(a.z[i]) && isfinite(a.d[i]) && a.d[i] > 0.0 &&
+                  isfinite(a.v[i]) && a.v[i] > 0.0 && (a.flags[i] & ~(FLAG_CHANGED | FLAG_STATIC)) == 0;
+  if (!ok) atomicMin(bad, (unsigned long long)i);
+}
+
+void launch_state_gather(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, void *staging) {
+  if (n <= 0) return;
+  k_state_gather<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, state_arrays(staging, n));
+}
+
+void launch_state_check(cudaStream_t st, int64_t n, const void *staging, unsigned long long *bad) {
+  if (n <= 0) return;
+  k_state_check<<<blocks_for(n, kThreads), kThreads, 0, st>>>(n, state_arrays(const_cast<void *>(staging), n), bad);
+}
+
+void launch_state_scatter(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, int64_t cap,
+                          const void *staging) {
+  if (cap <= 0) return;
+  k_state_scatter<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, sim, base, n, cap,
+                                                                  state_arrays(const_cast<void *>(staging), n));
+}
+
 }  // namespace bdm
