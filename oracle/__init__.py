@@ -33,8 +33,9 @@ class OrcParams(C.Structure):
         ("max_displacement", C.c_double), ("dt", C.c_double), ("box_length", C.c_double),
         ("growth_rate", C.c_double), ("divide_volume", C.c_double),
         ("precision", C.c_int32), ("detect_static", C.c_int32),
-        ("sort_interval", C.c_int32), ("reserved", C.c_int32),
+        ("sort_interval", C.c_int32), ("boundary", C.c_int32),
         ("seed", C.c_uint64), ("capacity", C.c_int64),
+        ("bound_min", C.c_double), ("bound_max", C.c_double),
     ]
 
 
@@ -80,6 +81,8 @@ def lib():
         L.orc_forces.argtypes = [C.c_void_p, i64p, C.c_int64, dp, i32p, dp]
         L.orc_step.restype = C.c_int
         L.orc_step.argtypes = [C.c_void_p, C.c_int32]
+        L.orc_remove.restype = C.c_int
+        L.orc_remove.argtypes = [C.c_void_p, C.c_int64, i64p]
         L.orc_neighbors.restype = C.c_int64
         L.orc_neighbors.argtypes = [C.c_void_p, C.c_double, C.c_int64, i64p]
         L.orc_interleave.restype = C.c_uint64
@@ -120,7 +123,8 @@ def make_params(p=None, **kw) -> OrcParams:
     """OrcParams from a ``SimParams``-like object (or keyword overrides)."""
     d = dict(k=2.0, gamma=1.0, adherence=0.4, max_displacement=3.0, dt=0.01,
              box_length=0.0, growth_rate=0.0, divide_volume=0.0, precision=0,
-             detect_static=0, sort_interval=0, seed=0, capacity=0)
+             detect_static=0, sort_interval=0, seed=0, capacity=0, boundary=0,
+             bound_min=0.0, bound_max=0.0)
     if p is not None:
         src = p.as_dict() if hasattr(p, "as_dict") else dict(p)
         for k in d:
@@ -129,8 +133,8 @@ def make_params(p=None, **kw) -> OrcParams:
     d.update(kw)
     return OrcParams(d["k"], d["gamma"], d["adherence"], d["max_displacement"], d["dt"],
                      d["box_length"], d["growth_rate"], d["divide_volume"], int(d["precision"]),
-                     int(d["detect_static"]), int(d["sort_interval"]), 0, int(d["seed"]),
-                     int(d["capacity"]))
+                     int(d["detect_static"]), int(d["sort_interval"]), int(d["boundary"]), int(d["seed"]),
+                     int(d["capacity"]), float(d["bound_min"]), float(d["bound_max"]))
 
 
 class Sim:
@@ -164,6 +168,13 @@ class Sim:
         rc = self._L.orc_step(self._h, int(iterations))
         if rc:
             raise RuntimeError(f"oracle step failed ({rc})")
+
+    def remove(self, ids):
+        """Remove the agents `ids` (the swaps of §5.3.2, see orc_remove)."""
+        ids = np.ascontiguousarray(ids, dtype=np.int64).reshape(-1)
+        rc = self._L.orc_remove(self._h, ids.shape[0], _ptr(ids, C.c_int64))
+        if rc:
+            raise ValueError("oracle rejected the removal (IDs out of range or repeated)")
 
     def get(self):
         n = self.n

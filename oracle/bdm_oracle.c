@@ -29,7 +29,9 @@
  *   4. static-agent detection (§5.5, conditions (i)-(iv));
  *   5. growth and division (Table D.1 GrowthDivision, Cell::Divide), with
  *      the counter-based random numbers proposed in §7.1.4;
- *   6. Morton order of grid boxes by the gap algorithm (§5.4.2, Fig 5.4).
+ *   6. Morton order of grid boxes by the gap algorithm (§5.4.2, Fig 5.4);
+ *   7. the space boundary conditions of §4.4.11 (open, closed, toroidal);
+ *   8. agent removal with the swap of §5.3.2 (Fig 5.1).
  *
  * Readings taken where the thesis is silent (each one is listed with the
  * design notes of the repository):
@@ -47,7 +49,24 @@
  *     >= V_div at the start of t divides after the displacement commit
  *     (daughters V/2, d = cbrt(6V/pi) correctly rounded, mother keeps its
  *     ID and moves by -(d'/4)u, the new agent goes to +(d'/4)u); new IDs are
- *     given in ascending parent-ID order while the count is below capacity.
+ *     given in ascending parent-ID order while the count is below capacity;
+ *   - boundaries: the space is the cube [bound_min, bound_max] on every
+ *     axis.  Closed: every new position (displacement commit, daughter
+ *     placement) is clamped into it per coordinate.  Toroidal: every new
+ *     coordinate v is wrapped into [bound_min, bound_max): v - size when
+ *     v >= bound_max, v + size when v < bound_min, and bound_min if
+ *     rounding leaves it at bound_max; the grid tiles the space exactly with
+ *     n = floor(size / L) >= 3 boxes per axis of length size / n from
+ *     bound_min (n < 3 is an error), neighbour boxes wrap around, and the
+ *     difference of two coordinates is taken as the minimum image: dx =
+ *     x_i - x_j, then dx - size if dx > size / 2, dx + size if dx <
+ *     -size / 2.  Open: the open-space rules above.  An agent pushed by a
+ *     non-zero displacement counts as changed also when a wall stops it;
+ *   - removal: m agents leave, n' = n - m remain; survivors with an ID
+ *     below n' keep it, and the IDs below n' that removed agents held go,
+ *     in ascending order, to the survivors with IDs >= n' in ascending
+ *     order (the swaps of §5.3.2); every survivor then counts as changed for
+ *     one iteration (the removed agents' neighbourhoods changed).
  */
 #include <math.h>
 #include <stdint.h>
@@ -62,10 +81,41 @@ typedef struct {
   int32_t precision;     /* ignored: the oracle always computes in FP64 */
   int32_t detect_static;
   int32_t sort_interval; /* ignored: storage order never changes results */
-  int32_t reserved;
+  int32_t boundary;      /* 0 open, 1 closed, 2 toroidal (§4.4.11) */
   uint64_t seed;
   int64_t capacity;
+  double bound_min, bound_max;  /* the space of closed and toroidal boundaries */
 } orc_params;
+
+enum { ORC_OPEN = 0, ORC_CLOSED = 1, ORC_TORUS = 2 };
+
+/* A new coordinate under the boundary condition (§4.4.11). */
+static double bound_apply(const orc_params *p, double v) {
+  if (p->boundary == ORC_CLOSED) {
+    if (v < p->bound_min) return p->bound_min;
+    if (v > p->bound_max) return p->bound_max;
+    return v;
+  }
+  if (p->boundary == ORC_TORUS) {
+    const double size = p->bound_max - p->bound_min;
+    if (v >= p->bound_max) v = v - size;
+    else if (v < p->bound_min) v = v + size;
+    if (v >= p->bound_max) v = p->bound_min;
+    return v;
+  }
+  return v;
+}
+
+/* Coordinate difference a - b, as the minimum image on a torus. */
+static double coord_diff(const orc_params *p, double a, double b) {
+  double d = a - b;
+  if (p && p->boundary == ORC_TORUS) {
+    const double size = p->bound_max - p->bound_min, half = 0.5 * size;
+    if (d > half) d = d - size;
+    else if (d < -half) d = d + size;
+  }
+  return d;
+}
 
 /* ------------------------------------------------------------------------
  * Uniform grid (§4.4.3, §5.3.1).
@@ -74,6 +124,7 @@ typedef struct {
   double o[3];      /* origin: per-axis minimum of the agent centers */
   double L;         /* box length */
   int64_t dims[3];  /* boxes per axis: floor((max - o) / L) + 1 */
+  int torus;        /* the grid tiles a toroidal space (neighbour boxes wrap) */
   int64_t n;
   int64_t *c;       /* box coordinates, 3 per agent */
   int64_t *box;     /* linear box index c_x + n_x (c_y + n_y c_z) */
@@ -108,25 +159,41 @@ static double grid_box_length(int64_t n, const double *d, double box_length) {
   return L;
 }
 
-/* Build the grid over the snapshot (x, y, z).  Returns 0 on success. */
+/* Build the grid over the snapshot (x, y, z).  Open space: origin and
+ * extent from the agents.  Toroidal space (bp->boundary): the space from
+ * bound_min, n = floor(size / L) >= 3 boxes per axis of length size / n.
+ * Returns 0 on success. */
 static int grid_build(grid_t *g, int64_t n, const double *x, const double *y,
-                      const double *z, double L) {
+                      const double *z, double L, const orc_params *bp) {
   memset(g, 0, sizeof(*g));
   g->n = n;
   g->L = L;
   if (n == 0) { g->dims[0] = g->dims[1] = g->dims[2] = 0; return 0; }
   if (!(L > 0.0) || !isfinite(L)) return -1;
   const double *p[3] = {x, y, z};
-  double mx[3];
-  for (int a = 0; a < 3; ++a) {
-    g->o[a] = p[a][0];
-    mx[a] = p[a][0];
-    for (int64_t i = 1; i < n; ++i) {
-      if (p[a][i] < g->o[a]) g->o[a] = p[a][i];
-      if (p[a][i] > mx[a]) mx[a] = p[a][i];
+  if (bp && bp->boundary == ORC_TORUS) {
+    const double size = bp->bound_max - bp->bound_min;
+    const double nb = floor(size / L);
+    if (!(nb >= 3.0) || nb > 2097151.0) return -3;
+    g->torus = 1;
+    g->L = size / nb;
+    for (int a = 0; a < 3; ++a) {
+      g->o[a] = bp->bound_min;
+      g->dims[a] = (int64_t)nb;
     }
-    g->dims[a] = (int64_t)floor((mx[a] - g->o[a]) / L) + 1;
+  } else {
+    double mx[3];
+    for (int a = 0; a < 3; ++a) {
+      g->o[a] = p[a][0];
+      mx[a] = p[a][0];
+      for (int64_t i = 1; i < n; ++i) {
+        if (p[a][i] < g->o[a]) g->o[a] = p[a][i];
+        if (p[a][i] > mx[a]) mx[a] = p[a][i];
+      }
+      g->dims[a] = (int64_t)floor((mx[a] - g->o[a]) / L) + 1;
+    }
   }
+  L = g->L;
   g->c = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)n);
   g->box = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
   g->sorted = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
@@ -134,7 +201,11 @@ static int grid_build(grid_t *g, int64_t n, const double *x, const double *y,
   box_id_pair *tmp = (box_id_pair *)malloc(sizeof(box_id_pair) * (size_t)n);
   if (!g->c || !g->box || !g->sorted || !g->sbox || !tmp) { free(tmp); grid_free(g); return -2; }
   for (int64_t i = 0; i < n; ++i) {
-    for (int a = 0; a < 3; ++a) g->c[3 * i + a] = (int64_t)floor((p[a][i] - g->o[a]) / L);
+    for (int a = 0; a < 3; ++a) {
+      int64_t c = (int64_t)floor((p[a][i] - g->o[a]) / L);
+      if (g->torus) c = c < 0 ? 0 : (c >= g->dims[a] ? g->dims[a] - 1 : c);  /* rounding at the far face */
+      g->c[3 * i + a] = c;
+    }
     g->box[i] = g->c[3 * i] + g->dims[0] * (g->c[3 * i + 1] + g->dims[1] * g->c[3 * i + 2]);
     tmp[i].box = g->box[i];
     tmp[i].id = i;
@@ -166,17 +237,32 @@ static void idl_push(idlist *l, int64_t x) {
   l->v[l->n++] = x;
 }
 
+/* Stencil box (c + d) of a grid: 0 when it lies outside an open grid;
+ * wrapped around on a torus. */
+static int stencil_box(const grid_t *g, const int64_t *c, int dx, int dy, int dz, int64_t *b) {
+  int64_t cx = c[0] + dx, cy = c[1] + dy, cz = c[2] + dz;
+  if (g->torus) {
+    cx = (cx + g->dims[0]) % g->dims[0];
+    cy = (cy + g->dims[1]) % g->dims[1];
+    cz = (cz + g->dims[2]) % g->dims[2];
+  } else if (cx < 0 || cy < 0 || cz < 0 || cx >= g->dims[0] || cy >= g->dims[1] || cz >= g->dims[2]) {
+    return 0;
+  }
+  *b = cx + g->dims[0] * (cy + g->dims[1] * cz);
+  return 1;
+}
+
 /* Candidates of agent i: every other agent in the (up to) 27 boxes around
- * i's box that lie inside the grid (§5.3.1), in ascending ID order. */
+ * i's box that lie inside the grid (§5.3.1; on a torus the 27 boxes wrap
+ * around and are distinct, since every axis has at least 3 boxes), in
+ * ascending ID order. */
 static void grid_candidates(const grid_t *g, int64_t i, idlist *out) {
   out->n = 0;
   for (int dz = -1; dz <= 1; ++dz)
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
-        int64_t cx = g->c[3 * i] + dx, cy = g->c[3 * i + 1] + dy, cz = g->c[3 * i + 2] + dz;
-        if (cx < 0 || cy < 0 || cz < 0 || cx >= g->dims[0] || cy >= g->dims[1] || cz >= g->dims[2])
-          continue;
-        int64_t b = cx + g->dims[0] * (cy + g->dims[1] * cz);
+        int64_t b;
+        if (!stencil_box(g, &g->c[3 * i], dx, dy, dz, &b)) continue;
         for (int64_t k = grid_lower(g, b); k < g->n && g->sbox[k] == b; ++k)
           if (g->sorted[k] != i) idl_push(out, g->sorted[k]);
       }
@@ -186,12 +272,13 @@ static void grid_candidates(const grid_t *g, int64_t i, idlist *out) {
 /* ------------------------------------------------------------------------
  * Pairwise quantities (Eq 4.1, Eq 4.2).
  * ---------------------------------------------------------------------- */
-/* Squared center distance, summed as ((dx*dx + dy*dy) + dz*dz). */
-static double sq_dist(const double *x, const double *y, const double *z, int64_t i, int64_t j,
-                      double *dx, double *dy, double *dz) {
-  *dx = x[i] - x[j];
-  *dy = y[i] - y[j];
-  *dz = z[i] - z[j];
+/* Squared center distance, summed as ((dx*dx + dy*dy) + dz*dz); on a
+ * torus the differences are minimum images. */
+static double sq_dist(const orc_params *p, const double *x, const double *y, const double *z, int64_t i,
+                      int64_t j, double *dx, double *dy, double *dz) {
+  *dx = coord_diff(p, x[i], x[j]);
+  *dy = coord_diff(p, y[i], y[j]);
+  *dz = coord_diff(p, z[i], z[j]);
   return ((*dx) * (*dx) + (*dy) * (*dy)) + (*dz) * (*dz);
 }
 
@@ -209,7 +296,7 @@ static void pair_force(const orc_params *p, const double *x, const double *y, co
                        const double *d, int64_t i, int64_t j, double F[3], int32_t *nnz,
                        double *smag) {
   double dx, dy, dz;
-  double s = sq_dist(x, y, z, i, j, &dx, &dy, &dz);
+  double s = sq_dist(p, x, y, z, i, j, &dx, &dy, &dz);
   double dist = sqrt(s);
   double delta = overlap(d, i, j, dist);
   if (!(delta > 0.0)) return;
@@ -426,12 +513,26 @@ void orc_destroy(orc_sim *s) {
   free(s);
 }
 
+/* A position inside the space of a closed ([min, max]) or toroidal
+ * ([min, max)) boundary; any finite position in open space. */
+static int inside_space(const orc_params *p, double v) {
+  if (!isfinite(v)) return 0;
+  if (p->boundary == ORC_CLOSED) return v >= p->bound_min && v <= p->bound_max;
+  if (p->boundary == ORC_TORUS) return v >= p->bound_min && v < p->bound_max;
+  return 1;
+}
+
 orc_sim *orc_create(const orc_params *p, int64_t n, const double *xyz, const double *d) {
   if (n < 0) return NULL;
+  if (p->boundary < ORC_OPEN || p->boundary > ORC_TORUS) return NULL;
+  if (p->boundary != ORC_OPEN &&
+      !(isfinite(p->bound_min) && isfinite(p->bound_max) && p->bound_min < p->bound_max))
+    return NULL;
   int64_t cap = p->capacity > n ? p->capacity : n;
   if (cap < 1) cap = 1;
   for (int64_t i = 0; i < n; ++i) {
-    if (!isfinite(xyz[3 * i]) || !isfinite(xyz[3 * i + 1]) || !isfinite(xyz[3 * i + 2])) return NULL;
+    if (!inside_space(p, xyz[3 * i]) || !inside_space(p, xyz[3 * i + 1]) || !inside_space(p, xyz[3 * i + 2]))
+      return NULL;
     if (!(d[i] > 0.0) || !isfinite(d[i])) return NULL;
   }
   orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
@@ -484,7 +585,7 @@ void orc_last(const orc_sim *s, double *F, double *D, int32_t *nnz, uint8_t *sta
 int orc_grid(const orc_sim *s, int64_t *box, double origin_len[4], int64_t dims[3]) {
   grid_t g;
   double L = grid_box_length(s->n, s->d, s->p.box_length);
-  int rc = grid_build(&g, s->n, s->x, s->y, s->z, L);
+  int rc = grid_build(&g, s->n, s->x, s->y, s->z, L, &s->p);
   if (rc) return rc;
   if (box) for (int64_t i = 0; i < s->n; ++i) box[i] = g.box[i];
   if (origin_len) { origin_len[0] = g.o[0]; origin_len[1] = g.o[1]; origin_len[2] = g.o[2]; origin_len[3] = g.L; }
@@ -499,7 +600,7 @@ int orc_grid(const orc_sim *s, int64_t *box, double origin_len[4], int64_t dims[
 int orc_forces(const orc_sim *s, const int64_t *ids, int64_t m, double *F, int32_t *nnz, double *smag) {
   grid_t g;
   double L = grid_box_length(s->n, s->d, s->p.box_length);
-  int rc = grid_build(&g, s->n, s->x, s->y, s->z, L);
+  int rc = grid_build(&g, s->n, s->x, s->y, s->z, L, &s->p);
   if (rc) return rc;
   idlist cand = {0, 0, 0};
   int64_t count = ids ? m : s->n;
@@ -536,7 +637,7 @@ static int orc_iterate(orc_sim *s) {
   int64_t n = s->n;
   grid_t g;
   double L = grid_box_length(n, s->d, p->box_length);
-  int rc = grid_build(&g, n, s->x, s->y, s->z, L);
+  int rc = grid_build(&g, n, s->x, s->y, s->z, L, p);
   if (rc) return rc;
 
   /* Static detection (§5.5): the conditions must have held in the last
@@ -558,10 +659,8 @@ static int orc_iterate(orc_sim *s) {
       for (int dz = -1; dz <= 1 && !disturbed; ++dz)
         for (int dy = -1; dy <= 1 && !disturbed; ++dy)
           for (int dx = -1; dx <= 1 && !disturbed; ++dx) {
-            int64_t cx = g.c[3 * i] + dx, cy = g.c[3 * i + 1] + dy, cz = g.c[3 * i + 2] + dz;
-            if (cx < 0 || cy < 0 || cz < 0 || cx >= g.dims[0] || cy >= g.dims[1] || cz >= g.dims[2])
-              continue;
-            int64_t b = cx + g.dims[0] * (cy + g.dims[1] * cz);
+            int64_t b;
+            if (!stencil_box(&g, &g.c[3 * i], dx, dy, dz, &b)) continue;
             if (box_in_sorted(dirty, nd, b)) disturbed = 1;
           }
       stat[i] = (uint8_t)!disturbed;
@@ -587,11 +686,11 @@ static int orc_iterate(orc_sim *s) {
   }
   free(cand.v);
 
-  /* Commit (copy execution context). */
+  /* Commit (copy execution context), under the boundary condition. */
   for (int64_t i = 0; i < n; ++i) {
-    s->x[i] = s->x[i] + s->D[3 * i];
-    s->y[i] = s->y[i] + s->D[3 * i + 1];
-    s->z[i] = s->z[i] + s->D[3 * i + 2];
+    s->x[i] = bound_apply(p, s->x[i] + s->D[3 * i]);
+    s->y[i] = bound_apply(p, s->y[i] + s->D[3 * i + 1]);
+    s->z[i] = bound_apply(p, s->z[i] + s->D[3 * i + 2]);
     s->changed[i] = (uint8_t)(s->D[3 * i] != 0.0 || s->D[3 * i + 1] != 0.0 || s->D[3 * i + 2] != 0.0);
     s->stat[i] = stat[i];
     s->prev_box[i] = g.box[i];
@@ -615,12 +714,12 @@ static int orc_iterate(orc_sim *s) {
         orc_division_axis(p->seed, i, s->t, u);
         double off = 0.25 * dh;
         int64_t j = s->n++;
-        s->x[j] = s->x[i] + off * u[0];
-        s->y[j] = s->y[i] + off * u[1];
-        s->z[j] = s->z[i] + off * u[2];
-        s->x[i] = s->x[i] - off * u[0];
-        s->y[i] = s->y[i] - off * u[1];
-        s->z[i] = s->z[i] - off * u[2];
+        s->x[j] = bound_apply(p, s->x[i] + off * u[0]);
+        s->y[j] = bound_apply(p, s->y[i] + off * u[1]);
+        s->z[j] = bound_apply(p, s->z[i] + off * u[2]);
+        s->x[i] = bound_apply(p, s->x[i] - off * u[0]);
+        s->y[i] = bound_apply(p, s->y[i] - off * u[1]);
+        s->z[i] = bound_apply(p, s->z[i] - off * u[2]);
         s->v[i] = vh; s->v[j] = vh;
         s->d[i] = dh; s->d[j] = dh;
         s->changed[i] = 1; s->changed[j] = 1;
@@ -643,6 +742,42 @@ static int orc_iterate(orc_sim *s) {
   return 0;
 }
 
+/* Remove the m agents `ids` (distinct, in range; returns -1 otherwise and
+ * changes nothing).  The swaps of §5.3.2 (Fig 5.1): with n' = n - m, a
+ * removed agent below n' leaves a hole, and the holes, in ascending order,
+ * take the survivors at or above n', in ascending order; agents below n'
+ * that survive keep their ID.  Every survivor counts as changed for the
+ * next iteration. */
+int orc_remove(orc_sim *s, int64_t m, const int64_t *ids) {
+  int64_t n = s->n;
+  if (m < 0 || m > n) return -1;
+  uint8_t *gone = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+  for (int64_t k = 0; k < m; ++k) {
+    if (ids[k] < 0 || ids[k] >= n || gone[ids[k]]) { free(gone); return -1; }
+    gone[ids[k]] = 1;
+  }
+  const int64_t nn = n - m;
+  int64_t hole = 0, mover = nn;
+  for (;;) {
+    while (hole < nn && !gone[hole]) ++hole;
+    while (mover < n && gone[mover]) ++mover;
+    if (hole >= nn || mover >= n) break;
+    /* the survivor `mover` takes the ID `hole` */
+    s->x[hole] = s->x[mover]; s->y[hole] = s->y[mover]; s->z[hole] = s->z[mover];
+    s->d[hole] = s->d[mover]; s->v[hole] = s->v[mover];
+    for (int a = 0; a < 3; ++a) { s->F[3 * hole + a] = s->F[3 * mover + a]; s->D[3 * hole + a] = s->D[3 * mover + a]; }
+    s->nnz[hole] = s->nnz[mover];
+    s->stat[hole] = s->stat[mover];
+    s->prev_box[hole] = s->prev_box[mover];
+    ++hole;
+    ++mover;
+  }
+  s->n = nn;
+  for (int64_t i = 0; i < nn; ++i) s->changed[i] = 1;
+  free(gone);
+  return 0;
+}
+
 int orc_step(orc_sim *s, int32_t iterations) {
   for (int32_t it = 0; it < iterations; ++it) {
     int rc = orc_iterate(s);
@@ -662,7 +797,7 @@ int64_t orc_neighbors(const orc_sim *s, double radius, int64_t cap, int64_t *pai
   grid_t g;
   double L = grid_box_length(s->n, s->d, s->p.box_length);
   if (radius > L) L = radius;
-  if (grid_build(&g, s->n, s->x, s->y, s->z, L)) return -1;
+  if (grid_build(&g, s->n, s->x, s->y, s->z, L, &s->p)) return -1;
   double R2 = radius * radius;
   idlist cand = {0, 0, 0};
   int64_t count = 0;
@@ -672,7 +807,7 @@ int64_t orc_neighbors(const orc_sim *s, double radius, int64_t cap, int64_t *pai
       int64_t j = cand.v[k];
       if (j <= i) continue;
       double dx, dy, dz;
-      double sq = sq_dist(s->x, s->y, s->z, i, j, &dx, &dy, &dz);
+      double sq = sq_dist(&s->p, s->x, s->y, s->z, i, j, &dx, &dy, &dz);
       int hit = radius >= 0.0 ? (sq < R2) : (overlap(s->d, i, j, sqrt(sq)) > 0.0);
       if (!hit) continue;
       if (count < cap && pairs) { pairs[2 * count] = i; pairs[2 * count + 1] = j; }
@@ -780,7 +915,7 @@ int64_t orc_morton_sequence(int dim, const int64_t *dims, int64_t *codes) {
 int orc_morton_agent_order(const orc_sim *s, int64_t *ids) {
   grid_t g;
   double L = grid_box_length(s->n, s->d, s->p.box_length);
-  int rc = grid_build(&g, s->n, s->x, s->y, s->z, L);
+  int rc = grid_build(&g, s->n, s->x, s->y, s->z, L, &s->p);
   if (rc) return rc;
   box_id_pair *tmp = (box_id_pair *)malloc(sizeof(box_id_pair) * (size_t)(s->n > 0 ? s->n : 1));
   for (int64_t i = 0; i < s->n; ++i) {

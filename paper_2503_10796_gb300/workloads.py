@@ -40,6 +40,9 @@ class SimParams:
     sort_interval: int = 0         # Morton re-sort every n iterations (0 never)
     seed: int = 0                  # counter-RNG key (division axes)
     capacity: int = 0              # per-simulation agent cap (0: initial n)
+    boundary: int = 0              # 0 open, 1 closed, 2 toroidal space (§4.4.11)
+    bound_min: float = 0.0         # the space [bound_min, bound_max] per axis
+    bound_max: float = 0.0         #   (closed and toroidal boundaries)
 
     def as_dict(self):
         return asdict(self)
