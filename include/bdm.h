@@ -61,6 +61,20 @@ enum {
 
 enum { BDM_PREC_FP64 = 0, BDM_PREC_FP32_FORCE = 1 };
 
+/* Space boundary conditions (§4.4.11).  Open: the space grows with the
+ * agents (grid origin = per-axis minimum, as S0 states).  Closed: the space
+ * is the cube [bound_min, bound_max] per axis; a new position (displacement,
+ * daughter placement) is clamped into it per coordinate.  Toroidal: the
+ * space is [bound_min, bound_max) per axis; a new coordinate v becomes
+ * v - size when v >= bound_max, v + size when v < bound_min (bound_min if
+ * rounding leaves it at bound_max); the grid tiles the space with
+ * n = floor(size / L) >= 3 boxes per axis of length size / n from
+ * bound_min, stencil boxes wrap around, and coordinate differences are
+ * minimum images (dx - size when dx > size / 2, dx + size when
+ * dx < -size / 2).  Positions given to a closed or toroidal simulation must
+ * lie in its space. */
+enum { BDM_BOUNDARY_OPEN = 0, BDM_BOUNDARY_CLOSED = 1, BDM_BOUNDARY_TOROIDAL = 2 };
+
 /* flags of bdm_set_agents / bdm_get_agents */
 enum { BDM_DEVICE_PTRS = 1 };
 
@@ -77,9 +91,11 @@ typedef struct {
   int32_t precision;       /* BDM_PREC_FP64 or BDM_PREC_FP32_FORCE */
   int32_t detect_static;   /* 1: skip the force of static agents (§5.5) */
   int32_t sort_interval;   /* Morton re-sort every n iterations; 0 = never */
-  int32_t reserved;        /* must be 0 */
+  int32_t boundary;        /* BDM_BOUNDARY_OPEN (0), _CLOSED or _TOROIDAL */
   uint64_t seed;           /* key of the counter-based generator (division axes) */
   int64_t capacity;        /* agent capacity of this simulation; 0 = count at bdm_set_agents */
+  double bound_min;        /* the space of closed and toroidal boundaries, per axis */
+  double bound_max;
 } bdm_params;
 
 /* Counters of one simulation (bdm_get_stats). */
@@ -149,6 +165,18 @@ int bdm_update_agents(bdm_ctx* ctx, int32_t sim, int64_t n, const double* xyz,
 int bdm_get_state(bdm_ctx* ctx, int32_t sim, void* buf, int64_t cap_bytes, int64_t* size_out);
 int bdm_set_state(bdm_ctx* ctx, int32_t sim, const void* buf, int64_t size_bytes);
 
+/* Remove the agents `ids` (n_ids distinct caller IDs, host memory) from
+ * simulation `sim`, with the swaps of the thesis's parallel removal (§5.3.2,
+ * Fig 5.1): of the n' agents left, those with an ID below n' keep it, and
+ * the IDs below n' that removed agents held go, in ascending order, to the
+ * surviving agents with IDs >= n', in ascending order.  Every survivor
+ * counts as changed in the next iteration (the neighbourhoods of the removed
+ * agents changed: no agent is static then), the iteration counter and the
+ * last grid stay, and bdm_get_forces reports zeros until the next
+ * iteration.  Errors: BDM_E_INVAL (an ID out of range or repeated),
+ * BDM_E_STATE (no agents set), latched device errors as bdm_sync. */
+int bdm_remove_agents(bdm_ctx* ctx, int32_t sim, int64_t n_ids, const int64_t* ids);
+
 /* Run n_iterations iterations of every simulation (S0-S7), asynchronously
  * on the context's stream.  Errors: BDM_E_STATE (a simulation has no
  * agents set), BDM_E_NOMEM (box table growth failed), BDM_E_CUDA. */
@@ -157,7 +185,8 @@ int bdm_step(bdm_ctx* ctx, int32_t n_iterations);
 /* Wait for the context's stream and report latched device errors:
  * BDM_E_CAPACITY when a grid outgrew its box table or a box held more than
  * 1023 agents (that iteration's results are then undefined),
- * BDM_E_NONFINITE, BDM_E_TIMEOUT. */
+ * BDM_E_NONFINITE, BDM_E_TIMEOUT, BDM_E_INVAL when a toroidal space holds
+ * fewer than three boxes per axis (the largest diameter grew too large). */
 int bdm_sync(bdm_ctx* ctx);
 
 /* Copy the agents of `sim` out in caller-ID order: xyz (cap x 3) and

@@ -72,6 +72,7 @@ SIGNATURES = {
     "bdm_update_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _i32]),
     "bdm_step": (C.c_int, [_vp, _i32]),
     "bdm_get_state": (C.c_int, [_vp, _i32, _vp, _i64, _P(_i64)]),
+    "bdm_remove_agents": (C.c_int, [_vp, _i32, _i64, _vp]),
     "bdm_set_state": (C.c_int, [_vp, _i32, _vp, _i64]),
     "bdm_sync": (C.c_int, [_vp]),
     "bdm_get_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _P(_i64), _i32]),
@@ -217,6 +218,12 @@ class Context:
         """Replace simulation `sim` by a checkpoint (bdm_set_state)."""
         buf = C.create_string_buffer(bytes(state), len(state))
         self._check(self._lib.bdm_set_state(self._h, sim, buf, len(state)))
+
+    def remove_agents(self, sim: int, ids):
+        """Remove the agents `ids` of `sim` (bdm_remove_agents: the swaps of
+        the thesis's parallel removal renumber the survivors)."""
+        ids = np.ascontiguousarray(ids, dtype=np.int64).reshape(-1)
+        self._check(self._lib.bdm_remove_agents(self._h, sim, ids.shape[0], _dptr(ids) if ids.size else None))
 
     def step(self, iterations: int = 1):
         self._check(self._lib.bdm_step(self._h, int(iterations)))

@@ -25,7 +25,11 @@ enum : uint32_t {
   ERR_TIMEOUT = 4u,    // a bounded retry loop ran out
   ERR_TABLE = 8u,      // box table region too small for the grid
   ERR_COORD = 16u,     // box coordinate beyond 2^21 per axis
+  ERR_TORUS = 32u,     // a toroidal space narrower than three boxes per axis
 };
+
+// Space boundary conditions (§4.4.11).
+enum : int32_t { BOUND_OPEN = 0, BOUND_CLOSED = 1, BOUND_TORUS = 2 };
 
 // Flags per slot.
 enum : uint8_t { FLAG_CHANGED = 1u, FLAG_STATIC = 2u };
@@ -46,6 +50,10 @@ struct SimConst {
   uint64_t seed;
   int64_t base, cap;
   int64_t table_base, table_cap;
+  int32_t boundary;           // BOUND_*
+  int32_t pad;
+  double bmin, bmax;          // the space of closed and toroidal boundaries, per axis
+  double bsize, bhalf;        // bmax - bmin and half of it
 };
 
 // Per-simulation state (device-written).
@@ -196,26 +204,61 @@ __device__ __forceinline__ uint32_t grid_coord(const SimState &s, double x, int 
 
 __device__ __forceinline__ void set_err(Globals *g, uint32_t bits) { atomicOr(&g->err, bits); }
 
+// Table index of the stencil box (c + d) of simulation sc: false when it
+// lies outside an open grid; wrapped around on a torus (every axis of a
+// toroidal grid has at least three boxes, so the 27 boxes are distinct).
+__device__ __forceinline__ bool stencil_index(const SimConst &sc, const SimState &s, int64_t cx, int64_t cy,
+                                              int64_t cz, int dx, int dy, int dz, int64_t &idx) {
+  int64_t x = cx + dx, y = cy + dy, z = cz + dz;
+  if (sc.boundary == BOUND_TORUS) {
+    x = x < 0 ? x + s.dims[0] : (x >= s.dims[0] ? x - s.dims[0] : x);
+    y = y < 0 ? y + s.dims[1] : (y >= s.dims[1] ? y - s.dims[1] : y);
+    z = z < 0 ? z + s.dims[2] : (z >= s.dims[2] ? z - s.dims[2] : z);
+  } else if (x < 0 || x >= s.dims[0] || y < 0 || y >= s.dims[1] || z < 0 || z >= s.dims[2]) {
+    return false;
+  }
+  idx = sc.table_base + linear_box(s, x, y, z);
+  return true;
+}
+
+// Coordinate difference a - b; on a torus the minimum image (- size above
+// half of it, + size below minus half), IEEE FP64 as the definition orders it.
+__device__ __forceinline__ double coord_diff(const SimConst &sc, double a, double b) {
+  double d = __dsub_rn(a, b);
+  if (sc.boundary == BOUND_TORUS) {
+    if (d > sc.bhalf) d = __dsub_rn(d, sc.bsize);
+    else if (d < -sc.bhalf) d = __dadd_rn(d, sc.bsize);
+  }
+  return d;
+}
+
+// A new coordinate under the boundary condition: clamped into a closed
+// space, wrapped into a toroidal one (the rounding guard keeps it below
+// bmax).
+__device__ __forceinline__ double bound_apply(const SimConst &sc, double v) {
+  if (sc.boundary == BOUND_CLOSED) return v < sc.bmin ? sc.bmin : (v > sc.bmax ? sc.bmax : v);
+  if (sc.boundary == BOUND_TORUS) {
+    if (v >= sc.bmax) v = __dsub_rn(v, sc.bsize);
+    else if (v < sc.bmin) v = __dadd_rn(v, sc.bsize);
+    if (v >= sc.bmax) v = sc.bmin;
+  }
+  return v;
+}
+
 // Static check (§5.5): the agent itself is eligible (unchanged in the last
 // iteration, at most one non-zero pair force, grid unchanged) and no box of
 // its stencil carries a dirty mark of the current build.
 __device__ __forceinline__ bool is_static_cell(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t p,
                                           int64_t cx, int64_t cy, int64_t cz, uint32_t stamp) {
   if (!sc.detect_static || !s.same_grid || !(C.c.flag[p] & CELL_STATIC_ELIGIBLE)) return false;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int64_t z = cz + dz;
-    if (z < 0 || z >= s.dims[2]) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int64_t y = cy + dy;
-      if (y < 0 || y >= s.dims[1]) continue;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
-        int64_t x = cx + dx;
-        if (x < 0 || x >= s.dims[0]) continue;
-        const unsigned long long e = C.tab.e[sc.table_base + linear_box(s, x, y, z)];
+        int64_t idx;
+        if (!stencil_index(sc, s, cx, cy, cz, dx, dy, dz, idx)) continue;
+        const unsigned long long e = C.tab.e[idx];
         if (ent_stamp(e) == stamp && ent_dirty(e)) return false;
       }
-    }
-  }
   return true;
 }
 

@@ -133,8 +133,16 @@ int check_params(const bdm_params &p, std::string &why) {
     why = "precision must be BDM_PREC_FP64 or BDM_PREC_FP32_FORCE";
     return BDM_E_INVAL;
   }
-  if (p.sort_interval < 0 || p.capacity < 0 || p.reserved != 0) {
-    why = "sort_interval, capacity must be >= 0 and reserved 0";
+  if (p.sort_interval < 0 || p.capacity < 0) {
+    why = "sort_interval, capacity must be >= 0";
+    return BDM_E_INVAL;
+  }
+  if (p.boundary < BDM_BOUNDARY_OPEN || p.boundary > BDM_BOUNDARY_TOROIDAL) {
+    why = "boundary must be BDM_BOUNDARY_OPEN, _CLOSED or _TOROIDAL";
+    return BDM_E_INVAL;
+  }
+  if (p.boundary != BDM_BOUNDARY_OPEN && !(fin(p.bound_min) && fin(p.bound_max) && p.bound_min < p.bound_max)) {
+    why = "a closed or toroidal space needs finite bound_min < bound_max";
     return BDM_E_INVAL;
   }
   if (p.growth_rate > 0 && !(p.divide_volume > 0)) {
@@ -170,6 +178,11 @@ SimConst make_const(const bdm_params &p) {
   s.cap = 0;
   s.table_base = 0;
   s.table_cap = 0;
+  s.boundary = p.boundary;
+  s.bmin = p.bound_min;
+  s.bmax = p.bound_max;
+  s.bsize = p.boundary != BDM_BOUNDARY_OPEN ? p.bound_max - p.bound_min : 0.0;
+  s.bhalf = 0.5 * s.bsize;
   return s;
 }
 
@@ -245,10 +258,14 @@ void launch_iteration(bdm_ctx *c, int sort) {
   launch_bbox(D, st);
   launch_params(D, st, 1);
   stage_end(c);
-  bool any_static = false;
+  bool any_static = false, any_torus = false;
   for (int s = 0; s < c->n_sims; ++s)
-    if (c->params[s].precision != BDM_PREC_FP64 && c->params[s].detect_static) any_static = true;
-  const ForcePlan pl = plan_force(c->force_variant, any_static);
+    if (c->params[s].precision != BDM_PREC_FP64) {
+      if (c->params[s].detect_static) any_static = true;
+      if (c->params[s].boundary == BDM_BOUNDARY_TOROIDAL) any_torus = true;
+    }
+  // only the stream kernels walk a wrapped stencil
+  const ForcePlan pl = plan_force(any_torus && c->force_variant != 6 ? 5 : c->force_variant, any_static);
   stage_begin(c, 1);
   launch_count(D, st, 1);
   stage_end(c);
@@ -267,7 +284,7 @@ void launch_iteration(bdm_ctx *c, int sort) {
   launch_place(D, st, 1, pl.zero_f32 ? 1 : 0);
   stage_end(c);
   stage_begin(c, 4);
-  launch_force(D, st, pl.variant, c->any_fp32, c->any_fp64, any_static);
+  launch_force(D, st, pl.variant, c->any_fp32, c->any_fp64, any_static, any_torus);
   stage_end(c);
   stage_begin(c, 5);
   launch_displace(D, st);
@@ -312,6 +329,22 @@ int ensure_table(bdm_ctx *c, int iters, bool *resized) {
     double L = sc.box_length > 0 ? sc.box_length : dmax;
     double step = sc.max_disp;
     double Lmin = L;
+    if (sc.boundary == BDM_BOUNDARY_TOROIDAL) {
+      // the grid tiles the space: at most floor(size / Lmin) boxes per axis
+      // (and at least three, which k_params checks)
+      double Lt = L;
+      if (sc.grows && !(sc.box_length > 0)) {
+        const double ddiv = std::cbrt(6.0 * sc.divide_volume / M_PI);
+        Lt = std::min(dmax, ddiv * 0.7937005259840998) * 0.999;
+      }
+      const double dims = std::max(1.0, std::floor(sc.bsize / Lt));
+      if (!(Lt > 0) || dims >= (double)(1ll << kCoordBits))
+        return fail(c, BDM_E_CAPACITY, "toroidal grid needs more than 2^21 boxes per axis");
+      need[s] = (int64_t)(dims * dims * dims);
+      total += need[s];
+      max_dims = std::max(max_dims, dims);
+      continue;
+    }
     if (sc.grows) {
       double ddiv = std::cbrt(6.0 * sc.divide_volume / M_PI);
       step += 0.25 * std::max(dmax, ddiv);
@@ -407,8 +440,9 @@ int latched_error(bdm_ctx *c) {
   cudaStreamSynchronize(c->stream);
   if (bits & ERR_TABLE)
     return fail(c, BDM_E_CAPACITY, "grid outgrew its box table region, or a box held more than 1023 agents");
-  if (bits & ERR_COORD) return fail(c, BDM_E_CAPACITY, "box coordinate beyond 2^21 per axis");
+  if ((bits & ERR_COORD) && !(bits & ERR_TORUS)) return fail(c, BDM_E_CAPACITY, "box coordinate beyond 2^21 per axis");
   if (bits & ERR_TIMEOUT) return fail(c, BDM_E_TIMEOUT, "a bounded device retry loop ran out");
+  if (bits & ERR_TORUS) return fail(c, BDM_E_INVAL, "a toroidal space narrower than three boxes per axis");
   if (bits & ERR_NONFINITE) return fail(c, BDM_E_NONFINITE, "a position, force or grid value became non-finite");
   return BDM_OK;  // ERR_CAPACITY (division stopped at the cap) is informational
 }
@@ -713,7 +747,7 @@ int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const 
       dd = c->d_xfer + 3 * n;
     }
     cudaMemsetAsync(c->d_bad, 0xFF, sizeof(unsigned long long), c->stream);
-    launch_check_input(c->stream, n, dx, dd, c->d_bad);
+    launch_check_input(c->stream, n, dx, dd, c->d_bad, c->h_sc[sim].boundary, c->h_sc[sim].bmin, c->h_sc[sim].bmax);
     unsigned long long hb = ~0ull;
     cudaMemcpyAsync(&hb, c->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream);
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -766,7 +800,7 @@ int bdm_update_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, con
     }
   }
   cudaMemsetAsync(c->d_bad, 0xFF, sizeof(unsigned long long), c->stream);
-  launch_check_input(c->stream, n, dx, dd, c->d_bad);
+  launch_check_input(c->stream, n, dx, dd, c->d_bad, c->h_sc[sim].boundary, c->h_sc[sim].bmin, c->h_sc[sim].bmax);
   unsigned long long hb = ~0ull;
   cudaMemcpyAsync(&hb, c->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -933,6 +967,66 @@ int bdm_set_state(bdm_ctx *c, int32_t sim, const void *buf, int64_t size_bytes) 
   c->h_iter[sim] = h.t;
   c->need_radix[sim] = 1;
   return upload_order(c);
+}
+
+// Agent removal with the swaps of §5.3.2 (Fig 5.1): with n' agents left,
+// the IDs below n' that removed agents held (the holes), in ascending order,
+// go to the surviving agents with IDs >= n', in ascending order.  O(removed)
+// host work builds the pairs; the device moves the rows of the by-ID state.
+int bdm_remove_agents(bdm_ctx *c, int32_t sim, int64_t n_ids, const int64_t *ids) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
+  if (n_ids < 0 || (n_ids > 0 && !ids)) return fail(c, BDM_E_INVAL, "n_ids < 0 or NULL ids");
+  rc = latched_error(c);
+  if (rc) return rc;
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  const int64_t n = s.n;
+  std::vector<int64_t> gone(ids, ids + n_ids);
+  std::sort(gone.begin(), gone.end());
+  for (int64_t k = 0; k < n_ids; ++k)
+    if (gone[k] < 0 || gone[k] >= n || (k > 0 && gone[k] == gone[k - 1]))
+      return fail(c, BDM_E_INVAL, "an ID out of range or repeated");
+  if (n_ids == 0) return BDM_OK;
+  const int64_t nn = n - n_ids;
+  std::vector<int64_t> holes, movers;
+  {
+    size_t g = 0;
+    for (; g < gone.size() && gone[g] < nn; ++g) holes.push_back(gone[g]);
+    int64_t m = nn;
+    for (size_t k = 0; k < holes.size(); ++k) {
+      while (g < gone.size() && gone[g] == m) { ++g; ++m; }
+      movers.push_back(m++);
+    }
+  }
+  const int64_t np = (int64_t)holes.size();
+  const int64_t ab = state_array_bytes(n);
+  const size_t adbl = (size_t)((ab + 7) / 8);
+  rc = ensure_xfer(c, adbl + 2 * (size_t)np);
+  if (rc) return rc;
+  int64_t *dh = reinterpret_cast<int64_t *>(c->d_xfer + adbl), *dm = dh + np;
+  launch_state_gather(c->D, c->stream, c->h_sc[sim].base, n, c->d_xfer);
+  if (np > 0) {
+    cudaMemcpyAsync(dh, holes.data(), sizeof(int64_t) * (size_t)np, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(dm, movers.data(), sizeof(int64_t) * (size_t)np, cudaMemcpyHostToDevice, c->stream);
+  }
+  launch_state_remove(c->stream, c->d_xfer, n, nn, dh, dm, np);
+  // the arrays laid out for n agents hold the survivors in their first n' rows
+  launch_state_scatter(c->D, c->stream, sim, c->h_sc[sim].base, nn, c->h_sc[sim].cap, c->d_xfer, n);
+  // the simulation keeps its counters and last grid; the last iteration's
+  // per-agent results no longer match the agents (none are reported)
+  s.n = nn;
+  s.ncell = 0;
+  for (int a = 0; a < 3; ++a) { s.bmin[a] = ~0ull; s.bmax[a] = 0ull; }
+  s.dmax = 0ull;
+  cudaMemcpyAsync(&c->D.ss[sim], &s, sizeof(SimState), cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "removing agents");
+  c->n_set[sim] = nn;
+  c->need_radix[sim] = 1;
+  return BDM_OK;
 }
 
 int bdm_step(bdm_ctx *c, int32_t n_iterations) {
@@ -1370,7 +1464,8 @@ int bdm_set_tuning(bdm_ctx *c, const bdm_tuning *t) {
     if (iv > 0) any = true;
     // the box length shapes the static check's stencil: only simulations
     // without static detection (and without a box length of their own) scale it
-    const bool scalable = !c->params[s].detect_static && !(c->params[s].box_length > 0);
+    const bool scalable = !c->params[s].detect_static && !(c->params[s].box_length > 0) &&
+                          c->params[s].boundary != BDM_BOUNDARY_TOROIDAL;
     c->h_sc[s].box_scale = scalable ? c->box_scale_pct / 100.0 : 1.0;
   }
   if (any && !c->d_sort) {
@@ -1541,7 +1636,9 @@ int bdm_autotune(bdm_ctx *c, int32_t iterations, int32_t knobs, bdm_tuning *chos
     }
   bool scalable = false;
   for (int s = 0; s < c->n_sims; ++s)
-    if (!c->params[s].detect_static && !(c->params[s].box_length > 0)) scalable = true;
+    if (!c->params[s].detect_static && !(c->params[s].box_length > 0) &&
+        c->params[s].boundary != BDM_BOUNDARY_TOROIDAL)
+      scalable = true;
   if ((knobs & BDM_TUNE_BOX) && scalable)
     for (int pct : {100, 125, 150}) {
       if (rc) break;

@@ -443,7 +443,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
   if constexpr (!kDirect) warp_flush(C, hq, mine, p);
 }
 
-// S5: displacement.  Static agents keep their position and nnz.
+// S5: displacement, then the space boundary condition (§4.4.11) on the new
+// position.  Static agents keep their position and nnz.
 __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -471,9 +472,9 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
       }
       moved = (Dx != 0.0 || Dy != 0.0 || Dz != 0.0);
       if (moved) {
-        C.a.x[slot] = __dadd_rn(C.a.x[slot], Dx);
-        C.a.y[slot] = __dadd_rn(C.a.y[slot], Dy);
-        C.a.z[slot] = __dadd_rn(C.a.z[slot], Dz);
+        C.a.x[slot] = bound_apply(sc, __dadd_rn(C.a.x[slot], Dx));
+        C.a.y[slot] = bound_apply(sc, __dadd_rn(C.a.y[slot], Dy));
+        C.a.z[slot] = bound_apply(sc, __dadd_rn(C.a.z[slot], Dz));
       }
     }
   } else {
@@ -493,9 +494,9 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
       }
       moved = (Dx != 0.f || Dy != 0.f || Dz != 0.f);
       if (moved) {
-        C.a.x[slot] = __dadd_rn(C.a.x[slot], f2d(Dx));
-        C.a.y[slot] = __dadd_rn(C.a.y[slot], f2d(Dy));
-        C.a.z[slot] = __dadd_rn(C.a.z[slot], f2d(Dz));
+        C.a.x[slot] = bound_apply(sc, __dadd_rn(C.a.x[slot], f2d(Dx)));
+        C.a.y[slot] = bound_apply(sc, __dadd_rn(C.a.y[slot], f2d(Dy)));
+        C.a.z[slot] = bound_apply(sc, __dadd_rn(C.a.z[slot], f2d(Dz)));
       }
     }
   }
@@ -527,7 +528,8 @@ ForcePlan plan_force(int variant, bool any_static) {
   return pl;
 }
 
-void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64, bool any_static) {
+void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, bool has_fp64, bool any_static,
+                  bool any_torus) {
   const int th = force_threads(C.total_slots);
   const unsigned int nb = blocks_for(C.total_slots, th);
   if (has_fp32) {
@@ -535,8 +537,8 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, 
     else if (variant == 0) k_force32s<false><<<nb, th, 0, st>>>(C);
     else if (variant == 4) k_force32s<true><<<nb, th, 0, st>>>(C);
     else if (variant == 3) k_force32d<false><<<nb, th, 0, st>>>(C);
-    else if (variant == 5) launch_force_stream(C, st, any_static ? 1 : 0, th);
-    else if (variant == 6) launch_force_stream(C, st, any_static ? 2 : 0, th);
+    else if (variant == 5) launch_force_stream(C, st, any_static ? 1 : 0, th, any_torus);
+    else if (variant == 6) launch_force_stream(C, st, any_static ? 2 : 0, th, any_torus);
     else k_force32d<true><<<nb, th, 0, st>>>(C);
   }
   if (has_fp64) launch_force64(C, st);

@@ -83,9 +83,6 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
   const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
   const int dz = r / 3 - 1, dy = r % 3 - 1;
   const bool walk = !skip[a] && dz >= t.zlo && dz <= t.zhi && dy >= t.ylo && dy <= t.yhi;
-  const uint32_t row = walk ? ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
-                                  (uint32_t)t.cx
-                            : 0u;
   double4_32a o = {};
   if (walk) {
     o = C.c.r64[p];
@@ -93,7 +90,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
     const float Lh = s.Lh, marg = s.marg;
     const float sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh)), sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
     for (int dx = t.xlo; dx <= t.xhi; ++dx) {
-      const unsigned long long e = t.e[row + dx];
+      const unsigned long long e = t.e[t.box(dx, dy, dz)];
       const uint32_t cnt = ent_live(e, stamp);
       const int64_t j0 = ent_start(e);
       const float sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
@@ -115,7 +112,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
     // crowded row: evaluate it in place
     mine = 0;
     for (int dx = t.xlo; dx <= t.xhi; ++dx) {
-      const unsigned long long e = t.e[row + dx];
+      const unsigned long long e = t.e[t.box(dx, dy, dz)];
       const uint32_t cnt = ent_live(e, stamp);
       const int64_t j0 = ent_start(e);
       for (uint32_t m = 0; m < cnt; ++m) {
@@ -123,7 +120,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
         if (j == p) continue;
         double gx, gy, gz;
         bool nz, dir;
-        if (pair64(o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir)) append(a, j, gx, gy, gz, nz, dir);
+        if (pair64(sc, o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir)) append(a, j, gx, gy, gz, nz, dir);
       }
     }
   }
@@ -156,7 +153,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
         const int64_t j = (int64_t)rq[kk - ex][to];
         double gx, gy, gz;
         bool nz, dir;
-        if (pair64(C.c.r64[po], C.c.r64[j], so.k, so.gamma, gx, gy, gz, nz, dir)) append(agent, j, gx, gy, gz, nz, dir);
+        if (pair64(so, C.c.r64[po], C.c.r64[j], so.k, so.gamma, gx, gy, gz, nz, dir)) append(agent, j, gx, gy, gz, nz, dir);
       }
     }
   }
@@ -224,9 +221,7 @@ __global__ void __launch_bounds__(32 * kOvfWarps) k_force64o(DevCtx C) {
       int64_t bj = -1;
       for (int b = 0; b < nbox; ++b) {
         const int dx = t.xlo + b % nx, dy = t.ylo + (b / nx) % ny, dz = t.zlo + b / (nx * ny);
-        const uint32_t row = ((uint32_t)(t.cz + dz) * (uint32_t)t.d1 + (uint32_t)(t.cy + dy)) * (uint32_t)t.d0 +
-                             (uint32_t)t.cx;
-        const unsigned long long e = t.e[row + dx];
+        const unsigned long long e = t.e[t.box(dx, dy, dz)];
         const uint32_t cnt = ent_live(e, stamp);
         const int64_t j0 = ent_start(e);
         for (uint32_t m = (uint32_t)lane; m < cnt; m += 32u) {
@@ -236,7 +231,7 @@ __global__ void __launch_bounds__(32 * kOvfWarps) k_force64o(DevCtx C) {
           if ((int64_t)id <= last || id >= best) continue;
           double gx, gy, gz;
           bool nz, dir;
-          if (pair64(o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir)) {
+          if (pair64(sc, o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir)) {
             best = id;
             bj = j;
           }
@@ -250,7 +245,7 @@ __global__ void __launch_bounds__(32 * kOvfWarps) k_force64o(DevCtx C) {
       if (lane == 0) {
         double gx, gy, gz;
         bool nz, dir;
-        pair64(o, C.c.r64[jb], sc.k, sc.gamma, gx, gy, gz, nz, dir);
+        pair64(sc, o, C.c.r64[jb], sc.k, sc.gamma, gx, gy, gz, nz, dir);
         ++ovl;
         nnz += nz ? 1u : 0u;
         if (dir) {

@@ -105,7 +105,8 @@ __device__ __forceinline__ void stream_flush(const DevCtx &C, StreamShared &sh, 
   __syncwarp();
 }
 
-template <int kMode>
+// kTorus: some simulation of the launch is toroidal (stencil boxes wrap).
+template <int kMode, bool kTorus>
 __global__ void __launch_bounds__(kStreamThreads, 4) k_force32w(DevCtx C) {
   constexpr bool kSym = kMode != kModeFull;
   constexpr int kRows = kSym ? 5 : 9;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_force32w(DevCtx C) {
   sh.kc[wid][lane] = make_float4(Lh, s.Ll, sc.kf, sc.gammaf);
   sh.rw[wid][lane] = rw;
   const uint32_t lm_le = FULL >> (31 - lane), lm_lt = lm_le >> 1;  // lanes at or below / below this one
-  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
+  const Stencil t = make_stencil<kTorus>(C, sc, s, cx, cy, cz);
   const uint32_t row0 = ((uint32_t)t.cz * (uint32_t)t.d1 + (uint32_t)t.cy) * (uint32_t)t.d0 + (uint32_t)t.cx;
   // the word every lane may load when it has no box to read: its own box's
   // (placed in a valid grid), else the table's first word
@@ -182,7 +183,8 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_force32w(DevCtx C) {
         const bool own = dx == 0 && dy == 0 && dz == 0;
         const float d2 = __fadd_rn(__fadd_rn(ex[dx + 1], ey[dy + 1]), ez[dz + 1]);
         const bool use = inrow && dx >= t.xlo && dx <= t.xhi && (own || !(d2 > reach2));
-        const unsigned long long e = __ldg(use ? t.e + (rowb + dx) : e_idle);
+        const uint32_t bi = (kTorus && t.torus) ? t.box(dx, dy, dz) : rowb + dx;
+        const unsigned long long e = __ldg(use ? t.e + bi : e_idle);
         const uint32_t es = ent_start(e), ec = use ? ent_live(e, stamp) : 0u;
         uint32_t j0 = es, cnt = ec;
         if (own && kSym) {
@@ -290,16 +292,20 @@ __global__ void __launch_bounds__(kAgentThreads) k_static(DevCtx C) {
 
 static inline unsigned int stream_blocks(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
-void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads) {
+void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads, bool torus) {
   if (threads > kStreamThreads) threads = kStreamThreads;
   const unsigned int nb = stream_blocks(C.total_slots, threads);
-  if (mode == kModeSymMasked) {
+  if (mode == kModeSymMasked)
     k_static<<<stream_blocks(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
-    k_force32w<kModeSymMasked><<<nb, threads, 0, st>>>(C);
-  } else if (mode == kModeFull) {
-    k_force32w<kModeFull><<<nb, threads, 0, st>>>(C);
+  const int m = mode == kModeSymMasked ? kModeSymMasked : (mode == kModeFull ? kModeFull : kModeSym);
+  if (torus) {
+    if (m == kModeSymMasked) k_force32w<kModeSymMasked, true><<<nb, threads, 0, st>>>(C);
+    else if (m == kModeFull) k_force32w<kModeFull, true><<<nb, threads, 0, st>>>(C);
+    else k_force32w<kModeSym, true><<<nb, threads, 0, st>>>(C);
   } else {
-    k_force32w<kModeSym><<<nb, threads, 0, st>>>(C);
+    if (m == kModeSymMasked) k_force32w<kModeSymMasked, false><<<nb, threads, 0, st>>>(C);
+    else if (m == kModeFull) k_force32w<kModeFull, false><<<nb, threads, 0, st>>>(C);
+    else k_force32w<kModeSym, false><<<nb, threads, 0, st>>>(C);
   }
 }
 

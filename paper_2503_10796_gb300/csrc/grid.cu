@@ -195,14 +195,36 @@ __global__ void k_params(DevCtx C, int32_t step) {
     st.L = L;
     bool ok = L > 0.0 && isfinite(L);
     int64_t nb = 1;
-    for (int a = 0; a < 3; ++a) {
-      if (!isfinite(st.o[a]) || !isfinite(mx[a])) ok = false;
-      double q = ok ? floor(__ddiv_rn(__dsub_rn(mx[a], st.o[a]), L)) : 0.0;
-      if (!(q < (double)(1ll << kCoordBits) - 1.0)) { ok = false; q = 0.0; }
-      st.dims[a] = (int64_t)q + 1;
-      nb *= st.dims[a];
+    if (sc.boundary == BOUND_TORUS) {
+      // the grid tiles the space: floor(size / L) >= 3 boxes per axis of
+      // length size / n from bmin (§4.4.11, toroidal)
+      for (int a = 0; a < 3; ++a)
+        if (!isfinite(st.o[a]) || !isfinite(mx[a])) ok = false;
+      if (!ok) set_err(g, ERR_COORD | ERR_NONFINITE);
+      const double q = ok ? floor(__ddiv_rn(sc.bsize, L)) : 0.0;
+      if (ok && !(q >= 3.0 && q < (double)(1ll << kCoordBits) - 1.0)) {
+        set_err(g, ERR_COORD | ERR_TORUS);
+        ok = false;
+      }
+      if (ok) {
+        L = __ddiv_rn(sc.bsize, q);
+        st.L = L;
+      }
+      for (int a = 0; a < 3; ++a) {
+        st.o[a] = sc.bmin;
+        st.dims[a] = ok ? (int64_t)q : 1;
+        nb *= st.dims[a];
+      }
+    } else {
+      for (int a = 0; a < 3; ++a) {
+        if (!isfinite(st.o[a]) || !isfinite(mx[a])) ok = false;
+        double q = ok ? floor(__ddiv_rn(__dsub_rn(mx[a], st.o[a]), L)) : 0.0;
+        if (!(q < (double)(1ll << kCoordBits) - 1.0)) { ok = false; q = 0.0; }
+        st.dims[a] = (int64_t)q + 1;
+        nb *= st.dims[a];
+      }
+      if (!ok) set_err(g, ERR_COORD | ERR_NONFINITE);
     }
-    if (!ok) set_err(g, ERR_COORD | ERR_NONFINITE);
     st.nboxes = nb;
     if (ok && (nb > sc.table_cap || nb >= (1ll << 32))) {
       set_err(g, ERR_TABLE);

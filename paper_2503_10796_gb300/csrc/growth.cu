@@ -271,12 +271,13 @@ __global__ void k_divide(DevCtx C, GrowBufs B) {
   double off = __dmul_rn(0.25, dh);
   double px = C.a.x[slot], py = C.a.y[slot], pz = C.a.z[slot];
   int64_t j = sc.base + n0 + r;
-  C.a.x[j] = __dadd_rn(px, __dmul_rn(off, u[0]));
-  C.a.y[j] = __dadd_rn(py, __dmul_rn(off, u[1]));
-  C.a.z[j] = __dadd_rn(pz, __dmul_rn(off, u[2]));
-  C.a.x[slot] = __dsub_rn(px, __dmul_rn(off, u[0]));
-  C.a.y[slot] = __dsub_rn(py, __dmul_rn(off, u[1]));
-  C.a.z[slot] = __dsub_rn(pz, __dmul_rn(off, u[2]));
+  // daughters under the space boundary condition (§4.4.11)
+  C.a.x[j] = bound_apply(sc, __dadd_rn(px, __dmul_rn(off, u[0])));
+  C.a.y[j] = bound_apply(sc, __dadd_rn(py, __dmul_rn(off, u[1])));
+  C.a.z[j] = bound_apply(sc, __dadd_rn(pz, __dmul_rn(off, u[2])));
+  C.a.x[slot] = bound_apply(sc, __dsub_rn(px, __dmul_rn(off, u[0])));
+  C.a.y[slot] = bound_apply(sc, __dsub_rn(py, __dmul_rn(off, u[1])));
+  C.a.z[slot] = bound_apply(sc, __dsub_rn(pz, __dmul_rn(off, u[2])));
   C.a.v[slot] = vh;
   C.a.v[j] = vh;
   C.a.d[slot] = dh;

@@ -31,13 +31,15 @@ struct ForcePlan {
 };
 // any_static: some FP32-path simulation detects static agents
 ForcePlan plan_force(int variant, bool any_static);
+// any_torus: some FP32-path simulation is toroidal (only variants 5 and 6
+// wrap the stencil)
 void launch_force(const DevCtx &C, cudaStream_t st, int variant = 0, bool has_fp32 = true, bool has_fp64 = true,
-                  bool any_static = false);
+                  bool any_static = false, bool any_torus = false);
 // force64.cu: the FP64 path (row kernel, overflow kernel)
 void launch_force64(const DevCtx &C, cudaStream_t st);
 // force_stream.cu: mode 0 half stencil, 1 full stencil with static skip,
 // 2 static flags first, then the half stencil
-void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads);
+void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads, bool torus);
 void launch_displace(const DevCtx &C, cudaStream_t st);
 
 // diffusion.cu (soma-clustering slice)
@@ -68,15 +70,23 @@ void launch_set_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, 
                        const double *xyz, const double *diam);
 void launch_update_agents(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const double *xyz,
                           const double *diam);
-void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, unsigned long long *bad);
+// first invalid row into *bad: a position not finite (outside the space of
+// a closed or toroidal boundary), a diameter not finite and > 0
+void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, unsigned long long *bad,
+                        int boundary = BOUND_OPEN, double bmin = 0.0, double bmax = 0.0);
 
 // query.cu: checkpoint state arrays (by caller ID) in device staging memory
 int64_t state_array_bytes(int64_t n);
 void launch_state_gather(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, void *staging);
 // first invalid row into *bad (set to ~0 by the caller)
 void launch_state_check(cudaStream_t st, int64_t n, const void *staging, unsigned long long *bad);
+// n rows of arrays laid out for layout_n rows (-1: n)
 void launch_state_scatter(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, int64_t cap,
-                          const void *staging);
+                          const void *staging, int64_t layout_n = -1);
+// removal: rows movers[k] -> holes[k] of the arrays of n_old agents, then the
+// first n_new rows marked changed
+void launch_state_remove(cudaStream_t st, void *staging, int64_t n_old, int64_t n_new, const int64_t *holes,
+                         const int64_t *movers, int64_t np);
 
 // sort.cu
 void launch_cell_order(const DevCtx &C, cudaStream_t st, void *scratch);

@@ -80,7 +80,7 @@ extern "C" int bdm_forces_noalloc(const bdm_params *params, int64_t n, const dou
   if (n > kMaxAgents) return BDM_E_CAPACITY;
   const bdm_params &p = *params;
   if (!(p.k >= 0) || !(p.gamma >= 0) || !(p.box_length >= 0) ||
-      (p.precision != BDM_PREC_FP64 && p.precision != BDM_PREC_FP32_FORCE))
+      (p.precision != BDM_PREC_FP64 && p.precision != BDM_PREC_FP32_FORCE) || p.boundary == BDM_BOUNDARY_TOROIDAL)
     return BDM_E_INVAL;
   if (n == 0) return BDM_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;

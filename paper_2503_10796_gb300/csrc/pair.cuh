@@ -35,30 +35,45 @@ __device__ __forceinline__ void ff_diff(float hi_i, float lo_i, float hi_j, floa
 // Overlap of two spheres from the definition in FP64 (used only to decide
 // pairs whose float-float overlap is within rounding of zero).
 static __device__ __noinline__ double exact_delta(const DevCtx &C, int32_t si, int32_t sj) {
-  double dx = __dsub_rn(C.a.x[si], C.a.x[sj]);
-  double dy = __dsub_rn(C.a.y[si], C.a.y[sj]);
-  double dz = __dsub_rn(C.a.z[si], C.a.z[sj]);
+  const SimConst &sc = C.sc[C.a.sim[si]];  // minimum images on a torus
+  double dx = coord_diff(sc, C.a.x[si], C.a.x[sj]);
+  double dy = coord_diff(sc, C.a.y[si], C.a.y[sj]);
+  double dz = coord_diff(sc, C.a.z[si], C.a.z[sj]);
   double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
   double R = __dadd_rn(__dmul_rn(0.5, C.a.d[si]), __dmul_rn(0.5, C.a.d[sj]));
   return __dsub_rn(R, __dsqrt_rn(s));
 }
 
-// Stencil bounds of a box: neighbor offsets that stay inside the grid.
+// Stencil bounds of a box: neighbor offsets that stay inside the grid (on a
+// torus all of them, the boxes wrapping around).
 struct Stencil {
   int xlo, xhi, ylo, yhi, zlo, zhi;
-  int cx, cy, cz, d0, d1;
+  int cx, cy, cz, d0, d1, d2;
+  bool torus;
   const unsigned long long *e;    // this simulation's table words
+  // table index (in the simulation's region) of stencil box (dx, dy, dz)
+  __device__ __forceinline__ uint32_t box(int dx, int dy, int dz) const {
+    int x = cx + dx, y = cy + dy, z = cz + dz;
+    if (torus) {
+      x = x < 0 ? x + d0 : (x >= d0 ? x - d0 : x);
+      y = y < 0 ? y + d1 : (y >= d1 ? y - d1 : y);
+      z = z < 0 ? z + d2 : (z >= d2 ? z - d2 : z);
+    }
+    return ((uint32_t)z * (uint32_t)d1 + (uint32_t)y) * (uint32_t)d0 + (uint32_t)x;
+  }
 };
 
+// kTorus = false: the launch holds no toroidal simulation (no wrap code).
+template <bool kTorus = true>
 __device__ __forceinline__ Stencil make_stencil(const DevCtx &C, const SimConst &sc, const SimState &s, int64_t cx,
                                                 int64_t cy, int64_t cz) {
   Stencil t;
   t.cx = (int)cx; t.cy = (int)cy; t.cz = (int)cz;
-  t.d0 = (int)s.dims[0]; t.d1 = (int)s.dims[1];
-  const int d2 = (int)s.dims[2];
-  t.xlo = t.cx > 0 ? -1 : 0; t.xhi = t.cx < t.d0 - 1 ? 1 : 0;
-  t.ylo = t.cy > 0 ? -1 : 0; t.yhi = t.cy < t.d1 - 1 ? 1 : 0;
-  t.zlo = t.cz > 0 ? -1 : 0; t.zhi = t.cz < d2 - 1 ? 1 : 0;
+  t.d0 = (int)s.dims[0]; t.d1 = (int)s.dims[1]; t.d2 = (int)s.dims[2];
+  t.torus = kTorus && sc.boundary == BOUND_TORUS;
+  t.xlo = (t.torus || t.cx > 0) ? -1 : 0; t.xhi = (t.torus || t.cx < t.d0 - 1) ? 1 : 0;
+  t.ylo = (t.torus || t.cy > 0) ? -1 : 0; t.yhi = (t.torus || t.cy < t.d1 - 1) ? 1 : 0;
+  t.zlo = (t.torus || t.cz > 0) ? -1 : 0; t.zhi = (t.torus || t.cz < t.d2 - 1) ? 1 : 0;
   t.e = C.tab.e + sc.table_base;
   return t;
 }
@@ -138,9 +153,9 @@ __device__ __forceinline__ bool pair32_vec(const DevCtx &C, int64_t p, const flo
 // Pair force of the FP64 path, the definition operation by operation (Eq.
 // 4.1/4.2 and the unit vector from j to i): false when the pair does not
 // overlap.  nz: the scalar force is not zero.
-__device__ __forceinline__ bool pair64(const double4_32a &o, const double4_32a &q, double k, double gam, double &gx,
-                                       double &gy, double &gz, bool &nz, bool &dir) {
-  const double ddx = __dsub_rn(o.x, q.x), ddy = __dsub_rn(o.y, q.y), ddz = __dsub_rn(o.z, q.z);
+__device__ __forceinline__ bool pair64(const SimConst &sc, const double4_32a &o, const double4_32a &q, double k,
+                                       double gam, double &gx, double &gy, double &gz, bool &nz, bool &dir) {
+  const double ddx = coord_diff(sc, o.x, q.x), ddy = coord_diff(sc, o.y, q.y), ddz = coord_diff(sc, o.z, q.z);
   const double s2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
   const double R = __dadd_rn(o.w, q.w);
   const double dist = __dsqrt_rn(s2);

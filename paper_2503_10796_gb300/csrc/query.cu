@@ -36,8 +36,9 @@ void launch_boxids(const DevCtx &C, cudaStream_t st, int sim, int64_t *out_by_id
 // offsets come from an exclusive scan over IDs, and each agent sorts its own
 // short list, so the output is ordered by (i, j).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool pair_hit(double4_32a a, double4_32a b, double R2, bool radius_mode) {
-  double dx = __dsub_rn(a.x, b.x), dy = __dsub_rn(a.y, b.y), dz = __dsub_rn(a.z, b.z);
+__device__ __forceinline__ bool pair_hit(const SimConst &sc, double4_32a a, double4_32a b, double R2,
+                                         bool radius_mode) {
+  const double dx = coord_diff(sc, a.x, b.x), dy = coord_diff(sc, a.y, b.y), dz = coord_diff(sc, a.z, b.z);
   double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
   if (radius_mode) return s < R2;
   return __dsub_rn(__dadd_rn(a.w, b.w), __dsqrt_rn(s)) > 0.0;
@@ -59,15 +60,10 @@ __global__ void k_pairs(DevCtx C, int sim, int64_t cell_base, int64_t n, double 
   int64_t cnt = 0;
   int64_t off = kWrite ? offsets[id] : 0;
   for (int dz = -1; dz <= 1; ++dz) {
-    int64_t z = cz + dz;
-    if (z < 0 || z >= s.dims[2]) continue;
     for (int dy = -1; dy <= 1; ++dy) {
-      int64_t y = cy + dy;
-      if (y < 0 || y >= s.dims[1]) continue;
       for (int dx = -1; dx <= 1; ++dx) {
-        int64_t x = cx + dx;
-        if (x < 0 || x >= s.dims[0]) continue;
-        int64_t idx = sc.table_base + linear_box(s, x, y, z);
+        int64_t idx;
+        if (!stencil_index(sc, s, cx, cy, cz, dx, dy, dz, idx)) continue;
         const unsigned long long e = C.tab.e[idx];
         const uint32_t c = ent_live(e, stamp);
         if (!c) continue;
@@ -75,7 +71,7 @@ __global__ void k_pairs(DevCtx C, int sim, int64_t cell_base, int64_t n, double 
         for (int64_t j = start; j < start + c; ++j) {
           int64_t jd = C.a.id[Q.slot[j]];
           if (jd <= id) continue;
-          if (!pair_hit(o, Q.r64[j], R2, radius_mode != 0)) continue;
+          if (!pair_hit(sc, o, Q.r64[j], R2, radius_mode != 0)) continue;
           if (kWrite) {
             int64_t k = off + cnt;
             if (k < cap) {
@@ -342,17 +338,24 @@ void launch_update_agents(const DevCtx &C, cudaStream_t st, int64_t base, int64_
 
 // Smallest row with a non-finite coordinate or (diam given) a diameter that
 // is not finite and > 0 (*bad stays all-ones when every row is valid).
-__global__ void k_check_input(int64_t n, const double *xyz, const double *diam, unsigned long long *bad) {
+__global__ void k_check_input(int64_t n, const double *xyz, const double *diam, unsigned long long *bad, int boundary,
+                              double bmin, double bmax) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  bool ok = isfinite(xyz[3 * i]) && isfinite(xyz[3 * i + 1]) && isfinite(xyz[3 * i + 2]) &&
-            (!diam || (diam[i] > 0.0 && isfinite(diam[i])));
+  bool ok = (!diam || (diam[i] > 0.0 && isfinite(diam[i])));
+  for (int a = 0; a < 3; ++a) {
+    const double v = xyz[3 * i + a];
+    ok = ok && isfinite(v);
+    // positions of a closed space lie in [bmin, bmax], of a torus in [bmin, bmax)
+    if (boundary == BOUND_CLOSED) ok = ok && v >= bmin && v <= bmax;
+    if (boundary == BOUND_TORUS) ok = ok && v >= bmin && v < bmax;
+  }
   if (!ok) atomicMin(bad, (unsigned long long)i);
 }
 
-void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, unsigned long long *bad) {
-  if (n <= 0) return;
-  k_check_input<<<blocks_for(n, kThreads), kThreads, 0, st>>>(n, xyz, diam, bad);
+void launch_check_input(cudaStream_t st, int64_t n, const double *xyz, const double *diam, unsigned long long *bad,
+                        int boundary, double bmin, double bmax) {
+  k_check_input<<<blocks_for(n, kThreads), kThreads, 0, st>>>(n, xyz, diam, bad, boundary, bmin, bmax);
 }
 
 // ---------------------------------------------------------------------------
@@ -428,10 +431,33 @@ void launch_state_check(cudaStream_t st, int64_t n, const void *staging, unsigne
 }
 
 void launch_state_scatter(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, int64_t cap,
-                          const void *staging) {
+                          const void *staging, int64_t layout_n) {
   if (cap <= 0) return;
-  k_state_scatter<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, sim, base, n, cap,
-                                                                  state_arrays(const_cast<void *>(staging), n));
+  k_state_scatter<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(
+      C, sim, base, n, cap, state_arrays(const_cast<void *>(staging), layout_n < 0 ? n : layout_n));
+}
+
+// Removal (§5.3.2): rows of the by-ID state arrays move from movers[k] into
+// holes[k] (holes below the new count, movers at or above it, so no row is
+// both); then every surviving row counts as changed and not static.
+__global__ void k_state_move(StateArrays a, const int64_t *holes, const int64_t *movers, int64_t np) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const int64_t h = holes[k], m = movers[k];
+  a.x[h] = a.x[m]; a.y[h] = a.y[m]; a.z[h] = a.z[m]; a.d[h] = a.d[m]; a.v[h] = a.v[m];
+  a.pkey[h] = a.pkey[m]; a.nnz[h] = a.nnz[m];
+}
+
+__global__ void k_state_mark_changed(StateArrays a, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a.flags[i] = FLAG_CHANGED;
+}
+
+void launch_state_remove(cudaStream_t st, void *staging, int64_t n_old, int64_t n_new, const int64_t *holes,
+                         const int64_t *movers, int64_t np) {
+  const StateArrays a = state_arrays(staging, n_old);
+  if (np > 0) k_state_move<<<blocks_for(np, kThreads), kThreads, 0, st>>>(a, holes, movers, np);
+  if (n_new > 0) k_state_mark_changed<<<blocks_for(n_new, kThreads), kThreads, 0, st>>>(a, n_new);
 }
 
 }  // namespace bdm
