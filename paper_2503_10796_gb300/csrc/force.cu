@@ -444,12 +444,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
 }
 
 // S5: displacement, then the space boundary condition (§4.4.11) on the new
-// position.  Static agents keep their position and nnz.
+// position.  Static agents keep their position and nnz.  kOne: a context
+// of one simulation (no per-cell simulation index to wait for).
+template <bool kOne>
 __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
-  int sim = C.c.sim[p];
+  int sim = kOne ? 0 : C.c.sim[p];
   const SimConst &sc = C.sc[sim];
   if (!C.ss[sim].valid) return;
   int32_t slot = C.c.slot[p];
@@ -545,7 +547,10 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, 
 }
 
 void launch_displace(const DevCtx &C, cudaStream_t st) {
-  k_displace<<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
+  if (C.n_sims == 1)
+    k_displace<true><<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
+  else
+    k_displace<false><<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
 }
 
 }  // namespace bdm

@@ -106,7 +106,9 @@ __device__ __forceinline__ void stream_flush(const DevCtx &C, StreamShared &sh, 
 }
 
 // kTorus: some simulation of the launch is toroidal (stencil boxes wrap).
-template <int kMode, bool kTorus>
+// kOne: the context holds one simulation (its constants need no per-cell
+// simulation index, which would be the first load every later one waits on).
+template <int kMode, bool kTorus, bool kOne>
 __global__ void __launch_bounds__(kStreamThreads, 4) k_force32w(DevCtx C) {
   constexpr bool kSym = kMode != kModeFull;
   constexpr int kRows = kSym ? 5 : 9;
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_force32w(DevCtx C) {
   const int64_t p = p0 + lane;
   bool active = p < ncell;
   const int64_t pc = active ? p : p0;  // a valid cell for every lane
-  const int sim = C.c.sim[pc];
+  const int sim = kOne ? 0 : C.c.sim[pc];
   const SimConst &sc = C.sc[sim];
   const SimState &s = C.ss[sim];
   active = active && s.valid && sc.precision != BDM_PREC_FP64;
@@ -292,20 +294,25 @@ __global__ void __launch_bounds__(kAgentThreads) k_static(DevCtx C) {
 
 static inline unsigned int stream_blocks(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
+template <bool kTorus, bool kOne>
+static void launch_stream_mode(const DevCtx &C, cudaStream_t st, int mode, unsigned int nb, int threads) {
+  if (mode == kModeSymMasked) k_force32w<kModeSymMasked, kTorus, kOne><<<nb, threads, 0, st>>>(C);
+  else if (mode == kModeFull) k_force32w<kModeFull, kTorus, kOne><<<nb, threads, 0, st>>>(C);
+  else k_force32w<kModeSym, kTorus, kOne><<<nb, threads, 0, st>>>(C);
+}
+
 void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads, bool torus) {
   if (threads > kStreamThreads) threads = kStreamThreads;
   const unsigned int nb = stream_blocks(C.total_slots, threads);
   if (mode == kModeSymMasked)
     k_static<<<stream_blocks(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
-  const int m = mode == kModeSymMasked ? kModeSymMasked : (mode == kModeFull ? kModeFull : kModeSym);
+  const bool one = C.n_sims == 1;
   if (torus) {
-    if (m == kModeSymMasked) k_force32w<kModeSymMasked, true><<<nb, threads, 0, st>>>(C);
-    else if (m == kModeFull) k_force32w<kModeFull, true><<<nb, threads, 0, st>>>(C);
-    else k_force32w<kModeSym, true><<<nb, threads, 0, st>>>(C);
+    if (one) launch_stream_mode<true, true>(C, st, mode, nb, threads);
+    else launch_stream_mode<true, false>(C, st, mode, nb, threads);
   } else {
-    if (m == kModeSymMasked) k_force32w<kModeSymMasked, false><<<nb, threads, 0, st>>>(C);
-    else if (m == kModeFull) k_force32w<kModeFull, false><<<nb, threads, 0, st>>>(C);
-    else k_force32w<kModeSym, false><<<nb, threads, 0, st>>>(C);
+    if (one) launch_stream_mode<false, true>(C, st, mode, nb, threads);
+    else launch_stream_mode<false, false>(C, st, mode, nb, threads);
   }
 }
 

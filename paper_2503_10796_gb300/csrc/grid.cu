@@ -306,11 +306,14 @@ __device__ __forceinline__ void tab_mark_dirty(unsigned long long *e, uint32_t s
 // query keys and leaves the history alone.  Every load that does not depend
 // on another is issued before the first test, so that one thread waits for
 // few round trips in a row.
+// kOne: the context holds one simulation, which owns every slot below
+// total_slots (no per-slot simulation index to wait for).
+template <bool kOne>
 __global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool in = slot < C.total_slots;
   const int64_t sl = in ? slot : C.total_slots - 1;
-  const int sim = C.a.sim[sl];
+  const int sim = kOne ? 0 : C.a.sim[sl];
   const double p[3] = {C.a.x[sl], C.a.y[sl], C.a.z[sl]};
   const uint64_t pk_prev_in = step ? C.a.pkey[sl] : 0ull;
   const uint8_t fl = step ? C.a.flags[sl] : (uint8_t)0;
@@ -427,7 +430,7 @@ __device__ __forceinline__ void tile_publish(unsigned long long *w, uint32_t sta
       ((unsigned long long)stamp << 34) | ((unsigned long long)state << 32) | (unsigned long long)v;
 }
 
-template <bool kOrdered>
+template <bool kOrdered, bool kOne>
 __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t *keys) {
   __shared__ uint32_t sh[33];
   __shared__ uint32_t s_tile, s_base;
@@ -447,7 +450,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
   int sim[kScanItems];
   if (base + kScanItems <= C.total_slots) {
     const uint4 r4 = *reinterpret_cast<const uint4 *>(C.a.rank + base);
-    const int4 s4 = *reinterpret_cast<const int4 *>(C.a.sim + base);
+    const int4 s4 = kOne ? make_int4(0, 0, 0, 0) : *reinterpret_cast<const int4 *>(C.a.sim + base);
     const ulonglong2 k01 = *reinterpret_cast<const ulonglong2 *>(keys + base);
     const ulonglong2 k23 = *reinterpret_cast<const ulonglong2 *>(keys + base + 2);
     rank[0] = r4.x; rank[1] = r4.y; rank[2] = r4.z; rank[3] = r4.w;
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
       const int64_t sl = slot < C.total_slots ? slot : C.total_slots - 1;
       rank[i] = C.a.rank[sl];
       pk[i] = keys[sl];
-      sim[i] = slot < C.total_slots ? C.a.sim[sl] : -1;
+      sim[i] = slot < C.total_slots ? (kOne ? 0 : C.a.sim[sl]) : -1;
     }
   }
   unsigned long long e[kScanItems];
@@ -575,12 +578,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
 
 // zero_f32: clear the FP32 force of every placed FP32-path agent (the
 // symmetric force walk adds into it).
+template <bool kOne>
 __global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, const uint64_t *keys, int fp64_records,
                                                    int zero_f32) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= C.total_slots) return;
   // every per-slot load first: they do not depend on one another
-  const int sim = C.a.sim[slot];
+  const int sim = kOne ? 0 : C.a.sim[slot];
   const uint64_t pk = keys[slot];
   const uint32_t rank = C.a.rank[slot];
   const double pos[3] = {C.a.x[slot], C.a.y[slot], C.a.z[slot]};
@@ -643,22 +647,35 @@ void launch_bbox(const DevCtx &C, cudaStream_t st) {
 void launch_params(const DevCtx &C, cudaStream_t st, int step) { k_params<<<1, 256, 0, st>>>(C, step); }
 
 void launch_count(const DevCtx &C, cudaStream_t st, int step) {
-  k_count<<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C, step);
+  if (C.n_sims == 1)
+    k_count<true><<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C, step);
+  else
+    k_count<false><<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C, step);
 }
 
 int64_t scan_tiles(int64_t total_slots) { return (total_slots + kScanTile - 1) / kScanTile; }
 
 void launch_scan(const DevCtx &C, cudaStream_t st, int step, int ordered) {
   const int64_t G = scan_tiles(C.total_slots);
-  if (ordered)
-    k_scan<true><<<(unsigned int)G, kScanThreads, 0, st>>>(C, step ? C.a.pkey : C.qkey);
-  else
-    k_scan<false><<<(unsigned int)G, kScanThreads, 0, st>>>(C, step ? C.a.pkey : C.qkey);
+  const uint64_t *keys = step ? C.a.pkey : C.qkey;
+  const bool one = C.n_sims == 1;
+  if (ordered) {
+    if (one) k_scan<true, true><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys);
+    else k_scan<true, false><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys);
+  } else {
+    if (one) k_scan<false, true><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys);
+    else k_scan<false, false><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys);
+  }
 }
 
 void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32) {
-  k_place<<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C, step ? C.c : C.q, step ? C.a.pkey : C.qkey,
-                                                                     step ? 0 : 1, step ? zero_f32 : 0);
+  const unsigned int nb = blocks_for(C.total_slots, kAgentThreads);
+  if (C.n_sims == 1)
+    k_place<true><<<nb, kAgentThreads, 0, st>>>(C, step ? C.c : C.q, step ? C.a.pkey : C.qkey, step ? 0 : 1,
+                                                 step ? zero_f32 : 0);
+  else
+    k_place<false><<<nb, kAgentThreads, 0, st>>>(C, step ? C.c : C.q, step ? C.a.pkey : C.qkey, step ? 0 : 1,
+                                                  step ? zero_f32 : 0);
 }
 
 }  // namespace bdm
