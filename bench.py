@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--static-leg", type=int, default=-1,
                     help="static detection on/off leg; -1: on for the clustered 8M workload")
     ap.add_argument("--static-steps", type=int, default=100)
+    ap.add_argument("--iter-batch", type=int, default=-1, help="iterations per graph; -1: autotune")
+    ap.add_argument("--box-scale", type=int, default=-1, help="box length in %% of the largest diameter; -1: autotune")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default tuning (with the fixed settings), e.g. for a profiler capture")
     args = ap.parse_args()
@@ -415,6 +417,12 @@ def main():
     if args.force_variant >= 0:
         fixed["force_variant"] = args.force_variant
         knobs &= ~binding.TUNE_FORCE
+    if args.iter_batch >= 0:
+        fixed["iter_batch"] = args.iter_batch
+        knobs &= ~binding.TUNE_BATCH
+    if args.box_scale >= 0:
+        fixed["box_scale_pct"] = args.box_scale
+        knobs &= ~binding.TUNE_BOX
     if fixed:
         t = ctx.get_tuning()
         t.update(fixed)

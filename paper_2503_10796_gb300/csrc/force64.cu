@@ -21,11 +21,9 @@
 // partner ID and adds it up.  An agent with more than kSortCap overlapping
 // partners is left to k_force64o.
 //
-// k_force64o: a warp per such agent.  The warp finds the agent's pairs in
-// ascending partner ID one at a time (each lane scans a share of the
-// stencil's candidates for the smallest partner ID above the last one),
-// evaluates each and adds it: quadratic in the partner count, for the rare
-// crowded agent, and without a limit on the count.
+// k_force64o: a warp per such agent: the overlapping pairs of the whole
+// stencil in shared memory, sorted by partner ID, added in that order (and,
+// beyond kOvfCap partners, a selection of the next partner ID at a time).
 #include "pair.cuh"
 
 namespace bdm {
@@ -192,16 +190,78 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
 }
 
 // One warp per overflow agent (grid-stride over the list the row kernel
-// wrote; the grid is fixed, so the launch can be captured).
-constexpr int kOvfWarps = 4;
+// wrote; the grid is fixed, so the launch can be captured).  The warp
+// evaluates the agent's candidates 32 at a time and keeps the overlapping
+// ones in shared memory, sorts them by partner ID (bitonic sort of packed
+// {ID, slot} keys) and adds them in that order.  More than kOvfCap partners
+// (a pathological crowd) take the selection loop below instead.
+constexpr int kOvfCap = 704;
+constexpr int kOvfKeys = 1024;  // bitonic sort size (a power of two >= kOvfCap)
 
-__global__ void __launch_bounds__(32 * kOvfWarps) k_force64o(DevCtx C) {
+struct OvfShared {
+  unsigned long long key[kOvfKeys];  // partner ID << 32 | index of the contribution
+  double gx[kOvfCap], gy[kOvfCap], gz[kOvfCap];
+  uint32_t flags[kOvfCap];
+};
+
+__device__ void ovf_selection(const DevCtx &C, const SimConst &sc, const Stencil &t, int64_t p, const double4_32a &o,
+                              uint32_t stamp, int lane, double &fx, double &fy, double &fz, uint32_t &nnz,
+                              uint32_t &ovl) {
+  const unsigned FULL = 0xffffffffu;
+  const int nx = t.xhi - t.xlo + 1, ny = t.yhi - t.ylo + 1, nzb = t.zhi - t.zlo + 1;
+  const int nbox = nx * ny * nzb;
+  int64_t last = -1;  // partner ID added last
+  for (;;) {
+    // the overlapping partner with the smallest ID above `last`
+    uint32_t best = 0xFFFFFFFFu;
+    int64_t bj = -1;
+    for (int b = 0; b < nbox; ++b) {
+      const int dx = t.xlo + b % nx, dy = t.ylo + (b / nx) % ny, dz = t.zlo + b / (nx * ny);
+      const unsigned long long e = t.e[t.box(dx, dy, dz)];
+      const uint32_t cnt = ent_live(e, stamp);
+      const int64_t j0 = ent_start(e);
+      for (uint32_t m = (uint32_t)lane; m < cnt; m += 32u) {
+        const int64_t j = j0 + m;
+        if (j == p) continue;
+        const uint32_t id = partner_id(C, j);
+        if ((int64_t)id <= last || id >= best) continue;
+        double gx, gy, gz;
+        bool nz, dir;
+        if (pair64(sc, o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir)) {
+          best = id;
+          bj = j;
+        }
+      }
+    }
+    const uint32_t wbest = __reduce_min_sync(FULL, best);
+    if (wbest == 0xFFFFFFFFu) break;
+    const unsigned who = __ballot_sync(FULL, best == wbest && bj >= 0);
+    const int src = __ffs(who) - 1;
+    const int64_t jb = __shfl_sync(FULL, bj, src);
+    if (lane == 0) {
+      double gx, gy, gz;
+      bool nz, dir;
+      pair64(sc, o, C.c.r64[jb], sc.k, sc.gamma, gx, gy, gz, nz, dir);
+      ++ovl;
+      nnz += nz ? 1u : 0u;
+      if (dir) {
+        fx = __dadd_rn(fx, gx);
+        fy = __dadd_rn(fy, gy);
+        fz = __dadd_rn(fz, gz);
+      }
+    }
+    last = (int64_t)wbest;
+  }
+}
+
+__global__ void __launch_bounds__(32) k_force64o(DevCtx C) {
+  __shared__ OvfShared sh;
   if (C.g->err & ERR_TABLE) return;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const uint32_t nov = C.g->n_ovf;
   const uint32_t stamp = C.g->stamp & kStampMask;
-  for (uint32_t w = blockIdx.x * kOvfWarps + (threadIdx.x >> 5); w < nov; w += gridDim.x * kOvfWarps) {
+  for (uint32_t w = blockIdx.x; w < nov; w += gridDim.x) {
     const int64_t p = C.ovf[w];
     const int sim = C.c.sim[p];
     const SimConst &sc = C.sc[sim];
@@ -212,54 +272,72 @@ __global__ void __launch_bounds__(32 * kOvfWarps) k_force64o(DevCtx C) {
     const double4_32a o = C.c.r64[p];
     const int nx = t.xhi - t.xlo + 1, ny = t.yhi - t.ylo + 1, nzb = t.zhi - t.zlo + 1;
     const int nbox = nx * ny * nzb;
+    // every overlapping pair of the stencil, 32 candidates at a time
+    uint32_t n = 0;  // overlapping pairs found (warp-uniform)
+    for (int b = 0; b < nbox; ++b) {
+      const int dx = t.xlo + b % nx, dy = t.ylo + (b / nx) % ny, dz = t.zlo + b / (nx * ny);
+      const unsigned long long e = t.e[t.box(dx, dy, dz)];
+      const uint32_t cnt = ent_live(e, stamp);
+      const int64_t j0 = ent_start(e);
+      for (uint32_t m0 = 0; m0 < cnt; m0 += 32u) {
+        const uint32_t m = m0 + (uint32_t)lane;
+        const int64_t j = j0 + m;
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        bool nz = false, dir = false, hit = false;
+        if (m < cnt && j != p) hit = pair64(sc, o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir);
+        const unsigned B = __ballot_sync(FULL, hit);
+        const uint32_t k = n + (uint32_t)__popc(B & ((1u << lane) - 1u));
+        if (hit && k < (uint32_t)kOvfCap) {
+          sh.key[k] = ((unsigned long long)partner_id(C, j) << 32) | k;
+          sh.gx[k] = gx; sh.gy[k] = gy; sh.gz[k] = gz;
+          sh.flags[k] = (nz ? 1u : 0u) | (dir ? 2u : 0u);
+        }
+        n += (uint32_t)__popc(B);
+      }
+    }
     double fx = 0.0, fy = 0.0, fz = 0.0;
     uint32_t nnz = 0, ovl = 0;
-    int64_t last = -1;  // partner ID added last
-    for (;;) {
-      // the overlapping partner with the smallest ID above `last`
-      uint32_t best = 0xFFFFFFFFu;
-      int64_t bj = -1;
-      for (int b = 0; b < nbox; ++b) {
-        const int dx = t.xlo + b % nx, dy = t.ylo + (b / nx) % ny, dz = t.zlo + b / (nx * ny);
-        const unsigned long long e = t.e[t.box(dx, dy, dz)];
-        const uint32_t cnt = ent_live(e, stamp);
-        const int64_t j0 = ent_start(e);
-        for (uint32_t m = (uint32_t)lane; m < cnt; m += 32u) {
-          const int64_t j = j0 + m;
-          if (j == p) continue;
-          const uint32_t id = partner_id(C, j);
-          if ((int64_t)id <= last || id >= best) continue;
-          double gx, gy, gz;
-          bool nz, dir;
-          if (pair64(sc, o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir)) {
-            best = id;
-            bj = j;
+    if (n <= (uint32_t)kOvfCap) {
+      uint32_t n2 = 32;  // the sort's size: a power of two >= n
+      while (n2 < n) n2 <<= 1;
+      for (uint32_t k = n + (uint32_t)lane; k < n2; k += 32u) sh.key[k] = ~0ull;
+      __syncwarp();
+      // bitonic sort of the keys, ascending
+      for (uint32_t size = 2; size <= n2; size <<= 1)
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+          for (uint32_t i = (uint32_t)lane; i < n2; i += 32u) {
+            const uint32_t jx = i ^ stride;
+            if (jx > i) {
+              const unsigned long long a = sh.key[i], bk = sh.key[jx];
+              const bool up = (i & size) == 0;
+              if ((a > bk) == up) {
+                sh.key[i] = bk;
+                sh.key[jx] = a;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      if (lane == 0) {
+        for (uint32_t q = 0; q < n; ++q) {
+          const uint32_t k = (uint32_t)sh.key[q];
+          nnz += sh.flags[k] & 1u;
+          if (sh.flags[k] & 2u) {
+            fx = __dadd_rn(fx, sh.gx[k]);
+            fy = __dadd_rn(fy, sh.gy[k]);
+            fz = __dadd_rn(fz, sh.gz[k]);
           }
         }
+        ovl = n;
       }
-      const uint32_t wbest = __reduce_min_sync(FULL, best);
-      if (wbest == 0xFFFFFFFFu) break;
-      const unsigned who = __ballot_sync(FULL, best == wbest && bj >= 0);
-      const int src = __ffs(who) - 1;
-      const int64_t jb = __shfl_sync(FULL, bj, src);
-      if (lane == 0) {
-        double gx, gy, gz;
-        bool nz, dir;
-        pair64(sc, o, C.c.r64[jb], sc.k, sc.gamma, gx, gy, gz, nz, dir);
-        ++ovl;
-        nnz += nz ? 1u : 0u;
-        if (dir) {
-          fx = __dadd_rn(fx, gx);
-          fy = __dadd_rn(fy, gy);
-          fz = __dadd_rn(fz, gz);
-        }
-      }
-      last = (int64_t)wbest;
+    } else {
+      ovf_selection(C, sc, t, p, o, stamp, lane, fx, fy, fz, nnz, ovl);
     }
     if (lane == 0) {
       C.c.f64[p] = make_double4_32a(fx, fy, fz, (double)ovl);
       C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
     }
+    __syncwarp();
   }
 }
 
@@ -267,7 +345,7 @@ __global__ void __launch_bounds__(32 * kOvfWarps) k_force64o(DevCtx C) {
 
 void launch_force64(const DevCtx &C, cudaStream_t st) {
   k_force64r<<<(unsigned int)((C.total_slots + kRowAgents - 1) / kRowAgents), kRowThreads, 0, st>>>(C);
-  k_force64o<<<152, 32 * kOvfWarps, 0, st>>>(C);
+  k_force64o<<<152 * 6, 32, 0, st>>>(C);
 }
 
 }  // namespace bdm

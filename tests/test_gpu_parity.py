@@ -706,6 +706,31 @@ def test_fp64_growth_division_bit_exact(orc):
         assert np.array_equal(d_g, d_o) and np.array_equal(x_g, x_o), t
 
 
+def test_fp64_crowd_beyond_the_sort_capacity(orc):
+    """760 agents of diameter 9.5-10.5 in a cube of side 5: every pair
+    overlaps (the cube's diagonal is 8.7), so each agent has 759 partners,
+    more than the FP64 overflow kernel sorts in shared memory (704), and its
+    selection of the next partner ID takes over; the forces are still added
+    in ascending partner ID, bit for bit the oracle's."""
+    rng = np.random.default_rng(21)
+    xyz = 100.0 + rng.uniform(0.0, 5.0, (760, 3))
+    d = rng.uniform(9.5, 10.5, 760)
+    pop = workloads.Population(xyz, d, workloads.SimParams(precision=0, dt=0.01))
+    ctx = ctx_for(pop)
+    o = orc_for(pop)
+    for t in range(3):
+        ctx.step(1)
+        o.step(1)
+        x_g, _ = ctx.get_agents(0)
+        x_o, _, _ = o.get()
+        assert np.array_equal(x_g, x_o), t
+        F_g, nnz_g, _, ov = ctx.forces(0, overlaps=True)
+        F_o, _, nnz_o, _, _ = o.last()
+        assert np.array_equal(F_g, F_o) and np.array_equal(nnz_g, np.minimum(nnz_o, 255)), t
+        if t == 0:
+            assert (ov == 759).all()
+
+
 def test_fp64_batched_simulations_bit_exact(orc):
     pops = workloads.batched_sweep(n_sims=5, lo=50, hi=3000, seed=9, precision=0)
     ctx = ctx_for(pops)
