@@ -53,10 +53,11 @@ ALG_BYTES_BOX = 8.0
 # DRAM bytes (read + write) per agent of a force kernel, from an ncu capture
 # of the 1M-agent clustered case (the per-cluster shape of the 8M case),
 # scaled by the agents of a launch for the clustered workloads and null
-# elsewhere.  An entry holds only while the kernel is the one captured.
-FORCE_TRAFFIC_B_PER_AGENT = {"k_force32w": 104.6}
+# elsewhere.  Keyed by force variant; an entry holds only while the
+# variant's kernel is the one captured.
+FORCE_TRAFFIC_B_PER_AGENT = {5: 104.6}
 FORCE_KERNEL = {0: "k_force32s", 1: "k_force32d", 2: "k_force", 3: "k_force32d", 4: "k_force32s (direct)",
-                5: "k_force32w", 6: "k_static + k_force32w"}
+                5: "k_force32w", 6: "k_static + k_force32w", 7: "k_force32w", 8: "k_static + k_force32w"}
 # Workloads whose configuration fixes the re-sort (interval, curve): the
 # autotuner leaves those two knobs alone there.
 FIXED_SORT = {"clustered_8M": (10, 0), "clustered_1M": (10, 0)}
@@ -477,8 +478,8 @@ def main():
         variant = 1  # the symmetric walks do not run with static detection
     kernel = FORCE_KERNEL.get(variant, "k_force") if prec == 1 else "k_force64r"
     traffic = None
-    if kernel in FORCE_TRAFFIC_B_PER_AGENT and args.workload.startswith("clustered"):
-        traffic = FORCE_TRAFFIC_B_PER_AGENT[kernel] * (n_agents - st_static)
+    if prec == 1 and variant in FORCE_TRAFFIC_B_PER_AGENT and args.workload.startswith("clustered"):
+        traffic = FORCE_TRAFFIC_B_PER_AGENT[variant] * (n_agents - st_static)
     achieved = alg / (force_ms * 1e-3) / 1e9
 
     # end to end through the public API with host buffers: every step moves

@@ -292,7 +292,10 @@ typedef struct {
                               agents); 1 direct walk, rows flattened, pair
                               evaluation deferred; 2 direct loop, pairs evaluated
                               in the walk; 3 as 1 box by box; 4 as 0 with every
-                              pair evaluated in the walk (crowded agents) */
+                              pair evaluated in the walk (crowded agents); 7 and
+                              8 as 5 and 6 with the stream pipelined (the whole
+                              half stencil read at once, each round's candidate
+                              records requested one round ahead) */
   int32_t sort_interval;   /* -1: every simulation's own sort_interval;
                               >= 0: this re-sort interval for all simulations */
   int32_t sort_curve;      /* order the re-sort gives the storage: 0 Morton order of the

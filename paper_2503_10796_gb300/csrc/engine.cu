@@ -265,7 +265,7 @@ void launch_iteration(bdm_ctx *c, int sort) {
       if (c->params[s].boundary == BDM_BOUNDARY_TOROIDAL) any_torus = true;
     }
   // only the stream kernels walk a wrapped stencil
-  const ForcePlan pl = plan_force(any_torus && c->force_variant != 6 ? 5 : c->force_variant, any_static);
+  const ForcePlan pl = plan_force(any_torus && c->force_variant < 5 ? 5 : c->force_variant, any_static);
   stage_begin(c, 1);
   launch_count(D, st, 1);
   stage_end(c);
@@ -573,6 +573,9 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
     if (check_params(per_sim[s], why)) return fail(nullptr, BDM_E_INVAL, "simulation " + std::to_string(s) + ": " + why);
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return fail(nullptr, BDM_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  // kernel attributes are per device; set before any launch or capture
+  e = init_force_stream();
+  if (e != cudaSuccess) return fail(nullptr, BDM_E_CUDA, std::string("stream kernel attributes: ") + cudaGetErrorString(e));
   bdm_ctx *c = new bdm_ctx();
   c->device = device;
   c->n_sims = n_sims;

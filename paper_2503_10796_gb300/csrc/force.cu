@@ -526,7 +526,8 @@ ForcePlan plan_force(int variant, bool any_static) {
   // partner would miss them, so simulations with static detection take the
   // deferred walk instead of 0 and 4
   if ((variant == 0 || variant == 4) && any_static) pl.variant = 1;
-  pl.zero_f32 = pl.variant == 0 || pl.variant == 4 || pl.variant == 6 || (pl.variant == 5 && !any_static);
+  pl.zero_f32 = pl.variant == 0 || pl.variant == 4 || pl.variant == 6 || pl.variant == 8 ||
+                ((pl.variant == 5 || pl.variant == 7) && !any_static);
   return pl;
 }
 
@@ -539,8 +540,8 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, 
     else if (variant == 0) k_force32s<false><<<nb, th, 0, st>>>(C);
     else if (variant == 4) k_force32s<true><<<nb, th, 0, st>>>(C);
     else if (variant == 3) k_force32d<false><<<nb, th, 0, st>>>(C);
-    else if (variant == 5) launch_force_stream(C, st, any_static ? 1 : 0, th, any_torus);
-    else if (variant == 6) launch_force_stream(C, st, any_static ? 2 : 0, th, any_torus);
+    else if (variant == 5 || variant == 7) launch_force_stream(C, st, any_static ? 1 : 0, th, any_torus, variant == 7);
+    else if (variant == 6 || variant == 8) launch_force_stream(C, st, any_static ? 2 : 0, th, any_torus, variant == 8);
     else k_force32d<true><<<nb, th, 0, st>>>(C);
   }
   if (has_fp64) launch_force64(C, st);

@@ -18,12 +18,13 @@
 // pairs one per lane and round (a row with more candidates evaluates them in
 // place).  Each evaluated pair appends {partner ID, force} to its agent's
 // list in shared memory; the agent's first thread then orders the list by
-// partner ID and adds it up.  An agent with more than kSortCap overlapping
-// partners is left to k_force64o.
+// partner ID and adds it up.  An agent with more than kSortCap candidates
+// passing the filter evaluates nothing here and is left to k_force64o.
 //
 // k_force64o: a warp per such agent: the overlapping pairs of the whole
-// stencil in shared memory, sorted by partner ID, added in that order (and,
-// beyond kOvfCap partners, a selection of the next partner ID at a time).
+// stencil (found through the same FP32 filter) in shared memory, sorted by
+// partner ID, added in that order (and, beyond kOvfCap partners, a
+// selection of the next partner ID at a time).
 #include "pair.cuh"
 
 namespace bdm {
@@ -46,6 +47,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
   __shared__ uint32_t rq[kRowCap][kRowThreads];
   __shared__ uint8_t skip[kRowAgents];
   __shared__ uint32_t ncon[kRowAgents];
+  __shared__ uint32_t nfil[kRowAgents];  // candidates that pass the FP32 filter, per agent
   __shared__ Contrib con[kRowAgents][kSortCap];
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   const int a = threadIdx.x / 9, r = threadIdx.x % 9;
@@ -66,6 +68,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
     }
     skip[a] = (!active || st) ? 1 : 0;
     ncon[a] = 0u;
+    nfil[a] = 0u;
   }
   __syncthreads();
   auto append = [&](int agent, int64_t j, double gx, double gy, double gz, bool nz, bool dir) {
@@ -82,11 +85,23 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
   const int dz = r / 3 - 1, dy = r % 3 - 1;
   const bool walk = !skip[a] && dz >= t.zlo && dz <= t.zhi && dy >= t.ylo && dy <= t.yhi;
   double4_32a o = {};
+  float4 o0 = {};
+  float sy = 0.f, sz = 0.f;
+  const float Lh = s.Lh, marg = s.marg;
+  // the FP32 filter: box-relative leading parts with a margin above their
+  // error, so every pair that overlaps in FP64 passes
+  auto passes = [&](int64_t j, float sx) {
+    const float4 q = C.c.r0[j];
+    const float ddx = __fsub_rn(sx, q.x), ddy = __fsub_rn(sy, q.y), ddz = __fsub_rn(sz, q.z);
+    const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+    const float Rm = __fadd_rn(__fadd_rn(o0.w, q.w), marg);
+    return s2 < __fmul_rn(Rm, Rm);
+  };
   if (walk) {
     o = C.c.r64[p];
-    const float4 o0 = C.c.r0[p];
-    const float Lh = s.Lh, marg = s.marg;
-    const float sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh)), sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
+    o0 = C.c.r0[p];
+    sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh));
+    sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
     for (int dx = t.xlo; dx <= t.xhi; ++dx) {
       const unsigned long long e = t.e[t.box(dx, dy, dz)];
       const uint32_t cnt = ent_live(e, stamp);
@@ -94,28 +109,29 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
       const float sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
       for (uint32_t m = 0; m < cnt; ++m) {
         const int64_t j = j0 + m;
-        if (j == p) continue;
-        const float4 q = C.c.r0[j];
-        const float ddx = __fsub_rn(sx, q.x), ddy = __fsub_rn(sy, q.y), ddz = __fsub_rn(sz, q.z);
-        const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
-        const float Rm = __fadd_rn(__fadd_rn(o0.w, q.w), marg);
-        if (!(s2 < __fmul_rn(Rm, Rm))) continue;
+        if (j == p || !passes(j, sx)) continue;
         if (n < (uint32_t)kRowCap) rq[n][threadIdx.x] = (uint32_t)j;
         ++n;
       }
     }
+    if (n) atomicAdd(&nfil[a], n);
   }
-  uint32_t mine = n;
-  if (n > (uint32_t)kRowCap) {
+  __syncthreads();
+  // an agent with more candidates than its list holds goes to k_force64o
+  // untouched; the others evaluate their rows
+  const bool crowded = nfil[a] > (uint32_t)kSortCap;
+  uint32_t mine = crowded ? 0u : n;
+  if (!crowded && n > (uint32_t)kRowCap) {
     // crowded row: evaluate it in place
     mine = 0;
     for (int dx = t.xlo; dx <= t.xhi; ++dx) {
       const unsigned long long e = t.e[t.box(dx, dy, dz)];
       const uint32_t cnt = ent_live(e, stamp);
       const int64_t j0 = ent_start(e);
+      const float sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
       for (uint32_t m = 0; m < cnt; ++m) {
         const int64_t j = j0 + m;
-        if (j == p) continue;
+        if (j == p || !passes(j, sx)) continue;
         double gx, gy, gz;
         bool nz, dir;
         if (pair64(sc, o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir)) append(a, j, gx, gy, gz, nz, dir);
@@ -158,7 +174,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
   __syncthreads();
   if (r == 0 && !skip[a]) {
     const uint32_t cnt = ncon[a];
-    if (cnt > (uint32_t)kSortCap) {
+    if (crowded) {
       C.ovf[atomicAdd(&C.g->n_ovf, 1u)] = (int32_t)p;
       return;
     }
@@ -190,24 +206,46 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
 }
 
 // One warp per overflow agent (grid-stride over the list the row kernel
-// wrote; the grid is fixed, so the launch can be captured).  The warp
-// evaluates the agent's candidates 32 at a time and keeps the overlapping
-// ones in shared memory, sorts them by partner ID (bitonic sort of packed
-// {ID, slot} keys) and adds them in that order.  More than kOvfCap partners
-// (a pathological crowd) take the selection loop below instead.
-constexpr int kOvfCap = 704;
-constexpr int kOvfKeys = 1024;  // bitonic sort size (a power of two >= kOvfCap)
+// wrote; the grid is fixed, so the launch can be captured).  The warp tests
+// the agent's candidates 32 at a time with the FP32 filter, evaluates those
+// that pass and keeps the overlapping pairs in shared memory, sorts them by
+// partner ID (bitonic sort of packed {ID, index} keys) and adds them in that
+// order.  More than kOvfCap partners (a pathological crowd) take the
+// selection loop below instead.
+constexpr int kOvfWarps = 4;
+constexpr int kOvfCap = 256;  // pairs sorted in shared memory (a power of two)
 
 struct OvfShared {
-  unsigned long long key[kOvfKeys];  // partner ID << 32 | index of the contribution
+  unsigned long long key[kOvfCap];  // partner ID << 32 | index of the contribution
   double gx[kOvfCap], gy[kOvfCap], gz[kOvfCap];
   uint32_t flags[kOvfCap];
 };
 
-__device__ void ovf_selection(const DevCtx &C, const SimConst &sc, const Stencil &t, int64_t p, const double4_32a &o,
-                              uint32_t stamp, int lane, double &fx, double &fy, double &fz, uint32_t &nnz,
-                              uint32_t &ovl) {
+// The agent's view of its stencil for the FP32 filter (box-relative
+// leading parts; the margin exceeds their error).
+struct OvfAgent {
+  const SimConst *sc;
+  Stencil t;
+  double4_32a o;
+  float4 o0;
+  float Lh, marg;
+  int64_t p;
+  __device__ bool passes(const DevCtx &C, int64_t j, int dx, int dy, int dz) const {
+    const float4 q = C.c.r0[j];
+    const float sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
+    const float sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh));
+    const float sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
+    const float ddx = __fsub_rn(sx, q.x), ddy = __fsub_rn(sy, q.y), ddz = __fsub_rn(sz, q.z);
+    const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+    const float Rm = __fadd_rn(__fadd_rn(o0.w, q.w), marg);
+    return s2 < __fmul_rn(Rm, Rm);
+  }
+};
+
+__device__ void ovf_selection(const DevCtx &C, const OvfAgent &A, uint32_t stamp, int lane, double &fx, double &fy,
+                              double &fz, uint32_t &nnz, uint32_t &ovl) {
   const unsigned FULL = 0xffffffffu;
+  const Stencil &t = A.t;
   const int nx = t.xhi - t.xlo + 1, ny = t.yhi - t.ylo + 1, nzb = t.zhi - t.zlo + 1;
   const int nbox = nx * ny * nzb;
   int64_t last = -1;  // partner ID added last
@@ -222,12 +260,12 @@ __device__ void ovf_selection(const DevCtx &C, const SimConst &sc, const Stencil
       const int64_t j0 = ent_start(e);
       for (uint32_t m = (uint32_t)lane; m < cnt; m += 32u) {
         const int64_t j = j0 + m;
-        if (j == p) continue;
+        if (j == A.p) continue;
         const uint32_t id = partner_id(C, j);
-        if ((int64_t)id <= last || id >= best) continue;
+        if ((int64_t)id <= last || id >= best || !A.passes(C, j, dx, dy, dz)) continue;
         double gx, gy, gz;
         bool nz, dir;
-        if (pair64(sc, o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir)) {
+        if (pair64(*A.sc, A.o, C.c.r64[j], A.sc->k, A.sc->gamma, gx, gy, gz, nz, dir)) {
           best = id;
           bj = j;
         }
@@ -241,7 +279,7 @@ __device__ void ovf_selection(const DevCtx &C, const SimConst &sc, const Stencil
     if (lane == 0) {
       double gx, gy, gz;
       bool nz, dir;
-      pair64(sc, o, C.c.r64[jb], sc.k, sc.gamma, gx, gy, gz, nz, dir);
+      pair64(*A.sc, A.o, C.c.r64[jb], A.sc->k, A.sc->gamma, gx, gy, gz, nz, dir);
       ++ovl;
       nnz += nz ? 1u : 0u;
       if (dir) {
@@ -254,22 +292,28 @@ __device__ void ovf_selection(const DevCtx &C, const SimConst &sc, const Stencil
   }
 }
 
-__global__ void __launch_bounds__(32) k_force64o(DevCtx C) {
-  __shared__ OvfShared sh;
+__global__ void __launch_bounds__(32 * kOvfWarps) k_force64o(DevCtx C) {
+  __shared__ OvfShared shw[kOvfWarps];
   if (C.g->err & ERR_TABLE) return;
   const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  OvfShared &sh = shw[wid];
   const uint32_t nov = C.g->n_ovf;
   const uint32_t stamp = C.g->stamp & kStampMask;
-  for (uint32_t w = blockIdx.x; w < nov; w += gridDim.x) {
-    const int64_t p = C.ovf[w];
-    const int sim = C.c.sim[p];
-    const SimConst &sc = C.sc[sim];
+  for (uint32_t w = blockIdx.x * kOvfWarps + wid; w < nov; w += gridDim.x * kOvfWarps) {
+    OvfAgent A;
+    A.p = C.ovf[w];
+    const int sim = C.c.sim[A.p];
+    A.sc = &C.sc[sim];
     const SimState &s = C.ss[sim];
     int64_t cx, cy, cz;
-    unpack_coords(C.c.pkey[p], cx, cy, cz);
-    const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
-    const double4_32a o = C.c.r64[p];
+    unpack_coords(C.c.pkey[A.p], cx, cy, cz);
+    A.t = make_stencil(C, *A.sc, s, cx, cy, cz);
+    A.o = C.c.r64[A.p];
+    A.o0 = C.c.r0[A.p];
+    A.Lh = s.Lh;
+    A.marg = s.marg;
+    const Stencil &t = A.t;
     const int nx = t.xhi - t.xlo + 1, ny = t.yhi - t.ylo + 1, nzb = t.zhi - t.zlo + 1;
     const int nbox = nx * ny * nzb;
     // every overlapping pair of the stencil, 32 candidates at a time
@@ -284,7 +328,8 @@ __global__ void __launch_bounds__(32) k_force64o(DevCtx C) {
         const int64_t j = j0 + m;
         double gx = 0.0, gy = 0.0, gz = 0.0;
         bool nz = false, dir = false, hit = false;
-        if (m < cnt && j != p) hit = pair64(sc, o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir);
+        if (m < cnt && j != A.p && A.passes(C, j, dx, dy, dz))
+          hit = pair64(*A.sc, A.o, C.c.r64[j], A.sc->k, A.sc->gamma, gx, gy, gz, nz, dir);
         const unsigned B = __ballot_sync(FULL, hit);
         const uint32_t k = n + (uint32_t)__popc(B & ((1u << lane) - 1u));
         if (hit && k < (uint32_t)kOvfCap) {
@@ -308,11 +353,11 @@ __global__ void __launch_bounds__(32) k_force64o(DevCtx C) {
           for (uint32_t i = (uint32_t)lane; i < n2; i += 32u) {
             const uint32_t jx = i ^ stride;
             if (jx > i) {
-              const unsigned long long a = sh.key[i], bk = sh.key[jx];
+              const unsigned long long ka = sh.key[i], kb = sh.key[jx];
               const bool up = (i & size) == 0;
-              if ((a > bk) == up) {
-                sh.key[i] = bk;
-                sh.key[jx] = a;
+              if ((ka > kb) == up) {
+                sh.key[i] = kb;
+                sh.key[jx] = ka;
               }
             }
           }
@@ -331,11 +376,11 @@ __global__ void __launch_bounds__(32) k_force64o(DevCtx C) {
         ovl = n;
       }
     } else {
-      ovf_selection(C, sc, t, p, o, stamp, lane, fx, fy, fz, nnz, ovl);
+      ovf_selection(C, A, stamp, lane, fx, fy, fz, nnz, ovl);
     }
     if (lane == 0) {
-      C.c.f64[p] = make_double4_32a(fx, fy, fz, (double)ovl);
-      C.c.nnz[p] = (uint8_t)(nnz > 255u ? 255u : nnz);
+      C.c.f64[A.p] = make_double4_32a(fx, fy, fz, (double)ovl);
+      C.c.nnz[A.p] = (uint8_t)(nnz > 255u ? 255u : nnz);
     }
     __syncwarp();
   }
@@ -345,7 +390,7 @@ __global__ void __launch_bounds__(32) k_force64o(DevCtx C) {
 
 void launch_force64(const DevCtx &C, cudaStream_t st) {
   k_force64r<<<(unsigned int)((C.total_slots + kRowAgents - 1) / kRowAgents), kRowThreads, 0, st>>>(C);
-  k_force64o<<<152 * 6, 32, 0, st>>>(C);
+  k_force64o<<<152 * 4, 32 * kOvfWarps, 0, st>>>(C);
 }
 
 }  // namespace bdm
