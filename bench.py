@@ -477,6 +477,8 @@ def main():
     if args.static and variant in (0, 4):
         variant = 1  # the symmetric walks do not run with static detection
     kernel = FORCE_KERNEL.get(variant, "k_force") if prec == 1 else "k_force64r"
+    if prec == 1 and not args.static and variant in (6, 8):
+        kernel = "k_force32w"  # no static flags to compute first
     traffic = None
     if prec == 1 and variant in FORCE_TRAFFIC_B_PER_AGENT and args.workload.startswith("clustered"):
         traffic = FORCE_TRAFFIC_B_PER_AGENT[variant] * (n_agents - st_static)

@@ -1629,9 +1629,16 @@ int bdm_autotune(bdm_ctx *c, int32_t iterations, int32_t knobs, bdm_tuning *chos
   };
   bool better = false;
   rc = rc ? rc : trial(best, &better);  // the current setting
+  bool static32 = false;  // an FP32-path simulation detects static agents
+  for (int s = 0; s < c->n_sims; ++s)
+    if (c->params[s].precision != BDM_PREC_FP64 && c->params[s].detect_static) static32 = true;
   if ((knobs & BDM_TUNE_FORCE) && c->any_fp32)
     for (int v = 0; v < kForceVariants && !rc; ++v) {
       if (v == best.force_variant) continue;
+      // without static detection 6 and 8 launch what 5 and 7 launch; with
+      // it 0 and 4 launch 1
+      if (!static32 && (v == 6 || v == 8)) continue;
+      if (static32 && (v == 0 || v == 4)) continue;
       bdm_tuning t = best;
       t.force_variant = v;
       rc = trial(t, &better);

@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kRowAgents = 32;
 constexpr int kRowThreads = kRowAgents * 9;
-constexpr int kRowCap = 4;
+constexpr int kRowCap = 8;
 constexpr int kSortCap = 24;
 
 struct Contrib {
@@ -207,18 +207,22 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
 
 // One warp per overflow agent (grid-stride over the list the row kernel
 // wrote; the grid is fixed, so the launch can be captured).  The warp tests
-// the agent's candidates 32 at a time with the FP32 filter, evaluates those
-// that pass and keeps the overlapping pairs in shared memory, sorts them by
-// partner ID (bitonic sort of packed {ID, index} keys) and adds them in that
-// order.  More than kOvfCap partners (a pathological crowd) take the
+// the agent's candidates 32 at a time with the FP32 filter and compacts
+// those that pass, evaluates them 32 at a time and keeps the overlapping
+// pairs in shared memory, sorts them by partner ID (bitonic sort of packed
+// {ID, index} keys) and adds them in that order.  More than kOvfCand
+// passing candidates or kOvfCap partners (a pathological crowd) take the
 // selection loop below instead.
 constexpr int kOvfWarps = 4;
 constexpr int kOvfCap = 256;  // pairs sorted in shared memory (a power of two)
+
+constexpr int kOvfCand = 512;  // candidates passing the filter, evaluated 32 at a time
 
 struct OvfShared {
   unsigned long long key[kOvfCap];  // partner ID << 32 | index of the contribution
   double gx[kOvfCap], gy[kOvfCap], gz[kOvfCap];
   uint32_t flags[kOvfCap];
+  uint32_t cand[kOvfCand];  // cells that passed the FP32 filter
 };
 
 // The agent's view of its stencil for the FP32 filter (box-relative
@@ -316,8 +320,10 @@ __global__ void __launch_bounds__(32 * kOvfWarps) k_force64o(DevCtx C) {
     const Stencil &t = A.t;
     const int nx = t.xhi - t.xlo + 1, ny = t.yhi - t.ylo + 1, nzb = t.zhi - t.zlo + 1;
     const int nbox = nx * ny * nzb;
-    // every overlapping pair of the stencil, 32 candidates at a time
-    uint32_t n = 0;  // overlapping pairs found (warp-uniform)
+    // the candidates of the stencil that pass the FP32 filter, compacted
+    // (FP64 instructions occupy the pipe for all 32 lanes, so the
+    // definition is evaluated only on full rounds of passing candidates)
+    uint32_t nc = 0;  // passing candidates (warp-uniform)
     for (int b = 0; b < nbox; ++b) {
       const int dx = t.xlo + b % nx, dy = t.ylo + (b / nx) % ny, dz = t.zlo + b / (nx * ny);
       const unsigned long long e = t.e[t.box(dx, dy, dz)];
@@ -326,10 +332,23 @@ __global__ void __launch_bounds__(32 * kOvfWarps) k_force64o(DevCtx C) {
       for (uint32_t m0 = 0; m0 < cnt; m0 += 32u) {
         const uint32_t m = m0 + (uint32_t)lane;
         const int64_t j = j0 + m;
+        const bool pass = m < cnt && j != A.p && A.passes(C, j, dx, dy, dz);
+        const unsigned B = __ballot_sync(FULL, pass);
+        const uint32_t k = nc + (uint32_t)__popc(B & ((1u << lane) - 1u));
+        if (pass && k < (uint32_t)kOvfCand) sh.cand[k] = (uint32_t)j;
+        nc += (uint32_t)__popc(B);
+      }
+    }
+    __syncwarp();
+    // every overlapping pair among them, 32 at a time
+    uint32_t n = 0;  // overlapping pairs found (warp-uniform)
+    if (nc <= (uint32_t)kOvfCand) {
+      for (uint32_t k0 = 0; k0 < nc; k0 += 32u) {
+        const uint32_t kk = k0 + (uint32_t)lane;
+        const int64_t j = kk < nc ? (int64_t)sh.cand[kk] : A.p;
         double gx = 0.0, gy = 0.0, gz = 0.0;
         bool nz = false, dir = false, hit = false;
-        if (m < cnt && j != A.p && A.passes(C, j, dx, dy, dz))
-          hit = pair64(*A.sc, A.o, C.c.r64[j], A.sc->k, A.sc->gamma, gx, gy, gz, nz, dir);
+        if (kk < nc) hit = pair64(*A.sc, A.o, C.c.r64[j], A.sc->k, A.sc->gamma, gx, gy, gz, nz, dir);
         const unsigned B = __ballot_sync(FULL, hit);
         const uint32_t k = n + (uint32_t)__popc(B & ((1u << lane) - 1u));
         if (hit && k < (uint32_t)kOvfCap) {
@@ -339,6 +358,8 @@ __global__ void __launch_bounds__(32 * kOvfWarps) k_force64o(DevCtx C) {
         }
         n += (uint32_t)__popc(B);
       }
+    } else {
+      n = (uint32_t)kOvfCap + 1u;  // too many candidates: the selection loop
     }
     double fx = 0.0, fy = 0.0, fz = 0.0;
     uint32_t nnz = 0, ovl = 0;
