@@ -57,7 +57,7 @@ ALG_BYTES_BOX = 8.0
 # variant's kernel is the one captured.
 FORCE_TRAFFIC_B_PER_AGENT = {5: 104.6}
 FORCE_KERNEL = {0: "k_force32s", 1: "k_force32d", 2: "k_force", 3: "k_force32d", 4: "k_force32s (direct)",
-                5: "k_force32w", 6: "k_static + k_force32w", 7: "k_force32w", 8: "k_static + k_force32w"}
+                5: "k_force32w", 6: "k_static + k_force32w"}
 # Workloads whose configuration fixes the re-sort (interval, curve): the
 # autotuner leaves those two knobs alone there.
 FIXED_SORT = {"clustered_8M": (10, 0), "clustered_1M": (10, 0)}
@@ -477,7 +477,7 @@ def main():
     if args.static and variant in (0, 4):
         variant = 1  # the symmetric walks do not run with static detection
     kernel = FORCE_KERNEL.get(variant, "k_force") if prec == 1 else "k_force64r"
-    if prec == 1 and not args.static and variant in (6, 8):
+    if prec == 1 and not args.static and variant == 6:
         kernel = "k_force32w"  # no static flags to compute first
     traffic = None
     if prec == 1 and variant in FORCE_TRAFFIC_B_PER_AGENT and args.workload.startswith("clustered"):

@@ -151,8 +151,8 @@ int bdm_update_agents(bdm_ctx* ctx, int32_t sim, int64_t n, const double* xyz,
  * (the magic "BDMSTATE", version 1, the agent count, the iterations done,
  * which are also the counter of the division axes' random numbers, the
  * agent-update counter and the grid of the last iteration) and, by caller
- * ID, positions, diameters, volumes, the box of the last grid, the changed
- * and static flags and the non-zero pair counts.  BDM_E_CAPACITY (nothing
+ * ID, positions, diameters, volumes, the box of the last grid, the changed,
+ * static and ghost flags and the non-zero pair counts.  BDM_E_CAPACITY (nothing
  * written) when cap_bytes is too small, BDM_E_STATE when no agents are set.
  * bdm_set_state replaces the agents of `sim` by such a state (of this or
  * another context or simulation; the parameters are the receiving
@@ -176,6 +176,23 @@ int bdm_set_state(bdm_ctx* ctx, int32_t sim, const void* buf, int64_t size_bytes
  * iteration.  Errors: BDM_E_INVAL (an ID out of range or repeated),
  * BDM_E_STATE (no agents set), latched device errors as bdm_sync. */
 int bdm_remove_agents(bdm_ctx* ctx, int32_t sim, int64_t n_ids, const int64_t* ids);
+
+/* Mark agents of simulation `sim` as ghosts, read-only neighbours: ghost[i]
+ * != 0 (host memory, n = the simulation's agent count, by caller ID) makes
+ * agent i a ghost, 0 an ordinary agent.  A ghost is a partner in every other
+ * agent's force, but bdm_step does not move, grow or divide it and never
+ * counts it static (its own force and nnz are still reported).  This is the
+ * halo of a domain decomposition (the aura of the thesis's distributed
+ * engine, §6.2): a rank steps its own agents with the agents of the
+ * neighbouring ranks within one largest diameter as ghosts, which puts every
+ * partner of an owned agent on the rank (Eq 4.1 needs a distance below
+ * r_i + r_j); with IDs in the global order the owned agents' FP64 results
+ * equal a single domain's bit for bit.  An agent whose flag changes counts
+ * as changed.  bdm_set_agents, bdm_set_state and bdm_remove_agents keep or
+ * reset the flags with the agents (bdm_set_agents: no ghosts).  Errors:
+ * BDM_E_INVAL (n differs from the agent count, NULL mask), BDM_E_STATE (no
+ * agents set), latched device errors as bdm_sync. */
+int bdm_set_ghosts(bdm_ctx* ctx, int32_t sim, int64_t n, const uint8_t* ghost);
 
 /* Run n_iterations iterations of every simulation (S0-S7), asynchronously
  * on the context's stream.  Errors: BDM_E_STATE (a simulation has no
@@ -292,10 +309,7 @@ typedef struct {
                               agents); 1 direct walk, rows flattened, pair
                               evaluation deferred; 2 direct loop, pairs evaluated
                               in the walk; 3 as 1 box by box; 4 as 0 with every
-                              pair evaluated in the walk (crowded agents); 7 and
-                              8 as 5 and 6 with the stream pipelined (the whole
-                              half stencil read at once, each round's candidate
-                              records requested one round ahead) */
+                              pair evaluated in the walk (crowded agents) */
   int32_t sort_interval;   /* -1: every simulation's own sort_interval;
                               >= 0: this re-sort interval for all simulations */
   int32_t sort_curve;      /* order the re-sort gives the storage: 0 Morton order of the

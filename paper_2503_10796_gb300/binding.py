@@ -73,6 +73,7 @@ SIGNATURES = {
     "bdm_step": (C.c_int, [_vp, _i32]),
     "bdm_get_state": (C.c_int, [_vp, _i32, _vp, _i64, _P(_i64)]),
     "bdm_remove_agents": (C.c_int, [_vp, _i32, _i64, _vp]),
+    "bdm_set_ghosts": (C.c_int, [_vp, _i32, _i64, _vp]),
     "bdm_set_state": (C.c_int, [_vp, _i32, _vp, _i64]),
     "bdm_sync": (C.c_int, [_vp]),
     "bdm_get_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _P(_i64), _i32]),
@@ -204,6 +205,12 @@ class Context:
                 raise ValueError("xyz and diameter differ in length")
         self._check(self._lib.bdm_update_agents(self._h, sim, xyz.shape[0], _dptr(xyz),
                                                 _dptr(d) if d is not None else None, 0))
+
+    def set_ghosts(self, sim: int, ghost):
+        """Ghost flags by ID (bdm_set_ghosts): True marks a read-only
+        neighbour, which bdm_step does not move, grow or divide."""
+        m = np.ascontiguousarray(np.asarray(ghost).reshape(-1) != 0, dtype=np.uint8)
+        self._check(self._lib.bdm_set_ghosts(self._h, sim, m.shape[0], _dptr(m)))
 
     def get_state(self, sim: int) -> bytes:
         """Checkpoint of simulation `sim` (bdm_get_state) as bytes."""

@@ -32,7 +32,10 @@ enum : uint32_t {
 enum : int32_t { BOUND_OPEN = 0, BOUND_CLOSED = 1, BOUND_TORUS = 2 };
 
 // Flags per slot.
-enum : uint8_t { FLAG_CHANGED = 1u, FLAG_STATIC = 2u };
+// FLAG_GHOST: a read-only neighbour (a halo agent owned elsewhere): a
+// partner in every other agent's force, but it does not move, grow or
+// divide in bdm_step and is never static.
+enum : uint8_t { FLAG_CHANGED = 1u, FLAG_STATIC = 2u, FLAG_GHOST = 4u };
 
 // Flags per cell (written by the placement kernel for the force kernel).
 enum : uint8_t { CELL_STATIC_ELIGIBLE = 1u };

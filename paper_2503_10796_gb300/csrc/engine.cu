@@ -573,9 +573,6 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
     if (check_params(per_sim[s], why)) return fail(nullptr, BDM_E_INVAL, "simulation " + std::to_string(s) + ": " + why);
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return fail(nullptr, BDM_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
-  // kernel attributes are per device; set before any launch or capture
-  e = init_force_stream();
-  if (e != cudaSuccess) return fail(nullptr, BDM_E_CUDA, std::string("stream kernel attributes: ") + cudaGetErrorString(e));
   bdm_ctx *c = new bdm_ctx();
   c->device = device;
   c->n_sims = n_sims;
@@ -813,6 +810,28 @@ int bdm_update_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, con
   launch_update_agents(c->D, c->stream, c->h_sc[sim].base, n, dx, dd);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "updating agents");
+  return BDM_OK;
+}
+
+int bdm_set_ghosts(bdm_ctx *c, int32_t sim, int64_t n, const uint8_t *ghost) {
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
+  if (n < 0 || (n > 0 && !ghost)) return fail(c, BDM_E_INVAL, "n < 0 or NULL mask");
+  rc = latched_error(c);
+  if (rc) return rc;
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  if (n != s.n) return fail(c, BDM_E_INVAL, "n differs from the agent count " + std::to_string(s.n));
+  if (n == 0) return BDM_OK;
+  rc = ensure_xfer(c, (size_t)((n + 7) / 8));
+  if (rc) return rc;
+  uint8_t *dm = (uint8_t *)c->d_xfer;
+  cudaMemcpyAsync(dm, ghost, (size_t)n, cudaMemcpyHostToDevice, c->stream);
+  launch_set_ghosts(c->D, c->stream, c->h_sc[sim].base, n, dm);
+  cudaError_t e = cudaStreamSynchronize(c->stream);  // the host mask may go once this returns
+  if (e != cudaSuccess) return cuda_fail(c, e, "setting ghost flags");
   return BDM_OK;
 }
 
@@ -1635,9 +1654,9 @@ int bdm_autotune(bdm_ctx *c, int32_t iterations, int32_t knobs, bdm_tuning *chos
   if ((knobs & BDM_TUNE_FORCE) && c->any_fp32)
     for (int v = 0; v < kForceVariants && !rc; ++v) {
       if (v == best.force_variant) continue;
-      // without static detection 6 and 8 launch what 5 and 7 launch; with
-      // it 0 and 4 launch 1
-      if (!static32 && (v == 6 || v == 8)) continue;
+      // without static detection 6 launches what 5 launches; with it 0 and
+      // 4 launch 1
+      if (!static32 && v == 6) continue;
       if (static32 && (v == 0 || v == 4)) continue;
       bdm_tuning t = best;
       t.force_variant = v;

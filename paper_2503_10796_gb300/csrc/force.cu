@@ -459,13 +459,14 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
     C.a.flags[slot] = FLAG_STATIC;
     return;
   }
+  const uint8_t ghost = C.a.flags[slot] & FLAG_GHOST;  // read-only: keeps its position
   bool moved = false, bad = false;
   if (sc.precision == BDM_PREC_FP64) {
     C.a.nnz[slot] = C.c.nnz[p];
     double4_32a F = C.c.f64[p];
     double fn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(F.x, F.x), __dmul_rn(F.y, F.y)), __dmul_rn(F.z, F.z)));
     bad = !isfinite(fn);
-    if (fn > sc.adherence) {
+    if (fn > sc.adherence && !ghost) {
       double Dx = __dmul_rn(sc.dt, F.x), Dy = __dmul_rn(sc.dt, F.y), Dz = __dmul_rn(sc.dt, F.z);
       double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(Dx, Dx), __dmul_rn(Dy, Dy)), __dmul_rn(Dz, Dz)));
       if (dn > sc.max_disp) {
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
     C.a.nnz[slot] = (uint8_t)(nz > 255u ? 255u : nz);
     float f2 = __fmaf_rn(F.z, F.z, __fmaf_rn(F.y, F.y, __fmul_rn(F.x, F.x)));
     bad = !isfinite(f2);
-    if (f2 > sc.adherence2f) {
+    if (f2 > sc.adherence2f && !ghost) {
       float Dx = __fmul_rn(sc.dtf, F.x), Dy = __fmul_rn(sc.dtf, F.y), Dz = __fmul_rn(sc.dtf, F.z);
       float d2 = __fmaf_rn(Dz, Dz, __fmaf_rn(Dy, Dy, __fmul_rn(Dx, Dx)));
       if (d2 > sc.max_disp2f) {
@@ -503,7 +504,7 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
     }
   }
   if (bad) set_err(C.g, ERR_NONFINITE);
-  C.a.flags[slot] = moved ? FLAG_CHANGED : 0;
+  C.a.flags[slot] = (uint8_t)(ghost | (moved ? FLAG_CHANGED : 0));
 }
 
 static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
@@ -526,8 +527,7 @@ ForcePlan plan_force(int variant, bool any_static) {
   // partner would miss them, so simulations with static detection take the
   // deferred walk instead of 0 and 4
   if ((variant == 0 || variant == 4) && any_static) pl.variant = 1;
-  pl.zero_f32 = pl.variant == 0 || pl.variant == 4 || pl.variant == 6 || pl.variant == 8 ||
-                ((pl.variant == 5 || pl.variant == 7) && !any_static);
+  pl.zero_f32 = pl.variant == 0 || pl.variant == 4 || pl.variant == 6 || (pl.variant == 5 && !any_static);
   return pl;
 }
 
@@ -540,8 +540,8 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, 
     else if (variant == 0) k_force32s<false><<<nb, th, 0, st>>>(C);
     else if (variant == 4) k_force32s<true><<<nb, th, 0, st>>>(C);
     else if (variant == 3) k_force32d<false><<<nb, th, 0, st>>>(C);
-    else if (variant == 5 || variant == 7) launch_force_stream(C, st, any_static ? 1 : 0, th, any_torus, variant == 7);
-    else if (variant == 6 || variant == 8) launch_force_stream(C, st, any_static ? 2 : 0, th, any_torus, variant == 8);
+    else if (variant == 5) launch_force_stream(C, st, any_static ? 1 : 0, th, any_torus);
+    else if (variant == 6) launch_force_stream(C, st, any_static ? 2 : 0, th, any_torus);
     else k_force32d<true><<<nb, th, 0, st>>>(C);
   }
   if (has_fp64) launch_force64(C, st);

@@ -41,19 +41,12 @@ namespace bdm {
 
 constexpr int kStreamWarps = 8;              // warps per block
 constexpr int kStreamThreads = 32 * kStreamWarps;
+constexpr int kPhaseBoxes = 9;               // stencil boxes per lane and phase (three rows)
+constexpr int kSegCap = 32 * kPhaseBoxes;    // segments per warp and phase
 constexpr int kPairCap = 64;                 // queued pairs per warp (flushed at 32)
 constexpr uint32_t kOffMask = (1u << 21) - 1u;
 
-// Stencil rows per phase: three (nine boxes), or five (fifteen) in the
-// pipelined kernel's half-stencil modes, which so read the whole half
-// stencil in one phase (kWide).
-template <bool kWide> struct StreamShape {
-  static constexpr int kRowsPerPhase = kWide ? 5 : 3;
-  static constexpr int kPhaseBoxes = 3 * kRowsPerPhase;  // stencil boxes per lane and phase
-  static constexpr int kSegCap = 32 * kPhaseBoxes;       // segments per warp and phase (< 512)
-};
-
-template <int kSegCap> struct StreamShared {
+struct StreamShared {
   uint2 seg[kStreamWarps][kSegCap];    // {first cell, candidate offset | owner << 21 | code << 26}
   uint2 pq[kStreamWarps][kPairCap];    // queued pairs {cell j, owner | code << 5}
   float4 acc[kStreamWarps][32];        // owner force and pair-count word
@@ -82,8 +75,8 @@ __device__ __forceinline__ void stream_row(int r, int &dy, int &dz, int &x0) {
 
 // Evaluates the first k queued pairs (one per lane) after moving the
 // entries beyond the first k (qn in all) down to the front.
-template <bool kSym, class Sh>
-__device__ __forceinline__ void stream_flush(const DevCtx &C, Sh &sh, int wid, int lane, int64_t p0,
+template <bool kSym>
+__device__ __forceinline__ void stream_flush(const DevCtx &C, StreamShared &sh, int wid, int lane, int64_t p0,
                                              uint32_t qn, uint32_t k) {
   __syncwarp();
   const uint32_t rest = qn - k;
@@ -115,20 +108,12 @@ __device__ __forceinline__ void stream_flush(const DevCtx &C, Sh &sh, int wid, i
 // kTorus: some simulation of the launch is toroidal (stencil boxes wrap).
 // kOne: the context holds one simulation (its constants need no per-cell
 // simulation index, which would be the first load every later one waits on).
-// kPipe: the pipelined kernel: five stencil rows per phase, and the
-// candidate records of round k + 1 requested before round k is filtered, so
-// that a warp waits for one load of the stencil and about one per flush
-// instead of one per phase and round.
-template <int kMode, bool kTorus, bool kOne, bool kPipe>
-__global__ void __launch_bounds__(kStreamThreads, kPipe ? 3 : 4) k_force32w(DevCtx C) {
+template <int kMode, bool kTorus, bool kOne>
+__global__ void __launch_bounds__(kStreamThreads, 4) k_force32w(DevCtx C) {
   constexpr bool kSym = kMode != kModeFull;
   constexpr int kRows = kSym ? 5 : 9;
-  constexpr bool kWide = kPipe && kSym;
-  constexpr int kRPP = StreamShape<kWide>::kRowsPerPhase;
-  constexpr int kPhaseBoxes = StreamShape<kWide>::kPhaseBoxes;
-  constexpr int kPhases = (kRows + kRPP - 1) / kRPP;
-  extern __shared__ __align__(16) unsigned char stream_smem[];
-  auto &sh = *reinterpret_cast<StreamShared<StreamShape<kWide>::kSegCap> *>(stream_smem);
+  constexpr int kPhases = (kRows + 2) / 3;   // three rows per phase
+  __shared__ StreamShared sh;
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -184,8 +169,8 @@ __global__ void __launch_bounds__(kStreamThreads, kPipe ? 3 : 4) k_force32w(DevC
     uint32_t sj[kPhaseBoxes], sn[kPhaseBoxes];
     uint32_t nseg = 0u, ncand = 0u;
 #pragma unroll
-    for (int rr = 0; rr < kRPP; ++rr) {
-      const int r = ph * kRPP + rr;
+    for (int rr = 0; rr < 3; ++rr) {
+      const int r = ph * 3 + rr;
       int dy = 0, dz = 0, x0 = 0;
       if (r < kRows) stream_row<kSym>(r, dy, dz, x0);
       const bool inrow = r < kRows && walk && dy >= t.ylo && dy <= t.yhi && dz >= t.zlo && dz <= t.zhi;
@@ -230,8 +215,8 @@ __global__ void __launch_bounds__(kStreamThreads, kPipe ? 3 : 4) k_force32w(DevC
       const uint32_t ex0 = incl - v;
       uint32_t pos = ex0 & 511u, off = ex0 >> 9;
 #pragma unroll
-      for (int rr = 0; rr < kRPP; ++rr) {
-        const int r = ph * kRPP + rr;
+      for (int rr = 0; rr < 3; ++rr) {
+        const int r = ph * 3 + rr;
         if (r >= kRows) continue;
         int dy, dz, x0;
         stream_row<kSym>(r, dy, dz, x0);
@@ -250,46 +235,23 @@ __global__ void __launch_bounds__(kStreamThreads, kPipe ? 3 : 4) k_force32w(DevC
     __syncwarp();
     uint32_t cur = 0u;  // segment of candidate `base`
     const uint32_t last = NS ? NS - 1u : 0u;
-    // this lane's candidate of the round that starts at `base`: its cell j
-    // and meta (owner | code << 5); a lane past the end gets a valid cell
-    auto lookup = [&](uint32_t base, uint32_t &j, uint32_t &meta) {
+    for (uint32_t base = 0u; base < T; base += 32u) {
       const uint32_t idx = cur + 1u + (uint32_t)lane;
       const uint32_t d = (sh.seg[wid][idx < NS ? idx : last].y & kOffMask) - base;
       const uint32_t M = __reduce_or_sync(FULL, (idx < NS && d < 32u) ? (1u << (d & 31u)) : 0u);
       const uint32_t sg = cur + (uint32_t)__popc(M & lm_le);
       cur += (uint32_t)__popc(M);
       const uint32_t c = base + (uint32_t)lane;
-      const uint2 rec = sh.seg[wid][c < T ? sg : last];
-      j = c < T ? rec.x + (c - (rec.y & kOffMask)) : rec.x;
-      meta = rec.y >> 21;
-    };
-    uint32_t jn = 0u, mn = 0u;  // the next round's candidate (kPipe)
-    float4 qn4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (kPipe && T) {
-      lookup(0u, jn, mn);
-      qn4 = __ldg(&C.c.r0[jn]);
-    }
-    for (uint32_t base = 0u; base < T; base += 32u) {
-      uint32_t j, meta;
-      float4 qv;
-      if (kPipe) {
-        j = jn;
-        meta = mn;
-        qv = qn4;
-        if (base + 32u < T) {  // warp-uniform
-          lookup(base + 32u, jn, mn);
-          qn4 = __ldg(&C.c.r0[jn]);
-        }
-      } else {
-        lookup(base, j, meta);
-        qv = __ldg(&C.c.r0[j]);
-      }
-      const bool in = base + (uint32_t)lane < T;
+      const bool in = c < T;
+      const uint2 rec = sh.seg[wid][in ? sg : last];
+      const uint32_t j = in ? rec.x + (c - (rec.y & kOffMask)) : rec.x;
+      const uint32_t meta = rec.y >> 21;
       const int o = (int)(meta & 31u), code = (int)(meta >> 5);
       const float4 ow = sh.r0[wid][o];
       const float lo = sh.kc[wid][o].x;
       const float fdx = (float)(code & 3) - 1.f, fdy = (float)((code >> 2) & 3) - 1.f, fdz = (float)(code >> 4) - 1.f;
       const float sx = __fmaf_rn(-fdx, lo, ow.x), sy = __fmaf_rn(-fdy, lo, ow.y), sz = __fmaf_rn(-fdz, lo, ow.z);
+      const float4 qv = __ldg(&C.c.r0[j]);
       const float ddx = __fsub_rn(sx, qv.x), ddy = __fsub_rn(sy, qv.y), ddz = __fsub_rn(sz, qv.z);
       const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
       const float Rm = __fadd_rn(sh.rw[wid][o], qv.w);
@@ -332,67 +294,26 @@ __global__ void __launch_bounds__(kAgentThreads) k_static(DevCtx C) {
 
 static inline unsigned int stream_blocks(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
-template <int kMode, bool kPipe> constexpr size_t stream_smem_bytes() {
-  return sizeof(StreamShared<StreamShape<kPipe && kMode != kModeFull>::kSegCap>);
-}
-
-template <int kMode, bool kTorus, bool kOne, bool kPipe>
-static cudaError_t stream_attr() {
-  return cudaFuncSetAttribute(k_force32w<kMode, kTorus, kOne, kPipe>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)stream_smem_bytes<kMode, kPipe>());
-}
-
-template <bool kTorus, bool kOne, bool kPipe>
-static cudaError_t stream_attrs() {
-  cudaError_t e = stream_attr<kModeSym, kTorus, kOne, kPipe>();
-  if (e == cudaSuccess) e = stream_attr<kModeFull, kTorus, kOne, kPipe>();
-  if (e == cudaSuccess) e = stream_attr<kModeSymMasked, kTorus, kOne, kPipe>();
-  return e;
-}
-
-template <bool kTorus, bool kOne, bool kPipe>
+template <bool kTorus, bool kOne>
 static void launch_stream_mode(const DevCtx &C, cudaStream_t st, int mode, unsigned int nb, int threads) {
-  if (mode == kModeSymMasked)
-    k_force32w<kModeSymMasked, kTorus, kOne, kPipe>
-        <<<nb, threads, stream_smem_bytes<kModeSymMasked, kPipe>(), st>>>(C);
-  else if (mode == kModeFull)
-    k_force32w<kModeFull, kTorus, kOne, kPipe><<<nb, threads, stream_smem_bytes<kModeFull, kPipe>(), st>>>(C);
-  else
-    k_force32w<kModeSym, kTorus, kOne, kPipe><<<nb, threads, stream_smem_bytes<kModeSym, kPipe>(), st>>>(C);
+  if (mode == kModeSymMasked) k_force32w<kModeSymMasked, kTorus, kOne><<<nb, threads, 0, st>>>(C);
+  else if (mode == kModeFull) k_force32w<kModeFull, kTorus, kOne><<<nb, threads, 0, st>>>(C);
+  else k_force32w<kModeSym, kTorus, kOne><<<nb, threads, 0, st>>>(C);
 }
 
-cudaError_t init_force_stream() {
-  cudaError_t e = stream_attrs<false, false, false>();
-  if (e == cudaSuccess) e = stream_attrs<false, true, false>();
-  if (e == cudaSuccess) e = stream_attrs<true, false, false>();
-  if (e == cudaSuccess) e = stream_attrs<true, true, false>();
-  if (e == cudaSuccess) e = stream_attrs<false, false, true>();
-  if (e == cudaSuccess) e = stream_attrs<false, true, true>();
-  if (e == cudaSuccess) e = stream_attrs<true, false, true>();
-  if (e == cudaSuccess) e = stream_attrs<true, true, true>();
-  return e;
-}
-
-template <bool kPipe>
-static void launch_stream_pipe(const DevCtx &C, cudaStream_t st, int mode, unsigned int nb, int threads,
-                               bool torus) {
-  const bool one = C.n_sims == 1;
-  if (torus) {
-    if (one) launch_stream_mode<true, true, kPipe>(C, st, mode, nb, threads);
-    else launch_stream_mode<true, false, kPipe>(C, st, mode, nb, threads);
-  } else {
-    if (one) launch_stream_mode<false, true, kPipe>(C, st, mode, nb, threads);
-    else launch_stream_mode<false, false, kPipe>(C, st, mode, nb, threads);
-  }
-}
-
-void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads, bool torus, bool pipe) {
+void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads, bool torus) {
   if (threads > kStreamThreads) threads = kStreamThreads;
   const unsigned int nb = stream_blocks(C.total_slots, threads);
   if (mode == kModeSymMasked)
     k_static<<<stream_blocks(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
-  if (pipe) launch_stream_pipe<true>(C, st, mode, nb, threads, torus);
-  else launch_stream_pipe<false>(C, st, mode, nb, threads, torus);
+  const bool one = C.n_sims == 1;
+  if (torus) {
+    if (one) launch_stream_mode<true, true>(C, st, mode, nb, threads);
+    else launch_stream_mode<true, false>(C, st, mode, nb, threads);
+  } else {
+    if (one) launch_stream_mode<false, true>(C, st, mode, nb, threads);
+    else launch_stream_mode<false, false>(C, st, mode, nb, threads);
+  }
 }
 
 }  // namespace bdm

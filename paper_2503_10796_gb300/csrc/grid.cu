@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, 
   cells.slot[p] = (int32_t)slot;
   cells.sim[p] = sim;
   cells.pkey[p] = pk;
-  if (cells.flag) cells.flag[p] = (!(fl & FLAG_CHANGED) && nz <= 1) ? CELL_STATIC_ELIGIBLE : 0;
+  if (cells.flag) cells.flag[p] = (!(fl & (FLAG_CHANGED | FLAG_GHOST)) && nz <= 1) ? CELL_STATIC_ELIGIBLE : 0;
   const double r = half_of(dia);
   const bool fp64 = sc.precision == BDM_PREC_FP64;
   if (fp64_records || fp64) cells.r64[p] = make_double4_32a(pos[0], pos[1], pos[2], r);

@@ -181,7 +181,7 @@ __global__ void k_grow_mark(DevCtx C, GrowBufs B) {
   if (sim < 0) return;
   const SimConst &sc = C.sc[sim];
   const SimState &s = C.ss[sim];
-  if (!sc.grows || slot - sc.base >= s.n) return;
+  if (!sc.grows || slot - sc.base >= s.n || (C.a.flags[slot] & FLAG_GHOST)) return;
   double V = C.a.v[slot];
   if (V < sc.divide_volume) {
     V = __dadd_rn(V, __dmul_rn(sc.growth_rate, sc.dt));

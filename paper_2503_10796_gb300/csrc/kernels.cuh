@@ -23,9 +23,8 @@ void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32 = 0);
 // deferred walk box by box, 4 as 0 without queue, 5 warp candidate stream
 // (force_stream.cu; half stencil, or the full one when a simulation detects
 // static agents), 6 as 5 with the static flags computed first and the half
-// stencil kept, 7 and 8 the pipelined stream kernel in the modes of 5 and 6.
-// The FP64 path runs the row kernel.
-constexpr int kForceVariants = 9;
+// stencil kept.  The FP64 path runs the row kernel.
+constexpr int kForceVariants = 7;
 struct ForcePlan {
   int variant;      // variant that runs
   bool zero_f32;    // the placement must zero the FP32 forces (symmetric walks)
@@ -40,9 +39,7 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant = 0, bool has_fp
 void launch_force64(const DevCtx &C, cudaStream_t st);
 // force_stream.cu: mode 0 half stencil, 1 full stencil with static skip,
 // 2 static flags first, then the half stencil
-void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads, bool torus, bool pipe);
-// Raises the dynamic shared-memory limit of the stream kernels (once per process).
-cudaError_t init_force_stream();
+void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads, bool torus);
 void launch_displace(const DevCtx &C, cudaStream_t st);
 
 // diffusion.cu (soma-clustering slice)
@@ -71,6 +68,7 @@ void launch_count_flags(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_
                         unsigned long long *counts2);
 void launch_set_agents(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t n, int64_t cap,
                        const double *xyz, const double *diam);
+void launch_set_ghosts(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const uint8_t *mask);
 void launch_update_agents(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const double *xyz,
                           const double *diam);
 // first invalid row into *bad: a position not finite (outside the space of

@@ -330,6 +330,22 @@ __global__ void k_update_agents(DevCtx C, int64_t base, int64_t n, const double 
   if (changed) C.a.flags[slot] |= FLAG_CHANGED;
 }
 
+// Ghost flags by ID (mask[id] != 0: read-only neighbour); an agent whose
+// flag changes counts as changed (its neighbours' static checks).
+__global__ void k_set_ghosts(DevCtx C, int64_t base, int64_t n, const uint8_t *mask) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t slot = base + i;
+  const uint8_t fl = C.a.flags[slot];
+  const uint8_t g = mask[C.a.id[slot]] ? FLAG_GHOST : 0;
+  if ((fl & FLAG_GHOST) != g) C.a.flags[slot] = (uint8_t)((fl & ~FLAG_GHOST & ~FLAG_STATIC) | g | FLAG_CHANGED);
+}
+
+void launch_set_ghosts(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const uint8_t *mask) {
+  if (n <= 0) return;
+  k_set_ghosts<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, mask);
+}
+
 void launch_update_agents(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const double *xyz,
                           const double *diam) {
   if (n <= 0) return;
@@ -416,7 +432,7 @@ __global__ void k_state_check(int64_t n, StateArrays a, unsigned long long *bad)
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const bool ok = isfinite(a.x[i]) && isfinite(a.y[i]) && isfinite(a.z[i]) && isfinite(a.d[i]) && a.d[i] > 0.0 &&
-                  isfinite(a.v[i]) && a.v[i] > 0.0 && (a.flags[i] & ~(FLAG_CHANGED | FLAG_STATIC)) == 0;
+                  isfinite(a.v[i]) && a.v[i] > 0.0 && (a.flags[i] & ~(FLAG_CHANGED | FLAG_STATIC | FLAG_GHOST)) == 0;
   if (!ok) atomicMin(bad, (unsigned long long)i);
 }
 

@@ -53,7 +53,7 @@ def _rank_main(rank, world, port, iters, out):
     import oracle
     pop = _population()
 
-    def engine(xyz, d):
+    def engine(xyz, d, ghost):
         s = oracle.Sim(xyz, d, pop.params)
         s.step(1)
         return s.get()[0]
@@ -100,4 +100,46 @@ def test_slab_ranks_match_one_domain(orc, world):
     got[ids] = xyz
     s = oracle.Sim(pop.xyz, pop.diameter, pop.params)
     s.step(iters)
+    assert np.array_equal(got, s.get()[0])
+
+
+def oracle_engine(params):
+    import oracle
+
+    def engine(xyz, d, ghost):
+        s = oracle.Sim(xyz, d, params)
+        s.step(1)
+        x = s.get()[0]
+        x[ghost] = xyz[ghost]  # ghosts stay (their results are not the rank's)
+        return x
+    return engine
+
+
+def run_local(pop, world, iters, engine):
+    z = pop.xyz[:, 2]
+    slabs = halo.Slabs(float(z.min()), float(z.max()), world)
+    doms = [halo.SlabDomain(slabs, r, np.arange(pop.n), pop.xyz, pop.diameter) for r in range(world)]
+    halo_in = moved = 0
+    for _ in range(iters):
+        for c in halo.step_local(doms, engine):
+            halo_in += c["halo_in"]
+            moved += c["migrated_out"]
+    ids = np.concatenate([dm.ids for dm in doms])
+    xyz = np.concatenate([dm.xyz for dm in doms])
+    assert np.array_equal(np.sort(ids), np.arange(pop.n))
+    got = np.empty_like(xyz)
+    got[ids] = xyz
+    return got, halo_in, moved
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_local_exchange_matches_one_domain(orc, world):
+    """The in-process exchange (every slab stepped by one process) equals a
+    single domain bit for bit, with ghosts left in place."""
+    import oracle
+    pop = _population()
+    got, halo_in, moved = run_local(pop, world, 4, oracle_engine(pop.params))
+    assert halo_in > 0 and moved > 0
+    s = oracle.Sim(pop.xyz, pop.diameter, pop.params)
+    s.step(4)
     assert np.array_equal(got, s.get()[0])
