@@ -36,6 +36,7 @@ class OrcParams(C.Structure):
         ("sort_interval", C.c_int32), ("boundary", C.c_int32),
         ("seed", C.c_uint64), ("capacity", C.c_int64),
         ("bound_min", C.c_double), ("bound_max", C.c_double),
+        ("execution_context", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -124,7 +125,7 @@ def make_params(p=None, **kw) -> OrcParams:
     d = dict(k=2.0, gamma=1.0, adherence=0.4, max_displacement=3.0, dt=0.01,
              box_length=0.0, growth_rate=0.0, divide_volume=0.0, precision=0,
              detect_static=0, sort_interval=0, seed=0, capacity=0, boundary=0,
-             bound_min=0.0, bound_max=0.0)
+             bound_min=0.0, bound_max=0.0, execution_context=0)
     if p is not None:
         src = p.as_dict() if hasattr(p, "as_dict") else dict(p)
         for k in d:
@@ -134,7 +135,8 @@ def make_params(p=None, **kw) -> OrcParams:
     return OrcParams(d["k"], d["gamma"], d["adherence"], d["max_displacement"], d["dt"],
                      d["box_length"], d["growth_rate"], d["divide_volume"], int(d["precision"]),
                      int(d["detect_static"]), int(d["sort_interval"]), int(d["boundary"]), int(d["seed"]),
-                     int(d["capacity"]), float(d["bound_min"]), float(d["bound_max"]))
+                     int(d["capacity"]), float(d["bound_min"]), float(d["bound_max"]),
+                     int(d["execution_context"]), 0)
 
 
 class Sim:

@@ -31,7 +31,8 @@
  *      the counter-based random numbers proposed in §7.1.4;
  *   6. Morton order of grid boxes by the gap algorithm (§5.4.2, Fig 5.4);
  *   7. the space boundary conditions of §4.4.11 (open, closed, toroidal);
- *   8. agent removal with the swap of §5.3.2 (Fig 5.1).
+ *   8. agent removal with the swap of §5.3.2 (Fig 5.1);
+ *   9. the in-place execution context (§5.2), as an alternative to copy.
  *
  * Readings taken where the thesis is silent (each one is listed with the
  * design notes of the repository):
@@ -66,7 +67,23 @@
  *     below n' keep it, and the IDs below n' that removed agents held go,
  *     in ascending order, to the survivors with IDs >= n' in ascending
  *     order (the swaps of §5.3.2); every survivor then counts as changed for
- *     one iteration (the removed agents' neighbourhoods changed).
+ *     one iteration (the removed agents' neighbourhoods changed);
+ *   - in-place execution context: an agent's new position is visible to
+ *     the agents processed after it in the same iteration.  The thesis
+ *     leaves the order to the scheduler; the order taken is: boxes by
+ *     colour, then boxes of a colour in ascending box index, then the
+ *     agents of a box in ascending ID.  The colour of a box is (c_x mod 2,
+ *     c_y mod 2, c_z mod 2), except that on a toroidal axis with an odd
+ *     number of boxes the last box of the axis has a third colour (it
+ *     touches box 0 across the seam); colours are ranked x + k_x (y + k_y
+ *     z), k_a = 2 or 3 colours per axis.  Boxes of one colour never lie in
+ *     each other's 27-box stencil, so their order inside the colour does
+ *     not matter.  Neighbours are the agents of the stencil in the grid of
+ *     the iteration's start, at their current positions; an agent's force
+ *     is summed over them in ascending ID and its displacement committed
+ *     (under the boundary condition) before the next agent.  Static
+ *     detection is not combined with it; growth and division follow the
+ *     mechanics as in the copy context.
  */
 #include <math.h>
 #include <stdint.h>
@@ -85,9 +102,12 @@ typedef struct {
   uint64_t seed;
   int64_t capacity;
   double bound_min, bound_max;  /* the space of closed and toroidal boundaries */
+  int32_t execution_context;    /* 0 copy, 1 in-place (§5.2) */
+  int32_t reserved;
 } orc_params;
 
 enum { ORC_OPEN = 0, ORC_CLOSED = 1, ORC_TORUS = 2 };
+enum { ORC_COPY = 0, ORC_INPLACE = 1 };
 
 /* A new coordinate under the boundary condition (§4.4.11). */
 static double bound_apply(const orc_params *p, double v) {
@@ -525,6 +545,8 @@ static int inside_space(const orc_params *p, double v) {
 orc_sim *orc_create(const orc_params *p, int64_t n, const double *xyz, const double *d) {
   if (n < 0) return NULL;
   if (p->boundary < ORC_OPEN || p->boundary > ORC_TORUS) return NULL;
+  if (p->execution_context != ORC_COPY && p->execution_context != ORC_INPLACE) return NULL;
+  if (p->execution_context == ORC_INPLACE && p->detect_static) return NULL;
   if (p->boundary != ORC_OPEN &&
       !(isfinite(p->bound_min) && isfinite(p->bound_max) && p->bound_min < p->bound_max))
     return NULL;
@@ -631,7 +653,52 @@ static int box_in_sorted(const int64_t *v, int64_t n, int64_t b) {
   return lo < n && v[lo] == b;
 }
 
-/* One iteration (§5.2 Algorithm 8 under the copy execution context). */
+/* Colour of box coordinates c in the in-place order (k[a] colours per axis). */
+static int box_colour(const grid_t *g, const int64_t *c, const int *k) {
+  int col[3];
+  for (int a = 0; a < 3; ++a)
+    col[a] = (k[a] == 3 && c[a] == g->dims[a] - 1) ? 2 : (int)(c[a] % 2);
+  return col[0] + k[0] * (col[1] + k[1] * col[2]);
+}
+
+/* Forces and displacements under the in-place execution context (§5.2):
+ * boxes by colour, boxes of a colour in ascending index, agents of a box in
+ * ascending ID; each agent's force from the current positions of the agents
+ * of its stencil in the grid g of the iteration's start, its displacement
+ * committed at once. */
+static void inplace_mechanics(orc_sim *s, const grid_t *g) {
+  const orc_params *p = &s->p;
+  const int64_t n = s->n;
+  int k[3];
+  for (int a = 0; a < 3; ++a) k[a] = (g->torus && (g->dims[a] % 2) == 1) ? 3 : 2;
+  const int ncol = k[0] * k[1] * k[2];
+  idlist cand = {0, 0, 0};
+  for (int col = 0; col < ncol; ++col) {
+    /* g->sorted lists the agents by (box, ID), boxes in ascending index */
+    for (int64_t q = 0; q < n; ++q) {
+      const int64_t i = g->sorted[q];
+      if (box_colour(g, &g->c[3 * i], k) != col) continue;
+      double f[3] = {0.0, 0.0, 0.0}, sm = 0.0;
+      int32_t nz = 0;
+      grid_candidates(g, i, &cand);
+      for (int64_t m = 0; m < cand.n; ++m) pair_force(p, s->x, s->y, s->z, s->d, i, cand.v[m], f, &nz, &sm);
+      s->F[3 * i] = f[0]; s->F[3 * i + 1] = f[1]; s->F[3 * i + 2] = f[2];
+      s->nnz[i] = nz;
+      double *D = &s->D[3 * i];
+      displacement(p, f, D);
+      s->x[i] = bound_apply(p, s->x[i] + D[0]);
+      s->y[i] = bound_apply(p, s->y[i] + D[1]);
+      s->z[i] = bound_apply(p, s->z[i] + D[2]);
+      s->changed[i] = (uint8_t)(D[0] != 0.0 || D[1] != 0.0 || D[2] != 0.0);
+      s->stat[i] = 0;
+      s->prev_box[i] = g->box[i];
+    }
+  }
+  free(cand.v);
+}
+
+/* One iteration (§5.2 Algorithm 8 under the copy execution context, or the
+ * in-place one). */
 static int orc_iterate(orc_sim *s) {
   const orc_params *p = &s->p;
   int64_t n = s->n;
@@ -668,32 +735,36 @@ static int orc_iterate(orc_sim *s) {
     free(dirty);
   }
 
-  /* Forces and displacements from the snapshot. */
-  idlist cand = {0, 0, 0};
-  for (int64_t i = 0; i < n; ++i) {
-    double f[3] = {0.0, 0.0, 0.0}, sm = 0.0;
-    if (stat[i]) {
-      s->D[3 * i] = s->D[3 * i + 1] = s->D[3 * i + 2] = 0.0;
-      s->F[3 * i] = s->F[3 * i + 1] = s->F[3 * i + 2] = 0.0;
-      continue;  /* static: keeps its nnz, does not move */
+  if (p->execution_context == ORC_INPLACE) {
+    inplace_mechanics(s, &g);
+  } else {
+    /* Forces and displacements from the snapshot. */
+    idlist cand = {0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+      double f[3] = {0.0, 0.0, 0.0}, sm = 0.0;
+      if (stat[i]) {
+        s->D[3 * i] = s->D[3 * i + 1] = s->D[3 * i + 2] = 0.0;
+        s->F[3 * i] = s->F[3 * i + 1] = s->F[3 * i + 2] = 0.0;
+        continue;  /* static: keeps its nnz, does not move */
+      }
+      int32_t nz = 0;
+      grid_candidates(&g, i, &cand);
+      for (int64_t k = 0; k < cand.n; ++k) pair_force(p, s->x, s->y, s->z, s->d, i, cand.v[k], f, &nz, &sm);
+      s->F[3 * i] = f[0]; s->F[3 * i + 1] = f[1]; s->F[3 * i + 2] = f[2];
+      s->nnz[i] = nz;
+      displacement(p, f, &s->D[3 * i]);
     }
-    int32_t nz = 0;
-    grid_candidates(&g, i, &cand);
-    for (int64_t k = 0; k < cand.n; ++k) pair_force(p, s->x, s->y, s->z, s->d, i, cand.v[k], f, &nz, &sm);
-    s->F[3 * i] = f[0]; s->F[3 * i + 1] = f[1]; s->F[3 * i + 2] = f[2];
-    s->nnz[i] = nz;
-    displacement(p, f, &s->D[3 * i]);
-  }
-  free(cand.v);
+    free(cand.v);
 
-  /* Commit (copy execution context), under the boundary condition. */
-  for (int64_t i = 0; i < n; ++i) {
-    s->x[i] = bound_apply(p, s->x[i] + s->D[3 * i]);
-    s->y[i] = bound_apply(p, s->y[i] + s->D[3 * i + 1]);
-    s->z[i] = bound_apply(p, s->z[i] + s->D[3 * i + 2]);
-    s->changed[i] = (uint8_t)(s->D[3 * i] != 0.0 || s->D[3 * i + 1] != 0.0 || s->D[3 * i + 2] != 0.0);
-    s->stat[i] = stat[i];
-    s->prev_box[i] = g.box[i];
+    /* Commit (copy execution context), under the boundary condition. */
+    for (int64_t i = 0; i < n; ++i) {
+      s->x[i] = bound_apply(p, s->x[i] + s->D[3 * i]);
+      s->y[i] = bound_apply(p, s->y[i] + s->D[3 * i + 1]);
+      s->z[i] = bound_apply(p, s->z[i] + s->D[3 * i + 2]);
+      s->changed[i] = (uint8_t)(s->D[3 * i] != 0.0 || s->D[3 * i + 1] != 0.0 || s->D[3 * i + 2] != 0.0);
+      s->stat[i] = stat[i];
+      s->prev_box[i] = g.box[i];
+    }
   }
   free(stat);
 

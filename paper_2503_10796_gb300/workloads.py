@@ -43,6 +43,7 @@ class SimParams:
     boundary: int = 0              # 0 open, 1 closed, 2 toroidal space (§4.4.11)
     bound_min: float = 0.0         # the space [bound_min, bound_max] per axis
     bound_max: float = 0.0         #   (closed and toroidal boundaries)
+    execution_context: int = 0     # 0 copy, 1 in-place (§5.2)
 
     def as_dict(self):
         return asdict(self)
