@@ -75,6 +75,22 @@ enum { BDM_PREC_FP64 = 0, BDM_PREC_FP32_FORCE = 1 };
  * lie in its space. */
 enum { BDM_BOUNDARY_OPEN = 0, BDM_BOUNDARY_CLOSED = 1, BDM_BOUNDARY_TOROIDAL = 2 };
 
+/* Execution contexts (§5.2).  Copy: every quantity of an iteration is
+ * computed from the snapshot at its start and committed after all agents.
+ * In-place: an agent's new position is visible to the agents processed
+ * after it in the same iteration.  The thesis leaves that order to its
+ * scheduler; here it is fixed: boxes by colour (the parity of each box
+ * coordinate, plus a third colour for the last box of a toroidal axis with
+ * an odd number of boxes; colours ranked x + k_x (y + k_y z)), boxes of a
+ * colour in ascending index, agents of a box in ascending ID.  Neighbours
+ * are the agents of the 27-box stencil in the grid of the iteration's start,
+ * at their current positions; each agent's force (summed in ascending
+ * partner ID) and displacement are committed before the next agent.  The
+ * in-place context runs the FP64 path without static detection
+ * (BDM_E_INVAL otherwise), and all simulations of a context share one
+ * context. */
+enum { BDM_EXEC_COPY = 0, BDM_EXEC_INPLACE = 1 };
+
 /* flags of bdm_set_agents / bdm_get_agents */
 enum { BDM_DEVICE_PTRS = 1 };
 
@@ -96,6 +112,8 @@ typedef struct {
   int64_t capacity;        /* agent capacity of this simulation; 0 = count at bdm_set_agents */
   double bound_min;        /* the space of closed and toroidal boundaries, per axis */
   double bound_max;
+  int32_t execution_context; /* BDM_EXEC_COPY (0, default) or BDM_EXEC_INPLACE */
+  int32_t reserved;        /* 0 */
 } bdm_params;
 
 /* Counters of one simulation (bdm_get_stats). */
@@ -269,8 +287,10 @@ int bdm_get_profile(bdm_ctx* ctx, int64_t launches[BDM_NUM_STAGES], double ms[BD
  * about 5 MB in the library's device memory, held by every GPU that loads
  * the library until the process exits.
  *
- * params: one parameter set (growth, static, sort and capacity fields are
- * ignored: the first iteration has no static agents).
+ * params: one parameter set (growth, static, sort, capacity and
+ * execution-context fields are ignored: the first iteration has no static
+ * agents, and the forces are those of the iteration's snapshot, as in the
+ * copy context).
  * xyz: device pointer, n x 3 doubles, row-major; diameter: device pointer,
  * n doubles; force: device pointer, n x 3 doubles written in row order;
  * nnz: device pointer, n int32 (non-zero pair forces per agent), or NULL.

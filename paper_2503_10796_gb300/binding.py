@@ -33,6 +33,7 @@ class BdmParams(C.Structure):
         ("precision", C.c_int32), ("detect_static", C.c_int32), ("sort_interval", C.c_int32),
         ("boundary", C.c_int32), ("seed", C.c_uint64), ("capacity", C.c_int64),
         ("bound_min", C.c_double), ("bound_max", C.c_double),
+        ("execution_context", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -126,7 +127,8 @@ class BdmError(RuntimeError):
 def make_params(p=None, **kw) -> BdmParams:
     d = dict(k=2.0, gamma=1.0, adherence=0.4, max_displacement=3.0, dt=0.01, box_length=0.0,
              growth_rate=0.0, divide_volume=0.0, precision=PREC_FP32_FORCE, detect_static=0,
-             sort_interval=0, seed=0, capacity=0, boundary=0, bound_min=0.0, bound_max=0.0)
+             sort_interval=0, seed=0, capacity=0, boundary=0, bound_min=0.0, bound_max=0.0,
+             execution_context=0)
     if p is not None:
         src = p.as_dict() if hasattr(p, "as_dict") else dict(p)
         for k in d:
@@ -136,7 +138,8 @@ def make_params(p=None, **kw) -> BdmParams:
     return BdmParams(d["k"], d["gamma"], d["adherence"], d["max_displacement"], d["dt"], d["box_length"],
                      d["growth_rate"], d["divide_volume"], int(d["precision"]), int(d["detect_static"]),
                      int(d["sort_interval"]), int(d["boundary"]), int(d["seed"]) & (2**64 - 1),
-                     int(d["capacity"]), float(d["bound_min"]), float(d["bound_max"]))
+                     int(d["capacity"]), float(d["bound_min"]), float(d["bound_max"]),
+                     int(d["execution_context"]), 0)
 
 
 def _dptr(a: np.ndarray):

@@ -54,7 +54,7 @@ struct SimConst {
   int64_t base, cap;
   int64_t table_base, table_cap;
   int32_t boundary;           // BOUND_*
-  int32_t pad;
+  int32_t exec_ctx;           // BDM_EXEC_COPY or BDM_EXEC_INPLACE
   double bmin, bmax;          // the space of closed and toroidal boundaries, per axis
   double bsize, bhalf;        // bmax - bmin and half of it
 };

@@ -53,6 +53,8 @@ struct bdm_ctx {
   size_t sort_bytes = 0;
   int sort_key_bits = 0;
   int force_variant = 5;     // force kernel variant of the FP32 path (see launch_force)
+  bool inplace = false;      // the in-place execution context (every simulation)
+  int inplace_colours = 8;   // box colours of its order (27 when a simulation is toroidal)
   int sort_override = -1;    // -1: per-simulation sort intervals
   int sort_curve = 0;        // 0: Morton order of boxes; 1: row-major box order
   int box_scale_pct = 100;   // box length in % of the largest diameter (simulations without static detection)
@@ -145,6 +147,14 @@ int check_params(const bdm_params &p, std::string &why) {
     why = "a closed or toroidal space needs finite bound_min < bound_max";
     return BDM_E_INVAL;
   }
+  if (p.execution_context != BDM_EXEC_COPY && p.execution_context != BDM_EXEC_INPLACE) {
+    why = "execution_context must be BDM_EXEC_COPY or BDM_EXEC_INPLACE";
+    return BDM_E_INVAL;
+  }
+  if (p.execution_context == BDM_EXEC_INPLACE && (p.precision != BDM_PREC_FP64 || p.detect_static)) {
+    why = "the in-place execution context runs the FP64 path without static detection";
+    return BDM_E_INVAL;
+  }
   if (p.growth_rate > 0 && !(p.divide_volume > 0)) {
     why = "growth needs divide_volume > 0";
     return BDM_E_INVAL;
@@ -179,6 +189,7 @@ SimConst make_const(const bdm_params &p) {
   s.table_base = 0;
   s.table_cap = 0;
   s.boundary = p.boundary;
+  s.exec_ctx = p.execution_context;
   s.bmin = p.bound_min;
   s.bmax = p.bound_max;
   s.bsize = p.boundary != BDM_BOUNDARY_OPEN ? p.bound_max - p.bound_min : 0.0;
@@ -283,12 +294,19 @@ void launch_iteration(bdm_ctx *c, int sort) {
   stage_begin(c, 3);
   launch_place(D, st, 1, pl.zero_f32 ? 1 : 0);
   stage_end(c);
-  stage_begin(c, 4);
-  launch_force(D, st, pl.variant, c->any_fp32, c->any_fp64, any_static, any_torus);
-  stage_end(c);
-  stage_begin(c, 5);
-  launch_displace(D, st);
-  stage_end(c);
+  if (c->inplace) {
+    // S4 + S5 of the in-place context: one launch per box colour
+    stage_begin(c, 4);
+    launch_inplace(D, st, c->inplace_colours);
+    stage_end(c);
+  } else {
+    stage_begin(c, 4);
+    launch_force(D, st, pl.variant, c->any_fp32, c->any_fp64, any_static, any_torus);
+    stage_end(c);
+    stage_begin(c, 5);
+    launch_displace(D, st);
+    stage_end(c);
+  }
   if (c->any_grow) {
     stage_begin(c, 6);
     launch_growth(D, st, c->d_grow, c->grow_bytes);
@@ -571,6 +589,9 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   std::string why;
   for (int s = 0; s < n_sims; ++s)
     if (check_params(per_sim[s], why)) return fail(nullptr, BDM_E_INVAL, "simulation " + std::to_string(s) + ": " + why);
+  for (int s = 1; s < n_sims; ++s)
+    if (per_sim[s].execution_context != per_sim[0].execution_context)
+      return fail(nullptr, BDM_E_INVAL, "all simulations of a context share one execution context");
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) return fail(nullptr, BDM_E_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
   bdm_ctx *c = new bdm_ctx();
@@ -578,6 +599,9 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   c->n_sims = n_sims;
   c->max_total = max_agents_total;
   c->params.assign(per_sim, per_sim + n_sims);
+  c->inplace = per_sim[0].execution_context == BDM_EXEC_INPLACE;
+  for (int s = 0; s < n_sims; ++s)
+    if (per_sim[s].boundary == BDM_BOUNDARY_TOROIDAL) c->inplace_colours = 27;
   c->n_set.assign(n_sims, -1);
   c->h_iter.assign(n_sims, 0);
   c->need_radix.assign(n_sims, 1);

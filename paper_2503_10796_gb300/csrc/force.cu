@@ -463,22 +463,13 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
   bool moved = false, bad = false;
   if (sc.precision == BDM_PREC_FP64) {
     C.a.nnz[slot] = C.c.nnz[p];
-    double4_32a F = C.c.f64[p];
-    double fn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(F.x, F.x), __dmul_rn(F.y, F.y)), __dmul_rn(F.z, F.z)));
-    bad = !isfinite(fn);
-    if (fn > sc.adherence && !ghost) {
-      double Dx = __dmul_rn(sc.dt, F.x), Dy = __dmul_rn(sc.dt, F.y), Dz = __dmul_rn(sc.dt, F.z);
-      double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(Dx, Dx), __dmul_rn(Dy, Dy)), __dmul_rn(Dz, Dz)));
-      if (dn > sc.max_disp) {
-        double f = __ddiv_rn(sc.max_disp, dn);
-        Dx = __dmul_rn(Dx, f); Dy = __dmul_rn(Dy, f); Dz = __dmul_rn(Dz, f);
-      }
-      moved = (Dx != 0.0 || Dy != 0.0 || Dz != 0.0);
-      if (moved) {
-        C.a.x[slot] = bound_apply(sc, __dadd_rn(C.a.x[slot], Dx));
-        C.a.y[slot] = bound_apply(sc, __dadd_rn(C.a.y[slot], Dy));
-        C.a.z[slot] = bound_apply(sc, __dadd_rn(C.a.z[slot], Dz));
-      }
+    const double4_32a F = C.c.f64[p];
+    double Dx, Dy, Dz;
+    moved = disp64(sc, F.x, F.y, F.z, Dx, Dy, Dz, bad) && !ghost;
+    if (moved) {
+      C.a.x[slot] = bound_apply(sc, __dadd_rn(C.a.x[slot], Dx));
+      C.a.y[slot] = bound_apply(sc, __dadd_rn(C.a.y[slot], Dy));
+      C.a.z[slot] = bound_apply(sc, __dadd_rn(C.a.z[slot], Dz));
     }
   } else {
     float4 F = C.c.f32[p];

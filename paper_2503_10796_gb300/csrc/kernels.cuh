@@ -40,6 +40,8 @@ void launch_force64(const DevCtx &C, cudaStream_t st);
 // force_stream.cu: mode 0 half stencil, 1 full stencil with static skip,
 // 2 static flags first, then the half stencil
 void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads, bool torus);
+// inplace.cu: S4 + S5 of the in-place execution context, one launch per box colour.
+void launch_inplace(const DevCtx &C, cudaStream_t st, int colours);
 void launch_displace(const DevCtx &C, cudaStream_t st);
 
 // diffusion.cu (soma-clustering slice)

@@ -177,6 +177,29 @@ __device__ __forceinline__ bool pair64(const SimConst &sc, const double4_32a &o,
   return true;
 }
 
+// Displacement of the FP64 path from the net force F (§4.5.1): zero while
+// |F| <= adherence, else dt F with its norm clamped to the maximum
+// displacement; operation by operation as the definition.  bad: |F| is not
+// finite.  Returns whether the displacement is non-zero.
+__device__ __forceinline__ bool disp64(const SimConst &sc, double fx, double fy, double fz, double &Dx, double &Dy,
+                                       double &Dz, bool &bad) {
+  const double fn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(fx, fx), __dmul_rn(fy, fy)), __dmul_rn(fz, fz)));
+  bad = !isfinite(fn);
+  Dx = Dy = Dz = 0.0;
+  if (!(fn > sc.adherence)) return false;
+  Dx = __dmul_rn(sc.dt, fx);
+  Dy = __dmul_rn(sc.dt, fy);
+  Dz = __dmul_rn(sc.dt, fz);
+  const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(Dx, Dx), __dmul_rn(Dy, Dy)), __dmul_rn(Dz, Dz)));
+  if (dn > sc.max_disp) {
+    const double f = __ddiv_rn(sc.max_disp, dn);
+    Dx = __dmul_rn(Dx, f);
+    Dy = __dmul_rn(Dy, f);
+    Dz = __dmul_rn(Dz, f);
+  }
+  return Dx != 0.0 || Dy != 0.0 || Dz != 0.0;
+}
+
 // Pair force of candidate j on an owner with records (o0, o1) and the
 // owner simulation's L (Lh, Ll), k and gamma, as a vector, for the stream
 // kernel: the arithmetic of pair32 with square roots as x rsqrt(x) (relative

@@ -45,7 +45,7 @@ def test_params_struct_layouts_agree():
     assert names_b == names_o
     assert set(workloads.SimParams().as_dict()) <= set(names_b)
     import ctypes
-    assert ctypes.sizeof(binding.BdmParams) == 8 * 8 + 4 * 4 + 8 + 8 + 2 * 8
+    assert ctypes.sizeof(binding.BdmParams) == 8 * 8 + 4 * 4 + 8 + 8 + 2 * 8 + 2 * 4
 
 
 def test_create_without_gpu_fails_loudly():

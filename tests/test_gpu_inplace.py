@@ -1,0 +1,128 @@
+"""The in-place execution context (§5.2) on the GPU against the oracle.
+
+The kernel runs one launch per box colour and one thread per box, and
+commits each agent's displacement before the next agent.  It follows the
+oracle's order (colour, box index, agent ID) and evaluates every definition
+in FP64 in the oracle's order of operations, so positions, forces and nnz
+equal the oracle's bit for bit at every iteration: in open space, on an odd
+torus (a third colour at the seam), in a closed box, for a crowd beyond the
+kernel's sorted partner list, with growth and division, and in a context of
+several simulations.
+"""
+import numpy as np
+import pytest
+
+from paper_2503_10796_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def ctx_for(pops, **kw):
+    from paper_2503_10796_gb300 import binding
+    pops = pops if isinstance(pops, list) else [pops]
+    ctx = binding.Context([binding.make_params(p.params, execution_context=1, **kw) for p in pops],
+                          sum(max(p.n, p.params.capacity) for p in pops) + 16)
+    for s, p in enumerate(pops):
+        ctx.set_agents(s, p.xyz, p.diameter)
+    return ctx
+
+
+def orc_for(pop):
+    import oracle
+    return oracle.Sim(pop.xyz, pop.diameter, pop.params, execution_context=1)
+
+
+def scenes():
+    from tests.test_oracle_pins import perturbed_scene
+    xyz, d = perturbed_scene()
+    rng = np.random.default_rng(3)
+    txyz = rng.uniform(0.0, 90.0, (2500, 3))
+    td = rng.uniform(8.0, 12.0, 2500)
+    cxyz = rng.uniform(0.0, 90.0, (2500, 3))
+    cd = rng.uniform(8.0, 12.0, 2500)
+    clump = rng.uniform(0.0, 20.0, (300, 3))
+    clump_d = rng.uniform(8.0, 12.0, 300)
+    base = workloads.clustered(n_clusters=5, per_cluster=700, side=600.0, sigma=25.0, seed=2)
+    return [
+        ("perturbed", workloads.Population(xyz, d, workloads.SimParams(dt=0.05, precision=0))),
+        ("clusters", workloads.Population(base.xyz, base.diameter, workloads.SimParams(precision=0))),
+        ("torus_odd", workloads.Population(txyz, td, workloads.SimParams(precision=0, boundary=2, bound_min=0.0,
+                                                                        bound_max=90.0))),
+        ("closed", workloads.Population(cxyz, cd, workloads.SimParams(precision=0, boundary=1, bound_min=0.0,
+                                                                     bound_max=90.0, dt=0.05))),
+        ("dense_clump", workloads.Population(clump, clump_d, workloads.SimParams(precision=0))),
+    ]
+
+
+@pytest.mark.parametrize("sort_interval", [0, 3])
+@pytest.mark.parametrize("scene", range(5))
+def test_inplace_trajectory_bit_exact(orc, scene, sort_interval):
+    name, pop = scenes()[scene]
+    ctx = ctx_for(pop, sort_interval=sort_interval)
+    o = orc_for(pop)
+    for t in range(10):
+        ctx.step(1)
+        o.step(1)
+        x, _ = ctx.get_agents(0)
+        x_o, _, _ = o.get()
+        assert np.array_equal(x, x_o), (name, t, np.abs(x - x_o).max())
+        F, nnz, st = ctx.forces(0)
+        F_o, _, nnz_o, _, _ = o.last()
+        assert np.array_equal(F, F_o), (name, t)
+        assert np.array_equal(nnz, np.minimum(nnz_o, 255)), (name, t)
+        assert not st.any()
+    # the in-place trajectory is not the copy context's
+    import oracle
+    c = oracle.Sim(pop.xyz, pop.diameter, pop.params)
+    c.step(10)
+    assert not np.array_equal(c.get()[0], x), name
+
+
+def test_inplace_crowd_beyond_the_partner_list(orc):
+    """Every agent of a tight clump overlaps all 99 others, more than the
+    48 partners the kernel sorts in place: the selection loop adds them."""
+    rng = np.random.default_rng(9)
+    pop = workloads.Population(100.0 + rng.uniform(0.0, 5.0, (100, 3)), rng.uniform(9.5, 10.5, 100),
+                               workloads.SimParams(precision=0, dt=0.01))
+    ctx = ctx_for(pop)
+    o = orc_for(pop)
+    for t in range(3):
+        ctx.step(1)
+        o.step(1)
+        assert np.array_equal(ctx.get_agents(0)[0], o.get()[0]), t
+    _, _, _, ov = ctx.forces(0, overlaps=True)
+    assert ov.max() > 48
+
+
+def test_inplace_growth_and_batched_sims_bit_exact(orc):
+    pop = workloads.growth_division(shape=(4, 4, 4), cap_factor=8, precision=0)
+    ctx = ctx_for(pop)
+    o = orc_for(pop)
+    for t in range(30):
+        ctx.step(1)
+        o.step(1)
+        assert ctx.count(0) == o.n, t
+    x, d = ctx.get_agents(0)
+    x_o, d_o, _ = o.get()
+    assert np.array_equal(d, d_o) and np.array_equal(x, x_o)
+    pops = workloads.batched_sweep(n_sims=4, lo=50, hi=2000, seed=11, precision=0)
+    ctx = ctx_for(pops)
+    ctx.step(6)
+    for s, p in enumerate(pops):
+        o = orc_for(p)
+        o.step(6)
+        assert np.array_equal(ctx.get_agents(s)[0], o.get()[0]), s
+
+
+def test_inplace_parameters_are_checked(orc):
+    from paper_2503_10796_gb300 import binding
+    pop = workloads.plain_fp64(n=100, precision=0)
+    for kw in (dict(precision=1), dict(detect_static=1), dict(execution_context=2)):
+        p = dict(execution_context=1)
+        p.update(kw)
+        with pytest.raises(binding.BdmError) as e:
+            binding.Context(binding.make_params(pop.params, **p), 128)
+        assert e.value.code == -1
+    with pytest.raises(binding.BdmError) as e:
+        binding.Context([binding.make_params(pop.params, execution_context=1), binding.make_params(pop.params)], 256)
+    assert e.value.code == -1
