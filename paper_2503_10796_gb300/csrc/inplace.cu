@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kInThreads) k_inplace(DevCtx C, int colour) {
         q = b0 + m;
       }
     }
+    if (q < 0) break;  // IDs are distinct: never taken
     last_id = (int64_t)qid;
     const int32_t sq = C.c.slot[q];
     const double4_32a o = current(C, q);
