@@ -346,7 +346,23 @@ typedef struct {
                               gives up after 64 polls per tile, so that the next
                               bdm_sync reports BDM_E_TIMEOUT (that iteration's
                               results are undefined; the context stays usable) */
-  int32_t reserved[2];     /* must be 0 */
+  int32_t grid_reuse;      /* 1: incremental grid (the thesis adapts its grid to
+                              incremental position updates, §6.2.5): an iteration
+                              keeps the last build's grid while every agent stays
+                              within the skin (L - largest diameter) / 2 of the box
+                              it is registered in, which still puts every
+                              interacting pair in neighbouring boxes; the moved
+                              agents' cell records are rewritten in place.  The grid
+                              is rebuilt when an agent left its skin, on re-sorts,
+                              and after any other call that changes agents or the
+                              grid.  Needs a box longer than the largest diameter
+                              (box_scale_pct > 100 or a box_length) to keep any
+                              grid; results are those of a rebuilt grid (FP64 path
+                              bit for bit).  Only for contexts without static
+                              detection, growth, toroidal boundaries or the
+                              in-place context (BDM_E_INVAL otherwise).  0: rebuild
+                              every iteration (default, §5.3.1). */
+  int32_t reserved;        /* must be 0 */
 } bdm_tuning;
 
 int bdm_set_tuning(bdm_ctx* ctx, const bdm_tuning* tuning);
@@ -379,14 +395,17 @@ enum {
 int bdm_autotune(bdm_ctx* ctx, int32_t iterations, int32_t knobs, bdm_tuning* chosen);
 
 /* Launch counters of a context since bdm_create: CUDA graphs replayed by
- * bdm_step, the kernels they and bdm_step's own table sizing launched, and
- * the iterations the graphs covered (iterations stepped while profiling is
- * enabled launch their kernels one by one and are not counted). */
+ * bdm_step, the kernels they and bdm_step's own table sizing launched, the
+ * iterations the graphs covered (iterations stepped while profiling is
+ * enabled launch their kernels one by one and are not counted), and the
+ * grid builds of stepped iterations (synchronizes the stream). */
 typedef struct {
   int64_t graph_launches;
   int64_t kernels;
   int64_t graph_iterations;
-  int64_t reserved[5];
+  int64_t grid_builds;     /* grid builds of stepped iterations (with grid_reuse,
+                              the iterations that rebuilt the grid) */
+  int64_t reserved[4];
 } bdm_counters;
 
 int bdm_get_counters(bdm_ctx* ctx, bdm_counters* out);

@@ -46,16 +46,17 @@ class BdmStats(C.Structure):
 class BdmTuning(C.Structure):
     _fields_ = [("force_variant", C.c_int32), ("sort_interval", C.c_int32), ("sort_curve", C.c_int32),
                 ("box_scale_pct", C.c_int32), ("iter_batch", C.c_int32), ("test_flags", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("grid_reuse", C.c_int32), ("reserved", C.c_int32)]
 
 
-TUNING_FIELDS = ("force_variant", "sort_interval", "sort_curve", "box_scale_pct", "iter_batch", "test_flags")
+TUNING_FIELDS = ("force_variant", "sort_interval", "sort_curve", "box_scale_pct", "iter_batch", "test_flags",
+                 "grid_reuse")
 TUNE_FORCE, TUNE_CURVE, TUNE_INTERVAL, TUNE_BOX, TUNE_BATCH, TUNE_ALL = 1, 2, 4, 8, 16, 31
 
 
 class BdmCounters(C.Structure):
     _fields_ = [("graph_launches", C.c_int64), ("kernels", C.c_int64), ("graph_iterations", C.c_int64),
-                ("reserved", C.c_int64 * 5)]
+                ("grid_builds", C.c_int64), ("reserved", C.c_int64 * 4)]
 
 
 class BdmDiffusionGrid(C.Structure):
@@ -374,9 +375,9 @@ class Context:
 
     # -- tuning ------------------------------------------------------------
     def set_tuning(self, force_variant: int = 0, sort_interval: int = -1, sort_curve: int = 0,
-                   box_scale_pct: int = 100, iter_batch: int = 1, test_flags: int = 0):
+                   box_scale_pct: int = 100, iter_batch: int = 1, test_flags: int = 0, grid_reuse: int = 0):
         t = BdmTuning(int(force_variant), int(sort_interval), int(sort_curve), int(box_scale_pct),
-                      int(iter_batch), int(test_flags))
+                      int(iter_batch), int(test_flags), int(grid_reuse))
         self._check(self._lib.bdm_set_tuning(self._h, C.byref(t)))
 
     def get_tuning(self) -> dict:
@@ -394,7 +395,8 @@ class Context:
     def counters(self) -> dict:
         c = BdmCounters()
         self._check(self._lib.bdm_get_counters(self._h, C.byref(c)))
-        return dict(graph_launches=c.graph_launches, kernels=c.kernels, graph_iterations=c.graph_iterations)
+        return dict(graph_launches=c.graph_launches, kernels=c.kernels, graph_iterations=c.graph_iterations,
+                    grid_builds=c.grid_builds)
 
     # -- profiling ---------------------------------------------------------
     def profile(self, enable: bool = True):

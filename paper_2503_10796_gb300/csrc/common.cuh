@@ -84,6 +84,7 @@ struct SimState {
   int64_t it;                 // index of the iteration being computed
   unsigned long long n_static, n_moved;
   unsigned long long updates;  // agent-updates stepped since the agents were set
+  double skin;                // grid reuse: how far an agent may leave its box before the grid is rebuilt
 };
 
 // Global counters of a context.
@@ -95,7 +96,10 @@ struct Globals {
   uint32_t tile_ticket;       // scan tiles claimed in this build (reset by k_params)
   uint32_t test_flags;        // TEST_* hooks (host-set; 0 in normal use)
   uint32_t n_ovf;             // FP64-path agents left to the overflow kernel (reset by k_params)
+  uint32_t regrid;            // grid reuse: the next iteration must rebuild the grid
+  uint32_t reuse;             // grid reuse: this iteration keeps the last build's grid
   uint32_t pad;
+  unsigned long long n_builds; // grid builds of step iterations
 };
 
 // Test hooks of Globals::test_flags.  TEST_SCAN_TIMEOUT: the ordered scan's

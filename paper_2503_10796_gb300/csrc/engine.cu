@@ -53,6 +53,8 @@ struct bdm_ctx {
   size_t sort_bytes = 0;
   int sort_key_bits = 0;
   int force_variant = 5;     // force kernel variant of the FP32 path (see launch_force)
+  bool grid_reuse = false;   // incremental grid: keep the last build while agents stay in their skins
+  bool host_touched = true;  // a call since the last bdm_step changed agents or the table
   bool inplace = false;      // the in-place execution context (every simulation)
   int inplace_colours = 8;   // box colours of its order (27 when a simulation is toroidal)
   int sort_override = -1;    // -1: per-simulation sort intervals
@@ -266,7 +268,8 @@ void launch_iteration(bdm_ctx *c, int sort) {
   const DevCtx &D = c->D;
   cudaStream_t st = c->stream;
   stage_begin(c, 0);
-  launch_bbox(D, st);
+  if (c->grid_reuse) launch_decide(D, st, sort);
+  launch_bbox(D, st, 1);
   launch_params(D, st, 1);
   stage_end(c);
   bool any_static = false, any_torus = false;
@@ -301,10 +304,11 @@ void launch_iteration(bdm_ctx *c, int sort) {
     stage_end(c);
   } else {
     stage_begin(c, 4);
+    if (c->grid_reuse && pl.zero_f32) launch_zero_f32(D, st);
     launch_force(D, st, pl.variant, c->any_fp32, c->any_fp64, any_static, any_torus);
     stage_end(c);
     stage_begin(c, 5);
-    launch_displace(D, st);
+    launch_displace(D, st, c->grid_reuse);
     stage_end(c);
   }
   if (c->any_grow) {
@@ -480,6 +484,7 @@ int read_state(bdm_ctx *c, int32_t sim, SimState *out) {
 
 // Build the grid of the current agents for queries (no step bookkeeping).
 int query_grid(bdm_ctx *c, bool with_cells, const std::vector<double> *boxes) {
+  c->host_touched = true;  // the query's build replaces the step's table words
   bool resized;
   int rc = ensure_table(c, 1, &resized);
   if (rc) return rc;
@@ -749,6 +754,7 @@ static int ensure_xfer(bdm_ctx *c, size_t doubles) {
 }
 
 int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const double *diameter, int32_t flags) {
+  if (c) c->host_touched = true;  // the next step rebuilds a reused grid
   int rc = check_sim(c, sim);
   if (rc) return rc;
   if (n < 0 || (n > 0 && (!xyz || !diameter))) return fail(c, BDM_E_INVAL, "n < 0 or NULL input");
@@ -800,6 +806,7 @@ int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const 
 }
 
 int bdm_update_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const double *diameter, int32_t flags) {
+  if (c) c->host_touched = true;  // the next step rebuilds a reused grid
   int rc = check_sim(c, sim);
   if (rc) return rc;
   if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
@@ -950,6 +957,7 @@ int bdm_get_state(bdm_ctx *c, int32_t sim, void *buf, int64_t cap_bytes, int64_t
 }
 
 int bdm_set_state(bdm_ctx *c, int32_t sim, const void *buf, int64_t size_bytes) {
+  if (c) c->host_touched = true;  // the next step rebuilds a reused grid
   int rc = check_sim(c, sim);
   if (rc) return rc;
   if (!buf || size_bytes < (int64_t)sizeof(StateHeader)) return fail(c, BDM_E_INVAL, "state buffer too small");
@@ -1020,6 +1028,7 @@ int bdm_set_state(bdm_ctx *c, int32_t sim, const void *buf, int64_t size_bytes) 
 // go to the surviving agents with IDs >= n', in ascending order.  O(removed)
 // host work builds the pairs; the device moves the rows of the by-ID state.
 int bdm_remove_agents(bdm_ctx *c, int32_t sim, int64_t n_ids, const int64_t *ids) {
+  if (c) c->host_touched = true;  // the next step rebuilds a reused grid
   int rc = check_sim(c, sim);
   if (rc) return rc;
   if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
@@ -1086,10 +1095,18 @@ int bdm_step(bdm_ctx *c, int32_t n_iterations) {
     bool resized = false;
     int rc = ensure_table(c, chunk, &resized);
     if (rc) return rc;
-    if (resized) c->graph_dirty = true;
+    if (resized) {
+      c->graph_dirty = true;
+      c->host_touched = true;
+    }
     rc = reserve_builds(c, chunk);
     if (rc) return rc;
     c->cnt_kernels += 1;  // the bounding box that sized the table
+    if (c->host_touched) {
+      // agents or the table changed outside the iterations: the next one rebuilds
+      if (c->grid_reuse) cudaMemsetAsync(&c->D.g->regrid, 1, 1, c->stream);
+      c->host_touched = false;
+    }
     if (c->graph_dirty) {
       drop_graphs(c);
       c->graph_dirty = false;
@@ -1225,6 +1242,7 @@ int bdm_secrete(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, double *u,
 
 int bdm_chemotaxis(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, const double *u, double weight,
                    int32_t flags) {
+  if (c) c->host_touched = true;  // the next step rebuilds a reused grid
   if (!c) return BDM_E_INVAL;
   const int64_t total = check_grid(c, g, u);
   if (total < 0) return (int)total;
@@ -1246,6 +1264,7 @@ int bdm_chemotaxis(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, const d
 // ---- epidemiology use case (§4.6.3, Algorithms 3-5) ----------------------
 int bdm_sir_step(bdm_ctx *c, int32_t sim, const bdm_sir_params *p, uint8_t *state, int64_t t0, int32_t n_steps,
                  int32_t flags) {
+  if (c) c->host_touched = true;  // the next step rebuilds a reused grid
   int rc = check_sim(c, sim);
   if (rc) return rc;
   if (!p || !state) return fail(c, BDM_E_INVAL, "NULL parameters or states");
@@ -1491,9 +1510,19 @@ int bdm_set_tuning(bdm_ctx *c, const bdm_tuning *t) {
   if (t->iter_batch < 0 || t->iter_batch > 64) return fail(c, BDM_E_INVAL, "iter_batch must be 0 to 64");
   if (t->test_flags != 0 && t->test_flags != (int32_t)TEST_SCAN_TIMEOUT)
     return fail(c, BDM_E_INVAL, "test_flags must be 0 or 1");
-  for (int k = 0; k < 2; ++k)
-    if (t->reserved[k]) return fail(c, BDM_E_INVAL, "reserved fields must be 0");
+  if (t->reserved) return fail(c, BDM_E_INVAL, "reserved fields must be 0");
+  if (t->grid_reuse != 0 && t->grid_reuse != 1) return fail(c, BDM_E_INVAL, "grid_reuse must be 0 or 1");
+  if (t->grid_reuse)
+    for (int s = 0; s < c->n_sims; ++s) {
+      const bdm_params &q = c->params[s];
+      if (q.detect_static || q.growth_rate > 0 || q.boundary == BDM_BOUNDARY_TOROIDAL ||
+          q.execution_context != BDM_EXEC_COPY)
+        return fail(c, BDM_E_INVAL, "grid reuse needs simulations without static detection, growth, a toroidal "
+                                    "boundary or the in-place context");
+    }
   cudaStreamSynchronize(c->stream);
+  c->grid_reuse = t->grid_reuse != 0;
+  c->host_touched = true;
   c->force_variant = t->force_variant;
   c->sort_override = t->sort_interval;
   c->sort_curve = t->sort_curve;
@@ -1533,6 +1562,7 @@ int bdm_get_tuning(bdm_ctx *c, bdm_tuning *t) {
   t->box_scale_pct = c->box_scale_pct;
   t->iter_batch = c->iter_batch;
   t->test_flags = (int32_t)c->test_flags;
+  t->grid_reuse = c->grid_reuse ? 1 : 0;
   return BDM_OK;
 }
 
@@ -1542,6 +1572,11 @@ int bdm_get_counters(bdm_ctx *c, bdm_counters *out) {
   out->graph_launches = c->cnt_graphs;
   out->kernels = c->cnt_kernels;
   out->graph_iterations = c->cnt_iters;
+  unsigned long long builds = 0;
+  cudaError_t e = cudaMemcpyAsync(&builds, &c->D.g->n_builds, sizeof(builds), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reading the build counter");
+  out->grid_builds = (int64_t)builds;
   return BDM_OK;
 }
 
@@ -1578,6 +1613,7 @@ void snap_free(bdm_ctx *c, Snapshot &S) {
 }
 
 int snap_copy(bdm_ctx *c, Snapshot &S, size_t M, bool save) {
+  if (!save) c->host_touched = true;  // restored agents: a reused grid no longer fits
   const Agents &A = c->D.a;
   auto cp = [&](void *snap, void *live, size_t bytes) {
     return save ? cudaMemcpyAsync(snap, live, bytes, cudaMemcpyDeviceToDevice, c->stream)
@@ -1631,6 +1667,7 @@ int timed_trial(bdm_ctx *c, int iters, float *ms) {
 }  // namespace
 
 int bdm_autotune(bdm_ctx *c, int32_t iterations, int32_t knobs, bdm_tuning *chosen) {
+  if (c) c->host_touched = true;  // the next step rebuilds a reused grid
   if (!c) return BDM_E_INVAL;
   if (iterations < 1) return fail(c, BDM_E_INVAL, "iterations must be >= 1");
   if (knobs & ~BDM_TUNE_ALL) return fail(c, BDM_E_INVAL, "unknown knob bits");

@@ -445,31 +445,38 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
 
 // S5: displacement, then the space boundary condition (§4.4.11) on the new
 // position.  Static agents keep their position and nnz.  kOne: a context
-// of one simulation (no per-cell simulation index to wait for).
-template <bool kOne>
+// of one simulation (no per-cell simulation index to wait for).  kTrack:
+// grid reuse: a moved agent's cell records are rewritten relative to the
+// box it is registered in (as the placement computes them), and an agent
+// that left its box by more than the build's skin on some axis makes the
+// next iteration rebuild the grid.
+template <bool kOne, bool kTrack>
 __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= C.g->n_cells) return;
   int sim = kOne ? 0 : C.c.sim[p];
   const SimConst &sc = C.sc[sim];
-  if (!C.ss[sim].valid) return;
+  const SimState &s = C.ss[sim];
+  if (!s.valid) return;
   int32_t slot = C.c.slot[p];
   if (C.c.stat[p]) {
     C.a.flags[slot] = FLAG_STATIC;
     return;
   }
   const uint8_t ghost = C.a.flags[slot] & FLAG_GHOST;  // read-only: keeps its position
+  const bool fp64 = sc.precision == BDM_PREC_FP64;
   bool moved = false, bad = false;
-  if (sc.precision == BDM_PREC_FP64) {
+  double np[3] = {0.0, 0.0, 0.0};  // the new position of a moved agent
+  if (fp64) {
     C.a.nnz[slot] = C.c.nnz[p];
     const double4_32a F = C.c.f64[p];
     double Dx, Dy, Dz;
     moved = disp64(sc, F.x, F.y, F.z, Dx, Dy, Dz, bad) && !ghost;
     if (moved) {
-      C.a.x[slot] = bound_apply(sc, __dadd_rn(C.a.x[slot], Dx));
-      C.a.y[slot] = bound_apply(sc, __dadd_rn(C.a.y[slot], Dy));
-      C.a.z[slot] = bound_apply(sc, __dadd_rn(C.a.z[slot], Dz));
+      np[0] = bound_apply(sc, __dadd_rn(C.a.x[slot], Dx));
+      np[1] = bound_apply(sc, __dadd_rn(C.a.y[slot], Dy));
+      np[2] = bound_apply(sc, __dadd_rn(C.a.z[slot], Dz));
     }
   } else {
     float4 F = C.c.f32[p];
@@ -488,10 +495,36 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
       }
       moved = (Dx != 0.f || Dy != 0.f || Dz != 0.f);
       if (moved) {
-        C.a.x[slot] = bound_apply(sc, __dadd_rn(C.a.x[slot], f2d(Dx)));
-        C.a.y[slot] = bound_apply(sc, __dadd_rn(C.a.y[slot], f2d(Dy)));
-        C.a.z[slot] = bound_apply(sc, __dadd_rn(C.a.z[slot], f2d(Dz)));
+        np[0] = bound_apply(sc, __dadd_rn(C.a.x[slot], f2d(Dx)));
+        np[1] = bound_apply(sc, __dadd_rn(C.a.y[slot], f2d(Dy)));
+        np[2] = bound_apply(sc, __dadd_rn(C.a.z[slot], f2d(Dz)));
       }
+    }
+  }
+  if (moved) {
+    C.a.x[slot] = np[0];
+    C.a.y[slot] = np[1];
+    C.a.z[slot] = np[2];
+    if (kTrack) {
+      const uint64_t pk = C.c.pkey[p];
+      const uint32_t c[3] = {(uint32_t)(pk & kCoordMask), (uint32_t)((pk >> kCoordBits) & kCoordMask),
+                             (uint32_t)((pk >> (2 * kCoordBits)) & kCoordMask)};
+      float h[3], l[3];
+      bool out = false;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        // offset inside the registered box, as the placement computes it
+        const double w = __fma_rn(neg_u32_to_double(c[a]), s.L, __dsub_rn(np[a], s.o[a]));
+        out = out || !(w >= -s.skin && w < __dadd_rn(s.L, s.skin));
+        split_ff(w, h[a], l[a]);
+      }
+      if (out) C.g->regrid = 1u;
+      const double r = half_of(C.a.d[slot]);
+      float rh, rl;
+      split_ff(r, rh, rl);
+      C.c.r0[p] = make_float4(h[0], h[1], h[2], rh);
+      if (fp64) C.c.r64[p] = make_double4_32a(np[0], np[1], np[2], r);
+      else C.c.r1[p] = make_float4(l[0], l[1], l[2], rl);
     }
   }
   if (bad) set_err(C.g, ERR_NONFINITE);
@@ -538,11 +571,15 @@ void launch_force(const DevCtx &C, cudaStream_t st, int variant, bool has_fp32, 
   if (has_fp64) launch_force64(C, st);
 }
 
-void launch_displace(const DevCtx &C, cudaStream_t st) {
-  if (C.n_sims == 1)
-    k_displace<true><<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
-  else
-    k_displace<false><<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
+void launch_displace(const DevCtx &C, cudaStream_t st, bool track) {
+  const unsigned int nb = blocks_for(C.total_slots, kAgentThreads);
+  if (C.n_sims == 1) {
+    if (track) k_displace<true, true><<<nb, kAgentThreads, 0, st>>>(C);
+    else k_displace<true, false><<<nb, kAgentThreads, 0, st>>>(C);
+  } else {
+    if (track) k_displace<false, true><<<nb, kAgentThreads, 0, st>>>(C);
+    else k_displace<false, false><<<nb, kAgentThreads, 0, st>>>(C);
+  }
 }
 
 }  // namespace bdm

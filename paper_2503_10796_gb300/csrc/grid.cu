@@ -69,9 +69,12 @@ __device__ void flush_box(const DevCtx &C, int sim, BoxAcc &acc, unsigned long l
   acc.reset();
 }
 
-__global__ void __launch_bounds__(kThreads) k_bbox(DevCtx C, int64_t chunk) {
+// step: the bounding box of a step iteration, which an iteration that
+// keeps the last build's grid (grid reuse) does not need.
+__global__ void __launch_bounds__(kThreads) k_bbox(DevCtx C, int64_t chunk, int step) {
   __shared__ unsigned long long sh[kThreads / 32][7];
   __shared__ int tile_sim[2];
+  if (step && C.g->reuse) return;
   BoxAcc acc;
   acc.reset();
   int cur = -1;  // simulation accumulated by the block
@@ -161,9 +164,25 @@ __global__ void __launch_bounds__(kThreads) k_bbox(DevCtx C, int64_t chunk) {
 // ---------------------------------------------------------------------------
 __device__ void split_pos(double v, float &h, float &l) { split_ff(v, h, l); }
 
-// One thread per simulation; thread 0 then lays out the cell ranges.
+// One thread per simulation; thread 0 then lays out the cell ranges.  An
+// iteration that keeps the last build's grid (grid reuse) only advances the
+// counters.
 __global__ void k_params(DevCtx C, int32_t step) {
   Globals *g = C.g;
+  if (step && g->reuse) {
+    for (int k = threadIdx.x; k < C.n_sims; k += blockDim.x) {
+      const int s = C.order[k];
+      if (s < 0) continue;
+      SimState &st = C.ss[s];
+      st.it = st.t;
+      st.t += 1;
+      st.updates += (unsigned long long)(st.n > 0 ? st.n : 0);
+      for (int a = 0; a < 3; ++a) { st.bmin[a] = ~0ull; st.bmax[a] = 0ull; }
+      st.dmax = 0ull;
+    }
+    if (threadIdx.x == 0) g->n_ovf = 0u;
+    return;
+  }
   for (int k = threadIdx.x; k < C.n_sims; k += blockDim.x) {
     int s = C.order[k];
     if (s < 0) continue;
@@ -242,6 +261,10 @@ __global__ void k_params(DevCtx C, int32_t step) {
     // below 2L; differences and squares add a few more ulps.
     st.marg = (float)(L * 0x1p-19) + 0x1p-30f;
     st.rmaxf = __double2float_ru(__dmul_rn(0.5, dmax));
+    // grid reuse: an agent that stays within `skin` of its box (per axis)
+    // still finds every partner in the 27-box stencil, as long as L - 2 skin
+    // >= the largest diameter (with room for rounding)
+    st.skin = __dsub_rn(__dmul_rn(0.5, __dsub_rn(L, dmax)), __dmul_rn(L, 0x1p-20));
     if (step) {
       for (int a = 0; a < 3; ++a) { st.prev_o[a] = st.o[a]; st.prev_dims[a] = st.dims[a]; }
       st.prev_L = L;
@@ -256,6 +279,7 @@ __global__ void k_params(DevCtx C, int32_t step) {
     g->stamp += 1u;
     g->tile_ticket = 0u;
     g->n_ovf = 0u;
+    if (step) g->n_builds += 1ull;
     int64_t cells = 0;
     for (int k = 0; k < C.n_sims; ++k) {
       const int s = C.order[k];
@@ -310,6 +334,7 @@ __device__ __forceinline__ void tab_mark_dirty(unsigned long long *e, uint32_t s
 // total_slots (no per-slot simulation index to wait for).
 template <bool kOne>
 __global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
+  if (step && C.g->reuse) return;  // the iteration keeps the last build's grid
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool in = slot < C.total_slots;
   const int64_t sl = in ? slot : C.total_slots - 1;
@@ -431,10 +456,11 @@ __device__ __forceinline__ void tile_publish(unsigned long long *w, uint32_t sta
 }
 
 template <bool kOrdered, bool kOne>
-__global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t *keys) {
+__global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t *keys, int step) {
   __shared__ uint32_t sh[33];
   __shared__ uint32_t s_tile, s_base;
   __shared__ int s_lo, s_hi;
+  if (step && C.g->reuse) return;  // every block: none waits for another
   if (threadIdx.x == 0) {
     s_tile = kOrdered ? atomicAdd(&C.g->tile_ticket, 1u) : blockIdx.x;
     s_base = 0u;
@@ -581,6 +607,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
 template <bool kOne>
 __global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, const uint64_t *keys, int fp64_records,
                                                    int zero_f32) {
+  // fp64_records is set only for query builds: a step iteration that keeps
+  // the last build's grid places nothing
+  if (!fp64_records && C.g->reuse) return;
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= C.total_slots) return;
   // every per-slot load first: they do not depend on one another
@@ -633,7 +662,39 @@ __global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, 
 // ---------------------------------------------------------------------------
 static inline unsigned int blocks_for(int64_t n, int t) { return (unsigned int)((n + t - 1) / t); }
 
-void launch_bbox(const DevCtx &C, cudaStream_t st) {
+// Grid reuse, at the start of a step iteration: keep the last build's grid
+// unless a rebuild is due (an agent left its skin, the host changed the
+// simulation, or this iteration re-sorts); an iteration that permutes the
+// storage into the cell order (sort == 2) makes the next one rebuild.
+__global__ void k_decide(DevCtx C, int sort) {
+  Globals *g = C.g;
+  bool ok = sort == 0 && g->regrid == 0u && g->n_builds > 0ull;
+  for (int k = 0; k < C.n_sims && ok; ++k) {
+    const int s = C.order[k];
+    if (s < 0) break;
+    const SimState &st = C.ss[s];
+    if (st.n > 0 && !(st.valid && st.skin > 0.0)) ok = false;
+  }
+  g->reuse = ok ? 1u : 0u;
+  g->regrid = sort == 2 ? 1u : 0u;
+}
+
+// Forces of the symmetric FP32 walks start from zero; the placement clears
+// them in iterations that build the grid, this kernel in those that keep it.
+__global__ void __launch_bounds__(kAgentThreads) k_zero_f32(DevCtx C) {
+  if (!C.g->reuse) return;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= C.g->n_cells) return;
+  if (C.sc[C.c.sim[p]].precision != BDM_PREC_FP64) C.c.f32[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+void launch_decide(const DevCtx &C, cudaStream_t st, int sort) { k_decide<<<1, 1, 0, st>>>(C, sort); }
+
+void launch_zero_f32(const DevCtx &C, cudaStream_t st) {
+  k_zero_f32<<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
+}
+
+void launch_bbox(const DevCtx &C, cudaStream_t st, int step) {
   int64_t nb = blocks_for(C.total_slots, kThreads);
   int64_t G = nb < 152 * 8 ? nb : 152 * 8;
   if (G < 1) G = 1;
@@ -641,7 +702,7 @@ void launch_bbox(const DevCtx &C, cudaStream_t st) {
   chunk = (chunk + kThreads - 1) / kThreads * kThreads;
   G = (C.total_slots + chunk - 1) / chunk;
   if (G < 1) G = 1;
-  k_bbox<<<(unsigned int)G, kThreads, 0, st>>>(C, chunk);
+  k_bbox<<<(unsigned int)G, kThreads, 0, st>>>(C, chunk, step);
 }
 
 void launch_params(const DevCtx &C, cudaStream_t st, int step) { k_params<<<1, 256, 0, st>>>(C, step); }
@@ -660,11 +721,11 @@ void launch_scan(const DevCtx &C, cudaStream_t st, int step, int ordered) {
   const uint64_t *keys = step ? C.a.pkey : C.qkey;
   const bool one = C.n_sims == 1;
   if (ordered) {
-    if (one) k_scan<true, true><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys);
-    else k_scan<true, false><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys);
+    if (one) k_scan<true, true><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys, step);
+    else k_scan<true, false><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys, step);
   } else {
-    if (one) k_scan<false, true><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys);
-    else k_scan<false, false><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys);
+    if (one) k_scan<false, true><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys, step);
+    else k_scan<false, false><<<(unsigned int)G, kScanThreads, 0, st>>>(C, keys, step);
   }
 }
 

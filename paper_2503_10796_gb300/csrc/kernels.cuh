@@ -6,7 +6,11 @@
 namespace bdm {
 
 // grid.cu
-void launch_bbox(const DevCtx &C, cudaStream_t st);
+void launch_bbox(const DevCtx &C, cudaStream_t st, int step = 0);
+// Grid reuse: the device decision at the start of a step iteration (sort:
+// its re-sort mode), and the force clearing of iterations that keep the grid.
+void launch_decide(const DevCtx &C, cudaStream_t st, int sort);
+void launch_zero_f32(const DevCtx &C, cudaStream_t st);
 void launch_params(const DevCtx &C, cudaStream_t st, int step);
 void launch_count(const DevCtx &C, cudaStream_t st, int step);
 // The scan needs tstat in the context: scan_tiles(total_slots) words,
@@ -42,7 +46,8 @@ void launch_force64(const DevCtx &C, cudaStream_t st);
 void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads, bool torus);
 // inplace.cu: S4 + S5 of the in-place execution context, one launch per box colour.
 void launch_inplace(const DevCtx &C, cudaStream_t st, int colours);
-void launch_displace(const DevCtx &C, cudaStream_t st);
+// track: grid reuse (cell records follow the moved agents; skin check).
+void launch_displace(const DevCtx &C, cudaStream_t st, bool track = false);
 
 // diffusion.cu (soma-clustering slice)
 typedef bdm_diffusion_grid DiffGrid;
