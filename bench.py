@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--static-leg", type=int, default=-1,
                     help="static detection on/off leg; -1: on for the clustered 8M workload")
     ap.add_argument("--static-steps", type=int, default=100)
+    ap.add_argument("--reuse-leg", type=int, default=-1,
+                    help="incremental-grid leg; -1: on for the clustered 8M workload")
     ap.add_argument("--iter-batch", type=int, default=-1, help="iterations per graph; -1: autotune")
     ap.add_argument("--box-scale", type=int, default=-1, help="box length in %% of the largest diameter; -1: autotune")
     ap.add_argument("--no-autotune", action="store_true",
@@ -367,6 +369,39 @@ def static_leg(args, local: int, tune_knobs: int, fixed: dict):
             "speedup": out["on"]["value"] / out["off"]["value"]}
 
 
+def reuse_leg(args, local: int, tuning: dict):
+    """The incremental grid (tuning grid_reuse) on the same workload and
+    settings as the timed run: iterations keep the last build's grid while
+    every agent stays within the skin of its box.  Times as many iterations
+    and reports the grid builds among them."""
+    import torch
+    from paper_2503_10796_gb300 import binding
+    pops, _ = make_workload(args.workload, args.precision, 0)
+    p = pops[0]
+    stream = torch.cuda.Stream(device=local)
+    ctx = binding.Context([binding.make_params(p.params)], p.n + 1024, device=local, stream=stream.cuda_stream)
+    ctx.set_agents(0, p.xyz, p.diameter)
+    ctx.step(args.settle)
+    t = ctx.get_tuning()
+    t.update(tuning)
+    t.update(grid_reuse=1, box_scale_pct=max(int(t.get("box_scale_pct") or 100), 125))
+    ctx.set_tuning(**t)
+    ctx.step(args.warmup)
+    ctx.sync()
+    b0 = ctx.counters()["grid_builds"]
+    ms = timed_steps(ctx, stream, args.steps)
+    builds = ctx.counters()["grid_builds"] - b0
+    ctx.close()
+    return {"what": "incremental grid: the last build kept while every agent stays within (L - largest "
+                    "diameter) / 2 of its box; rebuilt on re-sorts and when an agent leaves its skin",
+            "value": p.n * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "timed_iterations": args.steps, "grid_builds": builds, "tuning": ctx_tuning_dict(t)}
+
+
+def ctx_tuning_dict(t: dict) -> dict:
+    return {k: int(v) for k, v in t.items()}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -536,6 +571,11 @@ def main():
     want_leg = args.static_leg if args.static_leg >= 0 else int(args.workload == "clustered_8M" and world == 1)
     if want_leg and len(pops) == 1:
         leg = static_leg(args, local, knobs, {k: v for k, v in fixed.items() if k != "force_variant"})
+    rleg = None
+    want_reuse = args.reuse_leg if args.reuse_leg >= 0 else int(args.workload == "clustered_8M" and world == 1)
+    if want_reuse and len(pops) == 1 and prec == 1:
+        rleg = reuse_leg(args, local, tuning or {})
+        rleg["speedup_vs_rebuild"] = rleg["value"] / value
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -562,6 +602,7 @@ def main():
             "gpu_launches": c1["kernels"] - c0["kernels"],
             "graph_launches": c1["graph_launches"] - c0["graph_launches"],
             "static_skip_leg": leg,
+            "incremental_grid_leg": rleg,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
