@@ -85,6 +85,7 @@ struct SimState {
   unsigned long long n_static, n_moved;
   unsigned long long updates;  // agent-updates stepped since the agents were set
   double skin;                // grid reuse: how far an agent may leave its box before the grid is rebuilt
+  float skin_lo, skin_hi;     // the same bounds on a box-relative offset in FP32, rounded inwards
 };
 
 // Global counters of a context.

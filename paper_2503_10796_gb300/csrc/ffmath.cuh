@@ -161,6 +161,14 @@ BDM_HD void two_prod(float a, float b, float &p, float &e) {
   e = f_fma(a, b, -p);
 }
 
+// float-float (h, l) plus a float d, renormalized: the error of the result
+// is one rounding of the low part (about 2^-48 of the value).
+BDM_HD void ff_add_float(float h, float l, float d, float &rh, float &rl) {
+  float s, e;
+  two_sum(h, d, s, e);
+  two_sum(s, f_add(l, e), rh, rl);
+}
+
 // 2^k as a float for -126 <= k <= 127.
 BDM_HD float pow2f(int k) { return float_of((unsigned int)(k + 127) << 23); }
 

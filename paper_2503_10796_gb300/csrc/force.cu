@@ -446,10 +446,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_force32s(DevCtx C) {
 // S5: displacement, then the space boundary condition (§4.4.11) on the new
 // position.  Static agents keep their position and nnz.  kOne: a context
 // of one simulation (no per-cell simulation index to wait for).  kTrack:
-// grid reuse: a moved agent's cell records are rewritten relative to the
-// box it is registered in (as the placement computes them), and an agent
-// that left its box by more than the build's skin on some axis makes the
-// next iteration rebuild the grid.
+// grid reuse: a moved agent's cell records follow it, relative to the box
+// it is registered in (FP32 path: the float-float offset plus the FP32
+// displacement; FP64 path and wall-clamped moves: recomputed as the
+// placement computes them), and an agent that left its box by more than the
+// build's skin on some axis makes the next iteration rebuild the grid.
 template <bool kOne, bool kTrack>
 __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
@@ -468,6 +469,8 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
   const bool fp64 = sc.precision == BDM_PREC_FP64;
   bool moved = false, bad = false;
   double np[3] = {0.0, 0.0, 0.0};  // the new position of a moved agent
+  float df[3] = {0.f, 0.f, 0.f};   // FP32 path: its displacement
+  bool clamped = false;            // a wall cut the displacement short
   if (fp64) {
     C.a.nnz[slot] = C.c.nnz[p];
     const double4_32a F = C.c.f64[p];
@@ -495,9 +498,16 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
       }
       moved = (Dx != 0.f || Dy != 0.f || Dz != 0.f);
       if (moved) {
-        np[0] = bound_apply(sc, __dadd_rn(C.a.x[slot], f2d(Dx)));
-        np[1] = bound_apply(sc, __dadd_rn(C.a.y[slot], f2d(Dy)));
-        np[2] = bound_apply(sc, __dadd_rn(C.a.z[slot], f2d(Dz)));
+        const double u[3] = {__dadd_rn(C.a.x[slot], f2d(Dx)), __dadd_rn(C.a.y[slot], f2d(Dy)),
+                             __dadd_rn(C.a.z[slot], f2d(Dz))};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          np[a] = bound_apply(sc, u[a]);
+          clamped = clamped || np[a] != u[a];
+        }
+        df[0] = Dx;
+        df[1] = Dy;
+        df[2] = Dz;
       }
     }
   }
@@ -505,7 +515,24 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
     C.a.x[slot] = np[0];
     C.a.y[slot] = np[1];
     C.a.z[slot] = np[2];
-    if (kTrack) {
+    if (kTrack && !fp64 && !clamped) {
+      // FP32 path: the float-float offset plus the FP32 displacement (no
+      // FP64 operation: the FP64 pipe is the placement's limit); the
+      // radius parts stay
+      const float4 a0 = C.c.r0[p], a1 = C.c.r1[p];
+      float h[3], l[3];
+      ff_add_float(a0.x, a1.x, df[0], h[0], l[0]);
+      ff_add_float(a0.y, a1.y, df[1], h[1], l[1]);
+      ff_add_float(a0.z, a1.z, df[2], h[2], l[2]);
+      bool out = false;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) out = out || !(h[a] >= s.skin_lo && h[a] < s.skin_hi);
+      if (out) C.g->regrid = 1u;
+      C.c.r0[p] = make_float4(h[0], h[1], h[2], a0.w);
+      C.c.r1[p] = make_float4(l[0], l[1], l[2], a1.w);
+    } else if (kTrack) {
+      // FP64 path, or a displacement a wall cut short: the offset inside the
+      // registered box as the placement computes it
       const uint64_t pk = C.c.pkey[p];
       const uint32_t c[3] = {(uint32_t)(pk & kCoordMask), (uint32_t)((pk >> kCoordBits) & kCoordMask),
                              (uint32_t)((pk >> (2 * kCoordBits)) & kCoordMask)};
@@ -513,7 +540,6 @@ __global__ void __launch_bounds__(kAgentThreads) k_displace(DevCtx C) {
       bool out = false;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        // offset inside the registered box, as the placement computes it
         const double w = __fma_rn(neg_u32_to_double(c[a]), s.L, __dsub_rn(np[a], s.o[a]));
         out = out || !(w >= -s.skin && w < __dadd_rn(s.L, s.skin));
         split_ff(w, h[a], l[a]);

@@ -265,6 +265,10 @@ __global__ void k_params(DevCtx C, int32_t step) {
     // still finds every partner in the 27-box stencil, as long as L - 2 skin
     // >= the largest diameter (with room for rounding)
     st.skin = __dsub_rn(__dmul_rn(0.5, __dsub_rn(L, dmax)), __dmul_rn(L, 0x1p-20));
+    // bounds of the FP32 check on the leading part of an offset (its low
+    // part is below 2^-23 of it: an inward margin of 2^-21 L covers it)
+    st.skin_lo = -__double2float_rd(__dsub_rn(st.skin, __dmul_rn(L, 0x1p-21)));
+    st.skin_hi = __double2float_rd(__dsub_rn(__dadd_rn(L, st.skin), __dmul_rn(L, 0x1p-21)));
     if (step) {
       for (int a = 0; a < 3; ++a) { st.prev_o[a] = st.o[a]; st.prev_dims[a] = st.dims[a]; }
       st.prev_L = L;

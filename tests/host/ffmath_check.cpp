@@ -118,6 +118,35 @@ static void check_eft(std::mt19937_64 &rng) {
   report("error_free_transformations", cases, failures);
 }
 
+// ff_add_float: a float-float box-relative offset moved by FP32
+// displacements stays within a few ulps of its low part of the exact sum
+// (long double reference), over 100 updates in a row.
+static void check_ff_add(std::mt19937_64 &rng) {
+  std::uniform_real_distribution<double> U(0.0, 1.0);
+  long cases = 0, failures = 0;
+  for (int k = 0; k < 20000; ++k) {
+    const double L = 8.0 + 10.0 * U(rng);
+    float h, l;
+    split_ff((U(rng) * 1.4 - 0.2) * L, h, l);
+    long double exact = (long double)h + (long double)l;
+    for (int t = 0; t < 100; ++t) {
+      const float d = (float)((U(rng) - 0.5) * 0.2);
+      float rh, rl;
+      ff_add_float(h, l, d, rh, rl);
+      exact += (long double)d;
+      h = rh;
+      l = rl;
+      ++cases;
+      const long double err = ((long double)h + (long double)l) - exact;
+      const double tol = std::ldexp(L, -44);
+      if (!(std::fabs((double)err) <= tol)) ++failures;
+      // the leading part is the float nearest the value (to one ulp)
+      if (std::fabs((double)l) > std::ldexp(std::fabs((double)h) + 1e-30, -23) + std::ldexp(L, -60)) ++failures;
+    }
+  }
+  report("ff_add_float", cases, failures);
+}
+
 int main() {
   std::mt19937_64 rng(20250314);
   check_box_coord(rng, 2000, "box_coord_narrow");
@@ -126,5 +155,6 @@ int main() {
   check_split(rng);
   check_bits(rng);
   check_eft(rng);
+  check_ff_add(rng);
   return failures_total ? 1 : 0;
 }
