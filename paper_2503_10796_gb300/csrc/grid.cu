@@ -337,9 +337,7 @@ __device__ __forceinline__ void tab_mark_dirty(unsigned long long *e, uint32_t s
 // kOne: the context holds one simulation, which owns every slot below
 // total_slots (no per-slot simulation index to wait for).
 template <bool kOne>
-__global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
-  if (step && C.g->reuse) return;  // the iteration keeps the last build's grid
-  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void count_slot(const DevCtx &C, int step, int64_t slot) {
   const bool in = slot < C.total_slots;
   const int64_t sl = in ? slot : C.total_slots - 1;
   const int sim = kOne ? 0 : C.a.sim[sl];
@@ -394,6 +392,16 @@ __global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
       tab_mark_dirty(&C.tab.e[sc.table_base + linear_box(s, px, py, pz)], stamp);
   }
   C.a.rank[slot] = base + (uint32_t)(lane - start);
+}
+
+// A capped grid that walks the slots in tiles of a block (consecutive lanes
+// keep consecutive slots for the run aggregation), so that an iteration
+// that keeps the last build's grid retires few blocks.
+template <bool kOne>
+__global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
+  if (step && C.g->reuse) return;  // the iteration keeps the last build's grid
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < C.total_slots; b += (int64_t)gridDim.x * blockDim.x)
+    count_slot<kOne>(C, step, b + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -609,12 +617,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
 // zero_f32: clear the FP32 force of every placed FP32-path agent (the
 // symmetric force walk adds into it).
 template <bool kOne>
-__global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, const uint64_t *keys, int fp64_records,
-                                                   int zero_f32) {
-  // fp64_records is set only for query builds: a step iteration that keeps
-  // the last build's grid places nothing
-  if (!fp64_records && C.g->reuse) return;
-  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void place_slot(const DevCtx &C, const Cells &cells, const uint64_t *keys,
+                                           int fp64_records, int zero_f32, int64_t slot) {
   if (slot >= C.total_slots) return;
   // every per-slot load first: they do not depend on one another
   const int sim = kOne ? 0 : C.a.sim[slot];
@@ -661,6 +665,16 @@ __global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, 
   }
 }
 
+template <bool kOne>
+__global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, const uint64_t *keys, int fp64_records,
+                                                   int zero_f32) {
+  // fp64_records is set only for query builds: a step iteration that keeps
+  // the last build's grid places nothing
+  if (!fp64_records && C.g->reuse) return;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < C.total_slots; b += (int64_t)gridDim.x * blockDim.x)
+    place_slot<kOne>(C, cells, keys, fp64_records, zero_f32, b + threadIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
@@ -687,15 +701,22 @@ __global__ void k_decide(DevCtx C, int sort) {
 // them in iterations that build the grid, this kernel in those that keep it.
 __global__ void __launch_bounds__(kAgentThreads) k_zero_f32(DevCtx C) {
   if (!C.g->reuse) return;
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= C.g->n_cells) return;
-  if (C.sc[C.c.sim[p]].precision != BDM_PREC_FP64) C.c.f32[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t n = C.g->n_cells;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    if (C.sc[C.c.sim[p]].precision != BDM_PREC_FP64) C.c.f32[p] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 void launch_decide(const DevCtx &C, cudaStream_t st, int sort) { k_decide<<<1, 1, 0, st>>>(C, sort); }
 
+// Blocks of the looping per-slot kernels: at most 16 per SM (full occupancy
+// of 128-thread blocks).
+static inline unsigned int capped_blocks(int64_t n) {
+  const unsigned int nb = blocks_for(n, kAgentThreads);
+  return nb < 152u * 16u ? nb : 152u * 16u;
+}
+
 void launch_zero_f32(const DevCtx &C, cudaStream_t st) {
-  k_zero_f32<<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C);
+  k_zero_f32<<<capped_blocks(C.total_slots), kAgentThreads, 0, st>>>(C);
 }
 
 void launch_bbox(const DevCtx &C, cudaStream_t st, int step) {
@@ -713,9 +734,9 @@ void launch_params(const DevCtx &C, cudaStream_t st, int step) { k_params<<<1, 2
 
 void launch_count(const DevCtx &C, cudaStream_t st, int step) {
   if (C.n_sims == 1)
-    k_count<true><<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C, step);
+    k_count<true><<<capped_blocks(C.total_slots), kAgentThreads, 0, st>>>(C, step);
   else
-    k_count<false><<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C, step);
+    k_count<false><<<capped_blocks(C.total_slots), kAgentThreads, 0, st>>>(C, step);
 }
 
 int64_t scan_tiles(int64_t total_slots) { return (total_slots + kScanTile - 1) / kScanTile; }
@@ -734,7 +755,7 @@ void launch_scan(const DevCtx &C, cudaStream_t st, int step, int ordered) {
 }
 
 void launch_place(const DevCtx &C, cudaStream_t st, int step, int zero_f32) {
-  const unsigned int nb = blocks_for(C.total_slots, kAgentThreads);
+  const unsigned int nb = capped_blocks(C.total_slots);
   if (C.n_sims == 1)
     k_place<true><<<nb, kAgentThreads, 0, st>>>(C, step ? C.c : C.q, step ? C.a.pkey : C.qkey, step ? 0 : 1,
                                                  step ? zero_f32 : 0);
