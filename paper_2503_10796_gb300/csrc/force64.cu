@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kRowAgents = 32;
 constexpr int kRowThreads = kRowAgents * 9;
-constexpr int kRowCap = 8;
+constexpr int kRowCap = 4;
 constexpr int kSortCap = 24;
 
 struct Contrib {

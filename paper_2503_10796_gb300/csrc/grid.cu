@@ -337,7 +337,9 @@ __device__ __forceinline__ void tab_mark_dirty(unsigned long long *e, uint32_t s
 // kOne: the context holds one simulation, which owns every slot below
 // total_slots (no per-slot simulation index to wait for).
 template <bool kOne>
-__device__ __forceinline__ void count_slot(const DevCtx &C, int step, int64_t slot) {
+__global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
+  if (step && C.g->reuse) return;  // the iteration keeps the last build's grid
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool in = slot < C.total_slots;
   const int64_t sl = in ? slot : C.total_slots - 1;
   const int sim = kOne ? 0 : C.a.sim[sl];
@@ -394,14 +396,6 @@ __device__ __forceinline__ void count_slot(const DevCtx &C, int step, int64_t sl
   C.a.rank[slot] = base + (uint32_t)(lane - start);
 }
 
-// The slots in tiles of a block (consecutive lanes keep consecutive slots
-// for the run aggregation); launched as a full grid, one tile per block.
-template <bool kOne>
-__global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
-  if (step && C.g->reuse) return;  // the iteration keeps the last build's grid
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < C.total_slots; b += (int64_t)gridDim.x * blockDim.x)
-    count_slot<kOne>(C, step, b + threadIdx.x);
-}
 
 // ---------------------------------------------------------------------------
 // S2: every box gets a contiguous range of cells, claimed by its leader
@@ -616,8 +610,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(DevCtx C, const uint64_t 
 // zero_f32: clear the FP32 force of every placed FP32-path agent (the
 // symmetric force walk adds into it).
 template <bool kOne>
-__device__ __forceinline__ void place_slot(const DevCtx &C, const Cells &cells, const uint64_t *keys,
-                                           int fp64_records, int zero_f32, int64_t slot) {
+__global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, const uint64_t *keys, int fp64_records,
+                                                   int zero_f32) {
+  // fp64_records is set only for query builds: a step iteration that keeps
+  // the last build's grid places nothing
+  if (!fp64_records && C.g->reuse) return;
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= C.total_slots) return;
   // every per-slot load first: they do not depend on one another
   const int sim = kOne ? 0 : C.a.sim[slot];
@@ -664,15 +662,6 @@ __device__ __forceinline__ void place_slot(const DevCtx &C, const Cells &cells, 
   }
 }
 
-template <bool kOne>
-__global__ void __launch_bounds__(kAgentThreads) k_place(DevCtx C, Cells cells, const uint64_t *keys, int fp64_records,
-                                                   int zero_f32) {
-  // fp64_records is set only for query builds: a step iteration that keeps
-  // the last build's grid places nothing
-  if (!fp64_records && C.g->reuse) return;
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < C.total_slots; b += (int64_t)gridDim.x * blockDim.x)
-    place_slot<kOne>(C, cells, keys, fp64_records, zero_f32, b + threadIdx.x);
-}
 
 // ---------------------------------------------------------------------------
 // Host launchers.
@@ -732,8 +721,8 @@ void launch_bbox(const DevCtx &C, cudaStream_t st, int step) {
 void launch_params(const DevCtx &C, cudaStream_t st, int step) { k_params<<<1, 256, 0, st>>>(C, step); }
 
 void launch_count(const DevCtx &C, cudaStream_t st, int step) {
-  // a full grid (one slot per thread): a capped grid ran the count 0.14 ->
-  // 0.17 ms at 8.4M agents
+  // a full grid, one slot per thread (a capped grid looping over tiles ran
+  // the count 0.14 -> 0.17 ms at 8.4M agents)
   if (C.n_sims == 1)
     k_count<true><<<blocks_for(C.total_slots, kAgentThreads), kAgentThreads, 0, st>>>(C, step);
   else
