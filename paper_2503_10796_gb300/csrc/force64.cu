@@ -43,7 +43,7 @@ struct Contrib {
 
 __device__ __forceinline__ uint32_t partner_id(const DevCtx &C, int64_t j) { return (uint32_t)C.a.id[C.c.slot[j]]; }
 
-__global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
+__global__ void __launch_bounds__(kRowThreads, 3) k_force64r(DevCtx C) {
   __shared__ uint32_t rq[kRowCap][kRowThreads];
   __shared__ uint8_t skip[kRowAgents];
   __shared__ uint32_t ncon[kRowAgents];
@@ -84,13 +84,10 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
   const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
   const int dz = r / 3 - 1, dy = r % 3 - 1;
   const bool walk = !skip[a] && dz >= t.zlo && dz <= t.zhi && dy >= t.ylo && dy <= t.yhi;
-  double4_32a o = {};
-  float4 o0 = {};
-  float sy = 0.f, sz = 0.f;
   const float Lh = s.Lh, marg = s.marg;
   // the FP32 filter: box-relative leading parts with a margin above their
   // error, so every pair that overlaps in FP64 passes
-  auto passes = [&](int64_t j, float sx) {
+  auto passes = [&](const float4 &o0, int64_t j, float sx, float sy, float sz) {
     const float4 q = C.c.r0[j];
     const float ddx = __fsub_rn(sx, q.x), ddy = __fsub_rn(sy, q.y), ddz = __fsub_rn(sz, q.z);
     const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
@@ -98,10 +95,8 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
     return s2 < __fmul_rn(Rm, Rm);
   };
   if (walk) {
-    o = C.c.r64[p];
-    o0 = C.c.r0[p];
-    sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh));
-    sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
+    const float4 o0 = C.c.r0[p];
+    const float sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh)), sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
     for (int dx = t.xlo; dx <= t.xhi; ++dx) {
       const unsigned long long e = t.e[t.box(dx, dy, dz)];
       const uint32_t cnt = ent_live(e, stamp);
@@ -109,7 +104,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
       const float sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
       for (uint32_t m = 0; m < cnt; ++m) {
         const int64_t j = j0 + m;
-        if (j == p || !passes(j, sx)) continue;
+        if (j == p || !passes(o0, j, sx, sy, sz)) continue;
         if (n < (uint32_t)kRowCap) rq[n][threadIdx.x] = (uint32_t)j;
         ++n;
       }
@@ -122,8 +117,12 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
   const bool crowded = nfil[a] > (uint32_t)kSortCap;
   uint32_t mine = crowded ? 0u : n;
   if (!crowded && n > (uint32_t)kRowCap) {
-    // crowded row: evaluate it in place
+    // crowded row: evaluate it in place (the records are loaded again, so
+    // that nothing of the walk stays live across the barrier)
     mine = 0;
+    const double4_32a o = C.c.r64[p];
+    const float4 o0 = C.c.r0[p];
+    const float sy = __fsub_rn(o0.y, __fmul_rn((float)dy, Lh)), sz = __fsub_rn(o0.z, __fmul_rn((float)dz, Lh));
     for (int dx = t.xlo; dx <= t.xhi; ++dx) {
       const unsigned long long e = t.e[t.box(dx, dy, dz)];
       const uint32_t cnt = ent_live(e, stamp);
@@ -131,7 +130,7 @@ __global__ void __launch_bounds__(kRowThreads) k_force64r(DevCtx C) {
       const float sx = __fsub_rn(o0.x, __fmul_rn((float)dx, Lh));
       for (uint32_t m = 0; m < cnt; ++m) {
         const int64_t j = j0 + m;
-        if (j == p || !passes(j, sx)) continue;
+        if (j == p || !passes(o0, j, sx, sy, sz)) continue;
         double gx, gy, gz;
         bool nz, dir;
         if (pair64(sc, o, C.c.r64[j], sc.k, sc.gamma, gx, gy, gz, nz, dir)) append(a, j, gx, gy, gz, nz, dir);
