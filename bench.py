@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--static-leg", type=int, default=-1,
                     help="static detection on/off leg; -1: on for the clustered 8M workload")
     ap.add_argument("--static-steps", type=int, default=100)
+    ap.add_argument("--execution-context", type=int, default=0, choices=(0, 1),
+                    help="1: the in-place execution context (FP64 path, no static detection)")
     ap.add_argument("--reuse-leg", type=int, default=-1,
                     help="incremental-grid leg; -1: on for the clustered 8M workload")
     ap.add_argument("--iter-batch", type=int, default=-1, help="iterations per graph; -1: autotune")
@@ -94,7 +96,7 @@ def parse():
     return args
 
 
-def make_workload(name: str, precision: int, static: int, build: bool = True):
+def make_workload(name: str, precision: int, static: int, build: bool = True, exec_ctx: int = 0):
     """(populations, description); build=False describes the 200M-agent
     workload without generating it (populations None)."""
     from paper_2503_10796_gb300 import workloads as W
@@ -126,6 +128,9 @@ def make_workload(name: str, precision: int, static: int, build: bool = True):
         raise SystemExit(f"unknown workload {name}")
     for p in pops or []:
         p.params.detect_static = static
+        p.params.execution_context = exec_ctx
+    if exec_ctx:
+        desc.update(execution_context="in-place")
     slots = sum(max(p.n, p.params.capacity) for p in pops) if pops is not None else desc["agents"]
     desc.update(static_skip=bool(static),
                 l2="inputs larger than L2 (no flush needed)" if slots > 1_000_000 else "working set inside L2")
@@ -216,8 +221,9 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(name: str):
-    """The oracle, as it stands, on a bounded sample of the workload."""
+def cpu_baseline(name: str, exec_ctx: int = 0):
+    """The oracle, as it stands, on a bounded sample of the workload (in the
+    execution context of the GPU run)."""
     import oracle
     from paper_2503_10796_gb300 import workloads as W
     oracle.build()
@@ -234,7 +240,7 @@ def cpu_baseline(name: str):
         pops = W.batched_sweep()
         pop = pops[int(np.argsort([p.n for p in pops])[len(pops) // 2])]
         iters, sample = 5, f"5 iterations of the median simulation ({pop.n} agents)"
-    s = oracle.Sim(pop.xyz, pop.diameter, pop.params)
+    s = oracle.Sim(pop.xyz, pop.diameter, pop.params, execution_context=exec_ctx)
     t0 = time.perf_counter()
     s.step(iters)
     dt = time.perf_counter() - t0
@@ -276,7 +282,7 @@ def reference_arm(args):
         pops = W.batched_sweep()
         pop = pops[int(np.argsort([p.n for p in pops])[len(pops) // 2])]
         sample = f"each step: 1 iteration of the median simulation ({pop.n} agents)"
-    s = oracle.Sim(pop.xyz, pop.diameter, pop.params)
+    s = oracle.Sim(pop.xyz, pop.diameter, pop.params, execution_context=args.execution_context)
     for _ in range(args.warmup):
         s.step(1)
     t0 = time.perf_counter()
@@ -284,7 +290,8 @@ def reference_arm(args):
         s.step(1)
     dt = time.perf_counter() - t0
     v = pop.n * args.steps / dt
-    _, desc = make_workload(args.workload, args.precision, args.static, build=False)
+    _, desc = make_workload(args.workload, args.precision, args.static, build=False,
+                            exec_ctx=args.execution_context)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
@@ -423,7 +430,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    pops, desc = make_workload(args.workload, args.precision, args.static)
+    pops, desc = make_workload(args.workload, args.precision, args.static, exec_ctx=args.execution_context)
     if world > 1 and args.workload == "batched_sweep_256":
         # independent simulations: shard them, no exchange on the data path
         from paper_2503_10796_gb300 import sharding
@@ -569,6 +576,7 @@ def main():
 
     leg = None
     want_leg = args.static_leg if args.static_leg >= 0 else int(args.workload == "clustered_8M" and world == 1)
+    want_leg = want_leg and not args.execution_context  # static detection runs in the copy context only
     if want_leg and len(pops) == 1:
         leg = static_leg(args, local, knobs, {k: v for k, v in fixed.items() if k != "force_variant"})
     rleg = None
@@ -579,7 +587,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload)
+        cpu = cpu_baseline(args.workload, args.execution_context)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
