@@ -14,9 +14,10 @@
 //
 // An agent's neighbours are the agents of its stencil in the grid built at
 // the iteration's start, at their current positions (storage arrays, which
-// earlier colours and earlier agents of the box have updated).  Its pair
-// forces are evaluated by the definition (pair64) and added in ascending
-// partner ID; the displacement (disp64) and the boundary condition are
+// earlier colours and earlier agents of the box have updated).  Candidates
+// pass an FP32 filter on the start records first, widened by twice the
+// clamp (each agent moves once, by at most the clamp).  Pair forces are
+// evaluated by the definition (pair64) and added in ascending partner ID; the displacement (disp64) and the boundary condition are
 // applied at once.  Ghost agents stay in place.  The result equals the
 // oracle's in-place iteration bit for bit.
 #include "pair.cuh"
@@ -71,6 +72,21 @@ __global__ void __launch_bounds__(kInThreads) k_inplace(DevCtx C, int colour) {
   if (p != b0 || box_colour(sc, s, cx, cy, cz) != colour) return;  // one thread per box of this colour
   const int nx = t.xhi - t.xlo + 1, ny = t.yhi - t.ylo + 1, nzb = t.zhi - t.zlo + 1;
   const int nbox = nx * ny * nzb;
+  // FP32 filter on the records of the iteration's start (box-relative
+  // leading parts): an agent moves once per iteration, by at most the
+  // clamp, so a pair that overlaps at the current positions lies within
+  // r_i + r_j + 2 max_displacement at the start (plus the records' margin)
+  const float Lh = s.Lh;
+  const float grow = __fadd_rn(__fmul_rn(2.f, __double2float_ru(sc.max_disp)), s.marg);
+  auto may_overlap = [&](const float4 &a, int64_t j, int dx, int dy, int dz) {
+    const float4 b = C.c.r0[j];
+    const float ddx = __fsub_rn(__fsub_rn(a.x, __fmul_rn((float)dx, Lh)), b.x);
+    const float ddy = __fsub_rn(__fsub_rn(a.y, __fmul_rn((float)dy, Lh)), b.y);
+    const float ddz = __fsub_rn(__fsub_rn(a.z, __fmul_rn((float)dz, Lh)), b.z);
+    const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+    const float R = __fadd_rn(__fadd_rn(a.w, b.w), grow);
+    return s2 < __fmul_rn(R, R);
+  };
   int64_t last_id = -1;
   for (uint32_t done = 0; done < nb; ++done) {
     // the box's agent with the next ID
@@ -87,6 +103,7 @@ __global__ void __launch_bounds__(kInThreads) k_inplace(DevCtx C, int colour) {
     last_id = (int64_t)qid;
     const int32_t sq = C.c.slot[q];
     const double4_32a o = current(C, q);
+    const float4 a0 = C.c.r0[q];
     // its overlapping partners, kept sorted by ID while they fit
     Contrib con[kInCap];
     uint32_t n = 0;
@@ -97,7 +114,7 @@ __global__ void __launch_bounds__(kInThreads) k_inplace(DevCtx C, int colour) {
       const int64_t j0 = ent_start(e);
       for (uint32_t m = 0; m < cnt; ++m) {
         const int64_t j = j0 + m;
-        if (j == q) continue;
+        if (j == q || !may_overlap(a0, j, dx, dy, dz)) continue;
         double gx, gy, gz;
         bool nz, dir;
         if (!pair64(sc, o, current(C, j), sc.k, sc.gamma, gx, gy, gz, nz, dir)) continue;
@@ -141,7 +158,7 @@ __global__ void __launch_bounds__(kInThreads) k_inplace(DevCtx C, int colour) {
             const int64_t j = j0 + m;
             if (j == q) continue;
             const uint32_t id = agent_id(C, j);
-            if ((int64_t)id <= prev || id >= best) continue;
+            if ((int64_t)id <= prev || id >= best || !may_overlap(a0, j, dx, dy, dz)) continue;
             double gx, gy, gz;
             bool nz, dir;
             if (pair64(sc, o, current(C, j), sc.k, sc.gamma, gx, gy, gz, nz, dir)) {
