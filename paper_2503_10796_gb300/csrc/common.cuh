@@ -101,6 +101,9 @@ struct Globals {
   uint32_t reuse;             // grid reuse: this iteration keeps the last build's grid
   uint32_t pad;
   unsigned long long n_builds; // grid builds of step iterations
+  uint32_t ip_count[27];      // in-place context: boxes per colour of this iteration
+  uint32_t ip_cursor[27];     //   fill cursors of the colour lists
+  uint32_t ip_off[28];        //   start of each colour's list (in DevCtx::ovf)
 };
 
 // Test hooks of Globals::test_flags.  TEST_SCAN_TIMEOUT: the ordered scan's
@@ -165,7 +168,8 @@ struct DevCtx {
   int32_t *order;             // simulations in slot-region order (-1 padded)
   unsigned long long *tstat;  // per scan tile: stamp << 34 | state << 32 | sum (look-back)
   uint64_t *qkey;             // per slot: packed box of the last query build (queries only)
-  int32_t *ovf;               // FP64 path: cells with more overlapping partners than the row kernel keeps
+  int32_t *ovf;               // FP64 path: cells with more overlapping partners than the row kernel keeps;
+                              // in-place context: the box leaders of every colour
   int32_t n_sims;
   int64_t total_slots;
 };

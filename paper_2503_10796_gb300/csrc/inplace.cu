@@ -8,25 +8,38 @@
 // odd number of boxes the last box has a third colour (it touches box 0
 // across the seam); colours rank x + k_x (y + k_y z).  Two boxes of one
 // colour are never in each other's 27-box stencil, and an agent writes only
-// its own position, so all boxes of a colour run at once: one launch per
-// colour, one thread per box (its first cell), the box's agents in
-// ascending ID one after the other.
+// its own position, so all boxes of a colour run at once.
 //
-// An agent's neighbours are the agents of its stencil in the grid built at
-// the iteration's start, at their current positions (storage arrays, which
-// earlier colours and earlier agents of the box have updated).  Candidates
-// pass an FP32 filter on the start records first, widened by twice the
-// clamp (each agent moves once, by at most the clamp).  Pair forces are
-// evaluated by the definition (pair64) and added in ascending partner ID; the displacement (disp64) and the boundary condition are
-// applied at once.  Ghost agents stay in place.  The result equals the
-// oracle's in-place iteration bit for bit.
+// Per iteration: the box leaders (first cell of each occupied box) are
+// listed by colour (count, prefix, fill); then one launch per colour runs a
+// warp per box over that colour's list.  The warp takes the box's agents in
+// ascending ID, one after the other.  For each, its lanes filter the
+// stencil's candidates in FP32 on the records of the iteration's start
+// (widened by twice the clamp: each agent moves once, by at most the clamp,
+// so every pair that overlaps at the current positions passes), compact
+// them, evaluate the definition (pair64) on the current positions 32 at a
+// time, sort the overlapping pairs by partner ID (bitonic, in shared
+// memory) and add them in that order; lane 0 then applies the displacement
+// (disp64) and the boundary condition before the next agent.  A crowd beyond
+// the shared-memory lists takes a selection of the next partner ID.  Ghost
+// agents stay in place.  The result equals the oracle's in-place iteration
+// bit for bit.
 #include "pair.cuh"
 
 namespace bdm {
 namespace {
 
-constexpr int kInThreads = 128;
-constexpr int kInCap = 48;  // partners sorted in registers/local memory; more take the selection loop
+constexpr int kIpWarps = 4;      // warps (boxes) per block
+constexpr int kIpCand = 512;     // candidates passing the filter, per agent
+constexpr int kIpCap = 256;      // overlapping pairs sorted in shared memory (a power of two)
+constexpr int kIpThreads = 128;  // threads of the list kernels
+
+struct IpShared {
+  uint32_t cand[kIpCand];            // cells that passed the filter
+  unsigned long long key[kIpCap];    // partner ID << 32 | index of the contribution
+  double gx[kIpCap], gy[kIpCap], gz[kIpCap];
+  uint32_t flags[kIpCap];            // bit 0 non-zero force, bit 1 a direction (distance > 0)
+};
 
 __device__ __forceinline__ uint32_t agent_id(const DevCtx &C, int64_t j) { return (uint32_t)C.a.id[C.c.slot[j]]; }
 
@@ -49,162 +62,264 @@ __device__ __forceinline__ int box_colour(const SimConst &sc, const SimState &s,
   return col[0] + k[0] * (col[1] + k[1] * col[2]);
 }
 
-struct Contrib {
-  double gx, gy, gz;
-  uint32_t id, flags;  // flags: bit 0 non-zero force, bit 1 a direction (distance > 0)
-};
-
-__global__ void __launch_bounds__(kInThreads) k_inplace(DevCtx C, int colour) {
-  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= C.g->n_cells) return;
+// Colour of cell p's box when p leads it (its first cell) in an in-place
+// simulation, else -1.
+__device__ __forceinline__ int leader_colour(const DevCtx &C, int64_t p, uint32_t stamp) {
   const int sim = C.c.sim[p];
   const SimConst &sc = C.sc[sim];
   const SimState &s = C.ss[sim];
-  if (!s.valid || sc.exec_ctx != BDM_EXEC_INPLACE) return;
+  if (!s.valid || sc.exec_ctx != BDM_EXEC_INPLACE) return -1;
   int64_t cx, cy, cz;
   unpack_coords(C.c.pkey[p], cx, cy, cz);
-  const uint32_t stamp = C.g->stamp & kStampMask;
-  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
-  const unsigned long long eb = t.e[t.box(0, 0, 0)];
-  const int64_t b0 = ent_start(eb);
-  const uint32_t nb = ent_live(eb, stamp);
-  if (p != b0 || box_colour(sc, s, cx, cy, cz) != colour) return;  // one thread per box of this colour
+  const unsigned long long e = C.tab.e[sc.table_base + linear_box(s, cx, cy, cz)];
+  if (ent_live(e, stamp) == 0u || (int64_t)ent_start(e) != p) return -1;
+  return box_colour(sc, s, cx, cy, cz);
+}
+
+__global__ void k_ip_reset(DevCtx C) {
+  if (threadIdx.x < 27) C.g->ip_count[threadIdx.x] = 0u;
+}
+
+__global__ void __launch_bounds__(kIpThreads) k_ip_count(DevCtx C) {
+  if (C.g->err & ERR_TABLE) return;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= C.g->n_cells) return;
+  const int col = leader_colour(C, p, C.g->stamp & kStampMask);
+  if (col >= 0) atomicAdd(&C.g->ip_count[col], 1u);
+}
+
+__global__ void k_ip_prefix(DevCtx C) {
+  uint32_t o = 0;
+  for (int k = 0; k < 27; ++k) {
+    C.g->ip_off[k] = o;
+    C.g->ip_cursor[k] = o;
+    o += C.g->ip_count[k];
+  }
+  C.g->ip_off[27] = o;
+}
+
+__global__ void __launch_bounds__(kIpThreads) k_ip_fill(DevCtx C) {
+  if (C.g->err & ERR_TABLE) return;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= C.g->n_cells) return;
+  const int col = leader_colour(C, p, C.g->stamp & kStampMask);
+  if (col >= 0) C.ovf[atomicAdd(&C.g->ip_cursor[col], 1u)] = (int32_t)p;
+}
+
+// FP32 filter on the start records: cell j, in the box at offset (dx, dy,
+// dz) from the agent's, against the agent's record a; radii plus `grow`.
+__device__ __forceinline__ bool may_overlap(const DevCtx &C, const float4 &a, int64_t j, int dx, int dy, int dz,
+                                            float Lh, float grow) {
+  const float4 b = C.c.r0[j];
+  const float ddx = __fsub_rn(__fsub_rn(a.x, __fmul_rn((float)dx, Lh)), b.x);
+  const float ddy = __fsub_rn(__fsub_rn(a.y, __fmul_rn((float)dy, Lh)), b.y);
+  const float ddz = __fsub_rn(__fsub_rn(a.z, __fmul_rn((float)dz, Lh)), b.z);
+  const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
+  const float R = __fadd_rn(__fadd_rn(a.w, b.w), grow);
+  return s2 < __fmul_rn(R, R);
+}
+
+// The agent's force when its partners do not fit the shared-memory lists:
+// the overlapping partner with the next ID, one at a time (warp-wide search).
+__device__ void ip_selection(const DevCtx &C, const SimConst &sc, const Stencil &t, int64_t q, const double4_32a &o,
+                             const float4 &a0, uint32_t stamp, int lane, float Lh, float grow, double &fx,
+                             double &fy, double &fz, uint32_t &nnz, uint32_t &novl) {
+  const unsigned FULL = 0xffffffffu;
   const int nx = t.xhi - t.xlo + 1, ny = t.yhi - t.ylo + 1, nzb = t.zhi - t.zlo + 1;
   const int nbox = nx * ny * nzb;
-  // FP32 filter on the records of the iteration's start (box-relative
-  // leading parts): an agent moves once per iteration, by at most the
-  // clamp, so a pair that overlaps at the current positions lies within
-  // r_i + r_j + 2 max_displacement at the start (plus the records' margin)
-  const float Lh = s.Lh;
-  const float grow = __fadd_rn(__fmul_rn(2.f, __double2float_ru(sc.max_disp)), s.marg);
-  auto may_overlap = [&](const float4 &a, int64_t j, int dx, int dy, int dz) {
-    const float4 b = C.c.r0[j];
-    const float ddx = __fsub_rn(__fsub_rn(a.x, __fmul_rn((float)dx, Lh)), b.x);
-    const float ddy = __fsub_rn(__fsub_rn(a.y, __fmul_rn((float)dy, Lh)), b.y);
-    const float ddz = __fsub_rn(__fsub_rn(a.z, __fmul_rn((float)dz, Lh)), b.z);
-    const float s2 = __fmaf_rn(ddz, ddz, __fmaf_rn(ddy, ddy, __fmul_rn(ddx, ddx)));
-    const float R = __fadd_rn(__fadd_rn(a.w, b.w), grow);
-    return s2 < __fmul_rn(R, R);
-  };
-  int64_t last_id = -1;
-  for (uint32_t done = 0; done < nb; ++done) {
-    // the box's agent with the next ID
-    int64_t q = -1;
-    uint32_t qid = 0xFFFFFFFFu;
-    for (uint32_t m = 0; m < nb; ++m) {
-      const uint32_t id = agent_id(C, b0 + m);
-      if ((int64_t)id > last_id && id < qid) {
-        qid = id;
-        q = b0 + m;
-      }
-    }
-    if (q < 0) break;  // IDs are distinct: never taken
-    last_id = (int64_t)qid;
-    const int32_t sq = C.c.slot[q];
-    const double4_32a o = current(C, q);
-    const float4 a0 = C.c.r0[q];
-    // its overlapping partners, kept sorted by ID while they fit
-    Contrib con[kInCap];
-    uint32_t n = 0;
+  int64_t prev = -1;
+  for (;;) {
+    uint32_t best = 0xFFFFFFFFu;
+    int64_t bj = -1;
     for (int bb = 0; bb < nbox; ++bb) {
       const int dx = t.xlo + bb % nx, dy = t.ylo + (bb / nx) % ny, dz = t.zlo + bb / (nx * ny);
       const unsigned long long e = t.e[t.box(dx, dy, dz)];
       const uint32_t cnt = ent_live(e, stamp);
       const int64_t j0 = ent_start(e);
-      for (uint32_t m = 0; m < cnt; ++m) {
+      for (uint32_t m = (uint32_t)lane; m < cnt; m += 32u) {
         const int64_t j = j0 + m;
-        if (j == q || !may_overlap(a0, j, dx, dy, dz)) continue;
+        if (j == q) continue;
+        const uint32_t id = agent_id(C, j);
+        if ((int64_t)id <= prev || id >= best || !may_overlap(C, a0, j, dx, dy, dz, Lh, grow)) continue;
         double gx, gy, gz;
         bool nz, dir;
-        if (!pair64(sc, o, current(C, j), sc.k, sc.gamma, gx, gy, gz, nz, dir)) continue;
-        if (n < (uint32_t)kInCap) {
-          const uint32_t id = agent_id(C, j);
-          uint32_t k = n;
-          while (k > 0 && con[k - 1].id > id) {
-            con[k] = con[k - 1];
-            --k;
-          }
-          con[k].gx = gx; con[k].gy = gy; con[k].gz = gz;
-          con[k].id = id;
-          con[k].flags = (nz ? 1u : 0u) | (dir ? 2u : 0u);
+        if (pair64(sc, o, current(C, j), sc.k, sc.gamma, gx, gy, gz, nz, dir)) {
+          best = id;
+          bj = j;
         }
-        ++n;
       }
     }
-    double fx = 0.0, fy = 0.0, fz = 0.0;
-    uint32_t nnz = 0;
-    if (n <= (uint32_t)kInCap) {
-      for (uint32_t k = 0; k < n; ++k) {
-        nnz += con[k].flags & 1u;
-        if (con[k].flags & 2u) {
-          fx = __dadd_rn(fx, con[k].gx);
-          fy = __dadd_rn(fy, con[k].gy);
-          fz = __dadd_rn(fz, con[k].gz);
+    const uint32_t wbest = __reduce_min_sync(FULL, best);
+    if (wbest == 0xFFFFFFFFu) break;
+    const unsigned who = __ballot_sync(FULL, best == wbest && bj >= 0);
+    const int64_t jb = __shfl_sync(FULL, bj, __ffs(who) - 1);
+    if (lane == 0) {
+      double gx, gy, gz;
+      bool nz, dir;
+      pair64(sc, o, current(C, jb), sc.k, sc.gamma, gx, gy, gz, nz, dir);
+      ++novl;
+      nnz += nz ? 1u : 0u;
+      if (dir) {
+        fx = __dadd_rn(fx, gx);
+        fy = __dadd_rn(fy, gy);
+        fz = __dadd_rn(fz, gz);
+      }
+    }
+    prev = (int64_t)wbest;
+  }
+}
+
+// One warp per box of colour `colour` (grid-stride over the colour's list).
+__global__ void __launch_bounds__(32 * kIpWarps) k_inplace(DevCtx C, int colour) {
+  __shared__ IpShared shw[kIpWarps];
+  if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  IpShared &sh = shw[wid];
+  const uint32_t nlist = C.g->ip_count[colour], off = C.g->ip_off[colour];
+  const uint32_t stamp = C.g->stamp & kStampMask;
+  for (uint32_t w = blockIdx.x * kIpWarps + wid; w < nlist; w += gridDim.x * kIpWarps) {
+    const int64_t b0 = C.ovf[off + w];  // the box's first cell
+    const int sim = C.c.sim[b0];
+    const SimConst &sc = C.sc[sim];
+    const SimState &s = C.ss[sim];
+    int64_t cx, cy, cz;
+    unpack_coords(C.c.pkey[b0], cx, cy, cz);
+    const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
+    const uint32_t nb = ent_live(t.e[t.box(0, 0, 0)], stamp);
+    const int nx = t.xhi - t.xlo + 1, ny = t.yhi - t.ylo + 1, nzb = t.zhi - t.zlo + 1;
+    const int nbox = nx * ny * nzb;
+    const float Lh = s.Lh;
+    const float grow = __fadd_rn(__fmul_rn(2.f, __double2float_ru(sc.max_disp)), s.marg);
+    int64_t last_id = -1;
+    for (uint32_t done = 0; done < nb; ++done) {
+      // the box's agent with the next ID
+      uint32_t myid = 0xFFFFFFFFu;
+      int64_t myq = -1;
+      for (uint32_t m = (uint32_t)lane; m < nb; m += 32u) {
+        const uint32_t id = agent_id(C, b0 + m);
+        if ((int64_t)id > last_id && id < myid) {
+          myid = id;
+          myq = b0 + m;
         }
       }
-    } else {
-      // a crowd: the partner with the next ID, one at a time
-      int64_t prev = -1;
-      for (uint32_t k = 0; k < n; ++k) {
-        uint32_t best = 0xFFFFFFFFu;
-        int64_t bj = -1;
-        for (int bb = 0; bb < nbox; ++bb) {
-          const int dx = t.xlo + bb % nx, dy = t.ylo + (bb / nx) % ny, dz = t.zlo + bb / (nx * ny);
-          const unsigned long long e = t.e[t.box(dx, dy, dz)];
-          const uint32_t cnt = ent_live(e, stamp);
-          const int64_t j0 = ent_start(e);
-          for (uint32_t m = 0; m < cnt; ++m) {
-            const int64_t j = j0 + m;
-            if (j == q) continue;
-            const uint32_t id = agent_id(C, j);
-            if ((int64_t)id <= prev || id >= best || !may_overlap(a0, j, dx, dy, dz)) continue;
-            double gx, gy, gz;
-            bool nz, dir;
-            if (pair64(sc, o, current(C, j), sc.k, sc.gamma, gx, gy, gz, nz, dir)) {
-              best = id;
-              bj = j;
+      const uint32_t qid = __reduce_min_sync(FULL, myid);
+      const unsigned who = __ballot_sync(FULL, myid == qid && myq >= 0);
+      if (!who) break;  // IDs are distinct: never taken
+      const int64_t q = __shfl_sync(FULL, myq, __ffs(who) - 1);
+      last_id = (int64_t)qid;
+      const int32_t sq = C.c.slot[q];
+      const double4_32a o = current(C, q);
+      const float4 a0 = C.c.r0[q];
+      // the candidates that pass the filter, compacted
+      uint32_t nc = 0;
+      for (int bb = 0; bb < nbox; ++bb) {
+        const int dx = t.xlo + bb % nx, dy = t.ylo + (bb / nx) % ny, dz = t.zlo + bb / (nx * ny);
+        const unsigned long long e = t.e[t.box(dx, dy, dz)];
+        const uint32_t cnt = ent_live(e, stamp);
+        const int64_t j0 = ent_start(e);
+        for (uint32_t m0 = 0; m0 < cnt; m0 += 32u) {
+          const uint32_t m = m0 + (uint32_t)lane;
+          const int64_t j = j0 + m;
+          const bool pass = m < cnt && j != q && may_overlap(C, a0, j, dx, dy, dz, Lh, grow);
+          const unsigned B = __ballot_sync(FULL, pass);
+          const uint32_t k = nc + (uint32_t)__popc(B & lt);
+          if (pass && k < (uint32_t)kIpCand) sh.cand[k] = (uint32_t)j;
+          nc += (uint32_t)__popc(B);
+        }
+      }
+      __syncwarp();
+      // the overlapping pairs at the current positions, 32 at a time
+      uint32_t n = 0;
+      bool select = nc > (uint32_t)kIpCand;
+      if (!select) {
+        for (uint32_t k0 = 0; k0 < nc; k0 += 32u) {
+          const uint32_t kk = k0 + (uint32_t)lane;
+          const int64_t j = kk < nc ? (int64_t)sh.cand[kk] : q;
+          double gx = 0.0, gy = 0.0, gz = 0.0;
+          bool nz = false, dir = false, hit = false;
+          if (kk < nc) hit = pair64(sc, o, current(C, j), sc.k, sc.gamma, gx, gy, gz, nz, dir);
+          const unsigned B = __ballot_sync(FULL, hit);
+          const uint32_t k = n + (uint32_t)__popc(B & lt);
+          if (hit && k < (uint32_t)kIpCap) {
+            sh.key[k] = ((unsigned long long)agent_id(C, j) << 32) | k;
+            sh.gx[k] = gx; sh.gy[k] = gy; sh.gz[k] = gz;
+            sh.flags[k] = (nz ? 1u : 0u) | (dir ? 2u : 0u);
+          }
+          n += (uint32_t)__popc(B);
+        }
+        select = n > (uint32_t)kIpCap;
+      }
+      double fx = 0.0, fy = 0.0, fz = 0.0;
+      uint32_t nnz = 0, novl = 0;
+      if (!select) {
+        uint32_t n2 = 32;  // the sort's size: a power of two >= n
+        while (n2 < n) n2 <<= 1;
+        for (uint32_t k = n + (uint32_t)lane; k < n2; k += 32u) sh.key[k] = ~0ull;
+        __syncwarp();
+        for (uint32_t size = 2; size <= n2; size <<= 1)
+          for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t i = (uint32_t)lane; i < n2; i += 32u) {
+              const uint32_t jx = i ^ stride;
+              if (jx > i) {
+                const unsigned long long ka = sh.key[i], kb = sh.key[jx];
+                if ((ka > kb) == ((i & size) == 0)) {
+                  sh.key[i] = kb;
+                  sh.key[jx] = ka;
+                }
+              }
+            }
+            __syncwarp();
+          }
+        if (lane == 0) {
+          for (uint32_t r = 0; r < n; ++r) {
+            const uint32_t k = (uint32_t)sh.key[r];
+            nnz += sh.flags[k] & 1u;
+            if (sh.flags[k] & 2u) {
+              fx = __dadd_rn(fx, sh.gx[k]);
+              fy = __dadd_rn(fy, sh.gy[k]);
+              fz = __dadd_rn(fz, sh.gz[k]);
             }
           }
+          novl = n;
         }
-        if (bj < 0) break;
-        double gx, gy, gz;
-        bool nz, dir;
-        pair64(sc, o, current(C, bj), sc.k, sc.gamma, gx, gy, gz, nz, dir);
-        nnz += nz ? 1u : 0u;
-        if (dir) {
-          fx = __dadd_rn(fx, gx);
-          fy = __dadd_rn(fy, gy);
-          fz = __dadd_rn(fz, gz);
-        }
-        prev = (int64_t)best;
+      } else {
+        ip_selection(C, sc, t, q, o, a0, stamp, lane, Lh, grow, fx, fy, fz, nnz, novl);
       }
+      // the displacement, committed before the next agent
+      if (lane == 0) {
+        const uint8_t ghost = C.a.flags[sq] & FLAG_GHOST;
+        double Dx, Dy, Dz;
+        bool bad;
+        const bool moved = disp64(sc, fx, fy, fz, Dx, Dy, Dz, bad) && !ghost;
+        if (bad) set_err(C.g, ERR_NONFINITE);
+        if (moved) {
+          C.a.x[sq] = bound_apply(sc, __dadd_rn(o.x, Dx));
+          C.a.y[sq] = bound_apply(sc, __dadd_rn(o.y, Dy));
+          C.a.z[sq] = bound_apply(sc, __dadd_rn(o.z, Dz));
+        }
+        const uint8_t nz8 = (uint8_t)(nnz > 255u ? 255u : nnz);
+        C.c.f64[q] = make_double4_32a(fx, fy, fz, (double)novl);
+        C.c.nnz[q] = nz8;
+        C.c.stat[q] = 0;
+        C.a.nnz[sq] = nz8;
+        C.a.flags[sq] = (uint8_t)(ghost | (moved ? FLAG_CHANGED : 0));
+      }
+      __syncwarp();  // the new position is seen by the next agents of the box
     }
-    // the displacement, committed at once
-    const uint8_t ghost = C.a.flags[sq] & FLAG_GHOST;
-    double Dx, Dy, Dz;
-    bool bad;
-    const bool moved = disp64(sc, fx, fy, fz, Dx, Dy, Dz, bad) && !ghost;
-    if (bad) set_err(C.g, ERR_NONFINITE);
-    if (moved) {
-      C.a.x[sq] = bound_apply(sc, __dadd_rn(o.x, Dx));
-      C.a.y[sq] = bound_apply(sc, __dadd_rn(o.y, Dy));
-      C.a.z[sq] = bound_apply(sc, __dadd_rn(o.z, Dz));
-    }
-    const uint8_t nz8 = (uint8_t)(nnz > 255u ? 255u : nnz);
-    C.c.f64[q] = make_double4_32a(fx, fy, fz, (double)n);
-    C.c.nnz[q] = nz8;
-    C.c.stat[q] = 0;
-    C.a.nnz[sq] = nz8;
-    C.a.flags[sq] = (uint8_t)(ghost | (moved ? FLAG_CHANGED : 0));
   }
 }
 
 }  // namespace
 
 void launch_inplace(const DevCtx &C, cudaStream_t st, int colours) {
-  const unsigned int nb = (unsigned int)((C.total_slots + kInThreads - 1) / kInThreads);
-  for (int col = 0; col < colours; ++col) k_inplace<<<nb, kInThreads, 0, st>>>(C, col);
+  const unsigned int nb = (unsigned int)((C.total_slots + kIpThreads - 1) / kIpThreads);
+  k_ip_reset<<<1, 32, 0, st>>>(C);
+  k_ip_count<<<nb, kIpThreads, 0, st>>>(C);
+  k_ip_prefix<<<1, 1, 0, st>>>(C);
+  k_ip_fill<<<nb, kIpThreads, 0, st>>>(C);
+  for (int col = 0; col < colours; ++col) k_inplace<<<152 * 4, 32 * kIpWarps, 0, st>>>(C, col);
 }
 
 }  // namespace bdm
