@@ -130,3 +130,37 @@ def test_reuse_needs_eligible_simulations(orc):
         with pytest.raises(binding.BdmError) as e:
             ctx.set_tuning(**t)
         assert e.value.code == -1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_closed_box_walls_with_reuse(orc, precision):
+    """Agents pushed into the walls of a closed box: clamped moves take the
+    exact record path; FP64 trajectories stay bit-exact, FP32 forces of
+    every iteration meet the tolerance with exact overlap counts."""
+    import oracle
+    rng = np.random.default_rng(17)
+    xyz = rng.uniform(0.0, 90.0, (2500, 3))
+    d = rng.uniform(8.0, 12.0, 2500)
+    pop = workloads.Population(xyz, d, workloads.SimParams(precision=precision, boundary=1, bound_min=0.0,
+                                                           bound_max=90.0, dt=0.05))
+    ctx = reuse_ctx(pop)
+    b0 = ctx.counters()["grid_builds"]
+    o = oracle.Sim(pop.xyz, pop.diameter, pop.params)
+    for t in range(12):
+        x, dd = ctx.get_agents(0)
+        if precision == 1:
+            ref = oracle.Sim(x, dd, pop.params)
+            F0, _, smag = ref.forces()
+        ctx.step(1)
+        if precision == 0:
+            o.step(1)
+            assert np.array_equal(ctx.get_agents(0)[0], o.get()[0]), t
+        else:
+            F, _, _, ov = ctx.forces(0, overlaps=True)
+            err = np.linalg.norm(F - F0, axis=1) / np.maximum(smag, 1e-300)
+            err[smag == 0] = np.linalg.norm(F[smag == 0], axis=1)
+            assert err.max() <= 1e-5, (t, err.max())
+            assert np.array_equal(ov, overlap_counts(pop.n, ref.neighbors(-1.0))), t
+    x, _ = ctx.get_agents(0)
+    assert (x >= 0.0).all() and (x <= 90.0).all()
+    assert ctx.counters()["grid_builds"] - b0 <= 12
