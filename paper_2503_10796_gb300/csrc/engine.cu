@@ -1523,6 +1523,8 @@ int bdm_set_tuning(bdm_ctx *c, const bdm_tuning *t) {
   cudaStreamSynchronize(c->stream);
   c->grid_reuse = t->grid_reuse != 0;
   c->host_touched = true;
+  // without grid reuse no iteration decides it again: clear the last decision
+  if (!c->grid_reuse) cudaMemsetAsync(&c->D.g->reuse, 0, sizeof(uint32_t), c->stream);
   c->force_variant = t->force_variant;
   c->sort_override = t->sort_interval;
   c->sort_curve = t->sort_curve;

@@ -164,3 +164,22 @@ def test_closed_box_walls_with_reuse(orc, precision):
     x, _ = ctx.get_agents(0)
     assert (x >= 0.0).all() and (x <= 90.0).all()
     assert ctx.counters()["grid_builds"] - b0 <= 12
+
+
+def test_reuse_switched_off_and_on(orc):
+    """Turning grid reuse off after reused iterations (and on again) keeps the
+    trajectory exact: the next iteration builds its grid."""
+    import oracle
+    pop = clusters(0, seed=6)
+    ctx = reuse_ctx(pop)
+    o = oracle.Sim(pop.xyz, pop.diameter, pop.params)
+    for reuse in (1, 0, 1, 0):
+        t = ctx.get_tuning()
+        t.update(grid_reuse=reuse)
+        ctx.set_tuning(**t)
+        b = ctx.counters()["grid_builds"]
+        ctx.step(6)
+        o.step(6)
+        assert np.array_equal(ctx.get_agents(0)[0], o.get()[0]), reuse
+        builds = ctx.counters()["grid_builds"] - b
+        assert builds == 6 if reuse == 0 else builds < 6, (reuse, builds)
