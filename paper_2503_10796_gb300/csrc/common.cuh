@@ -99,7 +99,7 @@ struct Globals {
   uint32_t n_ovf;             // FP64-path agents left to the overflow kernel (reset by k_params)
   uint32_t regrid;            // grid reuse: the next iteration must rebuild the grid
   uint32_t reuse;             // grid reuse: this iteration keeps the last build's grid
-  uint32_t pad;
+  uint32_t reused;            // grid reuse: an iteration since the last build kept its grid
   unsigned long long n_builds; // grid builds of step iterations
   uint32_t ip_count[27];      // in-place context: boxes per colour of this iteration
   uint32_t ip_cursor[27];     //   fill cursors of the colour lists

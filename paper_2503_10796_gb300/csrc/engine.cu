@@ -958,6 +958,9 @@ int bdm_get_state(bdm_ctx *c, int32_t sim, void *buf, int64_t cap_bytes, int64_t
 
 int bdm_set_state(bdm_ctx *c, int32_t sim, const void *buf, int64_t size_bytes) {
   if (c) c->host_touched = true;  // the next step rebuilds a reused grid
+  // a state saved after iterations that kept their grid holds registered
+  // boxes: the next build computes every box again
+  if (c) cudaMemsetAsync(&c->D.g->reused, 1, 1, c->stream);
   int rc = check_sim(c, sim);
   if (rc) return rc;
   if (!buf || size_bytes < (int64_t)sizeof(StateHeader)) return fail(c, BDM_E_INVAL, "state buffer too small");

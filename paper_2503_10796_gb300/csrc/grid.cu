@@ -180,7 +180,10 @@ __global__ void k_params(DevCtx C, int32_t step) {
       for (int a = 0; a < 3; ++a) { st.bmin[a] = ~0ull; st.bmax[a] = 0ull; }
       st.dmax = 0ull;
     }
-    if (threadIdx.x == 0) g->n_ovf = 0u;
+    if (threadIdx.x == 0) {
+      g->n_ovf = 0u;
+      g->reused = 1u;
+    }
     return;
   }
   for (int k = threadIdx.x; k < C.n_sims; k += blockDim.x) {
@@ -250,7 +253,10 @@ __global__ void k_params(DevCtx C, int32_t step) {
       ok = false;
     }
     st.valid = ok ? 1 : 0;
-    st.same_grid = (step && st.has_prev && ok && st.o[0] == st.prev_o[0] && st.o[1] == st.prev_o[1] &&
+    // after iterations that kept their grid, an agent may have moved since
+    // the last build without moving in the last iteration: the count then
+    // cannot reuse its box, nor static detection its history
+    st.same_grid = (step && !g->reused && st.has_prev && ok && st.o[0] == st.prev_o[0] && st.o[1] == st.prev_o[1] &&
                     st.o[2] == st.prev_o[2] && L == st.prev_L && st.dims[0] == st.prev_dims[0] &&
                     st.dims[1] == st.prev_dims[1] && st.dims[2] == st.prev_dims[2]) ? 1 : 0;
     // float-float constants
@@ -283,7 +289,10 @@ __global__ void k_params(DevCtx C, int32_t step) {
     g->stamp += 1u;
     g->tile_ticket = 0u;
     g->n_ovf = 0u;
-    if (step) g->n_builds += 1ull;
+    if (step) {
+      g->n_builds += 1ull;
+      g->reused = 0u;
+    }
     int64_t cells = 0;
     for (int k = 0; k < C.n_sims; ++k) {
       const int s = C.order[k];
