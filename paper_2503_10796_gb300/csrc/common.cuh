@@ -75,6 +75,7 @@ struct SimState {
   int32_t same_grid;          // grid equals the previous iteration's
   int32_t valid;              // grid fits the table region
   int32_t has_prev;
+  int32_t keep_boxes;         // same_grid, and no agent moved since the last build unseen by its flags
   double prev_o[3], prev_L;
   int64_t prev_dims[3];
   int64_t cell_base;

@@ -253,12 +253,13 @@ __global__ void k_params(DevCtx C, int32_t step) {
       ok = false;
     }
     st.valid = ok ? 1 : 0;
-    // after iterations that kept their grid, an agent may have moved since
-    // the last build without moving in the last iteration: the count then
-    // cannot reuse its box, nor static detection its history
-    st.same_grid = (step && !g->reused && st.has_prev && ok && st.o[0] == st.prev_o[0] && st.o[1] == st.prev_o[1] &&
+    st.same_grid = (step && st.has_prev && ok && st.o[0] == st.prev_o[0] && st.o[1] == st.prev_o[1] &&
                     st.o[2] == st.prev_o[2] && L == st.prev_L && st.dims[0] == st.prev_dims[0] &&
                     st.dims[1] == st.prev_dims[1] && st.dims[2] == st.prev_dims[2]) ? 1 : 0;
+    // after iterations that kept their grid (or a restored state), an agent
+    // may have moved since the last build without moving in the last
+    // iteration: the count then computes every box
+    st.keep_boxes = (st.same_grid && !g->reused) ? 1 : 0;
     // float-float constants
     split_pos(L, st.Lh, st.Ll);
     double il = __ddiv_rn(1.0, L);
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(kAgentThreads) k_count(DevCtx C, int step) {
   const bool changed = valid && step && (fl & FLAG_CHANGED) != 0;
   uint32_t c[3] = {0u, 0u, 0u};
   if (!valid) {
-  } else if (step && s.same_grid && !changed) {
+  } else if (step && s.keep_boxes && !changed) {
     // unchanged agent, unchanged grid: the box of the last iteration
     c[0] = (uint32_t)(pk_prev_in & kCoordMask);
     c[1] = (uint32_t)((pk_prev_in >> kCoordBits) & kCoordMask);
