@@ -194,6 +194,7 @@ __global__ void k_params(DevCtx C, int32_t step) {
     st.ncell = st.n;
     st.valid = 0;
     st.same_grid = 0;
+    st.keep_boxes = 0;
     if (step) {
       st.it = st.t;
       st.t += 1;
