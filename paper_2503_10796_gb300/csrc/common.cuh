@@ -87,6 +87,7 @@ struct SimState {
   unsigned long long updates;  // agent-updates stepped since the agents were set
   double skin;                // grid reuse: how far an agent may leave its box before the grid is rebuilt
   float skin_lo, skin_hi;     // the same bounds on a box-relative offset in FP32, rounded inwards
+  float skin_pad;             // the skin rounded up (box pruning of iterations that keep the grid)
 };
 
 // Global counters of a context.

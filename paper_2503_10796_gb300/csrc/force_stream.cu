@@ -154,13 +154,17 @@ __global__ void __launch_bounds__(kStreamThreads, 4) k_force32w(DevCtx C) {
   // (placed in a valid grid), else the table's first word
   const unsigned long long *const e_idle = walk ? t.e + row0 : C.tab.e;
   // box pruning: squared distance from the centre to the neighbour box per
-  // axis and offset (-1: w, 0: 0, +1: L - w); reach = rw + r_max
-  const float reach = __fadd_rn(rw, s.rmaxf);
+  // axis and offset (-1: max(w, 0), 0: 0, +1: max(L - w, 0)); reach = rw +
+  // r_max, plus the skin in iterations that keep the last build's grid (a
+  // partner registered in a box may then lie up to the skin outside it)
+  const float reach = __fadd_rn(__fadd_rn(rw, s.rmaxf), C.g->reuse ? s.skin_pad : 0.f);
   const float reach2 = __fmul_rn(reach, reach);
-  const float lx = __fsub_rn(Lh, o0.x), ly = __fsub_rn(Lh, o0.y), lz = __fsub_rn(Lh, o0.z);
-  const float ex[3] = {__fmul_rn(o0.x, o0.x), 0.f, __fmul_rn(lx, lx)};
-  const float ey[3] = {__fmul_rn(o0.y, o0.y), 0.f, __fmul_rn(ly, ly)};
-  const float ez[3] = {__fmul_rn(o0.z, o0.z), 0.f, __fmul_rn(lz, lz)};
+  const float wx = fmaxf(o0.x, 0.f), wy = fmaxf(o0.y, 0.f), wz = fmaxf(o0.z, 0.f);
+  const float lx = fmaxf(__fsub_rn(Lh, o0.x), 0.f), ly = fmaxf(__fsub_rn(Lh, o0.y), 0.f),
+              lz = fmaxf(__fsub_rn(Lh, o0.z), 0.f);
+  const float ex[3] = {__fmul_rn(wx, wx), 0.f, __fmul_rn(lx, lx)};
+  const float ey[3] = {__fmul_rn(wy, wy), 0.f, __fmul_rn(ly, ly)};
+  const float ez[3] = {__fmul_rn(wz, wz), 0.f, __fmul_rn(lz, lz)};
   uint32_t qn = 0;  // queued pairs (warp-uniform)
   __syncwarp();
 #pragma unroll

@@ -277,6 +277,7 @@ __global__ void k_params(DevCtx C, int32_t step) {
     // part is below 2^-23 of it: an inward margin of 2^-21 L covers it)
     st.skin_lo = -__double2float_rd(__dsub_rn(st.skin, __dmul_rn(L, 0x1p-21)));
     st.skin_hi = __double2float_rd(__dsub_rn(__dadd_rn(L, st.skin), __dmul_rn(L, 0x1p-21)));
+    st.skin_pad = st.skin > 0.0 ? __double2float_ru(st.skin) : 0.f;
     if (step) {
       for (int a = 0; a < 3; ++a) { st.prev_o[a] = st.o[a]; st.prev_dims[a] = st.dims[a]; }
       st.prev_L = L;
