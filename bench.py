@@ -55,7 +55,7 @@ ALG_BYTES_BOX = 8.0
 # scaled by the agents of a launch for the clustered workloads and null
 # elsewhere.  Keyed by force variant; an entry holds only while the
 # variant's kernel is the one captured.
-FORCE_TRAFFIC_B_PER_AGENT = {5: 104.6}
+FORCE_TRAFFIC_B_PER_AGENT = {5: 104.9}
 FORCE_KERNEL = {0: "k_force32s", 1: "k_force32d", 2: "k_force", 3: "k_force32d", 4: "k_force32s (direct)",
                 5: "k_force32w", 6: "k_static + k_force32w"}
 # Workloads whose configuration fixes the re-sort (interval, curve): the
