@@ -151,6 +151,37 @@ def test_clustered_8M_full_size(orc):
         ctx.close()
 
 
+def test_clustered_8M_grid_reuse_full_size(orc):
+    """The incremental grid at full size: after 52 iterations (settling,
+    re-sorts at 0, 10, ..., 50, reused iterations between), the forces of an
+    iteration that kept its grid, on 20,000 sampled agents, against the
+    oracle on the same positions; the overlap and non-zero counts of the
+    sample exact."""
+    import oracle
+    pop = workloads.clustered(sort_interval=10)
+    ctx = make_ctx([pop], force_variant=5, sort_interval=10, sort_curve=0, box_scale_pct=125, grid_reuse=1)
+    try:
+        ctx.step(52)
+        x, d = ctx.get_agents(0)
+        b = ctx.counters()["grid_builds"]
+        ctx.step(1)
+        ctx.sync()
+        assert ctx.counters()["grid_builds"] == b  # this iteration kept its grid
+        F_gpu, nnz_gpu, _, ov_gpu = ctx.forces(0, overlaps=True)
+        full = oracle.Sim(x, d, pop.params)
+        rng = np.random.default_rng(6)
+        sample = np.sort(rng.choice(pop.n, 20000, replace=False))
+        F0, nnz0, smag = full.forces(sample)
+        err = rel_err(F_gpu[sample], F0, smag)
+        report("clustered_8M grid reuse sampled", err)
+        assert err.max() <= TOL32
+        pairs = full.neighbors(-1.0)
+        assert np.array_equal(ov_gpu[sample], overlap_counts(pop.n, pairs)[sample])
+        check_nnz(nnz_gpu[sample], nnz0, sample, x, d, pairs, pop.params.k, pop.params.gamma)
+    finally:
+        ctx.close()
+
+
 def test_uniform_200M_full_size(orc):
     """200M agents at volume fraction 0.3: box indices, pairs, forces and
     positions of a corner region (at the grid origin) and a central one."""
