@@ -269,8 +269,8 @@ int bdm_get_stats(bdm_ctx* ctx, int32_t sim, bdm_stats* out);
  * stage, the number of launches and the summed device time in ms since
  * profiling was enabled, and the stage names in `names` (NULL allowed).
  * Stages: 0 bbox, 1 grid count, 2 grid scan, 3 grid place, 4 force,
- * 5 displace, 6 growth/division, 7 morton sort. */
-enum { BDM_NUM_STAGES = 8 };
+ * 5 displace, 6 growth/division, 7 morton sort, 8 substances. */
+enum { BDM_NUM_STAGES = 9 };
 int bdm_profile(bdm_ctx* ctx, int32_t enable);
 int bdm_get_profile(bdm_ctx* ctx, int64_t launches[BDM_NUM_STAGES], double ms[BDM_NUM_STAGES],
                     const char* names[BDM_NUM_STAGES]);
@@ -451,6 +451,28 @@ int bdm_secrete(bdm_ctx* ctx, int32_t sim, const bdm_diffusion_grid* grid, doubl
  * BDM_E_STATE when the simulation has no agents set. */
 int bdm_chemotaxis(bdm_ctx* ctx, int32_t sim, const bdm_diffusion_grid* grid, const double* u, double weight,
                    int32_t flags);
+
+/* The same three inside bdm_step (the cell-clustering use case of §4.6):
+ * simulation `sim` keeps a substance on `grid`, with initial concentrations
+ * u (host memory, or device memory with BDM_DEVICE_PTRS; copied, the caller
+ * keeps u).  After the mechanical step of every iteration (forces,
+ * displacement, growth), over all agents and each seeing the result of the
+ * one before: the agents secrete `quantity` into the boxes of their new
+ * positions (Algorithm 6), the substance takes one step of Eq 4.3 with the
+ * simulation's dt and nu, mu (>= 0), and the agents move by `weight` along
+ * its normalized gradient (Algorithm 7).  grid NULL removes the substance.
+ * Open space only.  Errors: BDM_E_INVAL (bad grid or values, a closed or
+ * toroidal simulation), BDM_E_NOMEM.  Grid reuse stays correct: agents that
+ * chemotaxis moves make the next iteration rebuild the grid. */
+int bdm_set_substance(bdm_ctx* ctx, int32_t sim, const bdm_diffusion_grid* grid, const double* u, double nu,
+                      double mu, double quantity, double weight, int32_t flags);
+
+/* The concentrations of simulation `sim`'s substance (grid order, as u of
+ * bdm_set_substance) into u (cap doubles; host, or device with
+ * BDM_DEVICE_PTRS); *n_out (may be NULL) receives the point count.
+ * BDM_E_STATE (no substance), BDM_E_CAPACITY (cap too small, nothing
+ * written). */
+int bdm_get_substance(bdm_ctx* ctx, int32_t sim, double* u, int64_t cap, int64_t* n_out, int32_t flags);
 
 /* ---- Epidemiology use case (§4.6.3) ------------------------------------
  * Persons are the agents of a simulation (their diameters play no part);

@@ -84,6 +84,8 @@ def lib():
         L.orc_step.argtypes = [C.c_void_p, C.c_int32]
         L.orc_remove.restype = C.c_int
         L.orc_remove.argtypes = [C.c_void_p, C.c_int64, i64p]
+        L.orc_set_positions.restype = C.c_int
+        L.orc_set_positions.argtypes = [C.c_void_p, dp]
         L.orc_neighbors.restype = C.c_int64
         L.orc_neighbors.argtypes = [C.c_void_p, C.c_double, C.c_int64, i64p]
         L.orc_interleave.restype = C.c_uint64
@@ -177,6 +179,14 @@ class Sim:
         rc = self._L.orc_remove(self._h, ids.shape[0], _ptr(ids, C.c_int64))
         if rc:
             raise ValueError("oracle rejected the removal (IDs out of range or repeated)")
+
+    def set_positions(self, xyz):
+        """New positions of the current agents by ID (orc_set_positions)."""
+        x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        if x.shape[0] != self.n:
+            raise ValueError("one position per agent")
+        if self._L.orc_set_positions(self._h, _ptr(x, C.c_double)):
+            raise ValueError("a position outside the space")
 
     def get(self):
         n = self.n

@@ -849,6 +849,25 @@ int orc_remove(orc_sim *s, int64_t m, const int64_t *ids) {
   return 0;
 }
 
+/* New positions of the current agents (xyz by ID, n x 3), as an operation
+ * after the mechanical step of an iteration (chemotaxis): an agent whose
+ * position changes counts as changed for static detection; its box of the
+ * last grid stays.  Returns -1 (nothing changed) on a position outside the
+ * space of a closed or toroidal boundary. */
+int orc_set_positions(orc_sim *s, const double *xyz) {
+  for (int64_t i = 0; i < s->n; ++i)
+    for (int a = 0; a < 3; ++a)
+      if (!inside_space(&s->p, xyz[3 * i + a])) return -1;
+  for (int64_t i = 0; i < s->n; ++i) {
+    const double nx = xyz[3 * i], ny = xyz[3 * i + 1], nz = xyz[3 * i + 2];
+    if (nx != s->x[i] || ny != s->y[i] || nz != s->z[i]) {
+      s->x[i] = nx; s->y[i] = ny; s->z[i] = nz;
+      s->changed[i] = 1;
+    }
+  }
+  return 0;
+}
+
 int orc_step(orc_sim *s, int32_t iterations) {
   for (int32_t it = 0; it < iterations; ++it) {
     int rc = orc_iterate(s);

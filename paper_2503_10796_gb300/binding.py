@@ -18,7 +18,7 @@ ERRORS = {-1: "BDM_E_INVAL", -2: "BDM_E_NOMEM", -3: "BDM_E_CUDA", -4: "BDM_E_CAP
           -5: "BDM_E_TIMEOUT", -6: "BDM_E_NONFINITE", -7: "BDM_E_STATE"}
 PREC_FP64, PREC_FP32_FORCE = 0, 1
 DEVICE_PTRS = 1
-NUM_STAGES = 8
+NUM_STAGES = 9
 
 # Every symbol the header declares, with (restype, argtypes).
 _P = C.POINTER
@@ -76,6 +76,8 @@ SIGNATURES = {
     "bdm_get_state": (C.c_int, [_vp, _i32, _vp, _i64, _P(_i64)]),
     "bdm_remove_agents": (C.c_int, [_vp, _i32, _i64, _vp]),
     "bdm_set_ghosts": (C.c_int, [_vp, _i32, _i64, _vp]),
+    "bdm_set_substance": (C.c_int, [_vp, _i32, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double, _i32]),
+    "bdm_get_substance": (C.c_int, [_vp, _i32, _vp, _i64, _P(_i64), _i32]),
     "bdm_set_state": (C.c_int, [_vp, _i32, _vp, _i64]),
     "bdm_sync": (C.c_int, [_vp]),
     "bdm_get_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _P(_i64), _i32]),
@@ -356,6 +358,27 @@ class Context:
         """Algorithm 7: moves the agents of `sim` up the gradient of u."""
         g, ptr, flags = self._diffusion_grid(u, lo, h)
         self._check(self._lib.bdm_chemotaxis(self._h, sim, C.byref(g), ptr, float(weight), flags))
+
+    def set_substance(self, sim: int, u, lo, h, nu: float, mu: float, quantity: float, weight: float):
+        """A substance of `sim` that bdm_step secretes into, diffuses and
+        follows every iteration (bdm_set_substance); u is copied."""
+        g, ptr, flags = self._diffusion_grid(u, lo, h)
+        self._substance_shape = getattr(self, "_substance_shape", {})
+        self._substance_shape[sim] = tuple(u.shape)
+        self._check(self._lib.bdm_set_substance(self._h, sim, C.byref(g), ptr, float(nu), float(mu), float(quantity),
+                                                float(weight), flags))
+
+    def clear_substance(self, sim: int):
+        self._check(self._lib.bdm_set_substance(self._h, sim, None, None, 0.0, 0.0, 0.0, 0.0, 0))
+
+    def get_substance(self, sim: int) -> np.ndarray:
+        """The substance's concentrations, shape (nz, ny, nx) as set."""
+        n = C.c_int64()
+        rc = self._lib.bdm_get_substance(self._h, sim, None, 0, C.byref(n), 0)
+        self._check_size_query(rc, n)
+        out = np.empty(getattr(self, "_substance_shape", {}).get(sim, (n.value,)), np.float64)
+        self._check(self._lib.bdm_get_substance(self._h, sim, _dptr(out), out.size, C.byref(n), 0))
+        return out
 
     # -- epidemiology (§4.6.3, Algorithms 3-5) -------------------------------
     def sir_step(self, sim: int, state, radius: float, p_infect: float, p_recover: float, speed: float,

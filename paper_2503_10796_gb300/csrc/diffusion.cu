@@ -83,8 +83,11 @@ __device__ __forceinline__ double diff_at(const double *u, const DiffGrid &g, in
 // Algorithm 6: every agent of the simulation inside the grid adds
 // `quantity` to its box.  The additions to one box commute exactly (equal
 // addends), so the result does not depend on the order of the atomics.
-__global__ void k_secrete(DevCtx C, int64_t base, int64_t n, DiffGrid g, double *u, double quantity) {
+// sim >= 0: a step of bdm_step, which takes the simulation's agent count
+// from the device (n is then the simulation's capacity).
+__global__ void k_secrete(DevCtx C, int64_t base, int64_t n, int sim, DiffGrid g, double *u, double quantity) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sim >= 0 && i >= C.ss[sim].n) return;
   if (i >= n) return;
   const int64_t slot = base + i;
   int64_t b0, b1, b2;
@@ -96,8 +99,10 @@ __global__ void k_secrete(DevCtx C, int64_t base, int64_t n, DiffGrid g, double 
 // normalized central-difference gradient of its box; the grid is only read.
 // Agents that move are marked changed (their box must be recomputed and
 // they disturb static neighbours).
-__global__ void k_chemotaxis(DevCtx C, int64_t base, int64_t n, DiffGrid g, const double *u, double weight) {
+__global__ void k_chemotaxis(DevCtx C, int64_t base, int64_t n, int sim, DiffGrid g, const double *u,
+                             double weight) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sim >= 0 && i >= C.ss[sim].n) return;
   if (i >= n) return;
   const int64_t slot = base + i;
   const double x = C.a.x[slot], y = C.a.y[slot], z = C.a.z[slot];
@@ -119,6 +124,7 @@ __global__ void k_chemotaxis(DevCtx C, int64_t base, int64_t n, DiffGrid g, cons
     C.a.y[slot] = ny;
     C.a.z[slot] = nz;
     C.a.flags[slot] |= FLAG_CHANGED;
+    C.g->regrid = 1u;  // moved outside the displacement: a kept grid no longer fits
   }
 }
 
@@ -139,13 +145,25 @@ void launch_diffuse_step(cudaStream_t st, const double *in, double *out, const D
 void launch_secrete(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const DiffGrid &g, double *u,
                     double quantity) {
   if (n <= 0) return;
-  k_secrete<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, g, u, quantity);
+  k_secrete<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, -1, g, u, quantity);
+}
+
+void launch_secrete_step(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t cap, const DiffGrid &g,
+                         double *u, double quantity) {
+  if (cap <= 0) return;
+  k_secrete<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, base, cap, sim, g, u, quantity);
+}
+
+void launch_chemotaxis_step(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t cap, const DiffGrid &g,
+                            const double *u, double weight) {
+  if (cap <= 0) return;
+  k_chemotaxis<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, base, cap, sim, g, u, weight);
 }
 
 void launch_chemotaxis(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const DiffGrid &g, const double *u,
                        double weight) {
   if (n <= 0) return;
-  k_chemotaxis<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, g, u, weight);
+  k_chemotaxis<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, -1, g, u, weight);
 }
 
 }  // namespace bdm

@@ -17,8 +17,8 @@ using namespace bdm;
 
 namespace {
 
-const char *kStageNames[kStages] = {"bbox", "grid_count", "grid_scan", "grid_place",
-                                    "force", "displace", "growth_division", "morton_sort"};
+const char *kStageNames[kStages] = {"bbox", "grid_count", "grid_scan", "grid_place", "force",
+                                    "displace", "growth_division", "morton_sort", "substances"};
 
 std::string g_create_error;
 int g_alloc_counter = 0;
@@ -53,6 +53,15 @@ struct bdm_ctx {
   size_t sort_bytes = 0;
   int sort_key_bits = 0;
   int force_variant = 5;     // force kernel variant of the FP32 path (see launch_force)
+  // a substance a simulation secretes into and follows in every iteration
+  struct Substance {
+    bool on = false;
+    bdm_diffusion_grid g{};
+    double *u = nullptr, *next = nullptr;
+    int64_t total = 0;
+    double nu = 0, mu = 0, quantity = 0, weight = 0;
+  };
+  std::vector<Substance> subst;
   bool grid_reuse = false;   // incremental grid: keep the last build while agents stay in their skins
   bool host_touched = true;  // a call since the last bdm_step changed agents or the table
   bool inplace = false;      // the in-place execution context (every simulation)
@@ -314,6 +323,19 @@ void launch_iteration(bdm_ctx *c, int sort) {
   if (c->any_grow) {
     stage_begin(c, 6);
     launch_growth(D, st, c->d_grow, c->grow_bytes);
+    stage_end(c);
+  }
+  // the simulations' substances: secretion at the new positions, one
+  // diffusion step, chemotaxis up the diffused gradient
+  for (int s = 0; s < c->n_sims; ++s) {
+    const bdm_ctx::Substance &S = c->subst[s];
+    if (!S.on) continue;
+    stage_begin(c, 8);
+    const SimConst &sc = c->h_sc[s];
+    launch_secrete_step(D, st, s, sc.base, sc.cap, S.g, S.u, S.quantity);
+    launch_diffuse_step(st, S.u, S.next, S.g, S.nu, S.mu, sc.dt);
+    cudaMemcpyAsync(S.u, S.next, sizeof(double) * (size_t)S.total, cudaMemcpyDeviceToDevice, st);
+    launch_chemotaxis_step(D, st, s, sc.base, sc.cap, S.g, S.u, S.weight);
     stage_end(c);
   }
   if (c->any_sort && sort == 2) {
@@ -608,6 +630,7 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   for (int s = 0; s < n_sims; ++s)
     if (per_sim[s].boundary == BDM_BOUNDARY_TOROIDAL) c->inplace_colours = 27;
   c->n_set.assign(n_sims, -1);
+  c->subst.assign(n_sims, bdm_ctx::Substance{});
   c->h_iter.assign(n_sims, 0);
   c->need_radix.assign(n_sims, 1);
   for (int s = 0; s < n_sims; ++s) {
@@ -1240,6 +1263,74 @@ int bdm_secrete(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, double *u,
   dfree(c, own);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "secretion");
+  return BDM_OK;
+}
+
+int bdm_set_substance(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, const double *u, double nu, double mu,
+                      double quantity, double weight, int32_t flags) {
+  if (!c) return BDM_E_INVAL;
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  bdm_ctx::Substance &S = c->subst[sim];
+  if (!g) {
+    // remove the substance
+    cudaStreamSynchronize(c->stream);
+    dfree(c, S.u);
+    dfree(c, S.next);
+    S = bdm_ctx::Substance{};
+    c->graph_dirty = true;
+    return BDM_OK;
+  }
+  const int64_t total = check_grid(c, g, u);
+  if (total < 0) return (int)total;
+  if (!fin(nu) || !fin(mu) || !fin(quantity) || !fin(weight) || nu < 0 || mu < 0)
+    return fail(c, BDM_E_INVAL, "nu, mu >= 0 and quantity, weight finite");
+  if (c->params[sim].boundary != BDM_BOUNDARY_OPEN)
+    return fail(c, BDM_E_INVAL, "substances are for simulations in open space");
+  cudaStreamSynchronize(c->stream);
+  if (S.total != total) {
+    dfree(c, S.u);
+    dfree(c, S.next);
+    S.u = S.next = nullptr;
+    rc = dalloc(c, &S.u, (size_t)total, "substance");
+    if (!rc) rc = dalloc(c, &S.next, (size_t)total, "substance step");
+    if (rc) {
+      dfree(c, S.u);
+      dfree(c, S.next);
+      S = bdm_ctx::Substance{};
+      return rc;
+    }
+  }
+  cudaMemcpyAsync(S.u, u, sizeof(double) * (size_t)total,
+                  (flags & BDM_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "uploading the substance");
+  S.on = true;
+  S.g = *g;
+  S.total = total;
+  S.nu = nu;
+  S.mu = mu;
+  S.quantity = quantity;
+  S.weight = weight;
+  c->graph_dirty = true;
+  c->host_touched = true;
+  return BDM_OK;
+}
+
+int bdm_get_substance(bdm_ctx *c, int32_t sim, double *u, int64_t cap, int64_t *n_out, int32_t flags) {
+  if (!c) return BDM_E_INVAL;
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  const bdm_ctx::Substance &S = c->subst[sim];
+  if (!S.on) return fail(c, BDM_E_STATE, "the simulation has no substance");
+  if (n_out) *n_out = S.total;
+  if (cap < S.total || !u) return fail(c, BDM_E_CAPACITY, "buffer smaller than the grid");
+  rc = latched_error(c);
+  if (rc) return rc;
+  cudaMemcpyAsync(u, S.u, sizeof(double) * (size_t)S.total,
+                  (flags & BDM_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "downloading the substance");
   return BDM_OK;
 }
 

@@ -57,6 +57,12 @@ void launch_secrete(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, c
                     double quantity);
 void launch_chemotaxis(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const DiffGrid &g, const double *u,
                        double weight);
+// The same two inside bdm_step: the agent count from the device, launched
+// over the simulation's capacity.
+void launch_secrete_step(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t cap, const DiffGrid &g,
+                         double *u, double quantity);
+void launch_chemotaxis_step(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t cap, const DiffGrid &g,
+                            const double *u, double weight);
 
 // sir.cu (epidemiology use case): one step on the query cells of `sim`
 void launch_sir_step(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, int64_t base,
