@@ -452,27 +452,38 @@ int bdm_secrete(bdm_ctx* ctx, int32_t sim, const bdm_diffusion_grid* grid, doubl
 int bdm_chemotaxis(bdm_ctx* ctx, int32_t sim, const bdm_diffusion_grid* grid, const double* u, double weight,
                    int32_t flags);
 
-/* The same three inside bdm_step (the cell-clustering use case of §4.6):
- * simulation `sim` keeps a substance on `grid`, with initial concentrations
- * u (host memory, or device memory with BDM_DEVICE_PTRS; copied, the caller
- * keeps u).  After the mechanical step of every iteration (forces,
- * displacement, growth), over all agents and each seeing the result of the
- * one before: the agents secrete `quantity` into the boxes of their new
- * positions (Algorithm 6), the substance takes one step of Eq 4.3 with the
- * simulation's dt and nu, mu (>= 0), and the agents move by `weight` along
- * its normalized gradient (Algorithm 7).  grid NULL removes the substance.
- * Open space only.  Errors: BDM_E_INVAL (bad grid or values, a closed or
- * toroidal simulation), BDM_E_NOMEM.  Grid reuse stays correct: agents that
- * chemotaxis moves make the next iteration rebuild the grid. */
-int bdm_set_substance(bdm_ctx* ctx, int32_t sim, const bdm_diffusion_grid* grid, const double* u, double nu,
-                      double mu, double quantity, double weight, int32_t flags);
+/* Agent kinds of simulation `sim` (the cell types of the soma-clustering
+ * benchmark, §4.6): kinds[i] in 0..3 for agent ID i (host memory, n = the
+ * agent count).  A daughter takes its mother's kind, removal renumbers the
+ * kinds with the agents, and bdm_set_agents and bdm_set_state reset every
+ * kind to 0 (a state does not hold them).  Errors: BDM_E_INVAL (n differs
+ * from the agent count, a kind above 3), BDM_E_STATE, BDM_E_NOMEM. */
+int bdm_set_agent_kinds(bdm_ctx* ctx, int32_t sim, int64_t n, const uint8_t* kinds);
 
-/* The concentrations of simulation `sim`'s substance (grid order, as u of
- * bdm_set_substance) into u (cap doubles; host, or device with
- * BDM_DEVICE_PTRS); *n_out (may be NULL) receives the point count.
- * BDM_E_STATE (no substance), BDM_E_CAPACITY (cap too small, nothing
+/* The same three inside bdm_step (the cell-clustering use case of §4.6):
+ * the agents of kind `kind` (0..3) of simulation `sim` keep a substance on
+ * `grid`, with initial concentrations u (host memory, or device memory with
+ * BDM_DEVICE_PTRS; copied, the caller keeps u).  After the mechanical step
+ * of every iteration (forces, displacement, growth), over the agents of that
+ * kind and each seeing the result of the one before: they secrete
+ * `quantity` into the boxes of their new positions (Algorithm 6), the
+ * substance takes one step of Eq 4.3 with the simulation's dt and nu, mu
+ * (>= 0), and they move by `weight` along its normalized gradient
+ * (Algorithm 7).  Kinds touch neither each other's agents nor substances.
+ * grid NULL removes the substance.  Open space only.  Errors: BDM_E_INVAL
+ * (bad kind, grid or values, a closed or toroidal simulation), BDM_E_NOMEM.
+ * Grid reuse stays correct: agents that chemotaxis moves make the next
+ * iteration rebuild the grid. */
+int bdm_set_substance(bdm_ctx* ctx, int32_t sim, int32_t kind, const bdm_diffusion_grid* grid, const double* u,
+                      double nu, double mu, double quantity, double weight, int32_t flags);
+
+/* The concentrations of the substance of kind `kind` of simulation `sim`
+ * (grid order, as u of bdm_set_substance) into u (cap doubles; host, or
+ * device with BDM_DEVICE_PTRS); *n_out (may be NULL) receives the point
+ * count.  BDM_E_STATE (no substance), BDM_E_CAPACITY (cap too small, nothing
  * written). */
-int bdm_get_substance(bdm_ctx* ctx, int32_t sim, double* u, int64_t cap, int64_t* n_out, int32_t flags);
+int bdm_get_substance(bdm_ctx* ctx, int32_t sim, int32_t kind, double* u, int64_t cap, int64_t* n_out,
+                      int32_t flags);
 
 /* ---- Epidemiology use case (§4.6.3) ------------------------------------
  * Persons are the agents of a simulation (their diameters play no part);

@@ -76,8 +76,10 @@ SIGNATURES = {
     "bdm_get_state": (C.c_int, [_vp, _i32, _vp, _i64, _P(_i64)]),
     "bdm_remove_agents": (C.c_int, [_vp, _i32, _i64, _vp]),
     "bdm_set_ghosts": (C.c_int, [_vp, _i32, _i64, _vp]),
-    "bdm_set_substance": (C.c_int, [_vp, _i32, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double, _i32]),
-    "bdm_get_substance": (C.c_int, [_vp, _i32, _vp, _i64, _P(_i64), _i32]),
+    "bdm_set_agent_kinds": (C.c_int, [_vp, _i32, _i64, _vp]),
+    "bdm_set_substance": (C.c_int, [_vp, _i32, _i32, _vp, _vp, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    _i32]),
+    "bdm_get_substance": (C.c_int, [_vp, _i32, _i32, _vp, _i64, _P(_i64), _i32]),
     "bdm_set_state": (C.c_int, [_vp, _i32, _vp, _i64]),
     "bdm_sync": (C.c_int, [_vp]),
     "bdm_get_agents": (C.c_int, [_vp, _i32, _i64, _vp, _vp, _P(_i64), _i32]),
@@ -359,25 +361,32 @@ class Context:
         g, ptr, flags = self._diffusion_grid(u, lo, h)
         self._check(self._lib.bdm_chemotaxis(self._h, sim, C.byref(g), ptr, float(weight), flags))
 
-    def set_substance(self, sim: int, u, lo, h, nu: float, mu: float, quantity: float, weight: float):
-        """A substance of `sim` that bdm_step secretes into, diffuses and
-        follows every iteration (bdm_set_substance); u is copied."""
+    def set_agent_kinds(self, sim: int, kinds):
+        """Agent kinds (0..3) by ID (bdm_set_agent_kinds)."""
+        k = np.ascontiguousarray(kinds, dtype=np.uint8).reshape(-1)
+        self._check(self._lib.bdm_set_agent_kinds(self._h, sim, k.shape[0], _dptr(k)))
+
+    def set_substance(self, sim: int, u, lo, h, nu: float, mu: float, quantity: float, weight: float,
+                      kind: int = 0):
+        """A substance that the agents of `kind` secrete into, diffuse and
+        follow in every iteration of bdm_step (bdm_set_substance); u is
+        copied."""
         g, ptr, flags = self._diffusion_grid(u, lo, h)
         self._substance_shape = getattr(self, "_substance_shape", {})
-        self._substance_shape[sim] = tuple(u.shape)
-        self._check(self._lib.bdm_set_substance(self._h, sim, C.byref(g), ptr, float(nu), float(mu), float(quantity),
-                                                float(weight), flags))
+        self._substance_shape[(sim, kind)] = tuple(u.shape)
+        self._check(self._lib.bdm_set_substance(self._h, sim, int(kind), C.byref(g), ptr, float(nu), float(mu),
+                                                float(quantity), float(weight), flags))
 
-    def clear_substance(self, sim: int):
-        self._check(self._lib.bdm_set_substance(self._h, sim, None, None, 0.0, 0.0, 0.0, 0.0, 0))
+    def clear_substance(self, sim: int, kind: int = 0):
+        self._check(self._lib.bdm_set_substance(self._h, sim, int(kind), None, None, 0.0, 0.0, 0.0, 0.0, 0))
 
-    def get_substance(self, sim: int) -> np.ndarray:
+    def get_substance(self, sim: int, kind: int = 0) -> np.ndarray:
         """The substance's concentrations, shape (nz, ny, nx) as set."""
         n = C.c_int64()
-        rc = self._lib.bdm_get_substance(self._h, sim, None, 0, C.byref(n), 0)
+        rc = self._lib.bdm_get_substance(self._h, sim, int(kind), None, 0, C.byref(n), 0)
         self._check_size_query(rc, n)
-        out = np.empty(getattr(self, "_substance_shape", {}).get(sim, (n.value,)), np.float64)
-        self._check(self._lib.bdm_get_substance(self._h, sim, _dptr(out), out.size, C.byref(n), 0))
+        out = np.empty(getattr(self, "_substance_shape", {}).get((sim, kind), (n.value,)), np.float64)
+        self._check(self._lib.bdm_get_substance(self._h, sim, int(kind), _dptr(out), out.size, C.byref(n), 0))
         return out
 
     # -- epidemiology (§4.6.3, Algorithms 3-5) -------------------------------

@@ -170,6 +170,7 @@ struct DevCtx {
   int32_t *order;             // simulations in slot-region order (-1 padded)
   unsigned long long *tstat;  // per scan tile: stamp << 34 | state << 32 | sum (look-back)
   uint64_t *qkey;             // per slot: packed box of the last query build (queries only)
+  uint8_t *kind;              // agent kinds by ID (slot region base + ID), or NULL: every agent kind 0
   int32_t *ovf;               // FP64 path: cells with more overlapping partners than the row kernel keeps;
                               // in-place context: the box leaders of every colour
   int32_t n_sims;

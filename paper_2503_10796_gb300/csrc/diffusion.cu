@@ -84,12 +84,21 @@ __device__ __forceinline__ double diff_at(const double *u, const DiffGrid &g, in
 // `quantity` to its box.  The additions to one box commute exactly (equal
 // addends), so the result does not depend on the order of the atomics.
 // sim >= 0: a step of bdm_step, which takes the simulation's agent count
-// from the device (n is then the simulation's capacity).
-__global__ void k_secrete(DevCtx C, int64_t base, int64_t n, int sim, DiffGrid g, double *u, double quantity) {
+// from the device (n is then the simulation's capacity) and serves the
+// agents of one kind (kind < 0: every agent).
+__device__ __forceinline__ bool of_kind(const DevCtx &C, int64_t base, int64_t slot, int kind) {
+  if (kind < 0) return true;
+  const int k = C.kind ? (int)C.kind[base + C.a.id[slot]] : 0;
+  return k == kind;
+}
+
+__global__ void k_secrete(DevCtx C, int64_t base, int64_t n, int sim, int kind, DiffGrid g, double *u,
+                          double quantity) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (sim >= 0 && i >= C.ss[sim].n) return;
   if (i >= n) return;
   const int64_t slot = base + i;
+  if (!of_kind(C, base, slot, kind)) return;
   int64_t b0, b1, b2;
   if (!diff_box(g, C.a.x[slot], C.a.y[slot], C.a.z[slot], b0, b1, b2)) return;
   atomicAdd(&u[b0 + g.n[0] * (b1 + g.n[1] * b2)], quantity);
@@ -99,12 +108,13 @@ __global__ void k_secrete(DevCtx C, int64_t base, int64_t n, int sim, DiffGrid g
 // normalized central-difference gradient of its box; the grid is only read.
 // Agents that move are marked changed (their box must be recomputed and
 // they disturb static neighbours).
-__global__ void k_chemotaxis(DevCtx C, int64_t base, int64_t n, int sim, DiffGrid g, const double *u,
+__global__ void k_chemotaxis(DevCtx C, int64_t base, int64_t n, int sim, int kind, DiffGrid g, const double *u,
                              double weight) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (sim >= 0 && i >= C.ss[sim].n) return;
   if (i >= n) return;
   const int64_t slot = base + i;
+  if (!of_kind(C, base, slot, kind)) return;
   const double x = C.a.x[slot], y = C.a.y[slot], z = C.a.z[slot];
   int64_t b0, b1, b2;
   if (!diff_box(g, x, y, z, b0, b1, b2)) return;
@@ -145,25 +155,37 @@ void launch_diffuse_step(cudaStream_t st, const double *in, double *out, const D
 void launch_secrete(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const DiffGrid &g, double *u,
                     double quantity) {
   if (n <= 0) return;
-  k_secrete<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, -1, g, u, quantity);
+  k_secrete<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, -1, -1, g, u, quantity);
 }
 
-void launch_secrete_step(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t cap, const DiffGrid &g,
-                         double *u, double quantity) {
+void launch_secrete_step(const DevCtx &C, cudaStream_t st, int sim, int kind, int64_t base, int64_t cap,
+                         const DiffGrid &g, double *u, double quantity) {
   if (cap <= 0) return;
-  k_secrete<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, base, cap, sim, g, u, quantity);
+  k_secrete<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, base, cap, sim, kind, g, u, quantity);
 }
 
-void launch_chemotaxis_step(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t cap, const DiffGrid &g,
-                            const double *u, double weight) {
+void launch_chemotaxis_step(const DevCtx &C, cudaStream_t st, int sim, int kind, int64_t base, int64_t cap,
+                            const DiffGrid &g, const double *u, double weight) {
   if (cap <= 0) return;
-  k_chemotaxis<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, base, cap, sim, g, u, weight);
+  k_chemotaxis<<<blocks_for(cap, kThreads), kThreads, 0, st>>>(C, base, cap, sim, kind, g, u, weight);
+}
+
+// Kinds of the agents that removal renumbers: hole[k] takes mover[k]'s.
+__global__ void k_kinds_move(uint8_t *kind, int64_t base, const int64_t *hole, const int64_t *mover, int64_t np) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < np) kind[base + hole[k]] = kind[base + mover[k]];
+}
+
+void launch_kinds_move(const DevCtx &C, cudaStream_t st, int64_t base, const int64_t *hole, const int64_t *mover,
+                       int64_t np) {
+  if (!C.kind || np <= 0) return;
+  k_kinds_move<<<blocks_for(np, kThreads), kThreads, 0, st>>>(C.kind, base, hole, mover, np);
 }
 
 void launch_chemotaxis(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n, const DiffGrid &g, const double *u,
                        double weight) {
   if (n <= 0) return;
-  k_chemotaxis<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, -1, g, u, weight);
+  k_chemotaxis<<<blocks_for(n, kThreads), kThreads, 0, st>>>(C, base, n, -1, -1, g, u, weight);
 }
 
 }  // namespace bdm

@@ -3,6 +3,7 @@
 // sequence (captured once into a CUDA graph and replayed), per-stage CUDA
 // event profiling and error reporting.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -61,7 +62,8 @@ struct bdm_ctx {
     int64_t total = 0;
     double nu = 0, mu = 0, quantity = 0, weight = 0;
   };
-  std::vector<Substance> subst;
+  static constexpr int kKinds = 4;             // agent kinds with a substance of their own
+  std::vector<std::array<Substance, 4>> subst;  // per simulation and kind
   bool grid_reuse = false;   // incremental grid: keep the last build while agents stay in their skins
   bool host_touched = true;  // a call since the last bdm_step changed agents or the table
   bool inplace = false;      // the in-place execution context (every simulation)
@@ -327,17 +329,20 @@ void launch_iteration(bdm_ctx *c, int sort) {
   }
   // the simulations' substances: secretion at the new positions, one
   // diffusion step, chemotaxis up the diffused gradient
-  for (int s = 0; s < c->n_sims; ++s) {
-    const bdm_ctx::Substance &S = c->subst[s];
-    if (!S.on) continue;
-    stage_begin(c, 8);
-    const SimConst &sc = c->h_sc[s];
-    launch_secrete_step(D, st, s, sc.base, sc.cap, S.g, S.u, S.quantity);
-    launch_diffuse_step(st, S.u, S.next, S.g, S.nu, S.mu, sc.dt);
-    cudaMemcpyAsync(S.u, S.next, sizeof(double) * (size_t)S.total, cudaMemcpyDeviceToDevice, st);
-    launch_chemotaxis_step(D, st, s, sc.base, sc.cap, S.g, S.u, S.weight);
-    stage_end(c);
-  }
+  // (per agent kind: the kinds touch neither each other's agents nor
+  // substances, so their order does not matter)
+  for (int s = 0; s < c->n_sims; ++s)
+    for (int k = 0; k < bdm_ctx::kKinds; ++k) {
+      const bdm_ctx::Substance &S = c->subst[s][k];
+      if (!S.on) continue;
+      stage_begin(c, 8);
+      const SimConst &sc = c->h_sc[s];
+      launch_secrete_step(D, st, s, k, sc.base, sc.cap, S.g, S.u, S.quantity);
+      launch_diffuse_step(st, S.u, S.next, S.g, S.nu, S.mu, sc.dt);
+      cudaMemcpyAsync(S.u, S.next, sizeof(double) * (size_t)S.total, cudaMemcpyDeviceToDevice, st);
+      launch_chemotaxis_step(D, st, s, k, sc.base, sc.cap, S.g, S.u, S.weight);
+      stage_end(c);
+    }
   if (c->any_sort && sort == 2) {
     stage_begin(c, 7);
     launch_cell_order(D, st, c->d_sort);
@@ -630,7 +635,7 @@ int bdm_create(const bdm_params *per_sim, int32_t n_sims, int64_t max_agents_tot
   for (int s = 0; s < n_sims; ++s)
     if (per_sim[s].boundary == BDM_BOUNDARY_TOROIDAL) c->inplace_colours = 27;
   c->n_set.assign(n_sims, -1);
-  c->subst.assign(n_sims, bdm_ctx::Substance{});
+  c->subst.assign(n_sims, std::array<bdm_ctx::Substance, 4>{});
   c->h_iter.assign(n_sims, 0);
   c->need_radix.assign(n_sims, 1);
   for (int s = 0; s < n_sims; ++s) {
@@ -815,6 +820,7 @@ int bdm_set_agents(bdm_ctx *c, int32_t sim, int64_t n, const double *xyz, const 
   c->D.total_slots = c->used_slots;
   upload_consts(c);
   launch_set_agents(c->D, c->stream, sim, sc.base, n, sc.cap, dx, dd);
+  if (c->D.kind) cudaMemsetAsync(c->D.kind + sc.base, 0, (size_t)sc.cap, c->stream);  // every agent kind 0
   SimState s0;
   memset(&s0, 0, sizeof(s0));
   s0.n = n;
@@ -1027,6 +1033,7 @@ int bdm_set_state(bdm_ctx *c, int32_t sim, const void *buf, int64_t size_bytes) 
   c->D.total_slots = c->used_slots;
   upload_consts(c);
   launch_state_scatter(c->D, c->stream, sim, base, h.n, cap, c->d_xfer);
+  if (c->D.kind) cudaMemsetAsync(c->D.kind + base, 0, (size_t)cap, c->stream);  // kinds are not in a state
   SimState s0;
   memset(&s0, 0, sizeof(s0));
   s0.n = h.n;
@@ -1094,6 +1101,7 @@ int bdm_remove_agents(bdm_ctx *c, int32_t sim, int64_t n_ids, const int64_t *ids
     cudaMemcpyAsync(dm, movers.data(), sizeof(int64_t) * (size_t)np, cudaMemcpyHostToDevice, c->stream);
   }
   launch_state_remove(c->stream, c->d_xfer, n, nn, dh, dm, np);
+  launch_kinds_move(c->D, c->stream, c->h_sc[sim].base, dh, dm, np);
   // the arrays laid out for n agents hold the survivors in their first n' rows
   launch_state_scatter(c->D, c->stream, sim, c->h_sc[sim].base, nn, c->h_sc[sim].cap, c->d_xfer, n);
   // the simulation keeps its counters and last grid; the last iteration's
@@ -1266,12 +1274,37 @@ int bdm_secrete(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, double *u,
   return BDM_OK;
 }
 
-int bdm_set_substance(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, const double *u, double nu, double mu,
-                      double quantity, double weight, int32_t flags) {
+int bdm_set_agent_kinds(bdm_ctx *c, int32_t sim, int64_t n, const uint8_t *kinds) {
   if (!c) return BDM_E_INVAL;
   int rc = check_sim(c, sim);
   if (rc) return rc;
-  bdm_ctx::Substance &S = c->subst[sim];
+  if (c->n_set[sim] < 0) return fail(c, BDM_E_STATE, "no agents set");
+  if (n < 0 || (n > 0 && !kinds)) return fail(c, BDM_E_INVAL, "n < 0 or NULL kinds");
+  SimState s;
+  rc = read_state(c, sim, &s);
+  if (rc) return rc;
+  if (n != s.n) return fail(c, BDM_E_INVAL, "n differs from the agent count " + std::to_string(s.n));
+  for (int64_t i = 0; i < n; ++i)
+    if (kinds[i] >= bdm_ctx::kKinds) return fail(c, BDM_E_INVAL, "kinds must be 0 to 3");
+  if (!c->D.kind) {
+    rc = dalloc(c, &c->D.kind, (size_t)c->max_total, "agent kinds");
+    if (rc) return rc;
+    cudaMemsetAsync(c->D.kind, 0, (size_t)c->max_total, c->stream);
+    c->graph_dirty = true;  // the graphs hold the context's pointers
+  }
+  if (n > 0) cudaMemcpyAsync(c->D.kind + c->h_sc[sim].base, kinds, (size_t)n, cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "uploading agent kinds");
+  return BDM_OK;
+}
+
+int bdm_set_substance(bdm_ctx *c, int32_t sim, int32_t kind, const bdm_diffusion_grid *g, const double *u, double nu,
+                      double mu, double quantity, double weight, int32_t flags) {
+  if (!c) return BDM_E_INVAL;
+  int rc = check_sim(c, sim);
+  if (rc) return rc;
+  if (kind < 0 || kind >= bdm_ctx::kKinds) return fail(c, BDM_E_INVAL, "kind must be 0 to 3");
+  bdm_ctx::Substance &S = c->subst[sim][kind];
   if (!g) {
     // remove the substance
     cudaStreamSynchronize(c->stream);
@@ -1317,11 +1350,13 @@ int bdm_set_substance(bdm_ctx *c, int32_t sim, const bdm_diffusion_grid *g, cons
   return BDM_OK;
 }
 
-int bdm_get_substance(bdm_ctx *c, int32_t sim, double *u, int64_t cap, int64_t *n_out, int32_t flags) {
+int bdm_get_substance(bdm_ctx *c, int32_t sim, int32_t kind, double *u, int64_t cap, int64_t *n_out,
+                      int32_t flags) {
   if (!c) return BDM_E_INVAL;
   int rc = check_sim(c, sim);
   if (rc) return rc;
-  const bdm_ctx::Substance &S = c->subst[sim];
+  if (kind < 0 || kind >= bdm_ctx::kKinds) return fail(c, BDM_E_INVAL, "kind must be 0 to 3");
+  const bdm_ctx::Substance &S = c->subst[sim][kind];
   if (!S.on) return fail(c, BDM_E_STATE, "the simulation has no substance");
   if (n_out) *n_out = S.total;
   if (cap < S.total || !u) return fail(c, BDM_E_CAPACITY, "buffer smaller than the grid");

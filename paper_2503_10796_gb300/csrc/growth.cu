@@ -286,6 +286,7 @@ __global__ void k_divide(DevCtx C, GrowBufs B) {
   C.a.flags[j] = FLAG_CHANGED;
   C.a.nnz[j] = 0;
   C.a.id[j] = (int32_t)(n0 + r);
+  if (C.kind) C.kind[sc.base + n0 + r] = C.kind[sc.base + id];  // a daughter of the mother's kind
   C.a.pkey[j] = C.a.pkey[slot];
   C.a.rank[j] = 0;
 }

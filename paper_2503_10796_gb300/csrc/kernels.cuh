@@ -59,10 +59,13 @@ void launch_chemotaxis(const DevCtx &C, cudaStream_t st, int64_t base, int64_t n
                        double weight);
 // The same two inside bdm_step: the agent count from the device, launched
 // over the simulation's capacity.
-void launch_secrete_step(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t cap, const DiffGrid &g,
-                         double *u, double quantity);
-void launch_chemotaxis_step(const DevCtx &C, cudaStream_t st, int sim, int64_t base, int64_t cap, const DiffGrid &g,
-                            const double *u, double weight);
+void launch_secrete_step(const DevCtx &C, cudaStream_t st, int sim, int kind, int64_t base, int64_t cap,
+                         const DiffGrid &g, double *u, double quantity);
+void launch_chemotaxis_step(const DevCtx &C, cudaStream_t st, int sim, int kind, int64_t base, int64_t cap,
+                            const DiffGrid &g, const double *u, double weight);
+// Removal's renumbering applied to the agent kinds (by ID).
+void launch_kinds_move(const DevCtx &C, cudaStream_t st, int64_t base, const int64_t *hole, const int64_t *mover,
+                       int64_t np);
 
 // sir.cu (epidemiology use case): one step on the query cells of `sim`
 void launch_sir_step(const DevCtx &C, cudaStream_t st, int sim, int64_t cell_base, int64_t n, int64_t base,

@@ -87,3 +87,72 @@ def test_substance_errors(orc):
     with pytest.raises(binding.BdmError) as e:
         c2.set_substance(0, np.zeros((2, 2, 2)), [0, 0, 0], [5, 5, 5], NU, MU, Q, W)
     assert e.value.code == -1
+
+
+def oracle_kinds_iteration(o, us, kinds, dt):
+    """The oracle's iteration with a substance per kind (each kind's agents
+    secrete into and follow their own substance)."""
+    import oracle
+    o.step(1)
+    x, _, _ = o.get()
+    for k, u in us.items():
+        m = kinds == k
+        oracle.secrete(u, LO, H, x[m], Q)
+        oracle.diffuse(u, H, NU, MU, dt, 1)
+        x[m] = oracle.chemotaxis(u, LO, H, x[m], W)
+    o.set_positions(x)
+
+
+def test_two_kinds_soma_clustering_bit_exact(orc):
+    """Two cell kinds at random, each secreting its own substance and
+    following it (the soma-clustering benchmark of §4.6)."""
+    import oracle
+    from paper_2503_10796_gb300 import binding
+    rng = np.random.default_rng(12)
+    xyz = rng.uniform(0.0, 500.0, (3000, 3))
+    d = rng.uniform(8.0, 12.0, 3000)
+    pop = workloads.Population(xyz, d, workloads.SimParams(precision=0))
+    kinds = (rng.random(pop.n) < 0.5).astype(np.uint8)
+    ctx = binding.Context(binding.make_params(pop.params), pop.n + 16)
+    ctx.set_agents(0, pop.xyz, pop.diameter)
+    ctx.set_agent_kinds(0, kinds)
+    us = {k: rng.uniform(0.0, 1.0, SHAPE) for k in (0, 1)}
+    for k, u in us.items():
+        ctx.set_substance(0, u, LO, H, NU, MU, Q, W, kind=k)
+    o = oracle.Sim(pop.xyz, pop.diameter, pop.params)
+    for t in range(6):
+        ctx.step(1)
+        oracle_kinds_iteration(o, us, kinds, pop.params.dt)
+        assert np.array_equal(ctx.get_agents(0)[0], o.get()[0]), t
+        for k, u in us.items():
+            assert np.array_equal(ctx.get_substance(0, kind=k), u), (t, k)
+
+
+def test_kinds_follow_division_and_removal(orc):
+    import oracle
+    from paper_2503_10796_gb300 import binding
+    pop = workloads.growth_division(shape=(4, 4, 4), cap_factor=8, precision=0)
+    kinds = (np.arange(pop.n) % 2).astype(np.uint8)
+    ctx = binding.Context(binding.make_params(pop.params), pop.params.capacity + 16)
+    ctx.set_agents(0, pop.xyz, pop.diameter)
+    ctx.set_agent_kinds(0, kinds)
+    o = oracle.Sim(pop.xyz, pop.diameter, pop.params)
+    ctx.step(15)  # every agent divides at iteration 14: daughter n + i of mother i
+    o.step(15)
+    assert ctx.count(0) == o.n == 2 * pop.n
+    kinds = np.concatenate([kinds, kinds])
+    # removal renumbers by the swaps of §5.3.2: track the survivors' kinds by position
+    x_before, _, _ = o.get()
+    gone = np.random.default_rng(2).choice(o.n, 40, replace=False)
+    ctx.remove_agents(0, gone)
+    o.remove(gone)
+    x_after, _, _ = o.get()
+    where = {tuple(p): i for i, p in enumerate(x_before)}
+    kinds = kinds[[where[tuple(p)] for p in x_after]]
+    us = {1: np.random.default_rng(4).uniform(0.0, 1.0, SHAPE)}
+    ctx.set_substance(0, us[1], LO, H, NU, MU, Q, W, kind=1)
+    for t in range(4):
+        ctx.step(1)
+        oracle_kinds_iteration(o, us, kinds, pop.params.dt)
+        assert np.array_equal(ctx.get_agents(0)[0], o.get()[0]), t
+    assert np.array_equal(ctx.get_substance(0, kind=1), us[1])
