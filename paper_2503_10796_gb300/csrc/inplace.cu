@@ -192,16 +192,44 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_inplace(DevCtx C, int colour)
     const int nbox = nx * ny * nzb;
     const float Lh = s.Lh;
     const float grow = __fadd_rn(__fmul_rn(2.f, __double2float_ru(sc.max_disp)), s.marg);
+    // The box's agents share its stencil: lane b < nbox holds stencil box b's
+    // first cell and live count, and every lane the inclusive prefix of the
+    // counts up to its own (lanes from nbox on hold the total), read once per
+    // box instead of box by box for every agent.
+    int64_t bj0 = 0;
+    uint32_t bcnt = 0u;
+    if (lane < nbox) {
+      const int dx = t.xlo + lane % nx, dy = t.ylo + (lane / nx) % ny, dz = t.zlo + lane / (nx * ny);
+      const unsigned long long e = t.e[t.box(dx, dy, dz)];
+      bcnt = ent_live(e, stamp);
+      bj0 = ent_start(e);
+    }
+    uint32_t bincl = bcnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, bincl, d);
+      bincl += lane >= d ? y : 0u;
+    }
+    const uint32_t ntot = __shfl_sync(FULL, bincl, 31);
+    // IDs of the box's agents, one per lane, when they fit the warp
+    const uint32_t bid = (nb <= 32u && (uint32_t)lane < nb) ? agent_id(C, b0 + lane) : 0xFFFFFFFFu;
     int64_t last_id = -1;
     for (uint32_t done = 0; done < nb; ++done) {
       // the box's agent with the next ID
       uint32_t myid = 0xFFFFFFFFu;
       int64_t myq = -1;
-      for (uint32_t m = (uint32_t)lane; m < nb; m += 32u) {
-        const uint32_t id = agent_id(C, b0 + m);
-        if ((int64_t)id > last_id && id < myid) {
-          myid = id;
-          myq = b0 + m;
+      if (nb <= 32u) {
+        if ((uint32_t)lane < nb && (int64_t)bid > last_id) {
+          myid = bid;
+          myq = b0 + lane;
+        }
+      } else {
+        for (uint32_t m = (uint32_t)lane; m < nb; m += 32u) {
+          const uint32_t id = agent_id(C, b0 + m);
+          if ((int64_t)id > last_id && id < myid) {
+            myid = id;
+            myq = b0 + m;
+          }
         }
       }
       const uint32_t qid = __reduce_min_sync(FULL, myid);
@@ -212,22 +240,31 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_inplace(DevCtx C, int colour)
       const int32_t sq = C.c.slot[q];
       const double4_32a o = current(C, q);
       const float4 a0 = C.c.r0[q];
-      // the candidates that pass the filter, compacted
+      // the candidates that pass the filter, compacted in stencil-box order
+      // and, within a box, in cell order: 32 candidates of the stencil's
+      // ntot per round, each lane finding its box by a binary search over
+      // the prefix of the counts
       uint32_t nc = 0;
-      for (int bb = 0; bb < nbox; ++bb) {
-        const int dx = t.xlo + bb % nx, dy = t.ylo + (bb / nx) % ny, dz = t.zlo + bb / (nx * ny);
-        const unsigned long long e = t.e[t.box(dx, dy, dz)];
-        const uint32_t cnt = ent_live(e, stamp);
-        const int64_t j0 = ent_start(e);
-        for (uint32_t m0 = 0; m0 < cnt; m0 += 32u) {
-          const uint32_t m = m0 + (uint32_t)lane;
-          const int64_t j = j0 + m;
-          const bool pass = m < cnt && j != q && may_overlap(C, a0, j, dx, dy, dz, Lh, grow);
-          const unsigned B = __ballot_sync(FULL, pass);
-          const uint32_t k = nc + (uint32_t)__popc(B & lt);
-          if (pass && k < (uint32_t)kIpCand) sh.cand[k] = (uint32_t)j;
-          nc += (uint32_t)__popc(B);
+      for (uint32_t base = 0; base < ntot; base += 32u) {
+        const uint32_t c = base + (uint32_t)lane;
+        int lo = 0, hi = 31;  // the first lane whose inclusive prefix exceeds c
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+          const int mid = (lo + hi) >> 1;
+          const uint32_t v = __shfl_sync(FULL, bincl, mid);
+          if (v > c) hi = mid;
+          else lo = mid + 1;
         }
+        lo = lo < 31 ? lo : 31;  // only lanes past the last candidate get beyond
+        const uint32_t ib = __shfl_sync(FULL, bincl, lo), nbx = __shfl_sync(FULL, bcnt, lo);
+        const int64_t jb = __shfl_sync(FULL, bj0, lo);
+        const int64_t j = jb + (int64_t)(c - (ib - nbx));
+        const int dx = t.xlo + lo % nx, dy = t.ylo + (lo / nx) % ny, dz = t.zlo + lo / (nx * ny);
+        const bool pass = c < ntot && j != q && may_overlap(C, a0, j, dx, dy, dz, Lh, grow);
+        const unsigned B = __ballot_sync(FULL, pass);
+        const uint32_t k = nc + (uint32_t)__popc(B & lt);
+        if (pass && k < (uint32_t)kIpCand) sh.cand[k] = (uint32_t)j;
+        nc += (uint32_t)__popc(B);
       }
       __syncwarp();
       // the overlapping pairs at the current positions, 32 at a time
@@ -254,24 +291,28 @@ __global__ void __launch_bounds__(32 * kIpWarps) k_inplace(DevCtx C, int colour)
       double fx = 0.0, fy = 0.0, fz = 0.0;
       uint32_t nnz = 0, novl = 0;
       if (!select) {
-        uint32_t n2 = 32;  // the sort's size: a power of two >= n
-        while (n2 < n) n2 <<= 1;
-        for (uint32_t k = n + (uint32_t)lane; k < n2; k += 32u) sh.key[k] = ~0ull;
-        __syncwarp();
-        for (uint32_t size = 2; size <= n2; size <<= 1)
-          for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t i = (uint32_t)lane; i < n2; i += 32u) {
-              const uint32_t jx = i ^ stride;
-              if (jx > i) {
-                const unsigned long long ka = sh.key[i], kb = sh.key[jx];
-                if ((ka > kb) == ((i & size) == 0)) {
-                  sh.key[i] = kb;
-                  sh.key[jx] = ka;
+        if (n > 1u) {  // one pair or none needs no sort
+          uint32_t n2 = 32;  // the sort's size: a power of two >= n
+          while (n2 < n) n2 <<= 1;
+          for (uint32_t k = n + (uint32_t)lane; k < n2; k += 32u) sh.key[k] = ~0ull;
+          __syncwarp();
+          for (uint32_t size = 2; size <= n2; size <<= 1)
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+              for (uint32_t i = (uint32_t)lane; i < n2; i += 32u) {
+                const uint32_t jx = i ^ stride;
+                if (jx > i) {
+                  const unsigned long long ka = sh.key[i], kb = sh.key[jx];
+                  if ((ka > kb) == ((i & size) == 0)) {
+                    sh.key[i] = kb;
+                    sh.key[jx] = ka;
+                  }
                 }
               }
+              __syncwarp();
             }
-            __syncwarp();
-          }
+        } else {
+          __syncwarp();  // the one pair's entries, written by any lane
+        }
         if (lane == 0) {
           for (uint32_t r = 0; r < n; ++r) {
             const uint32_t k = (uint32_t)sh.key[r];

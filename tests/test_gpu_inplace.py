@@ -78,20 +78,28 @@ def test_inplace_trajectory_bit_exact(orc, scene, sort_interval):
     assert not np.array_equal(c.get()[0], x), name
 
 
-def test_inplace_crowd_beyond_the_partner_list(orc):
-    """Every agent of a tight clump overlaps all 99 others, more than the
-    48 partners the kernel sorts in place: the selection loop adds them."""
+@pytest.mark.parametrize("n", [32, 33, 100, 400, 600])
+def test_inplace_crowd_beyond_the_partner_list(orc, n):
+    """Every agent of a tight clump overlaps all others.  Up to 32 agents of
+    a box keep their IDs in the warp's lanes (33 take the loop over the box);
+    up to 256 overlapping partners are sorted in shared memory (100); beyond
+    that (400), or beyond the 512 candidates the filter keeps (600), the
+    selection loop adds the partners one ID after the other."""
     rng = np.random.default_rng(9)
-    pop = workloads.Population(100.0 + rng.uniform(0.0, 5.0, (100, 3)), rng.uniform(9.5, 10.5, 100),
+    pop = workloads.Population(100.0 + rng.uniform(0.0, 5.0, (n, 3)), rng.uniform(9.5, 10.5, n),
                                workloads.SimParams(precision=0, dt=0.01))
     ctx = ctx_for(pop)
     o = orc_for(pop)
     for t in range(3):
         ctx.step(1)
         o.step(1)
-        assert np.array_equal(ctx.get_agents(0)[0], o.get()[0]), t
-    _, _, _, ov = ctx.forces(0, overlaps=True)
-    assert ov.max() > 48
+        assert np.array_equal(ctx.get_agents(0)[0], o.get()[0]), (n, t)
+        F, nnz, _ = ctx.forces(0)
+        F_o, _, nnz_o, _, _ = o.last()
+        assert np.array_equal(F, F_o) and np.array_equal(nnz, np.minimum(nnz_o, 255)), (n, t)
+        if t == 0:  # the first agent of the iteration met the whole clump unmoved
+            _, _, _, ov = ctx.forces(0, overlaps=True)
+            assert ov.max() == n - 1, (n, ov.max())
 
 
 def test_inplace_growth_and_batched_sims_bit_exact(orc):
