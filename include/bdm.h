@@ -341,11 +341,14 @@ typedef struct {
                               stencil, §4.4.3; the static check's stencil would
                               change, so those simulations keep the thesis's rule) */
   int32_t iter_batch;      /* iterations per replayed CUDA graph, 1 to 64 (0 = 1) */
-  int32_t test_flags;      /* test hook, 0 in normal use.  1: the ordered grid scan's
-                              bounded wait looks for a word that nothing writes and
-                              gives up after 64 polls per tile, so that the next
+  int32_t test_flags;      /* test hooks, 0 in normal use.  Bit 0: the ordered grid
+                              scan's bounded wait looks for a word that nothing writes
+                              and gives up after 64 polls per tile, so that the next
                               bdm_sync reports BDM_E_TIMEOUT (that iteration's
-                              results are undefined; the context stays usable) */
+                              results are undefined; the context stays usable).
+                              Bit 1: the in-place context runs its boxes on groups of
+                              8 lanes (its form for 131,072 slots and more) whatever
+                              the context's size; results are the same */
   int32_t grid_reuse;      /* 1: incremental grid (the thesis adapts its grid to
                               incremental position updates, §6.2.5): an iteration
                               keeps the last build's grid while every agent stays

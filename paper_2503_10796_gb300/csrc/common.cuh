@@ -111,7 +111,13 @@ struct Globals {
 // Test hooks of Globals::test_flags.  TEST_SCAN_TIMEOUT: the ordered scan's
 // look-back waits for a tile word that no tile publishes and gives up after
 // kTestSpin polls, so that a test sees its bounded wait run out.
-enum : uint32_t { TEST_SCAN_TIMEOUT = 1u };
+// TEST_INPLACE_NARROW (read on the host): the in-place context runs its
+// boxes on groups of 8 lanes whatever the population's size.
+enum : uint32_t { TEST_SCAN_TIMEOUT = 1u, TEST_INPLACE_NARROW = 2u };
+
+// Slots from which the in-place context runs its boxes on groups of 8 lanes
+// (four boxes per warp) rather than a warp per box.
+constexpr int64_t kInplaceNarrowSlots = 131072;
 
 struct Agents {               // storage arrays (per slot)
   double *x, *y, *z, *d, *v;

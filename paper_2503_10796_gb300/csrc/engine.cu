@@ -303,7 +303,7 @@ void launch_iteration(bdm_ctx *c, int sort) {
   stage_begin(c, 2);
   // the cell order reaches the storage only when this iteration re-sorts
   // into it: only then must it follow the leaders' storage order
-  launch_scan(D, st, 1, ((c->any_sort && sort == 2) || c->test_flags) ? 1 : 0);
+  launch_scan(D, st, 1, ((c->any_sort && sort == 2) || (c->test_flags & TEST_SCAN_TIMEOUT)) ? 1 : 0);
   stage_end(c);
   stage_begin(c, 3);
   launch_place(D, st, 1, pl.zero_f32 ? 1 : 0);
@@ -311,7 +311,10 @@ void launch_iteration(bdm_ctx *c, int sort) {
   if (c->inplace) {
     // S4 + S5 of the in-place context: one launch per box colour
     stage_begin(c, 4);
-    launch_inplace(D, st, c->inplace_colours);
+    // boxes in groups of 8 lanes once the colours have boxes enough to
+    // occupy them (or under the test hook), else a warp per box
+    const bool narrow = D.total_slots >= kInplaceNarrowSlots || (c->test_flags & TEST_INPLACE_NARROW);
+    launch_inplace(D, st, c->inplace_colours, narrow);
     stage_end(c);
   } else {
     stage_begin(c, 4);
@@ -1637,8 +1640,8 @@ int bdm_set_tuning(bdm_ctx *c, const bdm_tuning *t) {
   if (t->box_scale_pct != 0 && (t->box_scale_pct < 100 || t->box_scale_pct > 400))
     return fail(c, BDM_E_INVAL, "box_scale_pct must be 0 or 100 to 400");
   if (t->iter_batch < 0 || t->iter_batch > 64) return fail(c, BDM_E_INVAL, "iter_batch must be 0 to 64");
-  if (t->test_flags != 0 && t->test_flags != (int32_t)TEST_SCAN_TIMEOUT)
-    return fail(c, BDM_E_INVAL, "test_flags must be 0 or 1");
+  if (t->test_flags & ~(int32_t)(TEST_SCAN_TIMEOUT | TEST_INPLACE_NARROW))
+    return fail(c, BDM_E_INVAL, "test_flags must be 0 to 3");
   if (t->reserved) return fail(c, BDM_E_INVAL, "reserved fields must be 0");
   if (t->grid_reuse != 0 && t->grid_reuse != 1) return fail(c, BDM_E_INVAL, "grid_reuse must be 0 or 1");
   if (t->grid_reuse)

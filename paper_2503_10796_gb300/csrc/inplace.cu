@@ -11,34 +11,55 @@
 // its own position, so all boxes of a colour run at once.
 //
 // Per iteration: the box leaders (first cell of each occupied box) are
-// listed by colour (count, prefix, fill); then one launch per colour runs a
-// warp per box over that colour's list.  The warp takes the box's agents in
-// ascending ID, one after the other.  For each, its lanes filter the
-// stencil's candidates in FP32 on the records of the iteration's start
-// (widened by twice the clamp: each agent moves once, by at most the clamp,
-// so every pair that overlaps at the current positions passes), compact
-// them, evaluate the definition (pair64) on the current positions 32 at a
-// time, sort the overlapping pairs by partner ID (bitonic, in shared
-// memory) and add them in that order; lane 0 then applies the displacement
-// (disp64) and the boundary condition before the next agent.  A crowd beyond
-// the shared-memory lists takes a selection of the next partner ID.  Ghost
-// agents stay in place.  The result equals the oracle's in-place iteration
-// bit for bit.
+// listed by colour (count, prefix, fill); then one launch per colour runs
+// groups of eight lanes, one box each, four boxes to a warp, so that one
+// FP64 instruction serves the agents of several boxes.  A group first loads
+// its box's stencil (first cell and live count of each of the 27 boxes,
+// with their prefix) into shared memory.  It then takes the box's agents in
+// ascending ID, one after the other; each group takes one agent per pass of
+// the loop, so the groups of a warp run side by side.  For each agent, its
+// lanes filter the stencil's candidates in FP32 on the records of the
+// iteration's start (widened by twice the clamp: each agent moves once, by
+// at most the clamp, so every pair that overlaps at the current positions
+// passes), compact them, evaluate the definition (pair64) on the current
+// positions, sort the overlapping pairs by partner ID (bitonic, in shared
+// memory) and add them in that order; the group's first lane then applies
+// the displacement (disp64) and the boundary condition before the next
+// agent.  A crowd beyond the shared-memory lists takes a selection of the
+// next partner ID.  Ghost agents stay in place.  The result equals the
+// oracle's in-place iteration bit for bit.
 #include "pair.cuh"
 
 namespace bdm {
 namespace {
 
-constexpr int kIpWarps = 4;      // warps (boxes) per block
-constexpr int kIpCand = 512;     // candidates passing the filter, per agent
-constexpr int kIpCap = 256;      // overlapping pairs sorted in shared memory (a power of two)
-constexpr int kIpThreads = 128;  // threads of the list kernels
+constexpr int kIpWarps = 2;        // warps per block
+constexpr int kIpBlocksPerSM = 8;  // 16 warps per SM
+constexpr int kIpThreads = 128;    // threads of the list kernels
 
-struct IpShared {
-  uint32_t cand[kIpCand];            // cells that passed the filter
-  unsigned long long key[kIpCap];    // partner ID << 32 | index of the contribution
-  double gx[kIpCap], gy[kIpCap], gz[kIpCap];
-  uint32_t flags[kIpCap];            // bit 0 non-zero force, bit 1 a direction (distance > 0)
+// G lanes per box: 8 (four boxes of a colour per warp) for large
+// populations, 32 (a box per warp) for small ones, where the colours have
+// too few boxes to occupy the groups and a whole warp serves an agent faster.
+template <int G>
+struct IpShared {                   // one per lane group
+  static constexpr int kCand = G == 32 ? 512 : 128;  // candidates passing the filter, per agent
+  static constexpr int kCap = G == 32 ? 256 : 64;    // overlapping pairs sorted here (a power of two)
+  unsigned long long key[kCap];     // partner ID << 32 | index of the contribution
+  double gx[kCap], gy[kCap], gz[kCap];
+  uint32_t cand[kCand];             // cells that passed the filter
+  uint32_t flags[kCap];             // bit 0 non-zero force, bit 1 a direction (distance > 0)
+  uint32_t bj[27], bn[27], bp[27];  // stencil boxes: first cell, live count, exclusive prefix of the counts
+};
+
+// The box a lane group works on.
+struct IpBox {
+  int64_t b0;                 // its first cell
+  uint32_t nb;                // its agents
+  uint32_t ntot;              // candidates of its stencil
+  uint32_t bid;               // this lane's agent ID when the agents fit the group
+  int nbox, nx, ny, xlo, ylo, zlo;
+  int sim;
+  float Lh, grow;
 };
 
 __device__ __forceinline__ uint32_t agent_id(const DevCtx &C, int64_t j) { return (uint32_t)C.a.id[C.c.slot[j]]; }
@@ -119,28 +140,82 @@ __device__ __forceinline__ bool may_overlap(const DevCtx &C, const float4 &a, in
   return s2 < __fmul_rn(R, R);
 }
 
+// Loads box b0 for a lane group (gl: lane in the group): its stencil's
+// boxes into shared memory, in the order dx fastest, then dy, then dz, with
+// the exclusive prefix of their live counts, and the IDs of its agents when
+// they fit the group.
+template <int G>
+__device__ void ip_load_box(const DevCtx &C, IpShared<G> &sh, IpBox &B, int64_t b0, uint32_t stamp, int gl,
+                            unsigned gmask) {
+  B.b0 = b0;
+  B.sim = C.c.sim[b0];
+  const SimConst &sc = C.sc[B.sim];
+  const SimState &s = C.ss[B.sim];
+  int64_t cx, cy, cz;
+  unpack_coords(C.c.pkey[b0], cx, cy, cz);
+  const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
+  B.nx = t.xhi - t.xlo + 1;
+  B.ny = t.yhi - t.ylo + 1;
+  B.nbox = B.nx * B.ny * (t.zhi - t.zlo + 1);
+  B.xlo = t.xlo;
+  B.ylo = t.ylo;
+  B.zlo = t.zlo;
+  B.Lh = s.Lh;
+  B.grow = __fadd_rn(__fmul_rn(2.f, __double2float_ru(sc.max_disp)), s.marg);
+  B.nb = ent_live(t.e[t.box(0, 0, 0)], stamp);
+  // lane gl takes stencil boxes kPer gl .. kPer gl + kPer - 1
+  constexpr int kPer = (27 + G - 1) / G;
+  uint32_t cnt[kPer], sum = 0u;
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int bb = kPer * gl + u;
+    cnt[u] = 0u;
+    if (bb < B.nbox) {
+      const int dx = t.xlo + bb % B.nx, dy = t.ylo + (bb / B.nx) % B.ny, dz = t.zlo + bb / (B.nx * B.ny);
+      const unsigned long long e = t.e[t.box(dx, dy, dz)];
+      cnt[u] = ent_live(e, stamp);
+      sh.bj[bb] = ent_start(e);
+      sh.bn[bb] = cnt[u];
+    }
+    sum += cnt[u];
+  }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int d = 1; d < G; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(gmask, incl, d, G);
+    incl += gl >= d ? y : 0u;
+  }
+  uint32_t run = incl - sum;
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int bb = kPer * gl + u;
+    if (bb < B.nbox) sh.bp[bb] = run;
+    run += cnt[u];
+  }
+  B.ntot = __shfl_sync(gmask, incl, G - 1, G);
+  B.bid = (B.nb <= (uint32_t)G && (uint32_t)gl < B.nb) ? agent_id(C, b0 + gl) : 0xFFFFFFFFu;
+  __syncwarp(gmask);
+}
+
 // The agent's force when its partners do not fit the shared-memory lists:
-// the overlapping partner with the next ID, one at a time (warp-wide search).
-__device__ void ip_selection(const DevCtx &C, const SimConst &sc, const Stencil &t, int64_t q, const double4_32a &o,
-                             const float4 &a0, uint32_t stamp, int lane, float Lh, float grow, double &fx,
-                             double &fy, double &fz, uint32_t &nnz, uint32_t &novl) {
-  const unsigned FULL = 0xffffffffu;
-  const int nx = t.xhi - t.xlo + 1, ny = t.yhi - t.ylo + 1, nzb = t.zhi - t.zlo + 1;
-  const int nbox = nx * ny * nzb;
+// the overlapping partner with the next ID, one at a time (group-wide search).
+template <int G>
+__device__ void ip_selection(const DevCtx &C, const SimConst &sc, const IpShared<G> &sh, const IpBox &B, int64_t q,
+                             const double4_32a &o, const float4 &a0, int gl, unsigned gmask, double &fx, double &fy,
+                             double &fz, uint32_t &nnz, uint32_t &novl) {
   int64_t prev = -1;
   for (;;) {
     uint32_t best = 0xFFFFFFFFu;
     int64_t bj = -1;
-    for (int bb = 0; bb < nbox; ++bb) {
-      const int dx = t.xlo + bb % nx, dy = t.ylo + (bb / nx) % ny, dz = t.zlo + bb / (nx * ny);
-      const unsigned long long e = t.e[t.box(dx, dy, dz)];
-      const uint32_t cnt = ent_live(e, stamp);
-      const int64_t j0 = ent_start(e);
-      for (uint32_t m = (uint32_t)lane; m < cnt; m += 32u) {
+    for (int bb = 0; bb < B.nbox; ++bb) {
+      const int dx = B.xlo + bb % B.nx, dy = B.ylo + (bb / B.nx) % B.ny, dz = B.zlo + bb / (B.nx * B.ny);
+      const uint32_t cnt = sh.bn[bb];
+      const int64_t j0 = sh.bj[bb];
+      for (uint32_t m = (uint32_t)gl; m < cnt; m += (uint32_t)G) {
         const int64_t j = j0 + m;
         if (j == q) continue;
         const uint32_t id = agent_id(C, j);
-        if ((int64_t)id <= prev || id >= best || !may_overlap(C, a0, j, dx, dy, dz, Lh, grow)) continue;
+        if ((int64_t)id <= prev || id >= best || !may_overlap(C, a0, j, dx, dy, dz, B.Lh, B.grow)) continue;
         double gx, gy, gz;
         bool nz, dir;
         if (pair64(sc, o, current(C, j), sc.k, sc.gamma, gx, gy, gz, nz, dir)) {
@@ -149,11 +224,11 @@ __device__ void ip_selection(const DevCtx &C, const SimConst &sc, const Stencil 
         }
       }
     }
-    const uint32_t wbest = __reduce_min_sync(FULL, best);
-    if (wbest == 0xFFFFFFFFu) break;
-    const unsigned who = __ballot_sync(FULL, best == wbest && bj >= 0);
-    const int64_t jb = __shfl_sync(FULL, bj, __ffs(who) - 1);
-    if (lane == 0) {
+    const uint32_t gbest = __reduce_min_sync(gmask, best);
+    if (gbest == 0xFFFFFFFFu) break;
+    const unsigned who = __ballot_sync(gmask, best == gbest && bj >= 0) & gmask;
+    const int64_t jb = __shfl_sync(gmask, bj, __ffs(who) - 1);
+    if (gl == 0) {
       double gx, gy, gz;
       bool nz, dir;
       pair64(sc, o, current(C, jb), sc.k, sc.gamma, gx, gy, gz, nz, dir);
@@ -165,202 +240,201 @@ __device__ void ip_selection(const DevCtx &C, const SimConst &sc, const Stencil 
         fz = __dadd_rn(fz, gz);
       }
     }
-    prev = (int64_t)wbest;
+    prev = (int64_t)gbest;
   }
 }
 
-// One warp per box of colour `colour` (grid-stride over the colour's list).
-__global__ void __launch_bounds__(32 * kIpWarps) k_inplace(DevCtx C, int colour) {
-  __shared__ IpShared shw[kIpWarps];
+// One agent of the group's box: the one with the next ID after last_id.
+// Returns false when the box has none left (never for a listed box).
+template <int G>
+__device__ bool ip_agent(const DevCtx &C, IpShared<G> &sh, const IpBox &B, int64_t &last_id, int gl, unsigned gmask,
+                         unsigned lt) {
+  constexpr uint32_t kCand = IpShared<G>::kCand, kCap = IpShared<G>::kCap;
+  const SimConst &sc = C.sc[B.sim];
+  uint32_t myid = 0xFFFFFFFFu;
+  int64_t myq = -1;
+  if (B.nb <= (uint32_t)G) {
+    if ((uint32_t)gl < B.nb && (int64_t)B.bid > last_id) {
+      myid = B.bid;
+      myq = B.b0 + gl;
+    }
+  } else {
+    for (uint32_t m = (uint32_t)gl; m < B.nb; m += (uint32_t)G) {
+      const uint32_t id = agent_id(C, B.b0 + m);
+      if ((int64_t)id > last_id && id < myid) {
+        myid = id;
+        myq = B.b0 + m;
+      }
+    }
+  }
+  const uint32_t qid = __reduce_min_sync(gmask, myid);
+  const unsigned who = __ballot_sync(gmask, myid == qid && myq >= 0) & gmask;
+  if (!who) return false;
+  const int64_t q = __shfl_sync(gmask, myq, __ffs(who) - 1);
+  last_id = (int64_t)qid;
+  const int32_t sq = C.c.slot[q];
+  const double4_32a o = current(C, q);
+  const float4 a0 = C.c.r0[q];
+  // the candidates that pass the filter, compacted in stencil-box order and,
+  // within a box, in cell order; a lane finds its candidate's box by a
+  // binary search over the prefix of the counts
+  uint32_t nc = 0;
+  for (uint32_t base = 0; base < B.ntot; base += (uint32_t)G) {
+    const uint32_t c = base + (uint32_t)gl;
+    bool pass = false;
+    int64_t j = q;
+    if (c < B.ntot) {
+      int lo = 0, hi = B.nbox - 1;  // the last stencil box whose prefix is at most c
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sh.bp[mid] <= c) lo = mid;
+        else hi = mid - 1;
+      }
+      j = (int64_t)sh.bj[lo] + (int64_t)(c - sh.bp[lo]);
+      const int dx = B.xlo + lo % B.nx, dy = B.ylo + (lo / B.nx) % B.ny, dz = B.zlo + lo / (B.nx * B.ny);
+      pass = j != q && may_overlap(C, a0, j, dx, dy, dz, B.Lh, B.grow);
+    }
+    const unsigned bal = __ballot_sync(gmask, pass) & gmask;
+    const uint32_t k = nc + (uint32_t)__popc(bal & lt);
+    if (pass && k < kCand) sh.cand[k] = (uint32_t)j;
+    nc += (uint32_t)__popc(bal);
+  }
+  __syncwarp(gmask);
+  // the overlapping pairs at the current positions, G at a time
+  uint32_t n = 0;
+  bool select = nc > kCand;
+  if (!select) {
+    for (uint32_t k0 = 0; k0 < nc; k0 += (uint32_t)G) {
+      const uint32_t kk = k0 + (uint32_t)gl;
+      double gx = 0.0, gy = 0.0, gz = 0.0;
+      bool nz = false, dir = false, hit = false;
+      int64_t j = q;
+      if (kk < nc) {
+        j = (int64_t)sh.cand[kk];
+        hit = pair64(sc, o, current(C, j), sc.k, sc.gamma, gx, gy, gz, nz, dir);
+      }
+      const unsigned bal = __ballot_sync(gmask, hit) & gmask;
+      const uint32_t k = n + (uint32_t)__popc(bal & lt);
+      if (hit && k < kCap) {
+        sh.key[k] = ((unsigned long long)agent_id(C, j) << 32) | k;
+        sh.gx[k] = gx;
+        sh.gy[k] = gy;
+        sh.gz[k] = gz;
+        sh.flags[k] = (nz ? 1u : 0u) | (dir ? 2u : 0u);
+      }
+      n += (uint32_t)__popc(bal);
+    }
+    select = n > kCap;
+  }
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  uint32_t nnz = 0, novl = 0;
+  if (!select) {
+    __syncwarp(gmask);  // the pairs' entries, written by any lane of the group
+    if (n > 1u) {       // one pair or none needs no sort
+      uint32_t n2 = 2;  // the sort's size: a power of two >= n
+      while (n2 < n) n2 <<= 1;
+      for (uint32_t k = n + (uint32_t)gl; k < n2; k += (uint32_t)G) sh.key[k] = ~0ull;
+      __syncwarp(gmask);
+      for (uint32_t size = 2; size <= n2; size <<= 1)
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+          for (uint32_t i = (uint32_t)gl; i < n2; i += (uint32_t)G) {
+            const uint32_t jx = i ^ stride;
+            if (jx > i) {
+              const unsigned long long ka = sh.key[i], kb = sh.key[jx];
+              if ((ka > kb) == ((i & size) == 0)) {
+                sh.key[i] = kb;
+                sh.key[jx] = ka;
+              }
+            }
+          }
+          __syncwarp(gmask);
+        }
+    }
+    if (gl == 0) {
+      for (uint32_t r = 0; r < n; ++r) {
+        const uint32_t k = (uint32_t)sh.key[r];
+        nnz += sh.flags[k] & 1u;
+        if (sh.flags[k] & 2u) {
+          fx = __dadd_rn(fx, sh.gx[k]);
+          fy = __dadd_rn(fy, sh.gy[k]);
+          fz = __dadd_rn(fz, sh.gz[k]);
+        }
+      }
+      novl = n;
+    }
+  } else {
+    ip_selection(C, sc, sh, B, q, o, a0, gl, gmask, fx, fy, fz, nnz, novl);
+  }
+  // the displacement, committed before the next agent
+  if (gl == 0) {
+    const uint8_t ghost = C.a.flags[sq] & FLAG_GHOST;
+    double Dx, Dy, Dz;
+    bool bad;
+    const bool moved = disp64(sc, fx, fy, fz, Dx, Dy, Dz, bad) && !ghost;
+    if (bad) set_err(C.g, ERR_NONFINITE);
+    if (moved) {
+      C.a.x[sq] = bound_apply(sc, __dadd_rn(o.x, Dx));
+      C.a.y[sq] = bound_apply(sc, __dadd_rn(o.y, Dy));
+      C.a.z[sq] = bound_apply(sc, __dadd_rn(o.z, Dz));
+    }
+    const uint8_t nz8 = (uint8_t)(nnz > 255u ? 255u : nnz);
+    C.c.f64[q] = make_double4_32a(fx, fy, fz, (double)novl);
+    C.c.nnz[q] = nz8;
+    C.c.stat[q] = 0;
+    C.a.nnz[sq] = nz8;
+    C.a.flags[sq] = (uint8_t)(ghost | (moved ? FLAG_CHANGED : 0));
+  }
+  __syncwarp(gmask);  // the new position is seen by the box's next agents
+  return true;
+}
+
+// Groups of G lanes, one box of colour `colour` each (grid-stride over the
+// colour's list).  Every group takes one agent per pass of the loop, so the
+// groups of a warp run their agents side by side.
+template <int G>
+__global__ void __launch_bounds__(32 * kIpWarps, kIpBlocksPerSM) k_inplace(DevCtx C, int colour) {
+  constexpr int kGroups = 32 / G;
+  __shared__ IpShared<G> shg[kIpWarps * kGroups];
   if (C.g->err & ERR_TABLE) return;  // boxes of this build emptied: cells not placed
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
-  IpShared &sh = shw[wid];
+  const int grp = lane / G, gl = lane % G;
+  const unsigned gmask = G == 32 ? FULL : ((1u << (G & 31)) - 1u) << (grp * G);
+  const unsigned lt = gmask & ((1u << lane) - 1u);  // lanes of the group below this one
+  IpShared<G> &sh = shg[wid * kGroups + grp];
   const uint32_t nlist = C.g->ip_count[colour], off = C.g->ip_off[colour];
   const uint32_t stamp = C.g->stamp & kStampMask;
-  for (uint32_t w = blockIdx.x * kIpWarps + wid; w < nlist; w += gridDim.x * kIpWarps) {
-    const int64_t b0 = C.ovf[off + w];  // the box's first cell
-    const int sim = C.c.sim[b0];
-    const SimConst &sc = C.sc[sim];
-    const SimState &s = C.ss[sim];
-    int64_t cx, cy, cz;
-    unpack_coords(C.c.pkey[b0], cx, cy, cz);
-    const Stencil t = make_stencil(C, sc, s, cx, cy, cz);
-    const uint32_t nb = ent_live(t.e[t.box(0, 0, 0)], stamp);
-    const int nx = t.xhi - t.xlo + 1, ny = t.yhi - t.ylo + 1, nzb = t.zhi - t.zlo + 1;
-    const int nbox = nx * ny * nzb;
-    const float Lh = s.Lh;
-    const float grow = __fadd_rn(__fmul_rn(2.f, __double2float_ru(sc.max_disp)), s.marg);
-    // The box's agents share its stencil: lane b < nbox holds stencil box b's
-    // first cell and live count, and every lane the inclusive prefix of the
-    // counts up to its own (lanes from nbox on hold the total), read once per
-    // box instead of box by box for every agent.
-    int64_t bj0 = 0;
-    uint32_t bcnt = 0u;
-    if (lane < nbox) {
-      const int dx = t.xlo + lane % nx, dy = t.ylo + (lane / nx) % ny, dz = t.zlo + lane / (nx * ny);
-      const unsigned long long e = t.e[t.box(dx, dy, dz)];
-      bcnt = ent_live(e, stamp);
-      bj0 = ent_start(e);
-    }
-    uint32_t bincl = bcnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, bincl, d);
-      bincl += lane >= d ? y : 0u;
-    }
-    const uint32_t ntot = __shfl_sync(FULL, bincl, 31);
-    // IDs of the box's agents, one per lane, when they fit the warp
-    const uint32_t bid = (nb <= 32u && (uint32_t)lane < nb) ? agent_id(C, b0 + lane) : 0xFFFFFFFFu;
-    int64_t last_id = -1;
-    for (uint32_t done = 0; done < nb; ++done) {
-      // the box's agent with the next ID
-      uint32_t myid = 0xFFFFFFFFu;
-      int64_t myq = -1;
-      if (nb <= 32u) {
-        if ((uint32_t)lane < nb && (int64_t)bid > last_id) {
-          myid = bid;
-          myq = b0 + lane;
-        }
-      } else {
-        for (uint32_t m = (uint32_t)lane; m < nb; m += 32u) {
-          const uint32_t id = agent_id(C, b0 + m);
-          if ((int64_t)id > last_id && id < myid) {
-            myid = id;
-            myq = b0 + m;
-          }
-        }
-      }
-      const uint32_t qid = __reduce_min_sync(FULL, myid);
-      const unsigned who = __ballot_sync(FULL, myid == qid && myq >= 0);
-      if (!who) break;  // IDs are distinct: never taken
-      const int64_t q = __shfl_sync(FULL, myq, __ffs(who) - 1);
-      last_id = (int64_t)qid;
-      const int32_t sq = C.c.slot[q];
-      const double4_32a o = current(C, q);
-      const float4 a0 = C.c.r0[q];
-      // the candidates that pass the filter, compacted in stencil-box order
-      // and, within a box, in cell order: 32 candidates of the stencil's
-      // ntot per round, each lane finding its box by a binary search over
-      // the prefix of the counts
-      uint32_t nc = 0;
-      for (uint32_t base = 0; base < ntot; base += 32u) {
-        const uint32_t c = base + (uint32_t)lane;
-        int lo = 0, hi = 31;  // the first lane whose inclusive prefix exceeds c
-#pragma unroll
-        for (int it = 0; it < 5; ++it) {
-          const int mid = (lo + hi) >> 1;
-          const uint32_t v = __shfl_sync(FULL, bincl, mid);
-          if (v > c) hi = mid;
-          else lo = mid + 1;
-        }
-        lo = lo < 31 ? lo : 31;  // only lanes past the last candidate get beyond
-        const uint32_t ib = __shfl_sync(FULL, bincl, lo), nbx = __shfl_sync(FULL, bcnt, lo);
-        const int64_t jb = __shfl_sync(FULL, bj0, lo);
-        const int64_t j = jb + (int64_t)(c - (ib - nbx));
-        const int dx = t.xlo + lo % nx, dy = t.ylo + (lo / nx) % ny, dz = t.zlo + lo / (nx * ny);
-        const bool pass = c < ntot && j != q && may_overlap(C, a0, j, dx, dy, dz, Lh, grow);
-        const unsigned B = __ballot_sync(FULL, pass);
-        const uint32_t k = nc + (uint32_t)__popc(B & lt);
-        if (pass && k < (uint32_t)kIpCand) sh.cand[k] = (uint32_t)j;
-        nc += (uint32_t)__popc(B);
-      }
-      __syncwarp();
-      // the overlapping pairs at the current positions, 32 at a time
-      uint32_t n = 0;
-      bool select = nc > (uint32_t)kIpCand;
-      if (!select) {
-        for (uint32_t k0 = 0; k0 < nc; k0 += 32u) {
-          const uint32_t kk = k0 + (uint32_t)lane;
-          const int64_t j = kk < nc ? (int64_t)sh.cand[kk] : q;
-          double gx = 0.0, gy = 0.0, gz = 0.0;
-          bool nz = false, dir = false, hit = false;
-          if (kk < nc) hit = pair64(sc, o, current(C, j), sc.k, sc.gamma, gx, gy, gz, nz, dir);
-          const unsigned B = __ballot_sync(FULL, hit);
-          const uint32_t k = n + (uint32_t)__popc(B & lt);
-          if (hit && k < (uint32_t)kIpCap) {
-            sh.key[k] = ((unsigned long long)agent_id(C, j) << 32) | k;
-            sh.gx[k] = gx; sh.gy[k] = gy; sh.gz[k] = gz;
-            sh.flags[k] = (nz ? 1u : 0u) | (dir ? 2u : 0u);
-          }
-          n += (uint32_t)__popc(B);
-        }
-        select = n > (uint32_t)kIpCap;
-      }
-      double fx = 0.0, fy = 0.0, fz = 0.0;
-      uint32_t nnz = 0, novl = 0;
-      if (!select) {
-        if (n > 1u) {  // one pair or none needs no sort
-          uint32_t n2 = 32;  // the sort's size: a power of two >= n
-          while (n2 < n) n2 <<= 1;
-          for (uint32_t k = n + (uint32_t)lane; k < n2; k += 32u) sh.key[k] = ~0ull;
-          __syncwarp();
-          for (uint32_t size = 2; size <= n2; size <<= 1)
-            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-              for (uint32_t i = (uint32_t)lane; i < n2; i += 32u) {
-                const uint32_t jx = i ^ stride;
-                if (jx > i) {
-                  const unsigned long long ka = sh.key[i], kb = sh.key[jx];
-                  if ((ka > kb) == ((i & size) == 0)) {
-                    sh.key[i] = kb;
-                    sh.key[jx] = ka;
-                  }
-                }
-              }
-              __syncwarp();
-            }
-        } else {
-          __syncwarp();  // the one pair's entries, written by any lane
-        }
-        if (lane == 0) {
-          for (uint32_t r = 0; r < n; ++r) {
-            const uint32_t k = (uint32_t)sh.key[r];
-            nnz += sh.flags[k] & 1u;
-            if (sh.flags[k] & 2u) {
-              fx = __dadd_rn(fx, sh.gx[k]);
-              fy = __dadd_rn(fy, sh.gy[k]);
-              fz = __dadd_rn(fz, sh.gz[k]);
-            }
-          }
-          novl = n;
-        }
-      } else {
-        ip_selection(C, sc, t, q, o, a0, stamp, lane, Lh, grow, fx, fy, fz, nnz, novl);
-      }
-      // the displacement, committed before the next agent
-      if (lane == 0) {
-        const uint8_t ghost = C.a.flags[sq] & FLAG_GHOST;
-        double Dx, Dy, Dz;
-        bool bad;
-        const bool moved = disp64(sc, fx, fy, fz, Dx, Dy, Dz, bad) && !ghost;
-        if (bad) set_err(C.g, ERR_NONFINITE);
-        if (moved) {
-          C.a.x[sq] = bound_apply(sc, __dadd_rn(o.x, Dx));
-          C.a.y[sq] = bound_apply(sc, __dadd_rn(o.y, Dy));
-          C.a.z[sq] = bound_apply(sc, __dadd_rn(o.z, Dz));
-        }
-        const uint8_t nz8 = (uint8_t)(nnz > 255u ? 255u : nnz);
-        C.c.f64[q] = make_double4_32a(fx, fy, fz, (double)novl);
-        C.c.nnz[q] = nz8;
-        C.c.stat[q] = 0;
-        C.a.nnz[sq] = nz8;
-        C.a.flags[sq] = (uint8_t)(ghost | (moved ? FLAG_CHANGED : 0));
-      }
-      __syncwarp();  // the new position is seen by the next agents of the box
+  const uint32_t stride = gridDim.x * (uint32_t)(kIpWarps * kGroups);
+  uint32_t w = (blockIdx.x * (uint32_t)kIpWarps + (uint32_t)wid) * (uint32_t)kGroups + (uint32_t)grp;
+  IpBox B{};
+  bool have = w < nlist;
+  if (have) ip_load_box(C, sh, B, C.ovf[off + w], stamp, gl, gmask);
+  uint32_t done = 0;
+  int64_t last_id = -1;
+  while (__any_sync(FULL, have)) {
+    if (!have) continue;
+    const bool more = ip_agent(C, sh, B, last_id, gl, gmask, lt);
+    if (!more || ++done >= B.nb) {
+      w += stride;
+      have = w < nlist;
+      done = 0;
+      last_id = -1;
+      if (have) ip_load_box(C, sh, B, C.ovf[off + w], stamp, gl, gmask);
     }
   }
 }
-
 }  // namespace
 
-void launch_inplace(const DevCtx &C, cudaStream_t st, int colours) {
+void launch_inplace(const DevCtx &C, cudaStream_t st, int colours, bool narrow) {
   const unsigned int nb = (unsigned int)((C.total_slots + kIpThreads - 1) / kIpThreads);
   k_ip_reset<<<1, 32, 0, st>>>(C);
   k_ip_count<<<nb, kIpThreads, 0, st>>>(C);
   k_ip_prefix<<<1, 1, 0, st>>>(C);
   k_ip_fill<<<nb, kIpThreads, 0, st>>>(C);
-  for (int col = 0; col < colours; ++col) k_inplace<<<152 * 4, 32 * kIpWarps, 0, st>>>(C, col);
+  for (int col = 0; col < colours; ++col) {
+    if (narrow) k_inplace<8><<<152 * kIpBlocksPerSM, 32 * kIpWarps, 0, st>>>(C, col);
+    else k_inplace<32><<<152 * kIpBlocksPerSM, 32 * kIpWarps, 0, st>>>(C, col);
+  }
 }
 
 }  // namespace bdm

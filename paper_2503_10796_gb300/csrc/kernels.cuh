@@ -45,7 +45,8 @@ void launch_force64(const DevCtx &C, cudaStream_t st);
 // 2 static flags first, then the half stencil
 void launch_force_stream(const DevCtx &C, cudaStream_t st, int mode, int threads, bool torus);
 // inplace.cu: S4 + S5 of the in-place execution context, one launch per box colour.
-void launch_inplace(const DevCtx &C, cudaStream_t st, int colours);
+// narrow: groups of 8 lanes per box (large populations), else a warp per box
+void launch_inplace(const DevCtx &C, cudaStream_t st, int colours, bool narrow);
 // track: grid reuse (cell records follow the moved agents; skin check).
 void launch_displace(const DevCtx &C, cudaStream_t st, bool track = false);
 

@@ -1,7 +1,8 @@
 """The in-place execution context (§5.2) on the GPU against the oracle.
 
-The kernel runs one launch per box colour and one thread per box, and
-commits each agent's displacement before the next agent.  It follows the
+The kernel runs one launch per box colour and a group of lanes per box (8
+for large populations, forced here by a test hook, or a whole warp), and
+commits each agent's displacement before the box's next agent.  It follows the
 oracle's order (colour, box index, agent ID) and evaluates every definition
 in FP64 in the oracle's order of operations, so positions, forces and nnz
 equal the oracle's bit for bit at every iteration: in open space, on an odd
@@ -17,13 +18,19 @@ from paper_2503_10796_gb300 import workloads
 pytestmark = pytest.mark.gpu
 
 
-def ctx_for(pops, **kw):
+def ctx_for(pops, narrow=False, **kw):
+    """narrow: the boxes on groups of 8 lanes (the form for large
+    populations; a test hook) instead of a warp per box."""
     from paper_2503_10796_gb300 import binding
     pops = pops if isinstance(pops, list) else [pops]
     ctx = binding.Context([binding.make_params(p.params, execution_context=1, **kw) for p in pops],
                           sum(max(p.n, p.params.capacity) for p in pops) + 16)
     for s, p in enumerate(pops):
         ctx.set_agents(s, p.xyz, p.diameter)
+    if narrow:
+        t = ctx.get_tuning()
+        t.update(test_flags=2)
+        ctx.set_tuning(**t)
     return ctx
 
 
@@ -54,11 +61,12 @@ def scenes():
     ]
 
 
+@pytest.mark.parametrize("narrow", [False, True])
 @pytest.mark.parametrize("sort_interval", [0, 3])
 @pytest.mark.parametrize("scene", range(5))
-def test_inplace_trajectory_bit_exact(orc, scene, sort_interval):
+def test_inplace_trajectory_bit_exact(orc, scene, sort_interval, narrow):
     name, pop = scenes()[scene]
-    ctx = ctx_for(pop, sort_interval=sort_interval)
+    ctx = ctx_for(pop, narrow=narrow, sort_interval=sort_interval)
     o = orc_for(pop)
     for t in range(10):
         ctx.step(1)
@@ -78,17 +86,20 @@ def test_inplace_trajectory_bit_exact(orc, scene, sort_interval):
     assert not np.array_equal(c.get()[0], x), name
 
 
-@pytest.mark.parametrize("n", [32, 33, 100, 400, 600])
-def test_inplace_crowd_beyond_the_partner_list(orc, n):
-    """Every agent of a tight clump overlaps all others.  Up to 32 agents of
-    a box keep their IDs in the warp's lanes (33 take the loop over the box);
-    up to 256 overlapping partners are sorted in shared memory (100); beyond
-    that (400), or beyond the 512 candidates the filter keeps (600), the
-    selection loop adds the partners one ID after the other."""
+@pytest.mark.parametrize("narrow,n", [(True, 8), (True, 9), (True, 40), (True, 100), (True, 200),
+                                      (False, 32), (False, 33), (False, 100), (False, 300), (False, 600)])
+def test_inplace_crowd_beyond_the_partner_list(orc, narrow, n):
+    """Every agent of a tight clump overlaps all others.  With groups of 8
+    lanes per box: up to 8 agents of a box keep their IDs in the group's
+    lanes (9 take the loop over the box); up to 64 overlapping partners are
+    sorted in shared memory (40); beyond that (100), or beyond the 128
+    candidates the filter keeps (200), the selection loop adds the partners
+    one ID after the other.  With a warp per box the limits are 32 IDs, 256
+    partners and 512 candidates (32, 33, 100, 300, 600)."""
     rng = np.random.default_rng(9)
     pop = workloads.Population(100.0 + rng.uniform(0.0, 5.0, (n, 3)), rng.uniform(9.5, 10.5, n),
                                workloads.SimParams(precision=0, dt=0.01))
-    ctx = ctx_for(pop)
+    ctx = ctx_for(pop, narrow=narrow)
     o = orc_for(pop)
     for t in range(3):
         ctx.step(1)
@@ -102,9 +113,10 @@ def test_inplace_crowd_beyond_the_partner_list(orc, n):
             assert ov.max() == n - 1, (n, ov.max())
 
 
-def test_inplace_growth_and_batched_sims_bit_exact(orc):
+@pytest.mark.parametrize("narrow", [False, True])
+def test_inplace_growth_and_batched_sims_bit_exact(orc, narrow):
     pop = workloads.growth_division(shape=(4, 4, 4), cap_factor=8, precision=0)
-    ctx = ctx_for(pop)
+    ctx = ctx_for(pop, narrow=narrow)
     o = orc_for(pop)
     for t in range(30):
         ctx.step(1)
@@ -114,7 +126,7 @@ def test_inplace_growth_and_batched_sims_bit_exact(orc):
     x_o, d_o, _ = o.get()
     assert np.array_equal(d, d_o) and np.array_equal(x, x_o)
     pops = workloads.batched_sweep(n_sims=4, lo=50, hi=2000, seed=11, precision=0)
-    ctx = ctx_for(pops)
+    ctx = ctx_for(pops, narrow=narrow)
     ctx.step(6)
     for s, p in enumerate(pops):
         o = orc_for(p)
