@@ -12,8 +12,10 @@
 //
 // Per iteration: the box leaders (first cell of each occupied box) are
 // listed by colour (count, prefix, fill); then one launch per colour runs
-// groups of eight lanes, one box each, four boxes to a warp, so that one
-// FP64 instruction serves the agents of several boxes.  A group first loads
+// a group of lanes per box: eight lanes, four boxes to a warp, so that one
+// FP64 instruction serves the agents of several boxes, once the context
+// holds 131,072 slots or more; a whole warp per box below that, where the
+// colours have too few boxes to occupy the groups.  A group first loads
 // its box's stencil (first cell and live count of each of the 27 boxes,
 // with their prefix) into shared memory.  It then takes the box's agents in
 // ascending ID, one after the other; each group takes one agent per pass of
