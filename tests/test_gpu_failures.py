@@ -89,3 +89,20 @@ def test_bounded_wait_reports_timeout(orc):
     o.step(2)
     x_o, _, _ = o.get()
     assert np.abs(x - x_o).max() <= 1e-9 * pop.diameter.max()
+
+
+def test_unknown_test_hooks_are_rejected(orc):
+    """Test hooks are bits 0 and 1 of test_flags; any other bit is refused
+    and leaves the tuning as it was."""
+    from paper_2503_10796_gb300 import binding
+    pop = workloads.plain_fp64(n=200, precision=0)
+    ctx = binding.Context(binding.make_params(pop.params), pop.n + 8)
+    ctx.set_agents(0, pop.xyz, pop.diameter)
+    t = ctx.get_tuning()
+    for bad in (4, 8, 1 << 30, -1):
+        with pytest.raises(binding.BdmError) as e:
+            ctx.set_tuning(**dict(t, test_flags=bad))
+        assert e.value.code == -1, bad
+    assert ctx.get_tuning() == t
+    ctx.step(2)
+    ctx.sync()
